@@ -1,0 +1,55 @@
+"""The seeded input generator: geometry counts, placement constraints, reproducibility."""
+import numpy as np
+import pytest
+
+from paper_1812_07993_gb300 import workloads as W
+
+
+def min_periodic_distance(a, b, Lx, Ly, same=False):
+    d = a[:, None, :] - b[None, :, :]
+    d[..., 0] -= Lx * np.round(d[..., 0] / Lx)
+    d[..., 1] -= Ly * np.round(d[..., 1] / Ly)
+    r = np.sqrt((d ** 2).sum(-1))
+    if same:
+        np.fill_diagonal(r, np.inf)
+    return r.min()
+
+
+def test_small_cylinder_system():
+    s = W.cylinder_pore_1k()
+    assert s.n_wall == 3480 and s.n_vapor == 1000       # 10 layers x 348 sites
+    z = np.abs(s.x0[:, 2])
+    assert (z > 5).all() and (z < 20).all()
+    assert min_periodic_distance(s.x0, s.x0, 20, 20, same=True) >= 0.9
+    assert min_periodic_distance(s.x0, s.wall, 20, 20) >= 0.9
+    assert np.abs(s.v0.mean(0)).max() < 1e-12
+    assert ((s.v0 ** 2).mean() - 1.0) < 0.1
+    rxy = np.hypot(s.wall[:, 0], s.wall[:, 1])
+    assert rxy.min() >= 4.0 and (np.abs(s.wall[:, 2]) < 5).all()
+
+
+def test_reproducible_by_seed():
+    a, b = W.cylinder_pore_1k(), W.cylinder_pore_1k()
+    np.testing.assert_array_equal(a.x0, b.x0)
+    np.testing.assert_array_equal(a.v0, b.v0)
+    c = W.cylinder_pore_1k(seed=2)
+    assert not np.array_equal(a.x0, c.x0)
+
+
+def test_pore_shape_wall_counts():
+    counts = [W.sc_wall(40, 40, 80, 10, 1.0, [p]).shape[0] for p in [
+        W.Pore(W.PORE_CYLINDER, r0=5.0), W.Pore(W.PORE_CONE, r0=3.0, r1=8.0),
+        W.Pore(W.PORE_SLIT, width=6.0), W.Pore(W.PORE_INKBOTTLE, r0=3.0, r_cavity=8.0)]]
+    assert counts == [30400, 29976, 27200, 29680]
+
+
+def test_replica_specs_ranges():
+    specs = W.replica_batch_specs(256, seed=4)
+    assert len(specs) == 256
+    ns = np.array([s["n"] for s in specs])
+    assert ns.min() >= 1000 and ns.max() <= 50000
+    for s in specs:
+        L = s["L"]
+        assert s["n"] / (L * L * (2 * L - 16)) == pytest.approx(0.02, rel=1e-6)
+        assert 2 <= s["R"] <= 10 and 0.8 <= s["T0"] <= 1.2 and s["kind"] in (1, 2, 3, 4)
+    assert specs == W.replica_batch_specs(256, seed=4)
