@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the pore / water-vapour MD hot path on one GB300.
+
+Workload: four independent 40 x 40 x 80 sigma systems advanced together in one batch -- cylinder
+(r = 5), cone (r 3 -> 8 across the slab), slit (width 6) and ink-bottle (neck 3, cavity 8) pores
+through a simple-cubic wall slab |z| < 10, 20,000 vapour molecules each, reduced LJ units, rc = 2.5,
+skin 0.3, dt = 0.005, T* = 1.0 with velocity rescaling every 10 steps. One bench step = one MD step
+of all four systems (half-kick/drift/reflect, device-decided list rebuild, pair forces, half-kick,
+thermostat).
+
+value: pair interactions per second -- unique vapour-vapour plus vapour-wall pairs with r < rc,
+counted exactly by the force kernel over the timed steps -- divided by the summed CUDA-event
+durations of the steps (L2 flushed between steps by a 256 MB write outside the timed events).
+
+Also reported: MD steps/s, the mixed-precision form (FP32 pair terms) with its RMS force error
+against the FP64 form, the pair-force kernel's roofline (timed live with CUDA events), the FP64 CPU
+oracle timed on the host cores (cpu_baseline), and an end-to-end figure through the C ABI with host
+buffers (state upload, one step, force read-back).
+
+--impl reference times the FP64 CPU oracle on the same workload (one system advanced per step, in
+turn) and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s & MD steps/s; mixed-FP32 vs FP64 at RMS force err ≤1e-5"
+UNIT = "pair-interactions/s"
+WORKLOAD = ("pore_shapes_4x20k: four 40x40x80 boxes (cylinder r5, cone r3->8, slit w6, "
+            "ink-bottle neck 3 / cavity 8) through an SC wall slab |z|<10, 20,000 vapour each, "
+            "rc 2.5, skin 0.3, dt 0.005, T*=1.0, rescale every 10 steps")
+# FP64 operations per pair interaction counted as algorithmic work (FMA = 2): dx, dy, dz (3);
+# r^2 (1 mul + 2 fma = 5); 1/r^2 (1); inv^6 (2 mul); force factor (fma + 2 mul = 4);
+# accumulate (3 fma = 6)
+FLOPS_PER_PAIR = 21
+# peak of the FP64 CUDA-core pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the pair kernels from one ncu capture, valid for the kernel source with
+# this SHA-256 (traffic is reported as null once the source has changed)
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--roofline-launches", type=int, default=50)
+    ap.add_argument("--small", action="store_true",
+                    help="a 1,000-molecule system instead of the bench workload (profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_workload(small: bool):
+    from paper_1812_07993_gb300 import workloads as W
+    if small:
+        return [W.cylinder_pore_1k()], "cylinder_pore_1k"
+    return W.pore_shape_systems_20k(), "pore_shapes_4x20k"
+
+
+def kernel_sha() -> str:
+    p = os.path.join(ROOT, "paper_1812_07993_gb300", "csrc", "md_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------------------------ oracle leg
+
+
+def oracle_rate(systems, seconds: float, nthreads: int = 0):
+    """Advance the systems with the FP64 CPU oracle, one MD step of one system at a time in turn,
+    until ``seconds`` have passed; returns (pairs/s, steps, pairs, elapsed, threads)."""
+    import oracle
+    from paper_1812_07993_gb300 import workloads as W
+    pot = W.Potential()
+    states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1,
+                           nthreads=nthreads) for s in systems]
+    steps = pairs = 0
+    t0 = time.perf_counter()
+    while True:
+        st = states[steps % len(states)]
+        st.run(1)
+        pairs += st.stats["pairs_vv"] + st.stats["pairs_vw"]
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    threads = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    return pairs / el, steps, pairs, el, threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1812_07993_gb300 import workloads as W
+    systems, wname = make_workload(args.small)
+    pot = W.Potential()
+    states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1, nthreads=0)
+              for s in systems]
+    for k in range(args.warmup):
+        states[k % len(states)].run(1)
+    pairs = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        st = states[k % len(states)]
+        st.run(1)
+        pairs += st.stats["pairs_vv"] + st.stats["pairs_vw"]
+    el = time.perf_counter() - t0
+    value = pairs / el
+    cores = os.cpu_count() or 1
+    sample = (f"{args.steps} oracle MD steps, one of the {len(systems)} systems per step in turn "
+              f"(FP64 cell-list oracle, OpenMP over molecules)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "description": WORKLOAD, "replicas": len(systems)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------ GPU leg
+
+
+def pair_total(sim, nrep):
+    return sim.observables(0)[0]["pair_evals_total"]
+
+
+def current_pairs(sim, nrep):
+    tot = 0
+    for r in range(nrep):
+        o = sim.observables(r)[0]
+        tot += o["pairs_vv"] + o["pairs_vw"]
+    return tot
+
+
+def time_steps(sim, torch, stream, flush, steps):
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(1)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def measure_precision(md, systems, precision, args, torch, stream, flush):
+    sim = md.Simulation(systems, precision=precision, stream=stream)
+    sim.set_tuning(use_graph=1, steps_per_graph=1)
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.step(1)
+    sim.sync()
+    p0 = pair_total(sim, len(systems))
+    l0 = sim.kernel_launches()
+    ms = time_steps(sim, torch, stream, flush, args.steps)
+    launches = sim.kernel_launches() - l0
+    p1 = pair_total(sim, len(systems))
+    return sim, ms, p1 - p0, launches
+
+
+def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision):
+    evs = []
+    for _ in range(nlaunch):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.compute_forces()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / nlaunch
+    flops = pairs_per_launch * FLOPS_PER_PAIR
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    kname = "k_forces_fp64" if precision == "fp64" else "k_forces_mixed"
+    tr = NCU_TRAFFIC.get(kname)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == kernel_sha() else None
+    return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz" if precision ==
+                            "fp64" else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+            "launch_ms": ms, "pairs_per_launch": pairs_per_launch,
+            "flops_per_pair": FLOPS_PER_PAIR}
+
+
+def e2e(sim, systems, nsteps, pairs_per_step):
+    import numpy as np
+    states = [sim.state(r) for r in range(len(systems))]
+    h0, d0 = sim.transfer_bytes()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        for r, (x, v) in enumerate(states):
+            sim.set_state(r, x, v)
+        sim.step(1)
+        for r in range(len(systems)):
+            sim.forces(r)
+    el = time.perf_counter() - t0
+    h1, d1 = sim.transfer_bytes()
+    return {"value": pairs_per_step * nsteps / el, "unit": UNIT,
+            "h2d_bytes_per_step": (h1 - h0) // nsteps, "d2h_bytes_per_step": (d1 - d0) // nsteps,
+            "ms_per_step": 1e3 * el / nsteps,
+            "path": "md_set_state (host arrays) + md_step(1) + md_get_forces per replica"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1812_07993_gb300 as md
+    from paper_1812_07993_gb300 import build as mdbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    mdbuild.build()
+    md.load_library()
+    systems, wname = make_workload(args.small)
+    nrep = len(systems)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    prec = md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED
+
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    sim, ms, pairs, launches = measure_precision(md, systems, prec, args, torch, stream, flush)
+    clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms, float(pairs)], dtype=torch.float64)
+        tmax = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms_job, pairs_job = float(tmax[0]), float(t[1])
+    else:
+        ms_job, pairs_job = ms, float(pairs)
+    value = pairs_job / (ms_job * 1e-3)
+    ms_per_step = ms_job / args.steps
+    pairs_per_step = pairs / args.steps
+
+    extra = {}
+    if rank == 0:
+        cur = current_pairs(sim, nrep)
+        extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
+                                     args.precision)
+        extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step)
+        if not args.no_mixed and args.precision == "fp64":
+            import oracle
+            from paper_1812_07993_gb300 import workloads as W
+            simm, msm, pairsm, _ = measure_precision(md, systems, md.MD_PREC_MIXED, args, torch,
+                                                     stream, flush)
+            # RMS force error of both GPU forms against the FP64 oracle at the mixed run's state
+            errs = []
+            with md.Simulation(systems, stream=stream) as sim64:
+                for r, s in enumerate(systems):
+                    x, v = simm.state(r)
+                    sim64.set_state(r, x, v)
+                    g, _, _ = oracle.forces(oracle.make_params(s, W.Potential()), x, s.wall,
+                                            method=1, nthreads=0)
+                    fm = simm.forces(r)
+                    f64 = sim64.forces(r)
+                    errs.append((((fm - g) ** 2).sum(), ((f64 - g) ** 2).sum(), (g ** 2).sum()))
+            den = sum(e[2] for e in errs)
+            vm = pairsm / (msm * 1e-3)
+            extra["mixed"] = {"value": vm, "unit": UNIT, "ms_per_step": msm / args.steps,
+                              "speedup_vs_fp64": vm / value,
+                              "rms_force_err": math.sqrt(sum(e[0] for e in errs) / den),
+                              "fp64_rms_force_err": math.sqrt(sum(e[1] for e in errs) / den),
+                              "md_steps_per_s": args.steps / (msm * 1e-3)}
+            simm.close()
+        if not args.no_cpu_baseline:
+            v, st, pr, el, thr = oracle_rate(systems, args.cpu_seconds)
+            extra["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                     "sample": f"{st} oracle MD steps (one system per step, in "
+                                               f"turn) in {el:.1f} s, {pr} pair interactions"}
+    sim.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": wname, "description": WORKLOAD, "replicas": nrep,
+                           "n_vapor": sum(s.n_vapor for s in systems),
+                           "n_wall": sum(s.n_wall for s in systems),
+                           "precision": args.precision,
+                           "l2": "flushed between timed steps (256 MB write outside the events)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "md_steps_per_s": 1e3 / ms_per_step,
+                "replica_steps_per_s": nrep * 1e3 / ms_per_step,
+                "pairs_per_step": pairs_per_step,
+                "gpu_launches": launches,
+                "clocks": clocks.summary()}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

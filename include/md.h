@@ -1,0 +1,213 @@
+/*
+ * md.h -- C ABI of the GB300 (sm_103a) molecular-dynamics library for water vapour near atomistic
+ * pore walls (Korenkov, Nikonov, Popovicova, arXiv:1812.07993).
+ *
+ * What one MD step computes (per replica, reduced Lennard-Jones units, sigma = eps = m = k_B = 1):
+ *   1. first half-kick and drift (Sec. 2 velocity Verlet; Fig. 2):
+ *        v <- v + (dt/2) f/m ;  r <- r + dt v
+ *      then specular reflection at z = +-Lz/2 and periodic wrap of x, y into [-L/2, L/2);
+ *   2. neighbour-list maintenance: when any molecule has moved more than skin/2 since the last
+ *      build, particles are binned into cells (counting sort) and Verlet lists rebuilt;
+ *   3. forces at r(t+dt) (Sec. 2, Eq. 2; Fig. 1): f_i = -dU/dr_i with U the Lennard-Jones 12-6
+ *      potential (Sec. 2) truncated at rc (vapour-vapour: eps, sigma, rc; vapour-wall: eps_w,
+ *      sigma_w, rc_w; wall atoms are fixed and feel no force);
+ *   4. second half-kick (Fig. 3): v <- v + (dt/2) f/m;
+ *   5. Berendsen scaling (Sec. 2; Fig. 4) when the step counter reaches a multiple of
+ *      thermostat_every: v <- lambda v, lambda = sqrt(1 + (n_th dt / tau_B)(T0/T - 1)),
+ *      T = m sum v^2 / (3 N).
+ * Observables (on demand): kinetic / potential energy, the pair virial sum_{pairs} r_ij . F_ij
+ * (the sum in the virial pressure of Sec. 2), pairs within the cutoff, pore occupancy, adsorbed
+ * count and axial density profile per pore.
+ *
+ * Conventions
+ *   - Box centred at the origin: x in [-Lx/2, Lx/2), y in [-Ly/2, Ly/2) periodic; z in
+ *     [-Lz/2, Lz/2] with reflecting ends. Positions/velocities/forces are FP64, xyz interleaved
+ *     (3*n doubles), in the caller's molecule order.
+ *   - Every pointer argument named host_* or documented as "host" is host memory owned by the
+ *     caller; the library copies from/to it and keeps no reference after the call returns.
+ *     The library owns all device memory it allocates and frees it in md_destroy.
+ *   - Work is enqueued on the CUDA stream given at creation (NULL: the library creates a
+ *     non-blocking stream of its own and destroys it in md_destroy).
+ *     md_step is asynchronous; md_sync, md_get_* and md_observables synchronise that stream.
+ *   - Errors: every entry point returns an md_status; no exception or abort crosses the ABI.
+ *     Conditions found on the device (list overflow, unstable motion, a spin wait that ran out)
+ *     are sticky per context: once set, later steps do no work and every call returns the code.
+ *     md_last_error gives a one-line description.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef MD_H
+#define MD_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_API_VERSION 1
+
+typedef enum {
+  MD_OK = 0,
+  MD_EINVAL = 1,     /* invalid argument (message in md_last_error) */
+  MD_ENOMEM = 2,     /* a device or host allocation failed */
+  MD_ECUDA = 3,      /* a CUDA runtime call failed */
+  MD_EOVERFLOW = 4,  /* a neighbour list or cell exceeded its capacity */
+  MD_EUNSTABLE = 5,  /* non-finite position or a molecule jumped further than the list skin */
+  MD_ETIMEOUT = 6    /* a bounded device spin wait gave up */
+} md_status;
+
+typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 } md_precision;
+
+typedef enum {
+  MD_PORE_CYLINDER = 1,   /* dx^2 + dy^2 < r0^2 */
+  MD_PORE_CONE = 2,       /* sqrt(dx^2 + dy^2) < r0 + (r1 - r0)(z + h)/(2h), narrow end at z = -h */
+  MD_PORE_SLIT = 3,       /* |dy| < width/2, spanning the whole x extent */
+  MD_PORE_INKBOTTLE = 4   /* dx^2 + dy^2 < r0^2  or  dx^2 + dy^2 + z^2 < r_cavity^2 */
+} md_pore_kind;
+
+/* One pore carved through the wall slab |z| < h. (dx, dy) is the minimum-image offset of a point
+ * from the pore axis (cx, cy). The carve predicates above decide which wall sites are removed
+ * when the library generates the wall, and which molecules count toward the pore's occupancy. */
+typedef struct {
+  int32_t kind;            /* md_pore_kind */
+  double cx, cy;           /* axis position */
+  double r0, r1;           /* radius (cylinder, neck), cone radii at z = -h and z = +h */
+  double r_cavity;         /* ink-bottle cavity radius */
+  double width;            /* slit width */
+} md_pore;
+
+/* One independent system (replica). */
+typedef struct {
+  double Lx, Ly, Lz;       /* box */
+  int64_t n_vapor;         /* mobile molecules */
+  const double* x0;        /* host, 3*n_vapor initial positions (inside the box) */
+  const double* v0;        /* host, 3*n_vapor initial velocities */
+  double T0;               /* thermostat target temperature */
+  double dt;               /* time step */
+  double tau_B;            /* Berendsen rise time; <= 0 means thermostat_every*dt (plain rescale) */
+  int32_t thermostat_every;/* n_th; 0 disables the thermostat */
+  double slab_half;        /* wall slab |z| < slab_half */
+  double lattice_a;        /* simple-cubic wall spacing when the library generates the wall */
+  const double* wall_xyz;  /* host, 3*n_wall fixed wall atoms, or NULL: generate the SC lattice
+                              -L/2 + (i + 1/2) a on each axis, |z| < slab_half, minus the pores */
+  int64_t n_wall;          /* length of wall_xyz (ignored when wall_xyz is NULL) */
+  const md_pore* pores;    /* host, n_pores pores (may be NULL when n_pores == 0) */
+  int32_t n_pores;
+} md_system;
+
+/* Interaction, list and observable parameters shared by every replica of a context. */
+typedef struct {
+  double eps, sigma, mass, rc;        /* vapour-vapour Lennard-Jones (cut at rc, strict r < rc) */
+  double eps_w, sigma_w, rc_w;        /* vapour-wall Lennard-Jones */
+  double skin;                        /* Verlet skin: lists hold pairs with r < max(rc, rc_w)+skin */
+  int32_t shift_energy;               /* 1: energy per pair is U(r) - U(cutoff) */
+  int32_t precision;                  /* md_precision: FP64 pair terms, or FP32 pair terms with
+                                         compensated accumulation and FP64 integration */
+  double r_ads;                       /* adsorbed: nearest wall atom closer than r_ads (<= rc_w) */
+  double bin_width;                   /* axial density-profile bin width */
+  int32_t max_neighbors;              /* per-molecule list capacity for vapour neighbours
+                                         (0 = default 160) */
+  int32_t max_wall_neighbors;         /* per-molecule list capacity for wall neighbours
+                                         (0 = default 224) */
+} md_potential;
+
+/* Launch-shape knobs chosen by the autotuner (all 0 = library defaults). */
+typedef struct {
+  int32_t force_block;     /* threads per block of the pair-force kernel (multiple of 32) */
+  int32_t force_tpp;       /* threads cooperating on one molecule in the pair-force kernel: 1..8 */
+  int32_t list_block;      /* threads per block of the list build (multiple of 32) */
+  int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 0: plain launches */
+  int32_t steps_per_graph; /* MD steps captured per graph replay (0 = 10) */
+} md_tuning;
+
+typedef struct {
+  int64_t step;            /* completed MD steps */
+  int64_t n_vapor, n_wall;
+  double ke, pe, pe_vv, pe_vw;
+  double T;                /* m sum v^2 / (3 N) */
+  double virial_vv, virial_vw;   /* sum over pairs within cutoff of r_ij . F_ij */
+  int64_t pairs_vv, pairs_vw;    /* unique pairs within cutoff at the current positions */
+  int64_t occupancy;       /* sum over pores */
+  int64_t adsorbed;        /* sum over groups */
+  int32_t n_groups;        /* max(n_pores, 1) */
+  int32_t n_bins;          /* ceil(Lz / bin_width) */
+  int64_t n_rebuilds;      /* neighbour-list builds since creation (whole context) */
+  int64_t pair_evals_total;/* pairs within cutoff summed over every step run so far
+                              (whole context: unique vapour-vapour + vapour-wall) */
+  int32_t max_nb_used, max_wall_nb_used; /* largest list lengths of the last build */
+} md_obs;
+
+typedef struct md_ctx md_ctx; /* opaque, library-owned */
+
+/* Create a context holding one replica on the current CUDA device.
+ * stream: a cudaStream_t on which all work is enqueued (NULL: a library-owned stream).
+ * On failure *out is NULL and md_last_error(NULL) describes the failure (per host thread).
+ * Copies every host input. Builds (or takes) the wall, bins it once, builds the first lists and
+ * evaluates the initial forces. Returns MD_EINVAL for inconsistent parameters (cutoff + skin not
+ * below half the periodic box, non-positive sizes, molecules outside the box, r_ads > rc_w). */
+md_status md_create(const md_system* sys, const md_potential* pot, void* stream, md_ctx** out);
+
+/* Create a context holding n_replicas independent systems that advance together: every kernel
+ * launch covers all replicas (uneven sizes allowed). Same rules as md_create per replica. */
+md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md_potential* pot,
+                          void* stream, md_ctx** out);
+
+/* Replace the launch-shape knobs (autotuner); takes effect at the next md_step. */
+md_status md_set_tuning(md_ctx* ctx, const md_tuning* t);
+md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
+
+/* Enqueue n velocity-Verlet steps for every replica (asynchronous). Returns a sticky device
+ * status found by earlier work, if any, without waiting for the GPU. */
+md_status md_step(md_ctx* ctx, int64_t n);
+
+/* Wait for all enqueued work; returns the sticky device status. */
+md_status md_sync(md_ctx* ctx);
+
+/* Copy replica state to caller-owned host arrays (3*n_vapor each, caller's molecule order).
+ * x: positions wrapped into the box; v: velocities; either may be NULL. Synchronises. */
+md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
+
+/* Overwrite replica state from host arrays (3*n_vapor each, caller's order; positions must lie
+ * inside the box). Forces are re-evaluated and lists rebuilt. The step counter is unchanged. */
+md_status md_set_state(md_ctx* ctx, int32_t replica, const double* x, const double* v);
+
+/* Enqueue one evaluation of the forces at the current positions with the same pair-force kernel
+ * and launch shape the step uses (Eq. 2, Fig. 1), without moving molecules or rebuilding lists.
+ * Asynchronous; meant for timing the pair kernel in isolation. */
+md_status md_compute_forces(md_ctx* ctx);
+
+/* Host<->device bytes the library has copied for this context since creation (state uploads,
+ * read-backs, status words). Either pointer may be NULL. */
+md_status md_transfer_bytes(const md_ctx* ctx, int64_t* h2d, int64_t* d2h);
+
+/* Copy the forces of the last evaluation (at the current positions) to host f (3*n_vapor). */
+md_status md_get_forces(md_ctx* ctx, int32_t replica, double* f);
+
+/* Observables of one replica at the current state. Fills *out; when non-NULL the arrays receive
+ * occupancy[n_pores], adsorbed[n_groups] and profile[n_groups * n_bins] (group-major).
+ * A molecule belongs to the pore whose axis is nearest in xy (slits: |dy|); ties go to the lower
+ * pore index. bins: floor((z + Lz/2)/bin_width), the last bin closed. Synchronises. */
+md_status md_observables(md_ctx* ctx, int32_t replica, md_obs* out, int64_t* occupancy,
+                         int64_t* adsorbed, int64_t* profile);
+
+/* Copy the wall atoms of a replica (3*n_wall doubles, as generated or given). */
+md_status md_get_wall(md_ctx* ctx, int32_t replica, double* wall_xyz);
+
+/* Number of replicas; sizes of one replica. */
+md_status md_get_sizes(const md_ctx* ctx, int32_t replica, int64_t* n_vapor, int64_t* n_wall,
+                       int32_t* n_groups, int32_t* n_bins);
+
+/* Kernel launches the library issued since creation (graph replays count each node). */
+int64_t md_kernel_launches(const md_ctx* ctx);
+
+/* Human-readable text of a status, and the last error message of a context (never NULL);
+ * md_last_error(NULL) gives the last md_create / md_create_batch failure of the calling thread. */
+const char* md_status_string(md_status s);
+const char* md_last_error(const md_ctx* ctx);
+
+/* Free every resource of the context (synchronises its stream). NULL is ignored. */
+void md_destroy(md_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

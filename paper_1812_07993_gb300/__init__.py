@@ -1,0 +1,291 @@
+"""GB300 (sm_103a) molecular dynamics of water vapour near atomistic pore walls.
+
+Python binding of the C ABI in ``include/md.h`` (ctypes, argument marshalling only): every step of
+the simulation runs in the CUDA kernels of ``libmd.so``. There is no CPU fallback; importing works
+without a GPU, but every call that needs the library raises if ``libmd.so`` is missing.
+
+The functions ``md_*`` mirror the C entry points one to one; ``Simulation`` wraps a context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import workloads
+
+__all__ = ["Simulation", "MDError", "load_library", "library_path", "md_potential_from",
+           "MD_PREC_FP64", "MD_PREC_MIXED"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmd.so")
+_lib = None
+
+MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = range(7)
+MD_PREC_FP64, MD_PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "MD_OK", 1: "MD_EINVAL", 2: "MD_ENOMEM", 3: "MD_ECUDA", 4: "MD_EOVERFLOW",
+                5: "MD_EUNSTABLE", 6: "MD_ETIMEOUT"}
+
+
+class md_pore(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("r0", ctypes.c_double), ("r1", ctypes.c_double), ("r_cavity", ctypes.c_double),
+                ("width", ctypes.c_double)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class md_system(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("n_vapor", ctypes.c_int64), ("x0", _DP), ("v0", _DP), ("T0", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tau_B", ctypes.c_double),
+                ("thermostat_every", ctypes.c_int32), ("slab_half", ctypes.c_double),
+                ("lattice_a", ctypes.c_double), ("wall_xyz", _DP), ("n_wall", ctypes.c_int64),
+                ("pores", ctypes.POINTER(md_pore)), ("n_pores", ctypes.c_int32)]
+
+
+class md_potential(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("mass", ctypes.c_double),
+                ("rc", ctypes.c_double), ("eps_w", ctypes.c_double), ("sigma_w", ctypes.c_double),
+                ("rc_w", ctypes.c_double), ("skin", ctypes.c_double),
+                ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("r_ads", ctypes.c_double), ("bin_width", ctypes.c_double),
+                ("max_neighbors", ctypes.c_int32), ("max_wall_neighbors", ctypes.c_int32)]
+
+
+class md_tuning(ctypes.Structure):
+    _fields_ = [("force_block", ctypes.c_int32), ("force_tpp", ctypes.c_int32),
+                ("list_block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32)]
+
+
+class md_obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("n_vapor", ctypes.c_int64), ("n_wall", ctypes.c_int64),
+                ("ke", ctypes.c_double), ("pe", ctypes.c_double), ("pe_vv", ctypes.c_double),
+                ("pe_vw", ctypes.c_double), ("T", ctypes.c_double),
+                ("virial_vv", ctypes.c_double), ("virial_vw", ctypes.c_double),
+                ("pairs_vv", ctypes.c_int64), ("pairs_vw", ctypes.c_int64),
+                ("occupancy", ctypes.c_int64), ("adsorbed", ctypes.c_int64),
+                ("n_groups", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("n_rebuilds", ctypes.c_int64), ("pair_evals_total", ctypes.c_int64),
+                ("max_nb_used", ctypes.c_int32), ("max_wall_nb_used", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_CTX = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); the same names as include/md.h
+_SIGNATURES = {
+    "md_create": (ctypes.c_int, [ctypes.POINTER(md_system), ctypes.POINTER(md_potential),
+                                 ctypes.c_void_p, ctypes.POINTER(_CTX)]),
+    "md_create_batch": (ctypes.c_int, [ctypes.POINTER(md_system), ctypes.c_int32,
+                                       ctypes.POINTER(md_potential), ctypes.c_void_p,
+                                       ctypes.POINTER(_CTX)]),
+    "md_set_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(md_tuning)]),
+    "md_get_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(md_tuning)]),
+    "md_step": (ctypes.c_int, [_CTX, ctypes.c_int64]),
+    "md_sync": (ctypes.c_int, [_CTX]),
+    "md_get_state": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP, _DP]),
+    "md_set_state": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP, _DP]),
+    "md_get_forces": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP]),
+    "md_compute_forces": (ctypes.c_int, [_CTX]),
+    "md_transfer_bytes": (ctypes.c_int, [_CTX, _I64P, _I64P]),
+    "md_observables": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(md_obs), _I64P, _I64P,
+                                      _I64P]),
+    "md_get_wall": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP]),
+    "md_get_sizes": (ctypes.c_int, [_CTX, ctypes.c_int32, _I64P, _I64P,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "md_kernel_launches": (ctypes.c_int64, [_CTX]),
+    "md_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "md_last_error": (ctypes.c_char_p, [_CTX]),
+    "md_destroy": (None, [_CTX]),
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load ``libmd.so`` (built by ``paper_1812_07993_gb300.build``). Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is not built; run paper_1812_07993_gb300.build.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class MDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, ctx=None):
+    if status != MD_OK:
+        msg = load_library().md_last_error(ctx).decode(errors="replace")
+        raise MDError(status, msg)
+
+
+def md_potential_from(pot: "workloads.Potential", precision: int = MD_PREC_FP64,
+                      max_neighbors: int = 0, max_wall_neighbors: int = 0) -> md_potential:
+    return md_potential(pot.eps, pot.sigma, pot.mass, pot.rc, pot.eps_w, pot.sigma_w, pot.rc_w,
+                        pot.skin, pot.shift_energy, precision, pot.r_ads, pot.bin_width,
+                        max_neighbors, max_wall_neighbors)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # a torch.cuda.Stream
+
+
+def _as3(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1, 3)
+    return a
+
+
+class Simulation:
+    """One context: a batch of replicas advanced together on the GPU.
+
+    ``systems`` are ``workloads.System`` objects (their wall arrays are passed explicitly, so the
+    GPU and the oracle see the same wall atoms unless ``generate_wall`` is set)."""
+
+    def __init__(self, systems, potential: "workloads.Potential" = None,
+                 precision: int = MD_PREC_FP64, stream=None, generate_wall: bool = False,
+                 max_neighbors: int = 0, max_wall_neighbors: int = 0):
+        lib = load_library()
+        if isinstance(systems, workloads.System):
+            systems = [systems]
+        self.systems = list(systems)
+        self.potential = potential or workloads.Potential()
+        self._keep = []
+        arr = (md_system * len(self.systems))()
+        for k, s in enumerate(self.systems):
+            x0, v0 = _as3(s.x0), _as3(s.v0)
+            wall = _as3(s.wall)
+            pores = (md_pore * max(1, len(s.pores)))()
+            for q, p in enumerate(s.pores):
+                pores[q] = md_pore(p.kind, p.cx, p.cy, p.r0, p.r1, p.r_cavity, p.width)
+            self._keep += [x0, v0, wall, pores]
+            arr[k] = md_system(s.Lx, s.Ly, s.Lz, len(x0), x0.ctypes.data_as(_DP),
+                               v0.ctypes.data_as(_DP), s.T0, s.dt, s.tau_B, s.thermostat_every,
+                               s.slab_half, s.lattice_a,
+                               None if generate_wall else wall.ctypes.data_as(_DP),
+                               0 if generate_wall else len(wall), pores, len(s.pores))
+        pot = md_potential_from(self.potential, precision, max_neighbors, max_wall_neighbors)
+        ctx = _CTX()
+        st = lib.md_create_batch(arr, len(self.systems), ctypes.byref(pot),
+                                 _stream_handle(stream), ctypes.byref(ctx))
+        self._keep = []
+        _check(st, None)
+        self.ctx = ctx
+        self.precision = precision
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "ctx", None):
+            load_library().md_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls
+    def step(self, n: int = 1):
+        _check(load_library().md_step(self.ctx, n), self.ctx)
+
+    def sync(self):
+        _check(load_library().md_sync(self.ctx), self.ctx)
+
+    def sizes(self, r: int = 0):
+        nv, nw = ctypes.c_int64(), ctypes.c_int64()
+        ng, nb = ctypes.c_int32(), ctypes.c_int32()
+        _check(load_library().md_get_sizes(self.ctx, r, ctypes.byref(nv), ctypes.byref(nw),
+                                           ctypes.byref(ng), ctypes.byref(nb)), self.ctx)
+        return nv.value, nw.value, ng.value, nb.value
+
+    def state(self, r: int = 0):
+        n = self.sizes(r)[0]
+        x = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        _check(load_library().md_get_state(self.ctx, r, x.ctypes.data_as(_DP),
+                                           v.ctypes.data_as(_DP)), self.ctx)
+        return x, v
+
+    def set_state(self, r: int, x, v):
+        x, v = _as3(x), _as3(v)
+        _check(load_library().md_set_state(self.ctx, r, x.ctypes.data_as(_DP),
+                                           v.ctypes.data_as(_DP)), self.ctx)
+
+    def forces(self, r: int = 0):
+        n = self.sizes(r)[0]
+        f = np.zeros((n, 3))
+        _check(load_library().md_get_forces(self.ctx, r, f.ctypes.data_as(_DP)), self.ctx)
+        return f
+
+    def wall(self, r: int = 0):
+        nw = self.sizes(r)[1]
+        w = np.zeros((nw, 3))
+        _check(load_library().md_get_wall(self.ctx, r, w.ctypes.data_as(_DP)), self.ctx)
+        return w
+
+    def observables(self, r: int = 0):
+        """Return (dict of md_obs fields, occupancy[n_pores], adsorbed[n_groups],
+        profile[n_groups, n_bins])."""
+        nv, nw, ng, nb = self.sizes(r)
+        npores = len(self.systems[r].pores)
+        occ = np.zeros(max(npores, 1), dtype=np.int64)
+        ads = np.zeros(ng, dtype=np.int64)
+        prof = np.zeros((ng, nb), dtype=np.int64)
+        o = md_obs()
+        _check(load_library().md_observables(self.ctx, r, ctypes.byref(o),
+                                             occ.ctypes.data_as(_I64P), ads.ctypes.data_as(_I64P),
+                                             prof.ctypes.data_as(_I64P)), self.ctx)
+        return o.as_dict(), occ[:npores], ads, prof
+
+    def set_tuning(self, force_block=0, force_tpp=0, list_block=0, use_graph=0, steps_per_graph=0):
+        t = md_tuning(force_block, force_tpp, list_block, use_graph, steps_per_graph)
+        _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)
+
+    def tuning(self):
+        t = md_tuning()
+        _check(load_library().md_get_tuning(self.ctx, ctypes.byref(t)), self.ctx)
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    def compute_forces(self):
+        """Enqueue one pair-force evaluation at the current positions (asynchronous)."""
+        _check(load_library().md_compute_forces(self.ctx), self.ctx)
+
+    def transfer_bytes(self):
+        h, d = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().md_transfer_bytes(self.ctx, ctypes.byref(h), ctypes.byref(d)),
+               self.ctx)
+        return h.value, d.value
+
+    def kernel_launches(self) -> int:
+        return int(load_library().md_kernel_launches(self.ctx))

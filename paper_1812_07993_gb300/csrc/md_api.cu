@@ -1,0 +1,803 @@
+// md_api.cu -- host side of the C ABI declared in include/md.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/md.h"
+#include "md_internal.cuh"
+
+using namespace mdk;
+
+extern "C" void md_destroy(md_ctx* c);
+
+struct ReplicaHost {
+  int64_t n_vap = 0, n_wall = 0;
+  int32_t n_pores = 0, n_groups = 1, n_bins = 0;
+  std::vector<double> wall;  // caller order, 3*n_wall
+};
+
+struct md_ctx {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Arrays a{};
+  PotDev pot{};
+  Tuning tun{};
+  bool mixed = false;
+  int n_reps = 0;
+  std::vector<RepDev> reps;
+  std::vector<ReplicaHost> rh;
+  int32_t* cell_rep = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+  int32_t* status_host = nullptr;   // pinned
+  cudaEvent_t status_event = nullptr;
+  bool status_pending = false;
+  int last_status_bits = 0;
+  long long launches = 0;
+  int64_t steps_done = 0;
+  int64_t bytes_h2d = 0, bytes_d2h = 0;
+  int use_graph = 0, steps_per_graph = 10;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_steps = 0;
+  size_t prof_total = 0, groups_total = 0, pores_total = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+md_status fail(md_ctx* c, md_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                            \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((ctx), MD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+md_status dalloc(md_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MD_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                  cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  e = cudaMemsetAsync(q, 0, bytes, c->stream);
+  if (e != cudaSuccess) return fail(c, MD_ECUDA, cudaGetErrorString(e));
+  return MD_OK;
+}
+
+uint32_t hi_word(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  return (uint32_t)(b >> 32);
+}
+
+double lj_u(double r2, double eps, double sigma) {
+  double s2 = sigma * sigma / r2, s6 = s2 * s2 * s2;
+  return 4.0 * eps * (s6 * s6 - s6);
+}
+
+md_status validate_potential(md_ctx* c, const md_potential* p) {
+  if (!p) return fail(c, MD_EINVAL, "potential is NULL");
+  if (!(p->eps >= 0 && p->sigma > 0 && p->mass > 0 && p->rc > 0 && p->eps_w >= 0 &&
+        p->sigma_w > 0 && p->rc_w > 0 && p->skin >= 0 && p->bin_width > 0))
+    return fail(c, MD_EINVAL, "potential: eps, eps_w >= 0; sigma, mass, rc, rc_w, bin_width > 0; skin >= 0");
+  if (p->r_ads > p->rc_w) return fail(c, MD_EINVAL, "r_ads must not exceed rc_w");
+  if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED)
+    return fail(c, MD_EINVAL, "unknown precision");
+  if (p->max_neighbors < 0 || p->max_wall_neighbors < 0)
+    return fail(c, MD_EINVAL, "negative list capacity");
+  return MD_OK;
+}
+
+md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
+  const std::string who = "replica " + std::to_string(r) + ": ";
+  if (!(s->Lx > 0 && s->Ly > 0 && s->Lz > 0 && s->dt > 0 && s->T0 >= 0 && s->slab_half >= 0))
+    return fail(c, MD_EINVAL, who + "box, dt must be > 0; T0, slab_half >= 0");
+  if (s->n_vapor < 0 || s->n_wall < 0 || s->n_pores < 0)
+    return fail(c, MD_EINVAL, who + "negative count");
+  if (s->n_vapor > 0 && (!s->x0 || !s->v0)) return fail(c, MD_EINVAL, who + "x0/v0 NULL");
+  if (s->n_pores > 0 && !s->pores) return fail(c, MD_EINVAL, who + "pores NULL");
+  if (s->thermostat_every < 0) return fail(c, MD_EINVAL, who + "thermostat_every < 0");
+  if (s->thermostat_every > 0 && s->tau_B > 0 && s->tau_B < s->thermostat_every * s->dt)
+    return fail(c, MD_EINVAL, who + "tau_B below thermostat_every*dt would over-correct");
+  if (!(std::floor(s->Lx / rl) >= 3 && std::floor(s->Ly / rl) >= 3))
+    return fail(c, MD_EINVAL, who + "box x/y must hold at least 3 cells of max(rc,rc_w)+skin");
+  if (std::floor(s->Lx / rl) > 1023 || std::floor(s->Ly / rl) > 1023 ||
+      std::floor(s->Lz / rl) > 1023)
+    return fail(c, MD_EINVAL, who + "more than 1023 cells along an axis");
+  if (!s->wall_xyz && !(s->lattice_a > 0) && s->slab_half > 0)
+    return fail(c, MD_EINVAL, who + "lattice_a must be > 0 to generate the wall");
+  for (int q = 0; q < s->n_pores; ++q) {
+    const md_pore& P = s->pores[q];
+    if (P.kind < 1 || P.kind > 4) return fail(c, MD_EINVAL, who + "unknown pore kind");
+    if (P.kind == MD_PORE_CONE && !(s->slab_half > 0))
+      return fail(c, MD_EINVAL, who + "a cone needs slab_half > 0");
+  }
+  const double hx = 0.5 * s->Lx, hy = 0.5 * s->Ly, hz = 0.5 * s->Lz;
+  for (int64_t i = 0; i < s->n_vapor; ++i) {
+    const double* x = s->x0 + 3 * i;
+    if (!(x[0] >= -hx && x[0] < hx && x[1] >= -hy && x[1] < hy && x[2] >= -hz && x[2] <= hz))
+      return fail(c, MD_EINVAL, who + "molecule " + std::to_string(i) + " outside the box");
+    const double* v = s->v0 + 3 * i;
+    if (!(std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2])))
+      return fail(c, MD_EINVAL, who + "non-finite velocity");
+  }
+  for (int64_t i = 0; s->wall_xyz && i < s->n_wall; ++i) {
+    const double* x = s->wall_xyz + 3 * i;
+    if (!(x[0] >= -hx && x[0] < hx && x[1] >= -hy && x[1] < hy && x[2] >= -hz && x[2] <= hz))
+      return fail(c, MD_EINVAL, who + "wall atom " + std::to_string(i) + " outside the box");
+  }
+  return MD_OK;
+}
+
+double min_img(double d, double L) {
+  if (d >= 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+// simple-cubic wall sites -L/2 + (i + 1/2) a in |z| < h, minus every pore's carved region
+std::vector<double> generate_wall(const md_system* s) {
+  std::vector<double> w;
+  if (!(s->slab_half > 0)) return w;
+  const double a = s->lattice_a;
+  const int nx = (int)std::llround(s->Lx / a), ny = (int)std::llround(s->Ly / a),
+            nz = (int)std::llround(s->Lz / a);
+  for (int k = 0; k < nz; ++k) {
+    const double z = -0.5 * s->Lz + (k + 0.5) * a;
+    if (!(std::fabs(z) < s->slab_half)) continue;
+    for (int j = 0; j < ny; ++j) {
+      const double y = -0.5 * s->Ly + (j + 0.5) * a;
+      for (int i = 0; i < nx; ++i) {
+        const double x = -0.5 * s->Lx + (i + 0.5) * a;
+        bool carved = false;
+        for (int q = 0; q < s->n_pores && !carved; ++q) {
+          const md_pore& P = s->pores[q];
+          carved = in_pore(P.kind, P.r0, P.r1, P.r_cavity, P.width, min_img(x - P.cx, s->Lx),
+                           min_img(y - P.cy, s->Ly), z, s->slab_half);
+        }
+        if (!carved) {
+          w.push_back(x);
+          w.push_back(y);
+          w.push_back(z);
+        }
+      }
+    }
+  }
+  return w;
+}
+
+int status_to_code(int bits) {
+  if (bits & kStatusOverflow) return MD_EOVERFLOW;
+  if (bits & kStatusUnstable) return MD_EUNSTABLE;
+  if (bits & kStatusTimeout) return MD_ETIMEOUT;
+  return MD_OK;
+}
+
+md_status device_status(md_ctx* c) {
+  if (c->last_status_bits) {
+    md_status s = (md_status)status_to_code(c->last_status_bits);
+    if (c->err.empty()) c->err = md_status_string(s);
+    return s;
+  }
+  return MD_OK;
+}
+
+md_status sync_status(md_ctx* c) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->status_host, c->a.status, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, c->stream));
+  c->bytes_d2h += sizeof(int32_t);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->status_pending = false;
+  c->last_status_bits = *c->status_host;
+  if (c->last_status_bits) {
+    md_status s = (md_status)status_to_code(c->last_status_bits);
+    c->err = std::string("device reported: ") + md_status_string(s);
+    return s;
+  }
+  return MD_OK;
+}
+
+void enqueue_step(md_ctx* c) {
+  launch_integrate_first(c->a, c->pot, c->mixed, c->stream);
+  launch_rebuild(c->a, c->pot, c->tun, c->cell_rep, c->stream);
+  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
+  launch_integrate_second(c->a, c->pot, c->stream);
+  launch_thermostat(c->a, c->pot, c->stream);
+}
+
+md_status rebuild_and_forces(md_ctx* c) {
+  const int one = 1;
+  CUDA_TRY(c, cudaMemcpyAsync(c->a.force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream));
+  c->bytes_h2d += sizeof(int);
+  launch_rebuild(c->a, c->pot, c->tun, c->cell_rep, c->stream);
+  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
+  c->launches += kernels_per_rebuild() + 1;
+  CUDA_TRY(c, cudaGetLastError());
+  return sync_status(c);
+}
+
+void destroy_graph(md_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_steps = 0;
+}
+
+md_status build_graph(md_ctx* c, int steps) {
+  destroy_graph(c);
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < steps; ++k) enqueue_step(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return fail(c, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph_steps = steps;
+  return MD_OK;
+}
+
+bool check_replica(md_ctx* c, int32_t r) { return c && r >= 0 && r < c->n_reps; }
+
+md_status create_impl(const md_system* systems, int32_t n_reps, const md_potential* pot,
+                      void* stream, md_ctx** out) {
+  if (!out) return MD_EINVAL;
+  *out = nullptr;
+  md_ctx* c = new md_ctx();
+  md_status st = MD_OK;
+  auto bail = [&](md_status s) {
+    g_create_error = c->err.empty() ? md_status_string(s) : c->err;
+    md_destroy(c);
+    return s;
+  };
+  // all argument checks come before the first CUDA call
+  if (!systems || n_reps <= 0) return bail(fail(c, MD_EINVAL, "no systems"));
+  if ((st = validate_potential(c, pot)) != MD_OK) return bail(st);
+  const double rl = std::max(pot->rc, pot->rc_w) + pot->skin;
+  for (int r = 0; r < n_reps; ++r)
+    if ((st = validate_system(c, &systems[r], r, rl)) != MD_OK) return bail(st);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
+    c->own_stream = true;
+  }
+  c->n_reps = n_reps;
+  c->mixed = pot->precision == MD_PREC_MIXED;
+
+  // ---- potential constants
+  PotDev& P = c->pot;
+  const double s6 = std::pow(pot->sigma, 6), s12 = s6 * s6;
+  const double w6 = std::pow(pot->sigma_w, 6), w12 = w6 * w6;
+  P.rc2 = pot->rc * pot->rc;
+  P.rcw2 = pot->rc_w * pot->rc_w;
+  P.a12 = 48.0 * pot->eps * s12;
+  P.b6 = 24.0 * pot->eps * s6;
+  P.a12w = 48.0 * pot->eps_w * w12;
+  P.b6w = 24.0 * pot->eps_w * w6;
+  P.e12 = 4.0 * pot->eps * s12;
+  P.e6 = 4.0 * pot->eps * s6;
+  P.e12w = 4.0 * pot->eps_w * w12;
+  P.e6w = 4.0 * pot->eps_w * w6;
+  P.ushift = pot->shift_energy ? lj_u(P.rc2, pot->eps, pot->sigma) : 0.0;
+  P.ushift_w = pot->shift_energy ? lj_u(P.rcw2, pot->eps_w, pot->sigma_w) : 0.0;
+  P.mass = pot->mass;
+  P.inv_mass = 1.0 / pot->mass;
+  P.half_skin2 = 0.25 * pot->skin * pot->skin;
+  P.r_ads2 = pot->r_ads * pot->r_ads;
+  P.rc2f = (float)P.rc2;
+  P.rcw2f = (float)P.rcw2;
+  P.rl2f = (float)((rl + 1e-4) * (rl + 1e-4));
+  P.a12f = (float)P.a12;
+  P.b6f = (float)P.b6;
+  P.a12wf = (float)P.a12w;
+  P.b6wf = (float)P.b6w;
+  P.e12f = (float)P.e12;
+  P.e6f = (float)P.e6;
+  P.e12wf = (float)P.e12w;
+  P.e6wf = (float)P.e6w;
+  P.cap_vv = pot->max_neighbors > 0 ? pot->max_neighbors : 160;
+  P.cap_vw = pot->max_wall_neighbors > 0 ? pot->max_wall_neighbors : 224;
+
+  // ---- replicas, walls, cells
+  c->reps.resize(n_reps);
+  c->rh.resize(n_reps);
+  std::vector<PoreDev> pores;
+  long long n_tot = 0, nw_tot = 0, ncell_tot = 0, groups = 0, prof = 0;
+  for (int r = 0; r < n_reps; ++r) {
+    const md_system* s = &systems[r];
+    ReplicaHost& H = c->rh[r];
+    if (s->wall_xyz)
+      H.wall.assign(s->wall_xyz, s->wall_xyz + 3 * s->n_wall);
+    else
+      H.wall = generate_wall(s);
+    H.n_vap = s->n_vapor;
+    H.n_wall = (int64_t)(H.wall.size() / 3);
+    H.n_pores = s->n_pores;
+    H.n_groups = std::max(1, s->n_pores);
+    H.n_bins = (int)std::ceil(s->Lz / pot->bin_width);
+    RepDev& R = c->reps[r];
+    R.Lx = s->Lx; R.Ly = s->Ly; R.Lz = s->Lz;
+    R.hx = 0.5 * s->Lx; R.hy = 0.5 * s->Ly; R.hz = 0.5 * s->Lz;
+    R.T0 = s->T0;
+    R.dt = s->dt;
+    R.n_th = s->thermostat_every;
+    const double tau = s->tau_B > 0 ? s->tau_B : s->thermostat_every * s->dt;
+    R.lam_coef = s->thermostat_every > 0 ? s->thermostat_every * s->dt / tau : 0.0;
+    R.slab_half = s->slab_half;
+    R.ncx = (int)std::floor(s->Lx / rl);
+    R.ncy = (int)std::floor(s->Ly / rl);
+    R.ncz = std::max(1, (int)std::floor(s->Lz / rl));
+    R.lcx = s->Lx / R.ncx; R.lcy = s->Ly / R.ncy; R.lcz = s->Lz / R.ncz;
+    R.lcxf = (float)R.lcx; R.lcyf = (float)R.lcy; R.lczf = (float)R.lcz;
+    R.hi_thr_x = hi_word(R.hx);
+    R.hi_thr_y = hi_word(R.hy);
+    R.bin_width = pot->bin_width;
+    R.vap_off = (int32_t)n_tot;
+    R.n_vap = (int32_t)H.n_vap;
+    R.wall_off = (int32_t)nw_tot;
+    R.n_wall = (int32_t)H.n_wall;
+    R.cell_off = (int32_t)ncell_tot;
+    R.pore_off = (int32_t)pores.size();
+    R.n_pores = s->n_pores;
+    R.group_off = (int32_t)groups;
+    R.n_groups = H.n_groups;
+    R.n_bins = H.n_bins;
+    R.prof_off = (int32_t)prof;
+    for (int q = 0; q < s->n_pores; ++q) {
+      const md_pore& Q = s->pores[q];
+      pores.push_back(PoreDev{Q.kind, Q.cx, Q.cy, Q.r0, Q.r1, Q.r_cavity, Q.width});
+    }
+    n_tot += H.n_vap;
+    nw_tot += H.n_wall;
+    ncell_tot += (long long)R.ncx * R.ncy * R.ncz;
+    groups += H.n_groups;
+    prof += (long long)H.n_groups * H.n_bins;
+  }
+  if (n_tot > kMaxIndex || nw_tot > kMaxIndex)
+    return bail(fail(c, MD_EINVAL, "more than 2^26 - 1 molecules or wall atoms in one context"));
+  if (ncell_tot > 4096LL * 4096LL) return bail(fail(c, MD_EINVAL, "too many cells"));
+  c->prof_total = (size_t)prof;
+  c->groups_total = (size_t)groups;
+  c->pores_total = pores.size();
+
+  // wall sorted by cell (stable): positions, FP32 offsets from the home-cell centre, CSR starts
+  std::vector<int> wcell(nw_tot);
+  std::vector<int32_t> wstart(ncell_tot + 1, 0);
+  std::vector<dvec4> wpos(nw_tot);
+  std::vector<float4> wlpos(nw_tot);
+  std::vector<int32_t> cell_rep(ncell_tot);
+  {
+    long long k = 0;
+    for (int r = 0; r < n_reps; ++r) {
+      const RepDev& R = c->reps[r];
+      for (long long q = 0; q < (long long)R.ncx * R.ncy * R.ncz; ++q) cell_rep[R.cell_off + q] = r;
+      const std::vector<double>& W = c->rh[r].wall;
+      for (int64_t i = 0; i < c->rh[r].n_wall; ++i, ++k) {
+        int ix = cell_coord(W[3 * i], R.hx, R.lcx, R.ncx);
+        int iy = cell_coord(W[3 * i + 1], R.hy, R.lcy, R.ncy);
+        int iz = cell_coord(W[3 * i + 2], R.hz, R.lcz, R.ncz);
+        wcell[k] = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
+        wstart[wcell[k] + 1] += 1;
+      }
+    }
+    for (long long q = 0; q < ncell_tot; ++q) wstart[q + 1] += wstart[q];
+    std::vector<int32_t> fill(wstart.begin(), wstart.end() - 1);
+    k = 0;
+    for (int r = 0; r < n_reps; ++r) {
+      const RepDev& R = c->reps[r];
+      const std::vector<double>& W = c->rh[r].wall;
+      for (int64_t i = 0; i < c->rh[r].n_wall; ++i, ++k) {
+        const int cell = wcell[k];
+        const int dst = fill[cell]++;
+        const double x = W[3 * i], y = W[3 * i + 1], z = W[3 * i + 2];
+        wpos[dst] = make_dvec4(x, y, z, 0.0);
+        const int local = cell - R.cell_off;
+        const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
+        const double cx = -R.hx + (ix + 0.5) * R.lcx, cy = -R.hy + (iy + 0.5) * R.lcy,
+                     cz = -R.hz + (iz + 0.5) * R.lcz;
+        wlpos[dst] = make_float4((float)min_img(x - cx, R.Lx), (float)min_img(y - cy, R.Ly),
+                                 (float)(z - cz), 0.f);
+      }
+    }
+  }
+
+  // ---- device memory
+  Arrays& A = c->a;
+  A.n_total = (int32_t)n_tot;
+  A.n_wall_total = (int32_t)nw_tot;
+  A.n_cells = (int32_t)ncell_tot;
+  A.n_reps = n_reps;
+  const size_t N = (size_t)n_tot;
+#define ALLOC(ptr, cnt)                                 \
+  if ((st = dalloc(c, &(ptr), (cnt))) != MD_OK) return bail(st)
+  ALLOC(A.pos, N); ALLOC(A.vel, N); ALLOC(A.frc, N); ALLOC(A.pos_ref, N);
+  ALLOC(A.pos_alt, N); ALLOC(A.vel_alt, N); ALLOC(A.frc_alt, N);
+  ALLOC(A.lpos, N);
+  ALLOC(A.home, N); ALLOC(A.id, N); ALLOC(A.rep, N); ALLOC(A.id_alt, N);
+  ALLOC(A.cell_tmp, N); ALLOC(A.slot_tmp, N); ALLOC(A.perm_tmp, N);
+  ALLOC(A.nbr_vv, N * (size_t)P.cap_vv); ALLOC(A.nbr_vw, N * (size_t)P.cap_vw);
+  ALLOC(A.n_vv, N); ALLOC(A.n_vw, N);
+  ALLOC(A.wpos, (size_t)nw_tot); ALLOC(A.wlpos, (size_t)nw_tot);
+  ALLOC(A.wstart, (size_t)ncell_tot + 1);
+  ALLOC(A.vcount, (size_t)ncell_tot); ALLOC(A.vstart, (size_t)ncell_tot + 1);
+  ALLOC(A.scan_tiles, 4096);
+  RepDev* reps_d = nullptr;
+  PoreDev* pores_d = nullptr;
+  ALLOC(reps_d, (size_t)n_reps);
+  ALLOC(pores_d, pores.size());
+  A.reps = reps_d;
+  A.pores = pores_d;
+  ALLOC(c->cell_rep, (size_t)ncell_tot);
+  ALLOC(A.lambda, (size_t)n_reps);
+  ALLOC(A.any_scale, 1);
+  ALLOC(A.step, 1);
+  ALLOC(A.max_disp2, 1);
+  ALLOC(A.force_rebuild, 1);
+  ALLOC(A.status, 1);
+  ALLOC(A.n_rebuilds, 1);
+  ALLOC(A.pair_count, 1);
+  ALLOC(A.max_nvv, 1); ALLOC(A.max_nvw, 1);
+  ALLOC(A.pe_i, N); ALLOC(A.pevw_i, N); ALLOC(A.vir_i, N); ALLOC(A.virw_i, N); ALLOC(A.d2w_i, N);
+  ALLOC(A.cnt_vv_i, N); ALLOC(A.cnt_vw_i, N);
+  ALLOC(A.occ, std::max<size_t>(pores.size(), 1));
+  ALLOC(A.ads, (size_t)groups);
+  ALLOC(A.prof, (size_t)prof);
+  ALLOC(A.rep_sums, (size_t)n_reps * 8);
+#undef ALLOC
+  cudaError_t e = cudaMallocHost(&c->status_host, sizeof(int32_t));
+  if (e != cudaSuccess) return bail(fail(c, MD_ENOMEM, "pinned status word"));
+  *c->status_host = 0;
+  e = cudaEventCreateWithFlags(&c->status_event, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
+
+  auto up = [&](void* dst, const void* src, size_t bytes) -> md_status {
+    if (bytes == 0) return MD_OK;
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return MD_OK;
+  };
+  // vapour in caller order
+  std::vector<dvec4> pos(N), vel(N);
+  std::vector<int32_t> id(N), rep(N);
+  for (int r = 0; r < n_reps; ++r) {
+    const md_system* s = &systems[r];
+    const int off = c->reps[r].vap_off;
+    for (int64_t i = 0; i < s->n_vapor; ++i) {
+      pos[off + i] = make_dvec4(s->x0[3 * i], s->x0[3 * i + 1], s->x0[3 * i + 2], 0.0);
+      vel[off + i] = make_dvec4(s->v0[3 * i], s->v0[3 * i + 1], s->v0[3 * i + 2], 0.0);
+      id[off + i] = (int32_t)i;
+      rep[off + i] = r;
+    }
+  }
+  if ((st = up(A.pos, pos.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
+  if ((st = up(A.pos_ref, pos.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
+  if ((st = up(A.vel, vel.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
+  if ((st = up(A.id, id.data(), N * sizeof(int32_t))) != MD_OK) return bail(st);
+  if ((st = up(A.rep, rep.data(), N * sizeof(int32_t))) != MD_OK) return bail(st);
+  if ((st = up(A.wpos, wpos.data(), wpos.size() * sizeof(dvec4))) != MD_OK) return bail(st);
+  if ((st = up(A.wlpos, wlpos.data(), wlpos.size() * sizeof(float4))) != MD_OK) return bail(st);
+  if ((st = up(A.wstart, wstart.data(), wstart.size() * sizeof(int32_t))) != MD_OK) return bail(st);
+  if ((st = up(c->cell_rep, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
+    return bail(st);
+  if ((st = up(reps_d, c->reps.data(), c->reps.size() * sizeof(RepDev))) != MD_OK) return bail(st);
+  if ((st = up(pores_d, pores.data(), pores.size() * sizeof(PoreDev))) != MD_OK) return bail(st);
+  // the host staging vectors above die at return: wait for the copies first
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if ((st = rebuild_and_forces(c)) != MD_OK) return bail(st);
+  *out = c;
+  return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* md_status_string(md_status s) {
+  switch (s) {
+    case MD_OK: return "ok";
+    case MD_EINVAL: return "invalid argument";
+    case MD_ENOMEM: return "out of memory";
+    case MD_ECUDA: return "CUDA error";
+    case MD_EOVERFLOW: return "neighbour list or cell capacity exceeded";
+    case MD_EUNSTABLE: return "unstable motion (non-finite or out-of-box position)";
+    case MD_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* md_last_error(const md_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+md_status md_create(const md_system* sys, const md_potential* pot, void* stream, md_ctx** out) {
+  return create_impl(sys, 1, pot, stream, out);
+}
+
+md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md_potential* pot,
+                          void* stream, md_ctx** out) {
+  return create_impl(systems, n_replicas, pot, stream, out);
+}
+
+md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
+  if (!c || !t) return MD_EINVAL;
+  Tuning nt = c->tun;
+  if (t->force_block) {
+    if (t->force_block % 32 || t->force_block < 32 || t->force_block > 1024)
+      return fail(c, MD_EINVAL, "force_block must be a multiple of 32 in [32, 1024]");
+    nt.force_block = t->force_block;
+  }
+  if (t->force_tpp) {
+    if (t->force_tpp != 1) return fail(c, MD_EINVAL, "force_tpp: only 1 is implemented");
+    nt.force_tpp = t->force_tpp;
+  }
+  if (t->list_block) {
+    if (t->list_block % 32 || t->list_block < 32 || t->list_block > 1024)
+      return fail(c, MD_EINVAL, "list_block must be a multiple of 32 in [32, 1024]");
+    nt.list_block = t->list_block;
+  }
+  if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
+  c->tun = nt;
+  c->use_graph = t->use_graph ? 1 : 0;
+  c->steps_per_graph = t->steps_per_graph > 0 ? t->steps_per_graph : 10;
+  destroy_graph(c);
+  return MD_OK;
+}
+
+md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
+  if (!c || !t) return MD_EINVAL;
+  t->force_block = c->tun.force_block;
+  t->force_tpp = c->tun.force_tpp;
+  t->list_block = c->tun.list_block;
+  t->use_graph = c->use_graph;
+  t->steps_per_graph = c->steps_per_graph;
+  return MD_OK;
+}
+
+md_status md_step(md_ctx* c, int64_t n) {
+  if (!c) return MD_EINVAL;
+  if (n < 0) return fail(c, MD_EINVAL, "negative step count");
+  // pick up the status copied at the end of the previous call, if it has landed
+  if (c->status_pending && cudaEventQuery(c->status_event) == cudaSuccess) {
+    c->status_pending = false;
+    c->last_status_bits = *c->status_host;
+  }
+  md_status prev = device_status(c);
+  if (prev != MD_OK) return prev;
+  int64_t left = n;
+  if (c->use_graph && n >= c->steps_per_graph) {
+    if (c->graph_steps != c->steps_per_graph) {
+      md_status s = build_graph(c, c->steps_per_graph);
+      if (s != MD_OK) return s;
+    }
+    while (left >= c->graph_steps) {
+      CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+      left -= c->graph_steps;
+      c->launches += (long long)c->graph_steps * kernels_per_step();
+    }
+  }
+  for (int64_t k = 0; k < left; ++k) {
+    enqueue_step(c);
+    c->launches += kernels_per_step();
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  c->steps_done += n;
+  if (!c->status_pending) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->status_host, c->a.status, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+    c->bytes_d2h += sizeof(int32_t);
+    CUDA_TRY(c, cudaEventRecord(c->status_event, c->stream));
+    c->status_pending = true;
+  }
+  return MD_OK;
+}
+
+md_status md_sync(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  return sync_status(c);
+}
+
+static md_status fetch_permuted(md_ctx* c, int32_t r, const dvec4* dsrc, double* out) {
+  const RepDev& R = c->reps[r];
+  const size_t n = (size_t)R.n_vap;
+  std::vector<dvec4> buf(n);
+  std::vector<int32_t> id(n);
+  if (n) {
+    CUDA_TRY(c, cudaMemcpyAsync(buf.data(), dsrc + R.vap_off, n * sizeof(dvec4),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(id.data(), c->a.id + R.vap_off, n * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->bytes_d2h += (int64_t)(n * (sizeof(dvec4) + sizeof(int32_t)));
+  for (size_t k = 0; k < n; ++k) {
+    const int i = id[k];
+    out[3 * i] = buf[k].x;
+    out[3 * i + 1] = buf[k].y;
+    out[3 * i + 2] = buf[k].z;
+  }
+  return MD_OK;
+}
+
+md_status md_get_state(md_ctx* c, int32_t r, double* x, double* v) {
+  if (!check_replica(c, r)) return fail(c, MD_EINVAL, "bad replica");
+  md_status s = sync_status(c);
+  if (s != MD_OK && s != MD_EOVERFLOW && s != MD_EUNSTABLE && s != MD_ETIMEOUT) return s;
+  md_status t;
+  if (x && (t = fetch_permuted(c, r, c->a.pos, x)) != MD_OK) return t;
+  if (v && (t = fetch_permuted(c, r, c->a.vel, v)) != MD_OK) return t;
+  return s;
+}
+
+md_status md_get_forces(md_ctx* c, int32_t r, double* f) {
+  if (!check_replica(c, r) || !f) return fail(c, MD_EINVAL, "bad replica or NULL output");
+  md_status s = sync_status(c);
+  if (s == MD_ECUDA) return s;
+  md_status t = fetch_permuted(c, r, c->a.frc, f);
+  return t != MD_OK ? t : s;
+}
+
+md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
+  if (!check_replica(c, r) || !x || !v) return fail(c, MD_EINVAL, "bad replica or NULL input");
+  md_status s = sync_status(c);
+  if (s != MD_OK) return s;
+  const RepDev& R = c->reps[r];
+  const size_t n = (size_t)R.n_vap;
+  std::vector<dvec4> pos(n), vel(n), zero(n, make_dvec4(0, 0, 0, 0));
+  std::vector<int32_t> id(n);
+  for (size_t i = 0; i < n; ++i) {
+    const double* q = x + 3 * i;
+    if (!(q[0] >= -R.hx && q[0] < R.hx && q[1] >= -R.hy && q[1] < R.hy && q[2] >= -R.hz &&
+          q[2] <= R.hz))
+      return fail(c, MD_EINVAL, "molecule " + std::to_string(i) + " outside the box");
+    pos[i] = make_dvec4(q[0], q[1], q[2], 0.0);
+    vel[i] = make_dvec4(v[3 * i], v[3 * i + 1], v[3 * i + 2], 0.0);
+    id[i] = (int32_t)i;
+  }
+  if (n) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->a.pos + R.vap_off, pos.data(), n * sizeof(dvec4),
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->a.pos_ref + R.vap_off, pos.data(), n * sizeof(dvec4),
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->a.vel + R.vap_off, vel.data(), n * sizeof(dvec4),
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->a.frc + R.vap_off, zero.data(), n * sizeof(dvec4),
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->a.id + R.vap_off, id.data(), n * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, c->stream));
+    c->bytes_h2d += (int64_t)(n * (4 * sizeof(dvec4) + sizeof(int32_t)));
+  }
+  return rebuild_and_forces(c);
+}
+
+md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, int64_t* adsorbed,
+                         int64_t* profile) {
+  if (!check_replica(c, r) || !out) return fail(c, MD_EINVAL, "bad replica or NULL output");
+  md_status s = sync_status(c);
+  if (s != MD_OK) return s;
+  Arrays& A = c->a;
+  CUDA_TRY(c, cudaMemsetAsync(A.occ, 0, std::max<size_t>(c->pores_total, 1) * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(A.ads, 0, c->groups_total * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(A.prof, 0, std::max<size_t>(c->prof_total, 1) * 8, c->stream));
+  launch_forces(A, c->pot, c->mixed, true, c->tun, c->stream);
+  launch_observables(A, c->pot, c->stream);
+  c->launches += 3;
+  CUDA_TRY(c, cudaGetLastError());
+  const RepDev& R = c->reps[r];
+  const ReplicaHost& H = c->rh[r];
+  double sums[8];
+  unsigned long long nreb = 0, pc = 0;
+  long long step = 0;
+  int32_t mv = 0, mw = 0;
+  std::vector<unsigned long long> occ(std::max(H.n_pores, 1)), ads(H.n_groups),
+      prof((size_t)H.n_groups * H.n_bins);
+  CUDA_TRY(c, cudaMemcpyAsync(sums, A.rep_sums + 8 * r, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&nreb, A.n_rebuilds, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&pc, A.pair_count, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&step, A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&mv, A.max_nvv, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&mw, A.max_nvw, 4, cudaMemcpyDeviceToHost, c->stream));
+  if (H.n_pores)
+    CUDA_TRY(c, cudaMemcpyAsync(occ.data(), A.occ + R.pore_off, H.n_pores * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(ads.data(), A.ads + R.group_off, H.n_groups * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (!prof.empty())
+    CUDA_TRY(c, cudaMemcpyAsync(prof.data(), A.prof + R.prof_off, prof.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->step = step;
+  out->n_vapor = H.n_vap;
+  out->n_wall = H.n_wall;
+  out->ke = sums[0];
+  out->pe_vv = sums[1];
+  out->pe_vw = sums[2];
+  out->pe = sums[1] + sums[2];
+  out->T = H.n_vap ? 2.0 * sums[0] / (3.0 * (double)H.n_vap) : 0.0;
+  out->virial_vv = sums[3];
+  out->virial_vw = sums[4];
+  out->pairs_vv = (int64_t)std::llround(sums[5]) / 2;
+  out->pairs_vw = (int64_t)std::llround(sums[6]);
+  out->n_groups = H.n_groups;
+  out->n_bins = H.n_bins;
+  out->n_rebuilds = (int64_t)nreb;
+  out->pair_evals_total = (int64_t)(pc / 2);
+  out->max_nb_used = mv;
+  out->max_wall_nb_used = mw;
+  for (int q = 0; q < H.n_pores; ++q) {
+    out->occupancy += (int64_t)occ[q];
+    if (occupancy) occupancy[q] = (int64_t)occ[q];
+  }
+  for (int g = 0; g < H.n_groups; ++g) {
+    out->adsorbed += (int64_t)ads[g];
+    if (adsorbed) adsorbed[g] = (int64_t)ads[g];
+  }
+  if (profile)
+    for (size_t k = 0; k < prof.size(); ++k) profile[k] = (int64_t)prof[k];
+  return sync_status(c);
+}
+
+md_status md_compute_forces(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  md_status prev = device_status(c);
+  if (prev != MD_OK) return prev;
+  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
+  c->launches += 1;
+  CUDA_TRY(c, cudaGetLastError());
+  return MD_OK;
+}
+
+md_status md_transfer_bytes(const md_ctx* c, int64_t* h2d, int64_t* d2h) {
+  if (!c) return MD_EINVAL;
+  if (h2d) *h2d = c->bytes_h2d;
+  if (d2h) *d2h = c->bytes_d2h;
+  return MD_OK;
+}
+
+md_status md_get_wall(md_ctx* c, int32_t r, double* w) {
+  if (!check_replica(c, r) || !w) return fail(c, MD_EINVAL, "bad replica or NULL output");
+  const std::vector<double>& W = c->rh[r].wall;
+  if (!W.empty()) std::memcpy(w, W.data(), W.size() * sizeof(double));
+  return MD_OK;
+}
+
+md_status md_get_sizes(const md_ctx* c, int32_t r, int64_t* n_vapor, int64_t* n_wall,
+                       int32_t* n_groups, int32_t* n_bins) {
+  if (!c || r < 0 || r >= c->n_reps) return MD_EINVAL;
+  const ReplicaHost& H = c->rh[r];
+  if (n_vapor) *n_vapor = H.n_vap;
+  if (n_wall) *n_wall = H.n_wall;
+  if (n_groups) *n_groups = H.n_groups;
+  if (n_bins) *n_bins = H.n_bins;
+  return MD_OK;
+}
+
+int64_t md_kernel_launches(const md_ctx* c) { return c ? c->launches : 0; }
+
+void md_destroy(md_ctx* c) {
+  if (!c) return;
+  if (c->stream || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  destroy_graph(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->status_host) cudaFreeHost(c->status_host);
+  if (c->status_event) cudaEventDestroy(c->status_event);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

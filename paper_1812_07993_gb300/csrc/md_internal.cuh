@@ -1,0 +1,144 @@
+// md_internal.cuh -- device data layout and kernel entry points of the pore / water-vapour MD
+// library (arXiv:1812.07993, Sec. 2-3). Internal to the library; the public ABI is include/md.h.
+//
+// Layout in HBM (all replicas of a context packed back to back):
+//   vapour, in cell-sorted order (re-sorted at every list build):
+//     pos, vel, frc   dvec4 (x, y, z, unused)  32 B each per molecule
+//     pos_ref         dvec4, positions at the last list build (skin check)
+//     lpos            float4, position relative to the centre of the home cell (FP32 staging for the
+//                     list build and the mixed-precision pair kernel)
+//     home, id, rep   int32: home cell (global id), caller index within the replica, replica
+//     nbr_vv, nbr_vw  uint32 Verlet lists, column-major [slot * n_total + molecule]
+//     n_vv, n_vw      int32 list lengths
+//   wall (static, sorted by cell once at creation): wpos dvec4, wlpos float4, wstart (CSR)
+//   cells: per-replica grids of side >= max(rc, rc_w) + skin, at least 3 across x and y.
+// A list entry packs the neighbour index (low 26 bits) and the neighbour's cell offset relative to
+// the molecule's home cell, 2 bits per axis (value + 1), in bits 26-31.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdk {
+
+// 32-byte aligned FP64 vector: one 256-bit load/store per molecule record
+using dvec4 = double4_32a;
+__host__ __device__ inline dvec4 make_dvec4(double x, double y, double z, double w) {
+  return make_double4_32a(x, y, z, w);
+}
+
+constexpr uint32_t kIndexBits = 26;
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int kMaxIndex = (1 << kIndexBits) - 1;
+
+// sticky device status bits
+constexpr int kStatusOverflow = 1;
+constexpr int kStatusUnstable = 2;
+constexpr int kStatusTimeout = 4;
+
+struct RepDev {
+  double Lx, Ly, Lz, hx, hy, hz;
+  double T0, dt, lam_coef;          // lam_coef = n_th dt / tau_B
+  double slab_half;
+  double lcx, lcy, lcz;             // cell sides
+  double bin_width;
+  float lcxf, lcyf, lczf;
+  uint32_t hi_thr_x, hi_thr_y;      // high word of L/2: |d| above it needs the periodic image
+  int32_t n_th;
+  int32_t vap_off, n_vap;
+  int32_t wall_off, n_wall;
+  int32_t cell_off, ncx, ncy, ncz;
+  int32_t pore_off, n_pores;
+  int32_t group_off, n_groups;      // adsorbed counters / profile rows
+  int32_t n_bins;
+  int32_t prof_off;                 // first profile counter of this replica
+};
+
+struct PoreDev {
+  int32_t kind;
+  double cx, cy, r0, r1, r_cavity, width;
+};
+
+struct PotDev {
+  double rc2, rcw2;
+  double a12, b6, a12w, b6w;        // force:  F/r = inv2 * inv6 * (a12 * inv6 - b6)
+  double e12, e6, e12w, e6w;        // energy: U = inv6 * (e12 * inv6 - e6)
+  double ushift, ushift_w;
+  double inv_mass, mass;
+  double half_skin2;                // rebuild when a displacement^2 reaches this
+  double r_ads2;
+  float rc2f, rcw2f, rl2f;          // FP32 cutoffs and the (padded) list radius^2
+  float a12f, b6f, a12wf, b6wf, e12f, e6f, e12wf, e6wf;
+  int32_t cap_vv, cap_vw;
+};
+
+// Device pointers of one context (passed by value to kernels).
+struct Arrays {
+  dvec4 *pos, *vel, *frc, *pos_ref;
+  dvec4 *pos_alt, *vel_alt, *frc_alt;
+  float4* lpos;
+  int32_t *home, *id, *rep, *id_alt;
+  int32_t *cell_tmp, *slot_tmp, *perm_tmp;
+  uint32_t *nbr_vv, *nbr_vw;
+  int32_t *n_vv, *n_vw;
+  dvec4* wpos;
+  float4* wlpos;
+  int32_t* wstart;                  // n_cells + 1
+  int32_t *vcount, *vstart;         // n_cells, n_cells + 1
+  int32_t* scan_tiles;              // tile sums of the cell scan
+  const RepDev* reps;
+  const PoreDev* pores;
+  // per-replica / global scalars
+  double* lambda;                   // per replica
+  int32_t* any_scale;
+  long long* step;
+  unsigned long long* max_disp2;    // bit pattern of a non-negative double
+  int32_t* force_rebuild;
+  int32_t* status;
+  unsigned long long* n_rebuilds;
+  unsigned long long* pair_count;   // pairs within cutoff, summed over steps (whole context)
+  int32_t *max_nvv, *max_nvw;
+  // observables (per molecule, then per replica)
+  double *pe_i, *pevw_i, *vir_i, *virw_i, *d2w_i;
+  int32_t *cnt_vv_i, *cnt_vw_i;
+  unsigned long long *occ, *ads, *prof;  // per pore, per group, per group*bin
+  double* rep_sums;                 // per replica: ke, pe_vv, pe_vw, vir_vv, vir_vw, pairs_vv, pairs_vw
+  int32_t n_total, n_wall_total, n_cells, n_reps;
+};
+
+struct Tuning {
+  int force_block = 128;
+  int force_tpp = 1;
+  int list_block = 128;
+};
+
+// carve predicate of a pore at offset (dx, dy) from its axis and height z (slab half-thickness h)
+__host__ __device__ inline bool in_pore(int kind, double r0, double r1, double rcav, double width,
+                                        double dx, double dy, double z, double h) {
+  double rxy2 = dx * dx + dy * dy;
+  switch (kind) {
+    case 1: return rxy2 < r0 * r0;
+    case 2: return sqrt(rxy2) < r0 + (r1 - r0) * (z + h) / (2.0 * h);
+    case 3: return fabs(dy) < 0.5 * width;
+    case 4: return rxy2 < r0 * r0 || rxy2 + z * z < rcav * rcav;
+    default: return false;
+  }
+}
+
+__host__ __device__ inline int cell_coord(double u, double half, double l, int nc) {
+  int c = (int)floor((u + half) / l);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// ---- launchers (md_kernels.cu); all enqueue on `s` and never synchronise
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, cudaStream_t s);
+void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, const int32_t* cell_rep,
+                    cudaStream_t s);
+void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, const Tuning& t,
+                   cudaStream_t s);
+void launch_integrate_second(const Arrays& a, const PotDev& p, cudaStream_t s);
+void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);
+void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s);
+int kernels_per_step();
+int kernels_per_rebuild();
+
+}  // namespace mdk

@@ -1,0 +1,106 @@
+"""The C-ABI library: builds, loads, exports every entry point declared in include/md.h, and the
+Python binding's struct layouts match the C compiler's. CPU only (no kernel is launched)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1812_07993_gb300 as md
+from paper_1812_07993_gb300 import build as mdbuild
+from paper_1812_07993_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "md.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mdbuild.build()
+    return md.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(md_\w+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", md.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(md_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+    assert set(md._SIGNATURES) == set(names)
+
+
+def test_struct_layout_matches_c(tmp_path):
+    structs = {"md_pore": md.md_pore, "md_system": md.md_system, "md_potential": md.md_potential,
+               "md_tuning": md.md_tuning, "md_obs": md.md_obs}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "md.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.md_status_string(s)
+    assert lib.md_status_string(99) == b"unknown status"
+
+
+def small_system(**kw):
+    s = W.make_system("t", 12.0, 12.0, 20.0, 3.0, [W.Pore(W.PORE_CYLINDER, r0=3.0)], 20, 1.0, 1)
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+@pytest.mark.parametrize("change,fragment", [
+    (dict(Lx=7.0), "3 cells"),
+    (dict(dt=0.0), "dt"),
+    (dict(thermostat_every=10, tau_B=0.01), "tau_B"),
+    (dict(x0=np.array([[100.0, 0.0, 0.0]] * 20)), "outside the box"),
+])
+def test_invalid_systems_rejected_before_any_gpu_work(lib, change, fragment):
+    s = small_system(**change)
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s)
+    assert ei.value.status == md.MD_EINVAL
+    assert fragment in str(ei.value)
+
+
+def test_invalid_potential_rejected(lib):
+    s = small_system()
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s, W.Potential(r_ads=3.0))
+    assert ei.value.status == md.MD_EINVAL and "r_ads" in str(ei.value)
+    with pytest.raises(md.MDError):
+        md.Simulation(s, W.Potential(sigma=0.0))
+
+
+def test_unknown_pore_kind_rejected(lib):
+    s = small_system(pores=[W.Pore(9, r0=1.0)])
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s, generate_wall=True)
+    assert ei.value.status == md.MD_EINVAL

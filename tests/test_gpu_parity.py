@@ -1,0 +1,297 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle on identical seeded inputs.
+
+Tolerances (FP64 path): per-step forces max_i |F_gpu - F_oracle| / RMS(F) <= 1e-10; 10-step
+trajectories |dr|, |dv| <= 1e-8; energies relative 1e-10; integer observables (pair counts,
+occupancy, adsorbed counts, density profiles) exactly equal. Mixed path: RMS force error
+sqrt(sum |dF|^2 / sum |F|^2) <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1812_07993_gb300 as md
+from paper_1812_07993_gb300 import build as mdbuild
+from paper_1812_07993_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POT = W.Potential()
+FORCE_TOL = 1e-10
+TRAJ_TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mdbuild.build()
+    md.load_library()
+
+
+def oracle_params(s, pot=POT, **over):
+    return oracle.make_params(s, pot, **over)
+
+
+def force_err(f, g):
+    rms = np.sqrt((g ** 2).sum(1).mean())
+    return np.abs(f - g).max() / rms
+
+
+def rms_rel_err(f, g):
+    return np.sqrt(((f - g) ** 2).sum() / (g ** 2).sum())
+
+
+def wrapped_diff(a, b, s):
+    d = a - b
+    d[:, 0] -= s.Lx * np.round(d[:, 0] / s.Lx)
+    d[:, 1] -= s.Ly * np.round(d[:, 1] / s.Ly)
+    return d
+
+
+def check_observables(sim, r, s, st, pot=POT):
+    o, occ, ads, prof = sim.observables(r)
+    p = oracle_params(s, pot)
+    f, d2, stats = oracle.forces(p, st.x, st.wall, method=1)
+    occ_o, ads_o, prof_o = oracle.observables(p, s.pores, st.x, d2)
+    assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+    np.testing.assert_array_equal(occ, occ_o)
+    np.testing.assert_array_equal(ads, ads_o)
+    np.testing.assert_array_equal(prof, prof_o)
+    pe_o = stats["pe_vv"] + stats["pe_vw"]
+    assert o["pe"] == pytest.approx(pe_o, rel=1e-10, abs=1e-10)
+    assert o["pe_vw"] == pytest.approx(stats["pe_vw"], rel=1e-10, abs=1e-10)
+    assert o["virial_vv"] == pytest.approx(stats["vir_vv"], rel=1e-10, abs=1e-10)
+    assert o["virial_vw"] == pytest.approx(stats["vir_vw"], rel=1e-10, abs=1e-10)
+    assert o["ke"] == pytest.approx(oracle.kinetic(p, st.v), rel=1e-12)
+    return o
+
+
+# ------------------------------------------------------------------------------------------ FP64
+
+
+def test_initial_forces_small_cylinder():
+    s = W.cylinder_pore_1k()
+    with md.Simulation(s) as sim:
+        f = sim.forces()
+    g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+    assert force_err(f, g) <= FORCE_TOL
+
+
+def test_ten_step_trajectory_small_cylinder_with_thermostat():
+    s = W.cylinder_pore_1k()
+    st = oracle.State(oracle_params(s), s.x0, s.v0, s.wall)
+    with md.Simulation(s) as sim:
+        sim.step(10)                     # the thermostat acts on step 10
+        x, v = sim.state()
+        f = sim.forces()
+        st.run(10)
+        assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL
+        assert np.abs(v - st.v).max() <= TRAJ_TOL
+        assert force_err(f, st.f) <= 1e-8
+        o = check_observables(sim, 0, s, st)
+        assert o["step"] == 10
+
+
+def test_per_step_energy_record_small_cylinder():
+    s = W.cylinder_pore_1k()
+    st = oracle.State(oracle_params(s), s.x0, s.v0, s.wall)
+    with md.Simulation(s) as sim:
+        for k in range(12):
+            sim.step(1)
+            ke, pe = st.run(1)
+            o, *_ = sim.observables()
+            assert o["pe"] == pytest.approx(pe[0], rel=1e-9)
+            # the library reports after the thermostat, the oracle log before it
+            if (k + 1) % 10:
+                assert o["ke"] == pytest.approx(ke[0], rel=1e-9)
+
+
+@pytest.fixture(scope="module")
+def shapes():
+    return W.pore_shape_systems_20k()
+
+
+def test_four_pore_shapes_batched_forces(shapes):
+    with md.Simulation(shapes) as sim:
+        for r, s in enumerate(shapes):
+            g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            assert force_err(sim.forces(r), g) <= FORCE_TOL, s.name
+
+
+def test_four_pore_shapes_batched_trajectory_and_observables(shapes):
+    states = [oracle.State(oracle_params(s), s.x0, s.v0, s.wall) for s in shapes]
+    with md.Simulation(shapes) as sim:
+        sim.step(10)
+        for r, (s, st) in enumerate(zip(shapes, states)):
+            st.run(10)
+            x, v = sim.state(r)
+            assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL, s.name
+            assert np.abs(v - st.v).max() <= TRAJ_TOL, s.name
+            check_observables(sim, r, s, st)
+
+
+def test_generated_wall_matches_generator(shapes):
+    with md.Simulation(shapes, generate_wall=True) as sim:
+        for r, s in enumerate(shapes):
+            w = sim.wall(r)
+            a = w[np.lexsort(w.T[::-1])]
+            b = s.wall[np.lexsort(s.wall.T[::-1])]
+            np.testing.assert_array_equal(a, b)
+
+
+def test_graph_replay_is_bitwise_identical_to_plain_launches():
+    s = W.cylinder_pore_1k()
+    with md.Simulation(s) as a, md.Simulation(s) as b:
+        b.set_tuning(use_graph=1, steps_per_graph=5)
+        a.step(23)
+        b.step(23)
+        xa, va = a.state()
+        xb, vb = b.state()
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+
+
+def test_runs_are_deterministic():
+    s = W.cylinder_pore_1k()
+    out = []
+    for _ in range(2):
+        with md.Simulation(s) as sim:
+            sim.step(60)
+            out.append(sim.state())
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_set_state_round_trip_and_restart_parity():
+    s = W.cylinder_pore_1k()
+    with md.Simulation(s) as sim:
+        sim.step(7)
+        x, v = sim.state()
+        sim.set_state(0, x, v)
+        x2, v2 = sim.state()
+        np.testing.assert_array_equal(x, x2)
+        np.testing.assert_array_equal(v, v2)
+        st = oracle.State(oracle_params(s), x, v, s.wall)
+        st.step = 7
+        sim.step(6)
+        st.run(6)
+        x3, v3 = sim.state()
+        assert np.abs(wrapped_diff(x3, st.x, s)).max() <= TRAJ_TOL
+
+
+def place_on(s, axis, value):
+    """Move some molecule onto the plane x[axis] = value without creating a close pair."""
+    for i in range(s.n_vapor):
+        c = s.x0[i].copy()
+        c[axis] = value
+        d = s.x0 - c
+        d[:, 0] -= s.Lx * np.round(d[:, 0] / s.Lx)
+        d[:, 1] -= s.Ly * np.round(d[:, 1] / s.Ly)
+        r = np.sqrt((d ** 2).sum(1))
+        r[i] = np.inf
+        if r.min() > 0.9:
+            s.x0[i] = c
+            return i
+    raise AssertionError("no molecule could be placed")
+
+
+def test_edge_cases_batch_empty_single_and_wall_free():
+    s_norm = W.make_system("a", 12.0, 12.0, 20.0, 3.0, [W.Pore(W.PORE_SLIT, width=3.0)], 300, 1.0, 5)
+    s_empty = W.make_system("b", 9.0, 9.0, 12.0, 2.0, [W.Pore(W.PORE_CYLINDER, r0=2.0)], 0, 1.0, 6)
+    s_one = W.make_system("c", 9.0, 9.0, 12.0, 2.0, [W.Pore(W.PORE_INKBOTTLE, r0=1.5, r_cavity=1.9)],
+                          1, 1.0, 7)
+    s_free = W.vapor_only_box(400, 10.0, 14.0, 1.2, seed=8)
+    # molecules exactly on cell faces and on the periodic edge of the wall-free box
+    place_on(s_free, 0, -5.0)
+    place_on(s_free, 1, -5.0 + 10.0 / 3.0)
+    systems = [s_norm, s_empty, s_one, s_free]
+    states = [oracle.State(oracle_params(s), s.x0, s.v0, s.wall) for s in systems]
+    with md.Simulation(systems) as sim:
+        for r, (s, st) in enumerate(zip(systems, states)):
+            if s.n_vapor:
+                assert force_err(sim.forces(r), st.f) <= FORCE_TOL or np.abs(st.f).max() == 0
+        sim.step(15)
+        for r, (s, st) in enumerate(zip(systems, states)):
+            st.run(15)
+            x, v = sim.state(r)
+            assert x.shape == (s.n_vapor, 3)
+            if s.n_vapor:
+                assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL, s.name
+                assert np.abs(v - st.v).max() <= TRAJ_TOL, s.name
+            o, occ, ads, prof = sim.observables(r)
+            assert prof.sum() == s.n_vapor
+
+
+def test_list_overflow_is_reported():
+    s = W.cylinder_pore_1k()
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s, max_neighbors=2)
+    assert ei.value.status == md.MD_EOVERFLOW
+
+
+def test_unstable_motion_is_reported_and_sticky():
+    s = W.make_system("u", 12.0, 12.0, 20.0, 3.0, [W.Pore(W.PORE_CYLINDER, r0=3.0)], 10, 1.0, 1)
+    s.x0[0] = [0.0, 0.0, 8.0]
+    s.x0[1] = [0.3, 0.0, 8.0]                            # nearly overlapping pair
+    with md.Simulation(s) as sim:
+        sim.step(2)
+        with pytest.raises(md.MDError) as ei:
+            sim.sync()
+        assert ei.value.status == md.MD_EUNSTABLE
+        with pytest.raises(md.MDError):
+            sim.step(1)
+
+
+def test_rebuilds_happen_and_lists_stay_complete():
+    """A long run: the device-decided rebuilds keep forces exact against a fresh oracle evaluation."""
+    s = W.cylinder_pore_1k()
+    with md.Simulation(s) as sim:
+        sim.step(400)
+        x, _ = sim.state()
+        f = sim.forces()
+        o, *_ = sim.observables()
+    assert o["n_rebuilds"] > 3
+    g, _, stats = oracle.forces(oracle_params(s), x, s.wall, method=1)
+    assert force_err(f, g) <= FORCE_TOL
+    assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+
+
+# ------------------------------------------------------------------------------------------ mixed
+
+
+def test_mixed_precision_force_error_small_cylinder():
+    s = W.cylinder_pore_1k()
+    with md.Simulation(s, precision=md.MD_PREC_MIXED) as sim:
+        f = sim.forces()
+        g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+        assert rms_rel_err(f, g) <= 1e-5
+        st = oracle.State(oracle_params(s), s.x0, s.v0, s.wall)
+        errs = []
+        for _ in range(10):
+            sim.step(1)
+            st.run(1)
+            x, _ = sim.state()
+            g2, _, _ = oracle.forces(oracle_params(s), x, s.wall, method=1)
+            errs.append(rms_rel_err(sim.forces(), g2))
+        assert max(errs) <= 1e-5
+
+
+def test_mixed_precision_four_shapes(shapes):
+    with md.Simulation(shapes, precision=md.MD_PREC_MIXED) as sim:
+        for r, s in enumerate(shapes):
+            g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            assert rms_rel_err(sim.forces(r), g) <= 1e-5, s.name
+
+
+# ------------------------------------------------------------------------------------------ large
+
+
+@pytest.mark.parametrize("precision,tol", [(md.MD_PREC_FP64, FORCE_TOL), (md.MD_PREC_MIXED, 1e-5)])
+def test_large_cylinder_forces(precision, tol):
+    """200,000 molecules and ~1.33 M wall atoms: every force against the oracle."""
+    s = W.cylinder_pore_200k()
+    g, _, stats = oracle.forces(oracle_params(s), s.x0, s.wall, method=1, nthreads=0)
+    with md.Simulation(s, precision=precision) as sim:
+        f = sim.forces()
+        o, *_ = sim.observables()
+    err = force_err(f, g) if precision == md.MD_PREC_FP64 else rms_rel_err(f, g)
+    assert err <= tol
+    assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
