@@ -304,7 +304,10 @@ def run_ours(args):
     md.load_library()
     systems, wname = make_workload(args.small)
     nrep = len(systems)
-    stream = torch.cuda.current_stream()
+    # one non-default stream carries the library's work, the L2 flush and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     prec = md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED
 
