@@ -189,6 +189,27 @@ md_status md_get_forces(md_ctx* ctx, int32_t replica, double* f);
 md_status md_observables(md_ctx* ctx, int32_t replica, md_obs* out, int64_t* occupancy,
                          int64_t* adsorbed, int64_t* profile);
 
+/* FP64 forces that allocate no memory (the paper has no counterpart: it is a service for callers
+ * that cannot allocate device memory, such as an application whose own pool allocator already
+ * holds nearly all of it, so a cudaMalloc would fail, or a latency-critical host thread that must
+ * not meet the implicit device synchronisation of cudaFree).
+ * Computes f_i = sum of Lennard-Jones pair forces (same potential and cutoffs as the context path,
+ * eps/sigma/rc and eps_w/sigma_w/rc_w of *pot, FP64) on n_vapor molecules at d_x from each other
+ * and from n_wall fixed wall atoms at d_wall, in a box Lx x Ly x Lz centred at the origin
+ * (periodic x, y). d_x (3*n_vapor), d_wall (3*n_wall) and d_f (3*n_vapor) are caller-owned DEVICE
+ * arrays, xyz interleaved; positions must lie inside the box. Work is enqueued on `stream`
+ * (NULL = legacy default stream) and is asynchronous.
+ * Scratch: a fixed array of about 4 MB inside the library, reserved on every GPU that loads the
+ * library until the process exits. Limits: n_vapor + n_wall <= 262144 atoms and at most 65536
+ * cells of side >= max(rc, rc_w), with at least 3 cells across x and y; larger inputs return
+ * MD_EINVAL with the reason in err (err_len bytes, may be NULL). The first call on a device looks
+ * up the scratch address once (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture. All calls share the scratch and its contents persist between
+ * calls: calls whose GPU work overlaps (other streams, other host threads) race and must not. */
+md_status md_forces_noalloc(const md_potential* pot, double Lx, double Ly, double Lz,
+                            const double* d_x, int64_t n_vapor, const double* d_wall,
+                            int64_t n_wall, double* d_f, void* stream, char* err, int32_t err_len);
+
 /* Copy the wall atoms of a replica (3*n_wall doubles, as generated or given). */
 md_status md_get_wall(md_ctx* ctx, int32_t replica, double* wall_xyz);
 

@@ -102,6 +102,11 @@ _SIGNATURES = {
     "md_get_sizes": (ctypes.c_int, [_CTX, ctypes.c_int32, _I64P, _I64P,
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "md_kernel_launches": (ctypes.c_int64, [_CTX]),
+    "md_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(md_potential), ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
+                                         ctypes.c_int32]),
     "md_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "md_last_error": (ctypes.c_char_p, [_CTX]),
     "md_destroy": (None, [_CTX]),
