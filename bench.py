@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--roofline-launches", type=int, default=50)
-    ap.add_argument("--small", action="store_true",
-                    help="a 1,000-molecule system instead of the bench workload (profiling)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -75,10 +75,27 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def make_workload(small: bool):
+WORKLOADS = {
+    "pore_shapes_4x20k": WORKLOAD,
+    "cylinder_pore_1k": "20x20x40 box, slab |z|<5, cylinder r4, 1,000 vapour, T*=1.0",
+    "cylinder_pore_200k": "150x150x300 box, slab |z|<30, cylinder r10, 200,000 vapour, T*=0.9",
+    "replica_batch_256": ("256 replicas: shape uniform over cylinder/cone/slit/ink-bottle, R~U[2,10], "
+                          "N log-uniform [1k,50k], T*~U[0.8,1.2], density 0.02 outside |z|<8"),
+    "pore_array_2m": ("400x400x200 box, 4x4 pores (cylinder/cone/ink-bottle, R~U[4,10]) in slab "
+                      "|z|<20, 2,000,000 vapour, T*=0.85"),
+}
+
+
+def make_workload(name: str):
     from paper_1812_07993_gb300 import workloads as W
-    if small:
-        return [W.cylinder_pore_1k()], "cylinder_pore_1k"
+    if name == "cylinder_pore_1k":
+        return [W.cylinder_pore_1k()], name
+    if name == "cylinder_pore_200k":
+        return [W.cylinder_pore_200k()], name
+    if name == "replica_batch_256":
+        return W.replica_batch(256), name
+    if name == "pore_array_2m":
+        return [W.pore_array_2m()], name
     return W.pore_shape_systems_20k(), "pore_shapes_4x20k"
 
 
@@ -169,7 +186,7 @@ def run_reference(args):
         return 0
     import oracle
     from paper_1812_07993_gb300 import workloads as W
-    systems, wname = make_workload(args.small)
+    systems, wname = make_workload(args.workload)
     pot = W.Potential()
     states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1, nthreads=0)
               for s in systems]
@@ -190,7 +207,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "description": WORKLOAD, "replicas": len(systems)},
+            "config": {"workload": wname, "description": WORKLOADS[wname],
+                       "replicas": len(systems)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -229,7 +247,11 @@ def time_steps(sim, torch, stream, flush, steps):
 
 
 def measure_precision(md, systems, precision, args, torch, stream, flush):
+    from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
+    sim.tune_info = None
+    if not args.no_autotune:
+        sim.tune_info = autotune.tune(sim, trials=9, use_cache=False)
     sim.set_tuning(use_graph=1, steps_per_graph=1)
     for _ in range(args.warmup):
         flush.zero_()
@@ -302,7 +324,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     mdbuild.build()
     md.load_library()
-    systems, wname = make_workload(args.small)
+    systems, wname = make_workload(args.workload)
     nrep = len(systems)
     # one non-default stream carries the library's work, the L2 flush and the timing events
     stream = torch.cuda.Stream()
@@ -329,6 +351,7 @@ def run_ours(args):
     ms_per_step = ms_job / args.steps
     pairs_per_step = pairs / args.steps
 
+    sim_tune = sim.tune_info
     extra = {}
     if rank == 0:
         cur = current_pairs(sim, nrep)
@@ -371,7 +394,7 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": wname, "description": WORKLOAD, "replicas": nrep,
+                "config": {"workload": wname, "description": WORKLOADS[wname], "replicas": nrep,
                            "n_vapor": sum(s.n_vapor for s in systems),
                            "n_wall": sum(s.n_wall for s in systems),
                            "precision": args.precision,
@@ -381,7 +404,8 @@ def run_ours(args):
                 "replica_steps_per_s": nrep * 1e3 / ms_per_step,
                 "pairs_per_step": pairs_per_step,
                 "gpu_launches": launches,
-                "clocks": clocks.summary()}
+                "clocks": clocks.summary(),
+                "autotune": sim_tune}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:

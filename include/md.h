@@ -104,19 +104,21 @@ typedef struct {
                                          compensated accumulation and FP64 integration */
   double r_ads;                       /* adsorbed: nearest wall atom closer than r_ads (<= rc_w) */
   double bin_width;                   /* axial density-profile bin width */
-  int32_t max_neighbors;              /* per-molecule list capacity for vapour neighbours
-                                         (0 = default 160) */
-  int32_t max_wall_neighbors;         /* per-molecule list capacity for wall neighbours
-                                         (0 = default 224) */
+  int32_t max_neighbors;              /* vapour neighbours a molecule may hold (0 = default 160) */
+  int32_t max_wall_neighbors;         /* wall neighbours a molecule may hold (0 = default 224);
+                                         one list holds both, of max_neighbors +
+                                         max_wall_neighbors entries (at most 1023) */
 } md_potential;
 
-/* Launch-shape knobs chosen by the autotuner (all 0 = library defaults). */
+/* Launch-shape knobs (0 in a field = keep the current value). */
 typedef struct {
-  int32_t force_block;     /* threads per block of the pair-force kernel (multiple of 32) */
-  int32_t force_tpp;       /* threads cooperating on one molecule in the pair-force kernel: 1..8 */
-  int32_t list_block;      /* threads per block of the list build (multiple of 32) */
-  int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 0: plain launches */
-  int32_t steps_per_graph; /* MD steps captured per graph replay (0 = 10) */
+  int32_t force_block;     /* threads per block of the pair-force kernel: 128 or 256 */
+  int32_t force_blocks_per_sm; /* resident pair-kernel blocks per SM: the grid is SMs x this and
+                              warps fetch chunks of molecules dynamically (1..32) */
+  int32_t force_tpp;       /* lanes that split one molecule's neighbour list: 1, 2, 4 or 8 */
+  int32_t order_by_length; /* 1: process molecules longest list first; 2: in cell order */
+  int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 2: plain launches */
+  int32_t steps_per_graph; /* MD steps captured per graph replay */
 } md_tuning;
 
 typedef struct {
@@ -133,7 +135,8 @@ typedef struct {
   int64_t n_rebuilds;      /* neighbour-list builds since creation (whole context) */
   int64_t pair_evals_total;/* pairs within cutoff summed over every step run so far
                               (whole context: unique vapour-vapour + vapour-wall) */
-  int32_t max_nb_used, max_wall_nb_used; /* largest list lengths of the last build */
+  int32_t max_list_used;   /* longest neighbour list of any build so far (whole context) */
+  int32_t list_capacity;   /* max_neighbors + max_wall_neighbors */
 } md_obs;
 
 typedef struct md_ctx md_ctx; /* opaque, library-owned */
@@ -151,9 +154,19 @@ md_status md_create(const md_system* sys, const md_potential* pot, void* stream,
 md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md_potential* pot,
                           void* stream, md_ctx** out);
 
-/* Replace the launch-shape knobs (autotuner); takes effect at the next md_step. */
+/* Replace the launch-shape knobs; takes effect at the next launch. Changing order_by_length
+ * rebuilds the lists (synchronises). */
 md_status md_set_tuning(md_ctx* ctx, const md_tuning* t);
 md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
+
+/* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 2 and 8): time
+ * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
+ * force_tpp {1,2,4,8} x force_blocks_per_sm {1,2,4,8} x force_block {128,256} x order_by_length
+ * {on,off} -- with CUDA events on the context's stream (median of `trials` launches each, trials
+ * clamped to [3, 101]), then apply the fastest. Positions and velocities are unchanged; forces are
+ * recomputed at the same positions. *best and *best_us (either may be NULL) receive the chosen
+ * shape and its median time in microseconds. Synchronises. */
+md_status md_autotune(md_ctx* ctx, int32_t trials, md_tuning* best, double* best_us);
 
 /* Enqueue n velocity-Verlet steps for every replica (asynchronous). Returns a sticky device
  * status found by earlier work, if any, without waiting for the GPU. */
@@ -183,11 +196,16 @@ md_status md_transfer_bytes(const md_ctx* ctx, int64_t* h2d, int64_t* d2h);
 md_status md_get_forces(md_ctx* ctx, int32_t replica, double* f);
 
 /* Observables of one replica at the current state. Fills *out; when non-NULL the arrays receive
- * occupancy[n_pores], adsorbed[n_groups] and profile[n_groups * n_bins] (group-major).
- * A molecule belongs to the pore whose axis is nearest in xy (slits: |dy|); ties go to the lower
- * pore index. bins: floor((z + Lz/2)/bin_width), the last bin closed. Synchronises. */
+ * occupancy[n_pores], adsorbed[n_groups], profile[n_groups * n_bins] (group-major) and
+ * pore_pressure[n_pores]. A molecule belongs to the pore whose axis is nearest in xy (slits:
+ * |dy|); ties go to the lower pore index. bins: floor((z + Lz/2)/bin_width), the last bin closed.
+ * pore_pressure: the virial pressure of Sec. 2 in each pore,
+ *   P = (sum_i m v_i^2 + sum_i W_i) / (3 V),
+ * over the molecules inside the pore (the occupancy predicate), W_i = half of r_ij . F_ij of each
+ * vapour pair plus r_iw . F_iw of each wall pair of molecule i, V the volume of the pore's carved
+ * region inside the slab. The forces of the last step are not changed. Synchronises. */
 md_status md_observables(md_ctx* ctx, int32_t replica, md_obs* out, int64_t* occupancy,
-                         int64_t* adsorbed, int64_t* profile);
+                         int64_t* adsorbed, int64_t* profile, double* pore_pressure);
 
 /* FP64 forces that allocate no memory (the paper has no counterpart: it is a service for callers
  * that cannot allocate device memory, such as an application whose own pool allocator already
@@ -217,7 +235,8 @@ md_status md_get_wall(md_ctx* ctx, int32_t replica, double* wall_xyz);
 md_status md_get_sizes(const md_ctx* ctx, int32_t replica, int64_t* n_vapor, int64_t* n_wall,
                        int32_t* n_groups, int32_t* n_bins);
 
-/* Kernel launches the library issued since creation (graph replays count each node). */
+/* Kernels the library has launched since creation, counted on the device (kernels inside a
+ * graph's skipped conditional branches do not run and are not counted). Synchronises. */
 int64_t md_kernel_launches(const md_ctx* ctx);
 
 /* Human-readable text of a status, and the last error message of a context (never NULL);

@@ -66,6 +66,14 @@ def _load(path: str):
     L.orc_forces.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D, ctypes.c_int64, _D,
                              _D, _D, ctypes.POINTER(Stats), ctypes.c_int, ctypes.c_int]
     L.orc_forces.restype = ctypes.c_int
+    L.orc_forces_w.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D, ctypes.c_int64, _D,
+                               _D, _D, _D, ctypes.POINTER(Stats), ctypes.c_int, ctypes.c_int]
+    L.orc_forces_w.restype = ctypes.c_int
+    L.orc_pore_volume.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(PoreC)]
+    L.orc_pore_volume.restype = ctypes.c_double
+    L.orc_pore_pressure.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(PoreC), ctypes.c_int,
+                                    ctypes.c_int64, _D, _D, _D, _D]
+    L.orc_pore_pressure.restype = ctypes.c_int
     L.orc_kinetic.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D]
     L.orc_kinetic.restype = ctypes.c_double
     L.orc_run.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D, _D, _D, ctypes.c_int64,
@@ -233,3 +241,40 @@ def observables(p: Params, pores: Sequence, x, d2wall):
     if rc != 0:
         raise ValueError("oracle observables failed")
     return occ[:npores], ads, prof
+
+
+def _pores_c(pores):
+    arr = (PoreC * max(len(pores), 1))()
+    for k, q in enumerate(pores):
+        arr[k] = PoreC(q.kind, q.cx, q.cy, q.r0, q.r1, q.r_cavity, q.width)
+    return arr
+
+
+def molecule_virials(p: Params, x, wall=None, method: int = 1, nthreads: int = 1):
+    """Per-molecule virials W_i (half of each vapour pair's r.F plus each wall pair's r.F)."""
+    x = _c3(x)
+    w = _c3(wall if wall is not None else np.zeros((0, 3)))
+    n = len(x)
+    f = np.zeros((n, 3))
+    d2 = np.zeros(n)
+    wv = np.zeros(n)
+    st = Stats()
+    if lib().orc_forces_w(ctypes.byref(p), n, _dp(x), len(w), _dp(w), _dp(f), _dp(d2), _dp(wv),
+                          ctypes.byref(st), method, nthreads) != 0:
+        raise ValueError("oracle: cutoff must be below half the periodic box")
+    return wv
+
+
+def pore_volume(p: Params, pore) -> float:
+    arr = _pores_c([pore])
+    return lib().orc_pore_volume(ctypes.byref(p), arr)
+
+
+def pore_pressure(p: Params, pores, x, v, wvir):
+    """Virial pressure per pore (Sec. 2) from positions, velocities and molecule virials."""
+    x, v = _c3(x), _c3(v)
+    wv = np.ascontiguousarray(np.asarray(wvir, dtype=np.float64))
+    out = np.zeros(max(len(pores), 1))
+    lib().orc_pore_pressure(ctypes.byref(p), _pores_c(pores), len(pores), len(x), _dp(x), _dp(v),
+                            _dp(wv), _dp(out))
+    return out[:len(pores)]

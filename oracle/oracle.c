@@ -3,6 +3,7 @@
  * loaded by the tests, the smoke check and the benchmark's CPU legs, never by the CUDA library.
  * See oracle.h for what each function computes and which part of the paper it follows.
  */
+#define _GNU_SOURCE
 #include "oracle.h"
 
 #include <math.h>
@@ -41,6 +42,9 @@ typedef struct {
   double fx, fy, fz, pe_vv, pe_vw, vir_vv, vir_vw, d2w;
   int64_t nvv, nvw;
 } acc_t;
+
+int orc_forces_w(const orc_params* p, int64_t n, const double* x, int64_t nw, const double* w,
+                 double* f, double* d2wall, double* wvir, orc_stats* st, int method, int nthreads);
 
 static void acc_zero(acc_t* a) {
   memset(a, 0, sizeof(*a));
@@ -190,6 +194,11 @@ static void forces_cells(const orc_params* p, int64_t n, const double* x, int64_
 
 int orc_forces(const orc_params* p, int64_t n, const double* x, int64_t nw, const double* w,
                double* f, double* d2wall, orc_stats* st, int method, int nthreads) {
+  return orc_forces_w(p, n, x, nw, w, f, d2wall, NULL, st, method, nthreads);
+}
+
+int orc_forces_w(const orc_params* p, int64_t n, const double* x, int64_t nw, const double* w,
+                 double* f, double* d2wall, double* wvir, orc_stats* st, int method, int nthreads) {
   const double rcut = p->rc > p->rc_w ? p->rc : p->rc_w;
   if (!(rcut < 0.5 * p->Lx) || !(rcut < 0.5 * p->Ly)) return -1;
 #ifdef _OPENMP
@@ -211,6 +220,7 @@ int orc_forces(const orc_params* p, int64_t n, const double* x, int64_t nw, cons
     f[3 * i + 1] = acc[i].fy;
     f[3 * i + 2] = acc[i].fz;
     if (d2wall) d2wall[i] = acc[i].d2w;
+    if (wvir) wvir[i] = acc[i].vir_vv + acc[i].vir_vw;
     s.pe_vv += acc[i].pe_vv;
     s.pe_vw += acc[i].pe_vw;
     s.vir_vv += acc[i].vir_vv;
@@ -326,6 +336,52 @@ int orc_observables(const orc_params* p, const orc_pore* pores, int npores, int6
     if (b < 0) b = 0;
     if (b >= nb) b = nb - 1;
     profile[(int64_t)g * nbins + b] += 1;
+  }
+  return 0;
+}
+
+/* cross-section area of a pore's carved region at height z */
+static double pore_area(const orc_params* p, const orc_pore* q, double z) {
+  const double h = p->slab_half;
+  switch (q->kind) {
+    case 1: return M_PI * q->r0 * q->r0;
+    case 2: {
+      double R = q->r0 + (q->r1 - q->r0) * (z + h) / (2.0 * h);
+      return M_PI * R * R;
+    }
+    case 3: return q->width * p->Lx;
+    case 4: {
+      double c = q->r_cavity * q->r_cavity - z * z;
+      double n2 = q->r0 * q->r0;
+      return M_PI * (c > n2 ? c : n2);
+    }
+    default: return 0.0;
+  }
+}
+
+double orc_pore_volume(const orc_params* p, const orc_pore* q) {
+  const int m = 20000; /* even */
+  const double a = -p->slab_half, b = p->slab_half, step = (b - a) / m;
+  double s = pore_area(p, q, a) + pore_area(p, q, b);
+  for (int k = 1; k < m; ++k) s += (k % 2 ? 4.0 : 2.0) * pore_area(p, q, a + k * step);
+  return s * step / 3.0;
+}
+
+int orc_pore_pressure(const orc_params* p, const orc_pore* pores, int npores, int64_t n,
+                      const double* x, const double* v, const double* wvir, double* pressure) {
+  for (int q = 0; q < npores; ++q) {
+    double sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double zi = x[3 * i + 2];
+      if (!(fabs(zi) < p->slab_half)) continue;
+      double dx = min_image(x[3 * i] - pores[q].cx, p->Lx);
+      double dy = min_image(x[3 * i + 1] - pores[q].cy, p->Ly);
+      if (!in_pore(&pores[q], dx, dy, zi, p->slab_half)) continue;
+      sum += p->mass * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+      sum += wvir[i];
+    }
+    const double vol = orc_pore_volume(p, &pores[q]);
+    pressure[q] = vol > 0.0 ? sum / (3.0 * vol) : 0.0;
   }
   return 0;
 }

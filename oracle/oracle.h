@@ -67,6 +67,22 @@ void orc_lj(double r2, double eps, double sigma, double* f_over_r, double* u);
 int orc_forces(const orc_params* p, int64_t n, const double* x, int64_t nw, const double* w,
                double* f, double* d2wall, orc_stats* st, int method, int nthreads);
 
+/* As orc_forces, and when wvir != NULL also each molecule's virial (n values): half of
+ * r_ij . F_ij for every vapour pair plus r_iw . F_iw for every wall pair, so that the molecules'
+ * virials add up to the pair virial sum. */
+int orc_forces_w(const orc_params* p, int64_t n, const double* x, int64_t nw, const double* w,
+                 double* f, double* d2wall, double* wvir, orc_stats* st, int method, int nthreads);
+
+/* Volume of a pore's carved region inside the slab |z| < slab_half: the integral over z of the
+ * cross-section area (cylinder pi r0^2, cone pi R(z)^2, slit width * Lx, ink-bottle
+ * pi max(r0^2, r_cav^2 - z^2)), by composite Simpson quadrature on 20000 intervals. */
+double orc_pore_volume(const orc_params* p, const orc_pore* q);
+
+/* Virial pressure in each pore (Sec. 2): P_q = (sum m v_i^2 + sum W_i) / (3 V_q) over the molecules
+ * inside pore q (the occupancy predicate), W_i from orc_forces_w. */
+int orc_pore_pressure(const orc_params* p, const orc_pore* pores, int npores, int64_t n,
+                      const double* x, const double* v, const double* wvir, double* pressure);
+
 /* Kinetic energy 1/2 m sum v^2. */
 double orc_kinetic(const orc_params* p, int64_t n, const double* v);
 

@@ -57,9 +57,9 @@ class md_potential(ctypes.Structure):
 
 
 class md_tuning(ctypes.Structure):
-    _fields_ = [("force_block", ctypes.c_int32), ("force_tpp", ctypes.c_int32),
-                ("list_block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("steps_per_graph", ctypes.c_int32)]
+    _fields_ = [("force_block", ctypes.c_int32), ("force_blocks_per_sm", ctypes.c_int32),
+                ("force_tpp", ctypes.c_int32), ("order_by_length", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32)]
 
 
 class md_obs(ctypes.Structure):
@@ -71,7 +71,7 @@ class md_obs(ctypes.Structure):
                 ("occupancy", ctypes.c_int64), ("adsorbed", ctypes.c_int64),
                 ("n_groups", ctypes.c_int32), ("n_bins", ctypes.c_int32),
                 ("n_rebuilds", ctypes.c_int64), ("pair_evals_total", ctypes.c_int64),
-                ("max_nb_used", ctypes.c_int32), ("max_wall_nb_used", ctypes.c_int32)]
+                ("max_list_used", ctypes.c_int32), ("list_capacity", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,6 +88,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(md_potential), ctypes.c_void_p,
                                        ctypes.POINTER(_CTX)]),
     "md_set_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(md_tuning)]),
+    "md_autotune": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(md_tuning),
+                                   ctypes.POINTER(ctypes.c_double)]),
     "md_get_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(md_tuning)]),
     "md_step": (ctypes.c_int, [_CTX, ctypes.c_int64]),
     "md_sync": (ctypes.c_int, [_CTX]),
@@ -97,7 +99,7 @@ _SIGNATURES = {
     "md_compute_forces": (ctypes.c_int, [_CTX]),
     "md_transfer_bytes": (ctypes.c_int, [_CTX, _I64P, _I64P]),
     "md_observables": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(md_obs), _I64P, _I64P,
-                                      _I64P]),
+                                      _I64P, _DP]),
     "md_get_wall": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP]),
     "md_get_sizes": (ctypes.c_int, [_CTX, ctypes.c_int32, _I64P, _I64P,
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -260,22 +262,39 @@ class Simulation:
         return w
 
     def observables(self, r: int = 0):
-        """Return (dict of md_obs fields, occupancy[n_pores], adsorbed[n_groups],
-        profile[n_groups, n_bins])."""
+        """Return (dict of md_obs fields plus "pore_pressure" [n_pores], occupancy[n_pores],
+        adsorbed[n_groups], profile[n_groups, n_bins])."""
         nv, nw, ng, nb = self.sizes(r)
         npores = len(self.systems[r].pores)
         occ = np.zeros(max(npores, 1), dtype=np.int64)
         ads = np.zeros(ng, dtype=np.int64)
         prof = np.zeros((ng, nb), dtype=np.int64)
+        press = np.zeros(max(npores, 1))
         o = md_obs()
         _check(load_library().md_observables(self.ctx, r, ctypes.byref(o),
                                              occ.ctypes.data_as(_I64P), ads.ctypes.data_as(_I64P),
-                                             prof.ctypes.data_as(_I64P)), self.ctx)
-        return o.as_dict(), occ[:npores], ads, prof
+                                             prof.ctypes.data_as(_I64P),
+                                             press.ctypes.data_as(_DP)), self.ctx)
+        d = o.as_dict()
+        d["pore_pressure"] = press[:npores]
+        return d, occ[:npores], ads, prof
 
-    def set_tuning(self, force_block=0, force_tpp=0, list_block=0, use_graph=0, steps_per_graph=0):
-        t = md_tuning(force_block, force_tpp, list_block, use_graph, steps_per_graph)
+    def set_tuning(self, force_block=0, force_blocks_per_sm=0, force_tpp=0, order_by_length=0,
+                   use_graph=0, steps_per_graph=0):
+        """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
+        order_by_length: 1 longest list first, 2 cell order."""
+        t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
+                      steps_per_graph)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)
+
+    def autotune(self, trials: int = 15):
+        """Time every launch shape of the pair kernel and keep the fastest (md_autotune).
+        Returns (tuning dict, median microseconds)."""
+        t = md_tuning()
+        us = ctypes.c_double()
+        _check(load_library().md_autotune(self.ctx, trials, ctypes.byref(t), ctypes.byref(us)),
+               self.ctx)
+        return {k: getattr(t, k) for k, _ in t._fields_}, us.value
 
     def tuning(self):
         t = md_tuning()

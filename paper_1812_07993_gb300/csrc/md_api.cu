@@ -23,6 +23,7 @@ struct ReplicaHost {
 
 struct md_ctx {
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;       // captures the bodies of conditional graph nodes
   bool own_stream = false;
   Arrays a{};
   PotDev pot{};
@@ -31,17 +32,15 @@ struct md_ctx {
   int n_reps = 0;
   std::vector<RepDev> reps;
   std::vector<ReplicaHost> rh;
-  int32_t* cell_rep = nullptr;
   std::vector<void*> allocs;
   std::string err;
   int32_t* status_host = nullptr;   // pinned
   cudaEvent_t status_event = nullptr;
   bool status_pending = false;
   int last_status_bits = 0;
-  long long launches = 0;
   int64_t steps_done = 0;
   int64_t bytes_h2d = 0, bytes_d2h = 0;
-  int use_graph = 0, steps_per_graph = 10;
+  int use_graph = 1, steps_per_graph = 10;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_steps = 0;
   size_t prof_total = 0, groups_total = 0, pores_total = 0;
@@ -101,6 +100,9 @@ md_status validate_potential(md_ctx* c, const md_potential* p) {
     return fail(c, MD_EINVAL, "unknown precision");
   if (p->max_neighbors < 0 || p->max_wall_neighbors < 0)
     return fail(c, MD_EINVAL, "negative list capacity");
+  if ((p->max_neighbors > 0 ? p->max_neighbors : 160) +
+          (p->max_wall_neighbors > 0 ? p->max_wall_neighbors : 224) > kMaxCap)
+    return fail(c, MD_EINVAL, "max_neighbors + max_wall_neighbors must not exceed 1023");
   return MD_OK;
 }
 
@@ -143,6 +145,27 @@ md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
       return fail(c, MD_EINVAL, who + "wall atom " + std::to_string(i) + " outside the box");
   }
   return MD_OK;
+}
+
+// volume of a pore's carved region inside the slab |z| < h (closed forms)
+double pore_volume(const md_pore& q, double Lx, double h) {
+  const double pi = 3.14159265358979323846;
+  switch (q.kind) {
+    case MD_PORE_CYLINDER: return pi * q.r0 * q.r0 * 2.0 * h;
+    case MD_PORE_CONE: return pi / 3.0 * 2.0 * h * (q.r0 * q.r0 + q.r0 * q.r1 + q.r1 * q.r1);
+    case MD_PORE_SLIT: return q.width * Lx * 2.0 * h;
+    case MD_PORE_INKBOTTLE: {
+      // neck cylinder plus the part of the cavity sphere outside it, within the slab
+      double v = pi * q.r0 * q.r0 * 2.0 * h;
+      const double a2 = q.r_cavity * q.r_cavity - q.r0 * q.r0;
+      if (a2 > 0.0) {
+        const double zt = std::min(std::sqrt(a2), h);
+        v += 2.0 * pi * (a2 * zt - zt * zt * zt / 3.0);
+      }
+      return v;
+    }
+    default: return 0.0;
+  }
 }
 
 double min_img(double d, double L) {
@@ -213,11 +236,12 @@ md_status sync_status(md_ctx* c) {
   return MD_OK;
 }
 
+// One step with plain launches: the rebuild and thermostat kernels always launch and return at
+// once when the device decides they have nothing to do.
 void enqueue_step(md_ctx* c) {
-  launch_integrate_first(c->a, c->pot, c->mixed, c->stream);
-  launch_rebuild(c->a, c->pot, c->tun, c->cell_rep, c->stream);
-  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
-  launch_integrate_second(c->a, c->pot, c->stream);
+  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, c->stream);
+  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+  launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
   launch_thermostat(c->a, c->pot, c->stream);
 }
 
@@ -226,9 +250,8 @@ md_status rebuild_and_forces(md_ctx* c) {
   CUDA_TRY(c, cudaMemcpyAsync(c->a.force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
                               c->stream));
   c->bytes_h2d += sizeof(int);
-  launch_rebuild(c->a, c->pot, c->tun, c->cell_rep, c->stream);
-  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
-  c->launches += kernels_per_rebuild() + 1;
+  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+  launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   return sync_status(c);
 }
@@ -239,16 +262,72 @@ void destroy_graph(md_ctx* c) {
   c->graph_steps = 0;
 }
 
+// Append an IF node on `handle` to the graph being captured on c->stream and capture `body`
+// (launches on the given stream) into its body graph.
+template <typename Body>
+cudaError_t add_conditional(md_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle handle, Body body) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t bg = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(c->aux, bg, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  body(c->aux);
+  cudaGraph_t out = nullptr;
+  return cudaStreamEndCapture(c->aux, &out);
+}
+
+// Capture `steps` MD steps as one graph. The rebuild chain and the thermostat sit in conditional
+// nodes whose condition the last block of k_integrate_first sets, so steps without a rebuild or a
+// thermostat launch only the integrate and force kernels.
 md_status build_graph(md_ctx* c, int steps) {
   destroy_graph(c);
-  cudaGraph_t g = nullptr;
+  if (!c->aux) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
   CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < steps; ++k) enqueue_step(c);
-  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-  if (e != cudaSuccess) return fail(c, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->graph_exec, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(c, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  cudaError_t e = cudaSuccess;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+    StepConds sc;
+    sc.use = 1;
+    e = cudaGraphConditionalHandleCreate(&sc.rebuild, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+      e = cudaGraphConditionalHandleCreate(&sc.thermo, g, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) break;
+    launch_integrate_first(c->a, c->pot, c->mixed, sc, c->stream);
+    e = add_conditional(c, g, sc.rebuild, [&](cudaStream_t s) {
+      launch_rebuild(c->a, c->pot, c->tun, c->mixed, s);
+    });
+    if (e != cudaSuccess) break;
+    launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
+    e = add_conditional(c, g, sc.thermo, [&](cudaStream_t s) { launch_thermostat(c->a, c->pot, s); });
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (captured) cudaGraphDestroy(captured);
+    cudaGetLastError();
+    return fail(c, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&c->graph_exec, captured, 0);
+  cudaGraphDestroy(captured);
+  if (e != cudaSuccess)
+    return fail(c, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   c->graph_steps = steps;
   return MD_OK;
 }
@@ -313,8 +392,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   P.e6f = (float)P.e6;
   P.e12wf = (float)P.e12w;
   P.e6wf = (float)P.e6w;
-  P.cap_vv = pot->max_neighbors > 0 ? pot->max_neighbors : 160;
-  P.cap_vw = pot->max_wall_neighbors > 0 ? pot->max_wall_neighbors : 224;
+  P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
+  P.rc2f_hi = (float)(P.rc2 * (1.0 + 1e-5));
+  P.rcw2f_lo = (float)(P.rcw2 * (1.0 - 1e-5));
+  P.rcw2f_hi = (float)(P.rcw2 * (1.0 + 1e-5));
+  P.cap_v = pot->max_neighbors > 0 ? pot->max_neighbors : 160;
+  P.cap = P.cap_v + (pot->max_wall_neighbors > 0 ? pot->max_wall_neighbors : 224);
 
   // ---- replicas, walls, cells
   c->reps.resize(n_reps);
@@ -363,7 +446,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     R.prof_off = (int32_t)prof;
     for (int q = 0; q < s->n_pores; ++q) {
       const md_pore& Q = s->pores[q];
-      pores.push_back(PoreDev{Q.kind, Q.cx, Q.cy, Q.r0, Q.r1, Q.r_cavity, Q.width});
+      pores.push_back(PoreDev{Q.kind, Q.cx, Q.cy, Q.r0, Q.r1, Q.r_cavity, Q.width,
+                              pore_volume(Q, s->Lx, s->slab_half)});
     }
     n_tot += H.n_vap;
     nw_tot += H.n_wall;
@@ -371,9 +455,11 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     groups += H.n_groups;
     prof += (long long)H.n_groups * H.n_bins;
   }
-  if (n_tot > kMaxIndex || nw_tot > kMaxIndex)
-    return bail(fail(c, MD_EINVAL, "more than 2^26 - 1 molecules or wall atoms in one context"));
+  if (n_tot + nw_tot > kMaxIndex)
+    return bail(fail(c, MD_EINVAL, "more than 2^26 - 1 molecules plus wall atoms in one context"));
   if (ncell_tot > 4096LL * 4096LL) return bail(fail(c, MD_EINVAL, "too many cells"));
+  if (!c->mixed && (unsigned long long)n_tot * (unsigned long long)c->pot.cap_v >= 0xffffffffull)
+    return bail(fail(c, MD_EINVAL, "FP64 pair buffer: molecules * max_neighbors must stay below 2^32"));
   c->prof_total = (size_t)prof;
   c->groups_total = (size_t)groups;
   c->pores_total = pores.size();
@@ -419,6 +505,13 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     }
   }
 
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      c->tun.sm_count = sms;
+    cudaGetLastError();
+  }
   // ---- device memory
   Arrays& A = c->a;
   A.n_total = (int32_t)n_tot;
@@ -433,8 +526,16 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.lpos, N);
   ALLOC(A.home, N); ALLOC(A.id, N); ALLOC(A.rep, N); ALLOC(A.id_alt, N);
   ALLOC(A.cell_tmp, N); ALLOC(A.slot_tmp, N); ALLOC(A.perm_tmp, N);
-  ALLOC(A.nbr_vv, N * (size_t)P.cap_vv); ALLOC(A.nbr_vw, N * (size_t)P.cap_vw);
-  ALLOC(A.n_vv, N); ALLOC(A.n_vw, N);
+  ALLOC(A.nbr, N * (size_t)P.cap);
+  ALLOC(A.n_front, N); ALLOC(A.n_back, N); ALLOC(A.n_vh, N);
+  ALLOC(A.order, N);
+  ALLOC(A.hist, (size_t)kMaxCap + 2); ALLOC(A.hstart, (size_t)kMaxCap + 2);
+  ALLOC(A.work, 1); ALLOC(A.work_done, 1);
+  if (!c->mixed) {
+    ALLOC(A.fwd, N * (size_t)P.cap_v);
+    ALLOC(A.pairbuf, N * (size_t)P.cap_v + 1);
+    ALLOC(A.fpart, N);
+  }
   ALLOC(A.wpos, (size_t)nw_tot); ALLOC(A.wlpos, (size_t)nw_tot);
   ALLOC(A.wstart, (size_t)ncell_tot + 1);
   ALLOC(A.vcount, (size_t)ncell_tot); ALLOC(A.vstart, (size_t)ncell_tot + 1);
@@ -445,21 +546,37 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(pores_d, pores.size());
   A.reps = reps_d;
   A.pores = pores_d;
-  ALLOC(c->cell_rep, (size_t)ncell_tot);
+  int32_t* cell_rep_d = nullptr;
+  ALLOC(cell_rep_d, (size_t)ncell_tot);
+  A.cell_rep = cell_rep_d;
   ALLOC(A.lambda, (size_t)n_reps);
   ALLOC(A.any_scale, 1);
   ALLOC(A.step, 1);
-  ALLOC(A.max_disp2, 1);
   ALLOC(A.force_rebuild, 1);
   ALLOC(A.status, 1);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);
-  ALLOC(A.max_nvv, 1); ALLOC(A.max_nvw, 1);
+  ALLOC(A.max_nb, 1);
+  ALLOC(A.blk_done, 1);
+  ALLOC(A.launch_count, 1);
   ALLOC(A.pe_i, N); ALLOC(A.pevw_i, N); ALLOC(A.vir_i, N); ALLOC(A.virw_i, N); ALLOC(A.d2w_i, N);
   ALLOC(A.cnt_vv_i, N); ALLOC(A.cnt_vw_i, N);
   ALLOC(A.occ, std::max<size_t>(pores.size(), 1));
   ALLOC(A.ads, (size_t)groups);
   ALLOC(A.prof, (size_t)prof);
+  {
+    long long chunks = 1;
+    for (int r = 0; r < n_reps; ++r) chunks = std::max<long long>(chunks, (c->rh[r].n_vap + 1023) / 1024);
+    A.rep_chunks = (int32_t)chunks;
+  }
+  ALLOC(A.rep_part, (size_t)n_reps * A.rep_chunks * 8);
+  {
+    int mp = 1;
+    for (int r = 0; r < n_reps; ++r) mp = std::max(mp, (int)c->rh[r].n_pores);
+    A.max_pores = mp;
+  }
+  ALLOC(A.pore_part, (size_t)n_reps * A.rep_chunks * A.max_pores);
+  ALLOC(A.pore_press, std::max<size_t>(pores.size(), 1));
   ALLOC(A.rep_sums, (size_t)n_reps * 8);
 #undef ALLOC
   cudaError_t e = cudaMallocHost(&c->status_host, sizeof(int32_t));
@@ -494,7 +611,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = up(A.wpos, wpos.data(), wpos.size() * sizeof(dvec4))) != MD_OK) return bail(st);
   if ((st = up(A.wlpos, wlpos.data(), wlpos.size() * sizeof(float4))) != MD_OK) return bail(st);
   if ((st = up(A.wstart, wstart.data(), wstart.size() * sizeof(int32_t))) != MD_OK) return bail(st);
-  if ((st = up(c->cell_rep, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
+  if ((st = up(cell_rep_d, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
     return bail(st);
   if ((st = up(reps_d, c->reps.data(), c->reps.size() * sizeof(RepDev))) != MD_OK) return bail(st);
   if ((st = up(pores_d, pores.data(), pores.size() * sizeof(PoreDev))) != MD_OK) return bail(st);
@@ -540,34 +657,112 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (!c || !t) return MD_EINVAL;
   Tuning nt = c->tun;
   if (t->force_block) {
-    if (t->force_block % 32 || t->force_block < 32 || t->force_block > 1024)
-      return fail(c, MD_EINVAL, "force_block must be a multiple of 32 in [32, 1024]");
+    if (t->force_block != 128 && t->force_block != 256)
+      return fail(c, MD_EINVAL, "force_block must be 128 or 256");
     nt.force_block = t->force_block;
   }
+  if (t->force_blocks_per_sm) {
+    if (t->force_blocks_per_sm < 1 || t->force_blocks_per_sm > 32)
+      return fail(c, MD_EINVAL, "force_blocks_per_sm must be in [1, 32]");
+    if (c->mixed) nt.force_blocks_per_sm_mixed = t->force_blocks_per_sm;
+    else nt.force_blocks_per_sm_fp64 = t->force_blocks_per_sm;
+  }
   if (t->force_tpp) {
-    if (t->force_tpp != 1) return fail(c, MD_EINVAL, "force_tpp: only 1 is implemented");
-    nt.force_tpp = t->force_tpp;
+    if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8)
+      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4 or 8");
+    if (c->mixed) nt.tpp_mixed = t->force_tpp;
+    else nt.tpp_fp64 = t->force_tpp;
   }
-  if (t->list_block) {
-    if (t->list_block % 32 || t->list_block < 32 || t->list_block > 1024)
-      return fail(c, MD_EINVAL, "list_block must be a multiple of 32 in [32, 1024]");
-    nt.list_block = t->list_block;
-  }
+  if (t->order_by_length < 0 || t->order_by_length > 2)
+    return fail(c, MD_EINVAL, "order_by_length must be 0 (keep), 1 (on) or 2 (off)");
+  if (t->use_graph < 0 || t->use_graph > 2)
+    return fail(c, MD_EINVAL, "use_graph must be 0 (keep), 1 (graph) or 2 (plain launches)");
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
+  const bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
+  if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   c->tun = nt;
-  c->use_graph = t->use_graph ? 1 : 0;
-  c->steps_per_graph = t->steps_per_graph > 0 ? t->steps_per_graph : 10;
+  if (t->use_graph) c->use_graph = t->use_graph == 1 ? 1 : 0;
+  if (t->steps_per_graph) c->steps_per_graph = t->steps_per_graph;
   destroy_graph(c);
+  // the processing order is built with the lists: rebuild them now
+  if (relist) return rebuild_and_forces(c);
   return MD_OK;
 }
 
 md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   if (!c || !t) return MD_EINVAL;
   t->force_block = c->tun.force_block;
-  t->force_tpp = c->tun.force_tpp;
-  t->list_block = c->tun.list_block;
-  t->use_graph = c->use_graph;
+  t->force_blocks_per_sm = c->mixed ? c->tun.force_blocks_per_sm_mixed : c->tun.force_blocks_per_sm_fp64;
+  t->force_tpp = c->mixed ? c->tun.tpp_mixed : c->tun.tpp_fp64;
+  t->order_by_length = c->tun.lpt ? 1 : 2;
+  t->use_graph = c->use_graph ? 1 : 2;
   t->steps_per_graph = c->steps_per_graph;
+  return MD_OK;
+}
+
+md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_us) {
+  if (!c) return MD_EINVAL;
+  md_status s = sync_status(c);
+  if (s != MD_OK) return s;
+  trials = std::max(3, std::min(101, trials));
+  std::vector<cudaEvent_t> ev(2 * (size_t)trials);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto& f : ev) if (f) cudaEventDestroy(f);
+      return fail(c, MD_ECUDA, "cudaEventCreate");
+    }
+  const Tuning saved = c->tun;
+  Tuning bestT = saved;
+  double bestv = 1e300;
+  md_status st = MD_OK;
+  const int tpps[4] = {1, 2, 4, 8}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
+  for (int lpt = 1; lpt >= 0 && st == MD_OK; --lpt) {
+    c->tun = saved;
+    c->tun.lpt = lpt;
+    if ((st = rebuild_and_forces(c)) != MD_OK) break;
+    for (int tp : tpps)
+      for (int bp : bpss)
+        for (int bk : blocks) {
+          Tuning t = c->tun;
+          t.force_block = bk;
+          if (c->mixed) {
+            t.tpp_mixed = tp;
+            t.force_blocks_per_sm_mixed = bp;
+          } else {
+            t.tpp_fp64 = tp;
+            t.force_blocks_per_sm_fp64 = bp;
+          }
+          launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);  // warm-up
+          for (int k = 0; k < trials; ++k) {
+            cudaEventRecord(ev[2 * k], c->stream);
+            launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);
+            cudaEventRecord(ev[2 * k + 1], c->stream);
+          }
+          if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            st = fail(c, MD_ECUDA, "autotune launch failed");
+            break;
+          }
+          std::vector<float> ms(trials);
+          for (int k = 0; k < trials; ++k) cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]);
+          std::nth_element(ms.begin(), ms.begin() + trials / 2, ms.end());
+          const double us = 1e3 * ms[trials / 2];
+          if (us < bestv) {
+            bestv = us;
+            bestT = t;
+          }
+        }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != MD_OK) {
+    c->tun = saved;
+    return st;
+  }
+  c->tun = bestT;
+  destroy_graph(c);
+  // lists (and their processing order) for the chosen shape; forces at the same positions
+  if ((st = rebuild_and_forces(c)) != MD_OK) return st;
+  if (best) md_get_tuning(c, best);
+  if (best_us) *best_us = bestv;
   return MD_OK;
 }
 
@@ -590,13 +785,9 @@ md_status md_step(md_ctx* c, int64_t n) {
     while (left >= c->graph_steps) {
       CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
       left -= c->graph_steps;
-      c->launches += (long long)c->graph_steps * kernels_per_step();
     }
   }
-  for (int64_t k = 0; k < left; ++k) {
-    enqueue_step(c);
-    c->launches += kernels_per_step();
-  }
+  for (int64_t k = 0; k < left; ++k) enqueue_step(c);
   CUDA_TRY(c, cudaGetLastError());
   c->steps_done += n;
   if (!c->status_pending) {
@@ -688,7 +879,7 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
 }
 
 md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, int64_t* adsorbed,
-                         int64_t* profile) {
+                         int64_t* profile, double* pore_pressure) {
   if (!check_replica(c, r) || !out) return fail(c, MD_EINVAL, "bad replica or NULL output");
   md_status s = sync_status(c);
   if (s != MD_OK) return s;
@@ -696,29 +887,30 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   CUDA_TRY(c, cudaMemsetAsync(A.occ, 0, std::max<size_t>(c->pores_total, 1) * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.ads, 0, c->groups_total * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.prof, 0, std::max<size_t>(c->prof_total, 1) * 8, c->stream));
-  launch_forces(A, c->pot, c->mixed, true, c->tun, c->stream);
+  launch_forces(A, c->pot, c->mixed, true, false, c->tun, c->stream);
   launch_observables(A, c->pot, c->stream);
-  c->launches += 3;
   CUDA_TRY(c, cudaGetLastError());
   const RepDev& R = c->reps[r];
   const ReplicaHost& H = c->rh[r];
   double sums[8];
   unsigned long long nreb = 0, pc = 0;
   long long step = 0;
-  int32_t mv = 0, mw = 0;
+  int32_t mv = 0;
   std::vector<unsigned long long> occ(std::max(H.n_pores, 1)), ads(H.n_groups),
       prof((size_t)H.n_groups * H.n_bins);
   CUDA_TRY(c, cudaMemcpyAsync(sums, A.rep_sums + 8 * r, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&nreb, A.n_rebuilds, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&pc, A.pair_count, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&step, A.step, 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(&mv, A.max_nvv, 4, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(&mw, A.max_nvw, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&mv, A.max_nb, 4, cudaMemcpyDeviceToHost, c->stream));
   if (H.n_pores)
     CUDA_TRY(c, cudaMemcpyAsync(occ.data(), A.occ + R.pore_off, H.n_pores * 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(ads.data(), A.ads + R.group_off, H.n_groups * 8, cudaMemcpyDeviceToHost, c->stream));
   if (!prof.empty())
     CUDA_TRY(c, cudaMemcpyAsync(prof.data(), A.prof + R.prof_off, prof.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (pore_pressure && H.n_pores)
+    CUDA_TRY(c, cudaMemcpyAsync(pore_pressure, A.pore_press + R.pore_off, H.n_pores * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   std::memset(out, 0, sizeof(*out));
   out->step = step;
@@ -737,8 +929,8 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   out->n_bins = H.n_bins;
   out->n_rebuilds = (int64_t)nreb;
   out->pair_evals_total = (int64_t)(pc / 2);
-  out->max_nb_used = mv;
-  out->max_wall_nb_used = mw;
+  out->max_list_used = mv;
+  out->list_capacity = c->pot.cap;
   for (int q = 0; q < H.n_pores; ++q) {
     out->occupancy += (int64_t)occ[q];
     if (occupancy) occupancy[q] = (int64_t)occ[q];
@@ -756,8 +948,7 @@ md_status md_compute_forces(md_ctx* c) {
   if (!c) return MD_EINVAL;
   md_status prev = device_status(c);
   if (prev != MD_OK) return prev;
-  launch_forces(c->a, c->pot, c->mixed, false, c->tun, c->stream);
-  c->launches += 1;
+  launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   return MD_OK;
 }
@@ -787,7 +978,17 @@ md_status md_get_sizes(const md_ctx* c, int32_t r, int64_t* n_vapor, int64_t* n_
   return MD_OK;
 }
 
-int64_t md_kernel_launches(const md_ctx* c) { return c ? c->launches : 0; }
+int64_t md_kernel_launches(const md_ctx* c) {
+  if (!c || !c->a.launch_count) return 0;
+  unsigned long long n = 0;
+  if (cudaMemcpyAsync(&n, c->a.launch_count, sizeof(n), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (int64_t)n;
+}
 
 void md_destroy(md_ctx* c) {
   if (!c) return;
@@ -797,6 +998,7 @@ void md_destroy(md_ctx* c) {
   if (c->status_host) cudaFreeHost(c->status_host);
   if (c->status_event) cudaEventDestroy(c->status_event);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
 }
 

@@ -3,17 +3,27 @@
 //
 // Layout in HBM (all replicas of a context packed back to back):
 //   vapour, in cell-sorted order (re-sorted at every list build):
-//     pos, vel, frc   dvec4 (x, y, z, unused)  32 B each per molecule
-//     pos_ref         dvec4, positions at the last list build (skin check)
+//     pos, vel, frc   32-byte aligned double4 (x, y, z, unused): one 256-bit access per molecule
+//     pos_ref         positions at the last list build (skin check)
 //     lpos            float4, position relative to the centre of the home cell (FP32 staging for the
 //                     list build and the mixed-precision pair kernel)
-//     home, id, rep   int32: home cell (global id), caller index within the replica, replica
-//     nbr_vv, nbr_vw  uint32 Verlet lists, column-major [slot * n_total + molecule]
-//     n_vv, n_vw      int32 list lengths
-//   wall (static, sorted by cell once at creation): wpos dvec4, wlpos float4, wstart (CSR)
+//     home, id, rep   int32: home cell (packed ix | iy << 10 | iz << 20), caller index within the
+//                     replica, replica
+//     nbr             Verlet list, one row of `cap` slots per molecule: partners j > i then wall
+//                     atoms from the front (vapour first), partners j < i from the back;
+//                     n_front / n_back / n_vh give the lengths (n_vh: vapour part of the front)
+//     order           optional processing order: molecules sorted by list length, longest first
+//   FP64 pair path (Newton's third law, deterministic):
+//     fwd             for each front vapour slot of a molecule, the pairbuf entry
+//                     partner * cap_v + (its back slot) that receives the pair force
+//     pairbuf         forces of the pairs held by lower partners, [molecule * cap_v + back slot],
+//                     plus one spare entry at the end
+//     fpart           partial force of the half-list pass
+//   wall (static, sorted by cell once at creation): wpos double4, wlpos float4, wstart (CSR)
 //   cells: per-replica grids of side >= max(rc, rc_w) + skin, at least 3 across x and y.
-// A list entry packs the neighbour index (low 26 bits) and the neighbour's cell offset relative to
-// the molecule's home cell, 2 bits per axis (value + 1), in bits 26-31.
+// A list entry packs the neighbour index in the low 26 bits -- a vapour molecule below n_total, a
+// wall atom at n_total + its index -- and the neighbour's home-cell offset relative to the
+// molecule's home cell, 2 bits per axis (value + 1), in bits 26-31.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,6 +39,7 @@ __host__ __device__ inline dvec4 make_dvec4(double x, double y, double z, double
 constexpr uint32_t kIndexBits = 26;
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kMaxIndex = (1 << kIndexBits) - 1;
+constexpr int kMaxCap = 1023;  // longest list (vapour + wall neighbours) a molecule may hold
 
 // sticky device status bits
 constexpr int kStatusOverflow = 1;
@@ -56,6 +67,7 @@ struct RepDev {
 struct PoreDev {
   int32_t kind;
   double cx, cy, r0, r1, r_cavity, width;
+  double vol;                       // volume of the carved region inside the slab
 };
 
 struct PotDev {
@@ -67,8 +79,10 @@ struct PotDev {
   double half_skin2;                // rebuild when a displacement^2 reaches this
   double r_ads2;
   float rc2f, rcw2f, rl2f;          // FP32 cutoffs and the (padded) list radius^2
+  float rc2f_lo, rc2f_hi, rcw2f_lo, rcw2f_hi;  // FP32 band around the cutoff decided in FP64
   float a12f, b6f, a12wf, b6wf, e12f, e6f, e12wf, e6wf;
-  int32_t cap_vv, cap_vw;
+  int32_t cap;                      // list capacity per molecule (vapour + wall)
+  int32_t cap_v;                    // vapour half-pair / reverse capacity per molecule
 };
 
 // Device pointers of one context (passed by value to kernels).
@@ -78,37 +92,56 @@ struct Arrays {
   float4* lpos;
   int32_t *home, *id, *rep, *id_alt;
   int32_t *cell_tmp, *slot_tmp, *perm_tmp;
-  uint32_t *nbr_vv, *nbr_vw;
-  int32_t *n_vv, *n_vw;
+  uint32_t* nbr;                    // [molecule * cap + slot]: front (j > i, walls), back (j < i)
+  int32_t *n_front, *n_back, *n_vh; // front / back lengths; vapour entries at the front
+  // optional processing order (longest list first)
+  int32_t *order, *hist, *hstart;
+  int32_t* work;                    // next chunk of the pair kernel
+  unsigned int* work_done;          // blocks of the pair kernel that finished
+  // FP64 half-list path
+  uint32_t* fwd;                    // [molecule * cap_v + front slot]: pairbuf entry of the pair
+  dvec4 *pairbuf, *fpart;           // pairbuf [molecule * cap_v + back slot] (+1 spare)
+  // wall and cells
   dvec4* wpos;
   float4* wlpos;
   int32_t* wstart;                  // n_cells + 1
   int32_t *vcount, *vstart;         // n_cells, n_cells + 1
   int32_t* scan_tiles;              // tile sums of the cell scan
+  const int32_t* cell_rep;          // replica of each cell
   const RepDev* reps;
   const PoreDev* pores;
   // per-replica / global scalars
   double* lambda;                   // per replica
   int32_t* any_scale;
   long long* step;
-  unsigned long long* max_disp2;    // bit pattern of a non-negative double
-  int32_t* force_rebuild;
+  int32_t* force_rebuild;           // set by the host or by a molecule past skin/2; cleared by the pair kernel
   int32_t* status;
+  unsigned int* blk_done;           // last-block detection in k_integrate_first
   unsigned long long* n_rebuilds;
-  unsigned long long* pair_count;   // pairs within cutoff, summed over steps (whole context)
-  int32_t *max_nvv, *max_nvw;
+  unsigned long long* pair_count;   // 2 x pairs within cutoff, summed over steps (whole context)
+  unsigned long long* launch_count; // kernels launched by the library
+  int32_t* max_nb;
   // observables (per molecule, then per replica)
   double *pe_i, *pevw_i, *vir_i, *virw_i, *d2w_i;
   int32_t *cnt_vv_i, *cnt_vw_i;
   unsigned long long *occ, *ads, *prof;  // per pore, per group, per group*bin
+  double* rep_part;                 // per (replica, chunk) partial sums, 8 each
   double* rep_sums;                 // per replica: ke, pe_vv, pe_vw, vir_vv, vir_vw, pairs_vv, pairs_vw
+  double *pore_part, *pore_press;   // per (replica, chunk, pore) partials; per pore pressure
+  int32_t max_pores;                // most pores of any replica (>= 1)
   int32_t n_total, n_wall_total, n_cells, n_reps;
+  int32_t rep_chunks;               // partial-sum chunks per replica
 };
 
 struct Tuning {
-  int force_block = 128;
-  int force_tpp = 1;
-  int list_block = 128;
+  int force_block = 256;
+  int force_blocks_per_sm_fp64 = 1;   // resident blocks per SM of the pair kernels (grid size)
+  int force_blocks_per_sm_mixed = 4;
+  int tpp_fp64 = 2;                   // lanes sharing one molecule's list in the pair kernels
+  int tpp_mixed = 4;
+  int gather_tpp = 2;                 // lanes per molecule in the FP64 reverse gather
+  int lpt = 1;                        // process molecules longest list first
+  int sm_count = 152;
 };
 
 // carve predicate of a pore at offset (dx, dy) from its axis and height z (slab half-thickness h)
@@ -129,16 +162,22 @@ __host__ __device__ inline int cell_coord(double u, double half, double l, int n
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// Conditional-node handles of one captured step (unused when launched outside a graph).
+struct StepConds {
+  cudaGraphConditionalHandle rebuild = 0, thermo = 0;
+  int use = 0;
+};
+
 // ---- launchers (md_kernels.cu); all enqueue on `s` and never synchronise
-void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, cudaStream_t s);
-void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, const int32_t* cell_rep,
-                    cudaStream_t s);
-void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, const Tuning& t,
-                   cudaStream_t s);
-void launch_integrate_second(const Arrays& a, const PotDev& p, cudaStream_t s);
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
+                            cudaStream_t s);
+void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
+// pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
+// second half-kick (Fig. 3), otherwise the gather only writes the forces
+void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
+                   const Tuning& t, cudaStream_t s);
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s);
-int kernels_per_step();
-int kernels_per_rebuild();
+int rebuild_kernel_count(bool mixed);
 
 }  // namespace mdk

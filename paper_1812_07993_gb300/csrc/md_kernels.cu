@@ -1,15 +1,19 @@
 // md_kernels.cu -- CUDA kernels (sm_103a) of the pore / water-vapour MD step.
 //
 // One MD step (Sec. 2 velocity Verlet, Figs. 1-4 of arXiv:1812.07993), all replicas per launch:
-//   k_integrate_first   half-kick + drift (Fig. 2), z reflection, x/y wrap, displacement max
-//   rebuild chain       only when a molecule moved >= skin/2 since the last build (decided on
-//                       the device; the kernels return at once otherwise):
+//   k_integrate_first   half-kick + drift (Fig. 2), z reflection, x/y wrap, skin check; its
+//                       last block decides whether the lists are rebuilt and whether the
+//                       thermostat acts (CUDA-graph conditional nodes)
+//   rebuild chain       only when a molecule moved >= skin/2 since the last build:
 //                         k_cell_count -> k_scan_* -> k_scatter -> k_permute -> k_copyback ->
-//                         k_list_build (warp per cell)
-//   k_forces_*          Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) from the Verlet lists
-//   k_integrate_second  half-kick (Fig. 3)
-//   k_thermo_reduce / k_thermo_scale   Berendsen scaling on thermostat steps (Fig. 4)
-// None of these kernels spins or waits on another block.
+//                         k_list_build (warp per cell) [-> FP64 half-list preparation]
+//   pair forces         Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) and the second half-kick
+//                       (Fig. 3): FP64 half list + reverse gather with the kick fused into the
+//                       gather, or mixed precision on the full list with the kick fused in
+//   k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on thermostat steps
+//                       (Fig. 4)
+// No kernel spins or waits on another block.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -21,13 +25,18 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ void count_launch(const Arrays& a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.launch_count, 1ull);
+}
+
 __device__ __forceinline__ bool halted(const Arrays& a) {
   return *reinterpret_cast<volatile const int32_t*>(a.status) != 0;
 }
 
+// lists are rebuilt when the host asks for it or when some molecule has moved at least skin/2
+// since the last build (k_integrate_first raises the same flag); the pair kernel clears it
 __device__ __forceinline__ bool need_rebuild(const Arrays& a, const PotDev& p) {
-  if (*a.force_rebuild) return true;
-  return __longlong_as_double((long long)*a.max_disp2) >= p.half_skin2;
+  return *reinterpret_cast<volatile const int32_t*>(a.force_rebuild) != 0;
 }
 
 // periodic image of a coordinate difference of two wrapped positions (|d| < L): the high word of
@@ -35,8 +44,8 @@ __device__ __forceinline__ bool need_rebuild(const Arrays& a, const PotDev& p) {
 // list are either closer than the list radius or further than L minus it, far from L/2.
 __device__ __forceinline__ double image_hi(double d, double L, uint32_t thr) {
   const int hw = __double2hiint(d);
-  if ((uint32_t)(hw & 0x7fffffff) >= thr) d += (hw < 0) ? L : -L;
-  return d;
+  const double sh = (uint32_t)(hw & 0x7fffffff) >= thr ? (hw < 0 ? L : -L) : 0.0;
+  return d + sh;  // one FP64 add; the shift is chosen by integer selects
 }
 
 // exact periodic wrap of a difference (compare form)
@@ -50,23 +59,25 @@ __device__ __forceinline__ int pack_home(int ix, int iy, int iz) {
   return ix | (iy << 10) | (iz << 20);
 }
 
-__device__ __forceinline__ void cell_center(const RepDev& R, int home, double& cx, double& cy,
-                                            double& cz) {
-  const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
-  cx = -R.hx + (ix + 0.5) * R.lcx;
-  cy = -R.hy + (iy + 0.5) * R.lcy;
-  cz = -R.hz + (iz + 0.5) * R.lcz;
-}
-
 __device__ __forceinline__ float4 local_offset(const RepDev& R, const dvec4& x, int home) {
-  double cx, cy, cz;
-  cell_center(R, home, cx, cy, cz);
+  const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
+  const double cx = -R.hx + (ix + 0.5) * R.lcx;
+  const double cy = -R.hy + (iy + 0.5) * R.lcy;
+  const double cz = -R.hz + (iz + 0.5) * R.lcz;
   float4 l;
   l.x = (float)wrap_diff(x.x - cx, R.Lx, R.hx);
   l.y = (float)wrap_diff(x.y - cy, R.Ly, R.hy);
   l.z = (float)(x.z - cz);
   l.w = 0.f;
   return l;
+}
+
+// 1/x by one Newton-Raphson step y <- y (2 - x y) from the correctly rounded FP32 reciprocal:
+// the relative error of the seed (<= 2^-24) is squared, ~4e-15 after the step.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double y = (double)__frcp_rn((float)x);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, e, y);
 }
 
 // error-free transformation s + x = t + e (Knuth's TwoSum); the error is collected in c
@@ -85,18 +96,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+inline int nblocks(long long n, int b) { return n > 0 ? (int)((n + b - 1) / b) : 1; }
+
 // ------------------------------------------------------------------------------------------------
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
 template <bool MIXED>
-__global__ void k_integrate_first(Arrays a, PotDev p) {
+__global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc) {
+  count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.step += 1;
     *a.any_scale = 0;
   }
-  if (halted(a)) return;
+  const bool halt = halted(a);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d2 = 0.0;
-  if (i < a.n_total) {
+  if (!halt && i < a.n_total) {
     const RepDev& R = a.reps[a.rep[i]];
     dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 f = a.frc[i];
@@ -129,69 +143,96 @@ __global__ void k_integrate_first(Arrays a, PotDev p) {
     a.vel[i] = v;
     if (MIXED) a.lpos[i] = local_offset(R, x, a.home[i]);
   }
-  unsigned long long b = (unsigned long long)__double_as_longlong(d2);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long t = __shfl_xor_sync(kFull, b, o);
-    b = t > b ? t : b;
+  // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
+  // below the threshold (nearly all steps) issue no atomic at all
+  if (__syncthreads_or(d2 >= p.half_skin2) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
+  if (!sc.use) return;
+  // the last block to finish decides this step's branches of the captured graph
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(a.blk_done, 1u) == gridDim.x - 1;
   }
-  if ((threadIdx.x & 31) == 0 && b) atomicMax(a.max_disp2, b);
-}
-
-// Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
-__global__ void k_integrate_second(Arrays a, PotDev p) {
-  if (halted(a)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total) return;
-  const RepDev& R = a.reps[a.rep[i]];
-  dvec4 v = a.vel[i];
-  const dvec4 f = a.frc[i];
-  const double h = 0.5 * R.dt * p.inv_mass;
-  v.x += h * f.x;
-  v.y += h * f.y;
-  v.z += h * f.z;
-  a.vel[i] = v;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const long long s = *reinterpret_cast<volatile long long*>(a.step);
+  int th = 0;
+  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x) {
+    const RepDev& R = a.reps[r];
+    if (R.n_th > 0 && R.n_vap > 0 && (s % R.n_th) == 0) th = 1;
+  }
+  th = __syncthreads_or(th);
+  if (threadIdx.x == 0) {
+    *a.blk_done = 0u;
+    const bool rb = !halt && atomicAdd(a.force_rebuild, 0) != 0;
+    cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
+    cudaGraphSetConditional(sc.thermo, (!halt && th) ? 1u : 0u);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Fig. 4 (Berendsen): one block per replica reduces m sum v^2 in a fixed order on thermostat steps
-__global__ void k_thermo_reduce(Arrays a, PotDev p) {
+// Fig. 4 (Berendsen) on thermostat steps. sum v^2 per replica in a fixed order: blocks
+// (replica, chunk of 1024 molecules) write partial sums, one warp per replica adds them in chunk
+// order and sets lambda, then every molecule is scaled.
+__device__ __forceinline__ bool thermo_step(const Arrays& a, const RepDev& R) {
+  return R.n_th > 0 && R.n_vap > 0 && (*a.step % R.n_th) == 0;
+}
+
+__global__ void __launch_bounds__(256) k_thermo_partial(Arrays a) {
+  count_launch(a);
   if (halted(a)) return;
-  const int r = blockIdx.x;
+  const int r = blockIdx.x / a.rep_chunks, ch = blockIdx.x % a.rep_chunks;
   const RepDev& R = a.reps[r];
-  const long long s = *a.step;
-  const bool act = R.n_th > 0 && R.n_vap > 0 && (s % R.n_th) == 0;
-  if (!act) {
-    if (threadIdx.x == 0) a.lambda[r] = 1.0;
-    return;
-  }
+  if (!thermo_step(a, R)) return;
+  const int k0 = ch * 1024, k1 = min(R.n_vap, k0 + 1024);
   double acc = 0.0;
-  for (int k = threadIdx.x; k < R.n_vap; k += blockDim.x) {
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const dvec4 v = a.vel[R.vap_off + k];
     acc += v.x * v.x + v.y * v.y + v.z * v.z;
   }
-  __shared__ double sh[32];
+  __shared__ double sh[8];
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    t = warp_sum(t);
-    if (threadIdx.x == 0) {
-      const double T = p.mass * t / (3.0 * (double)R.n_vap);
-      double lam = 1.0;
-      if (T > 0.0) lam = sqrt(1.0 + R.lam_coef * (R.T0 / T - 1.0));
-      a.lambda[r] = lam;
-      *a.any_scale = 1;
-    }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    a.rep_part[(size_t)blockIdx.x * 8] = t;
+  }
+}
+
+__global__ void k_thermo_lambda(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a)) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= a.n_reps) return;
+  const RepDev& R = a.reps[r];
+  if (!thermo_step(a, R)) {
+    if (lane == 0) a.lambda[r] = 1.0;
+    return;
+  }
+  const int nch = (R.n_vap + 1023) / 1024;
+  double t = 0.0;
+  for (int ch = lane; ch < nch; ch += 32) t += a.rep_part[((size_t)r * a.rep_chunks + ch) * 8];
+  t = warp_sum(t);  // fixed butterfly: deterministic
+  if (lane == 0) {
+    const double T = p.mass * t / (3.0 * (double)R.n_vap);
+    double lam = 1.0;
+    if (T > 0.0) lam = sqrt(1.0 + R.lam_coef * (R.T0 / T - 1.0));
+    a.lambda[r] = lam;
+    *a.any_scale = 1;
   }
 }
 
 __global__ void k_thermo_scale(Arrays a) {
-  if (halted(a) || *a.any_scale == 0) return;
+  count_launch(a);
+  if (halted(a) || *reinterpret_cast<volatile int*>(a.any_scale) == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total) return;
   const double lam = a.lambda[a.rep[i]];
+  if (lam == 1.0) return;
   dvec4 v = a.vel[i];
   v.x *= lam;
   v.y *= lam;
@@ -202,7 +243,8 @@ __global__ void k_thermo_scale(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // cell build: a counting sort of the vapour by cell, stable in the caller's molecule index
 
-__global__ void k_cell_count(Arrays a, PotDev p, const int32_t* __restrict__ cell_rep) {
+__global__ void k_cell_count(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total) return;
@@ -219,6 +261,7 @@ __global__ void k_cell_count(Arrays a, PotDev p, const int32_t* __restrict__ cel
 // exclusive scan of a 4096-element tile by 1024 threads; returns the tile total
 __device__ int tile_exclusive_scan(const int32_t* in, int32_t* out, int n, int base) {
   __shared__ int warp_tot[32];
+  __shared__ int total;
   const int t = threadIdx.x;
   int v[4];
   int run = 0;
@@ -237,14 +280,14 @@ __device__ int tile_exclusive_scan(const int32_t* in, int32_t* out, int n, int b
   if ((t & 31) == 31) warp_tot[t >> 5] = incl;
   __syncthreads();
   if (t < 32) {
-    int w = warp_tot[t];
+    const int w = warp_tot[t];
     int wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(kFull, wi, o);
       if (t >= o) wi += y;
     }
-    warp_tot[t] = wi - w;  // exclusive prefix of warp totals
+    warp_tot[t] = wi - w;
   }
   __syncthreads();
   int ex = warp_tot[t >> 5] + incl - run;
@@ -254,7 +297,6 @@ __device__ int tile_exclusive_scan(const int32_t* in, int32_t* out, int n, int b
     if (idx < n) out[idx] = ex;
     ex += v[k];
   }
-  __shared__ int total;
   if (t == 1023) total = ex;
   __syncthreads();
   const int r = total;
@@ -263,17 +305,20 @@ __device__ int tile_exclusive_scan(const int32_t* in, int32_t* out, int n, int b
 }
 
 __global__ void __launch_bounds__(1024) k_scan_tiles(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int tot = tile_exclusive_scan(a.vcount, a.vstart, a.n_cells, blockIdx.x * 4096);
   if (threadIdx.x == 0) a.scan_tiles[blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(1024) k_scan_top(Arrays a, PotDev p, int ntiles) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   tile_exclusive_scan(a.scan_tiles, a.scan_tiles, ntiles, 0);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_add(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int add = a.scan_tiles[blockIdx.x];
   for (int k = threadIdx.x; k < 4096; k += blockDim.x) {
@@ -283,7 +328,25 @@ __global__ void __launch_bounds__(1024) k_scan_add(Arrays a, PotDev p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
 }
 
+// the whole cell scan in one block (small grids): tile after tile with a running carry
+__global__ void __launch_bounds__(1024) k_scan_single(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  int carry = 0;
+  for (int base = 0; base < a.n_cells; base += 4096) {
+    const int tot = tile_exclusive_scan(a.vcount, a.vstart, a.n_cells, base);
+    for (int k = threadIdx.x; k < 4096; k += blockDim.x) {
+      const int idx = base + k;
+      if (idx < a.n_cells) a.vstart[idx] += carry;
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
+}
+
 __global__ void k_scatter(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total) return;
@@ -293,6 +356,7 @@ __global__ void k_scatter(Arrays a, PotDev p) {
 // within a cell, molecules are ordered by their caller index: the sorted order depends only on
 // the positions, not on the order in which atomics were served
 __global__ void k_permute(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n_total) return;
@@ -318,6 +382,7 @@ __global__ void k_permute(Arrays a, PotDev p) {
 }
 
 __global__ void k_copyback(Arrays a, PotDev p) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total) return;
@@ -328,292 +393,599 @@ __global__ void k_copyback(Arrays a, PotDev p) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Verlet-list build, one warp per cell. For each of the 27 neighbour cells the (molecule, candidate)
-// pairs of the cell are spread over the 32 lanes; hits are appended to each molecule's list in
-// (neighbour cell, candidate) order through a ballot/match prefix count, so lists are deterministic.
-// Distances use the FP32 cell-local offsets; the list radius carries a margin above the FP32 error.
+// Verlet-list build, one warp per cell. The candidates of the 27 neighbour cells form a stream --
+// first every vapour molecule of the 27 cells, then every wall atom -- and each lane holds one
+// candidate of a 32-wide chunk; the cell's molecules are tested against the chunk one after another
+// and hits are placed by ballot + prefix count, so lists are deterministic. A molecule i's list is
+// one row of `cap` slots (row-major): partners j > i and then wall atoms fill it from the front,
+// partners j < i from the back. The front is the FP64 half list (vapour partners first, so a
+// vapour entry's slot is its pairbuf slot); front + back is the full list. Distances use the FP32
+// cell-local offsets as (l_i - l_j) - dc*cell, which is exactly antisymmetric, so i lists j exactly
+// when j lists i; the list radius carries a margin above the FP32 error.
 
-template <bool WALL>
-__device__ __forceinline__ void list_pass(const Arrays& a, const PotDev& p, int i0, int nic,
-                                          int j0, int nj, uint32_t code, float ox, float oy,
-                                          float oz, int* cnt, int lane) {
-  const float4* __restrict__ lj = WALL ? a.wlpos : a.lpos;
-  uint32_t* __restrict__ out = WALL ? a.nbr_vw : a.nbr_vv;
-  const int cap = WALL ? p.cap_vw : p.cap_vv;
-  const int total = nic * nj;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int base = 0; base < total; base += 32) {
-    const int q = base + lane;
-    const bool valid = q < total;
-    int il = 0, jl = 0;
-    if (valid) {
-      il = q / nj;
-      jl = q - il * nj;
-    }
-    const int i = i0 + il, j = j0 + jl;
-    bool hit = false;
-    if (valid && (WALL || i != j)) {
-      const float4 li = a.lpos[i];
-      const float4 b = lj[j];
-      const float dx = (li.x - b.x) - ox;
-      const float dy = (li.y - b.y) - oy;
-      const float dz = (li.z - b.z) - oz;
-      hit = dx * dx + dy * dy + dz * dz < p.rl2f;
-    }
-    const unsigned hits = __ballot_sync(kFull, hit);
-    const unsigned same = __match_any_sync(kFull, valid ? il : 64 + lane);
-    if (hit) {
-      const int slot = cnt[il] + __popc(hits & same & lt);
-      if (slot < cap) out[(size_t)slot * a.n_total + i] = (uint32_t)j | code;
-    }
-    __syncwarp();
-    if (valid && (same & lt) == 0) cnt[il] += __popc(hits & same);
-    __syncwarp();
-  }
+__device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
+  // warp-aggregated histogram update: one atomic per distinct length in the warp
+  const unsigned act = __ballot_sync(kFull, on);
+  if (!on) return;
+  const unsigned grp = __match_any_sync(act, h);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.hist[h], __popc(grp));
 }
 
-__global__ void k_list_build(Arrays a, PotDev p, const int32_t* __restrict__ cell_rep) {
+constexpr int kListWarps = 4;      // warps (cells) per block of the list build
+constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
+
+__global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half, int lpt) {
+  count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
-  extern __shared__ int sh_cnt[];
-  const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + warp_in_block;
+  __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
+  __shared__ float4 sh_li[kListWarps][64];
+  __shared__ int sh_f[kListWarps][64], sh_b[kListWarps][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
   if (c >= a.n_cells) return;
-  int* cnt_vv = sh_cnt + warp_in_block * 64;
-  int* cnt_vw = cnt_vv + 32;
   const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
   if (lane == 0) a.vcount[c] = 0;  // ready for the next build
   if (i_end == i_begin) return;
-  const RepDev& R = a.reps[cell_rep[c]];
+  const RepDev& R = a.reps[a.cell_rep[c]];
   const int local = c - R.cell_off;
   const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
-  int max_vv = 0, max_vw = 0;
-  for (int i0 = i_begin; i0 < i_end; i0 += 32) {
-    const int nic = min(32, i_end - i0);
-    cnt_vv[lane] = 0;
-    cnt_vw[lane] = 0;
+  // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+  int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
+  uint32_t code = 0;
+  if (lane < 27) {
+    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+    const int jz = iz + dz;
+    if (jz >= 0 && jz < R.ncz) {
+      const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
+      const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+      vj0 = a.vstart[cn];
+      nv = a.vstart[cn + 1] - vj0;
+      wj0 = a.wstart[cn];
+      nw = a.wstart[cn + 1] - wj0;
+    }
+    code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) | ((uint32_t)(dz + 1) << 30);
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  const int N = a.n_total, cap = p.cap;
+  uint32_t* stream = sh_stream[w];
+  int max_n = 0;
+  for (int ib = i_begin; ib < i_end; ib += 64) {
+    const int nic = min(64, i_end - ib);
+    // the molecules of this group: offsets and front / back counts in shared memory
+    for (int q = lane; q < 64; q += 32) {
+      sh_li[w][q] = q < nic ? a.lpos[ib + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sh_f[w][q] = 0;
+      sh_b[w][q] = 0;
+    }
+    int vh0 = 0, vh1 = 0;
     __syncwarp();
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int jz = iz + dz;
-      if (jz < 0 || jz >= R.ncz) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int jy = (iy + dy + R.ncy) % R.ncy;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int jx = (ix + dx + R.ncx) % R.ncx;
-          const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
-          const uint32_t code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) |
-                                ((uint32_t)(dz + 1) << 30);
-          const float ox = dx * R.lcxf, oy = dy * R.lcyf, oz = dz * R.lczf;
-          const int vj0 = a.vstart[cn], vj1 = a.vstart[cn + 1];
-          if (vj1 > vj0)
-            list_pass<false>(a, p, i0, nic, vj0, vj1 - vj0, code, ox, oy, oz, cnt_vv, lane);
-          const int wj0 = a.wstart[cn], wj1 = a.wstart[cn + 1];
-          if (wj1 > wj0)
-            list_pass<true>(a, p, i0, nic, wj0, wj1 - wj0, code, ox, oy, oz, cnt_vw, lane);
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool wallpass = pass == 1;
+      const int tot = wallpass ? nw : nv;
+      const uint32_t base_idx = wallpass ? (uint32_t)(N + wj0) : (uint32_t)vj0;
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int T = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - tot;
+      for (int W0 = 0; W0 < T; W0 += kStreamWin) {
+        const int W1 = min(T, W0 + kStreamWin);
+        // lane l writes the part of its cell's candidates that falls in this window
+        for (int m = max(0, W0 - excl); m < tot && excl + m < W1; ++m)
+          stream[excl + m - W0] = (base_idx + (uint32_t)m) | code;
+        __syncwarp();
+        for (int base = W0; base < W1; base += 32) {
+          const int q = base + lane;
+          const bool valid = q < W1;
+          const uint32_t entry = valid ? stream[q - W0] : 0u;
+          const int jj = (int)(entry & kIndexMask);
+          const int j = wallpass ? jj - N : jj;
+          float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
+          const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
+          const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
+          const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
+          for (int il = 0; il < nic; ++il) {
+            const int i = ib + il;
+            const float4 li = sh_li[w][il];
+            const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
+            const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
+            const bool front = hit && (wallpass || j > i);
+            const bool back = hit && !front;
+            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
+            if (bf | bb) {
+              if (front) {
+                const int slot = sh_f[w][il] + __popc(bf & lt);
+                if (slot < cap) a.nbr[(size_t)i * cap + slot] = entry;
+              } else if (back) {
+                const int slot = cap - 1 - (sh_b[w][il] + __popc(bb & lt));
+                if (slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
+              }
+              __syncwarp();
+              if (lane == 0) {
+                sh_f[w][il] += __popc(bf);
+                sh_b[w][il] += __popc(bb);
+              }
+              __syncwarp();
+            }
+          }
         }
+        __syncwarp();
+      }
+      if (!wallpass) {
+        vh0 = sh_f[w][lane];
+        vh1 = sh_f[w][lane + 32];
       }
     }
-    if (lane < nic) {
-      const int nv = cnt_vv[lane], nw = cnt_vw[lane];
-      if (nv > p.cap_vv || nw > p.cap_vw) atomicOr(a.status, kStatusOverflow);
-      a.n_vv[i0 + lane] = min(nv, p.cap_vv);
-      a.n_vw[i0 + lane] = min(nw, p.cap_vw);
-      max_vv = max(max_vv, nv);
-      max_vw = max(max_vw, nw);
+    // counts, overflow, processing-order histogram
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int i = ib + g * 32 + lane;
+      const bool own = g * 32 + lane < nic;
+      const int nf = sh_f[w][g * 32 + lane], nb = sh_b[w][g * 32 + lane], nvh = g ? vh1 : vh0;
+      if (own) {
+        if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
+          atomicOr(a.status, kStatusOverflow);
+        a.n_front[i] = min(nf, cap);
+        a.n_back[i] = min(nb, cap - min(nf, cap));
+        a.n_vh[i] = min(nvh, p.cap_v);
+        max_n = max(max_n, nf + nb);
+      }
+      if (lpt) hist_add(a, min(half ? nf : nf + nb, cap), own);
     }
     __syncwarp();
   }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    max_vv = max(max_vv, __shfl_xor_sync(kFull, max_vv, o));
-    max_vw = max(max_vw, __shfl_xor_sync(kFull, max_vw, o));
-  }
-  if (lane == 0) {
-    atomicMax(a.max_nvv, max_vv);
-    atomicMax(a.max_nvw, max_vw);
-  }
+  for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
+  if (lane == 0) atomicMax(a.max_nb, max_n);
 }
 
 // ------------------------------------------------------------------------------------------------
-// Pair forces (Eq. 2, Fig. 1): f_i = sum_j F(r_ij)/r_ij * (r_i - r_j) over list entries with
-// r^2 < rc^2, F(r)/r = inv2 * inv6 * (48 eps s^12 inv6 - 24 eps s^6), inv2 = 1/r^2, inv6 = inv2^3.
-// The vapour list is full (each pair held by both molecules), so each molecule's force is a sum
-// it owns: no atomics, the result does not depend on scheduling.
-//
-// FP64 variant: everything in FP64.
+// Processing order (optional). Molecules sorted by the length of the list the pair kernel walks
+// (FP64: the front; mixed: front + back), longest first: warps see uniform lengths and the heaviest
+// chunks start first. Whatever the order, each molecule's force is a sum it owns, so the order
+// changes no result.
 
-template <bool STATS>
-__global__ void k_forces_fp64(Arrays a, PotDev p) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.max_disp2 = 0ull;
-    *a.force_rebuild = 0;
+// start of each list length in descending order of length; clears the histogram
+__global__ void __launch_bounds__(1024) k_order_scan(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  __shared__ int warp_tot[32];
+  const int t = threadIdx.x;
+  const int b = p.cap - t;  // thread t handles length b (longest first)
+  const int v = b >= 0 ? a.hist[b] : 0;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((t & 31) >= o) incl += y;
   }
-  if (halted(a)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = i < a.n_total;
-  int cnt = 0;
-  if (live) {
-    const RepDev& R = a.reps[a.rep[i]];
-    const dvec4 xi = a.pos[i];
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    double pe = 0.0, vir = 0.0, pew = 0.0, virw = 0.0, d2w = __longlong_as_double(0x7ff0000000000000ll);
-    int cvw = 0;
-    const int nv = a.n_vv[i];
-    const uint32_t* __restrict__ lv = a.nbr_vv + i;
-    for (int k = 0; k < nv; ++k) {
-      const int j = (int)(lv[(size_t)k * a.n_total] & kIndexMask);
-      const dvec4 xj = a.pos[j];
-      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
-      const double dz = xi.z - xj.z;
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < p.rc2) {
-        const double inv2 = 1.0 / r2;
-        const double inv6 = inv2 * inv2 * inv2;
-        const double fr = inv2 * inv6 * fma(p.a12, inv6, -p.b6);
-        fx = fma(fr, dx, fx);
-        fy = fma(fr, dy, fy);
-        fz = fma(fr, dz, fz);
-        ++cnt;
-        if (STATS) {
-          pe += 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift);
-          vir += 0.5 * fr * r2;
-        }
-      }
+  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    const int w = warp_tot[t];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, wi, o);
+      if (t >= o) wi += y;
     }
-    const int nw = a.n_vw[i];
-    const uint32_t* __restrict__ lw = a.nbr_vw + i;
-    for (int k = 0; k < nw; ++k) {
-      const int j = (int)(lw[(size_t)k * a.n_total] & kIndexMask);
-      const dvec4 xj = a.wpos[j];
-      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
-      const double dz = xi.z - xj.z;
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < p.rcw2) {
-        const double inv2 = 1.0 / r2;
-        const double inv6 = inv2 * inv2 * inv2;
-        const double fr = inv2 * inv6 * fma(p.a12w, inv6, -p.b6w);
-        fx = fma(fr, dx, fx);
-        fy = fma(fr, dy, fy);
-        fz = fma(fr, dz, fz);
-        ++cvw;
-        if (STATS) {
-          pew += inv6 * fma(p.e12w, inv6, -p.e6w) - p.ushift_w;
-          virw += fr * r2;
-          d2w = fmin(d2w, r2);
-        }
-      }
-    }
-    a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
-    if (STATS) {
-      a.pe_i[i] = pe;
-      a.pevw_i[i] = pew;
-      a.vir_i[i] = vir;
-      a.virw_i[i] = virw;
-      a.d2w_i[i] = d2w;
-      a.cnt_vv_i[i] = cnt;
-      a.cnt_vw_i[i] = cvw;
-    }
-    cnt += 2 * cvw;  // vapour pairs are seen from both ends: count twice, halve at read-out
+    warp_tot[t] = wi - w;
   }
-  if (!STATS) {
-    unsigned long long c = warp_sum((unsigned long long)cnt);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.pair_count, c);
+  __syncthreads();
+  if (b >= 0) {
+    a.hstart[b] = warp_tot[t >> 5] + incl - v;
+    a.hist[b] = 0;
   }
 }
 
-// Mixed variant: pair terms in FP32 from the cell-local FP32 offsets (the displacement is
-// (l_i - l_j) - dc * cell side, all terms small, so the FP32 rounding is relative to the cell size
-// rather than the box), per-molecule sums in compensated FP32 (TwoSum), written as FP64.
-// Energies and virials of the observable pass are accumulated in FP64.
+// processing position of each molecule (warp-aggregated atomics on the length starts)
+__global__ void k_order_assign(Arrays a, PotDev p, int half) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool own = i < a.n_total;
+  int h = 0;
+  if (own) h = min(half ? a.n_front[i] : a.n_front[i] + a.n_back[i], p.cap);
+  const unsigned act = __ballot_sync(kFull, own);
+  if (!own) return;
+  const unsigned grp = __match_any_sync(act, h);
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if ((threadIdx.x & 31) == leader) base = atomicAdd(&a.hstart[h], __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  const int pos = base + __popc(grp & ((1u << (threadIdx.x & 31)) - 1u));
+  if (pos < a.n_total) a.order[pos] = i;
+}
 
-template <bool STATS>
-__global__ void k_forces_mixed(Arrays a, PotDev p) {
+// FP64: for each vapour pair (i, j > i) at front slot k of i, find i in j's back region (slot m)
+// and record fwd[i, k] = j * cap_v + m: the half-list pass stores the pair force where j's gather
+// reads it, in j's own list order. Every back slot is the target of exactly one pair, so the gather
+// is deterministic and needs no atomics; a pair whose partner slot cannot be found (an overflowed
+// list, already flagged) points at the spare entry past the end of pairbuf.
+// One warp per molecule (grid-stride), lanes over the front slots; when the row length is a
+// multiple of 4 the back region is scanned four entries per 16-byte load.
+__global__ void __launch_bounds__(256) k_fwd_build(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  const int cap = p.cap, capv = p.cap_v;
+  const uint32_t spare = (uint32_t)((size_t)a.n_total * capv);
+  const bool vec = (cap & 3) == 0;
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.n_total; i += warps) {
+    const int nvh = a.n_vh[i];
+    const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+    uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
+    for (int k = threadIdx.x & 31; k < nvh; k += 32) {
+      const uint32_t j = row[k] & kIndexMask;
+      const int nb = min(a.n_back[j], capv);
+      const uint32_t* __restrict__ rj = a.nbr + (size_t)j * cap + cap;  // one past j's row
+      int m = -1;
+      if (vec) {
+        // entries cap-4q-4 .. cap-4q-1 hold back slots 4q+3 .. 4q; 4q < nb <= cap keeps the load
+        // inside row j
+        const uint4* __restrict__ r4 = reinterpret_cast<const uint4*>(rj);
+        for (int q = 0; 4 * q < nb; ++q) {
+          const uint4 e = r4[-1 - q];
+          if ((e.w & kIndexMask) == (uint32_t)i) { m = 4 * q; break; }
+          if ((e.z & kIndexMask) == (uint32_t)i) { m = 4 * q + 1; break; }
+          if ((e.y & kIndexMask) == (uint32_t)i) { m = 4 * q + 2; break; }
+          if ((e.x & kIndexMask) == (uint32_t)i) { m = 4 * q + 3; break; }
+        }
+      } else {
+        for (int q = 0; q < nb; ++q)
+          if ((rj[-1 - q] & kIndexMask) == (uint32_t)i) { m = q; break; }
+      }
+      if (m < 0 || m >= nb) {
+        atomicOr(a.status, kStatusOverflow);
+        fw[k] = spare;
+      } else {
+        fw[k] = j * (uint32_t)capv + (uint32_t)m;
+      }
+    }
+  }
+}
+
+// Warp-level dynamic work distribution over chunks of MPW molecules of the processing order.
+// Returns the chunk (or -1 when the work is exhausted). The counters are reset by the last block.
+template <int MPW>
+__device__ __forceinline__ int next_chunk(const Arrays& a) {
+  int c = 0;
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(a.work, 1);
+  c = __shfl_sync(kFull, c, 0);
+  return c * MPW < a.n_total ? c : -1;
+}
+
+// sum over the TPP lanes that share a molecule (fixed butterfly order: deterministic)
+template <int TPP, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = TPP / 2; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int TPP>
+__device__ __forceinline__ double group_min(double v) {
+#pragma unroll
+  for (int o = TPP / 2; o; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void finish_chunks(const Arrays& a) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.work_done, 1u) == gridDim.x - 1) {
+      *a.work = 0;
+      *a.work_done = 0u;
+    }
+  }
+}
+
+// positive doubles compare like their bit patterns: an integer test, no FP64 instruction
+__device__ __forceinline__ bool lt_pos(double x, double y) {
+  return __double_as_longlong(x) < __double_as_longlong(y);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pair forces (Eq. 2, Fig. 1): f_i = sum_j F(r_ij)/r_ij * (r_i - r_j) over pairs with r^2 < rc^2,
+// F(r)/r = inv2 * inv6 * (48 eps s^12 inv6 - 24 eps s^6), inv2 = 1/r^2, inv6 = inv2^3.
+// A warp takes chunks of 32/TPP molecules; the TPP lanes of a molecule split its list.
+//
+// FP64, half list: molecule i walks the front of its row; each vapour pair's force goes to the
+// partner's back slot in pairbuf (fwd), where the partner's gather reads it in list order.
+
+template <int TPP>
+__global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.max_disp2 = 0ull;
     *a.force_rebuild = 0;
   }
   if (halted(a)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = i < a.n_total;
+  const int N = a.n_total, cap = p.cap, capv = p.cap_v;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    int i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const dvec4 xi = a.pos[i];
+      const int n = a.n_front[i], nvh = a.n_vh[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      const uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
+      for (int k = sub; k < n; k += TPP) {
+        const int j = (int)(row[k] & kIndexMask);
+        const bool wall = j >= N;
+        const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+        const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+        const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+        const double dz = xi.z - xj.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double fr = 0.0;
+        if (lt_pos(r2, wall ? p.rcw2 : p.rc2)) {
+          const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+          const double inv2 = rcp_nr(r2);
+          const double inv6 = inv2 * inv2 * inv2;
+          fr = inv2 * inv6 * fma(a12, inv6, -b6);
+          fx = fma(fr, dx, fx);
+          fy = fma(fr, dy, fy);
+          fz = fma(fr, dz, fz);
+          ++cnt;
+        }
+        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(fr * dx, fr * dy, fr * dz, 0.0);
+      }
+    }
+    fx = group_sum<TPP>(fx);
+    fy = group_sum<TPP>(fy);
+    fz = group_sum<TPP>(fz);
+    if (live && sub == 0) a.fpart[i] = make_dvec4(fx, fy, fz, 0.0);
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
+// FP64 observable pass over the full row (front + back): per-molecule energy and virial (half of
+// each vapour pair to each end, wall pairs in full), pair counts and nearest wall atom. The forces
+// of the last step are left untouched.
+template <int TPP>
+__global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a)) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = g / TPP, sub = g & (TPP - 1);
+  const int N = a.n_total, cap = p.cap;
+  const bool live = i < N;
+  double pe = 0.0, vir = 0.0, pew = 0.0, virw = 0.0;
+  double d2w = __longlong_as_double(0x7ff0000000000000ll);
+  int cvv = 0, cvw = 0;
   if (live) {
     const RepDev& R = a.reps[a.rep[i]];
-    const float4 li = a.lpos[i];
-    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    double pe = 0.0, vir = 0.0, pew = 0.0, virw = 0.0, d2w = __longlong_as_double(0x7ff0000000000000ll);
-    int cvw = 0;
-    const int nv = a.n_vv[i];
-    const uint32_t* __restrict__ lv = a.nbr_vv + i;
-    for (int k = 0; k < nv; ++k) {
-      const uint32_t e = lv[(size_t)k * a.n_total];
-      const float4 b = a.lpos[e & kIndexMask];
-      const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
-      const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
-      const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < p.rc2f) {
-        const float inv2 = __frcp_rn(r2);
-        const float inv6 = inv2 * inv2 * inv2;
-        const float fr = inv2 * inv6 * fmaf(p.a12f, inv6, -p.b6f);
-        two_sum_acc(sx, cx, fr * dx);
-        two_sum_acc(sy, cy, fr * dy);
-        two_sum_acc(sz, cz, fr * dz);
-        ++cnt;
-        if (STATS) {
-          pe += 0.5 * ((double)(inv6 * fmaf(p.e12f, inv6, -p.e6f)) - p.ushift);
-          vir += 0.5 * (double)(fr * r2);
-        }
-      }
-    }
-    const int nw = a.n_vw[i];
-    const uint32_t* __restrict__ lw = a.nbr_vw + i;
-    for (int k = 0; k < nw; ++k) {
-      const uint32_t e = lw[(size_t)k * a.n_total];
-      const float4 b = a.wlpos[e & kIndexMask];
-      const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
-      const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
-      const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < p.rcw2f) {
-        const float inv2 = __frcp_rn(r2);
-        const float inv6 = inv2 * inv2 * inv2;
-        const float fr = inv2 * inv6 * fmaf(p.a12wf, inv6, -p.b6wf);
-        two_sum_acc(sx, cx, fr * dx);
-        two_sum_acc(sy, cy, fr * dy);
-        two_sum_acc(sz, cz, fr * dz);
+    const dvec4 xi = a.pos[i];
+    const int nf = a.n_front[i], n = nf + a.n_back[i];
+    const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+    for (int q = sub; q < n; q += TPP) {
+      const int j = (int)(row[q < nf ? q : cap - 1 - (q - nf)] & kIndexMask);
+      const bool wall = j >= N;
+      const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+      const double dz = xi.z - xj.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!lt_pos(r2, wall ? p.rcw2 : p.rc2)) continue;
+      const double inv2 = 1.0 / r2, inv6 = inv2 * inv2 * inv2;
+      if (wall) {
+        const double fr = inv2 * inv6 * fma(p.a12w, inv6, -p.b6w);
+        pew += inv6 * fma(p.e12w, inv6, -p.e6w) - p.ushift_w;
+        virw += fr * r2;
+        d2w = fmin(d2w, r2);
         ++cvw;
-        if (STATS) {
-          pew += (double)(inv6 * fmaf(p.e12wf, inv6, -p.e6wf)) - p.ushift_w;
-          virw += (double)(fr * r2);
-          d2w = fmin(d2w, (double)r2);
+      } else {
+        const double fr = inv2 * inv6 * fma(p.a12, inv6, -p.b6);
+        pe += 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift);
+        vir += 0.5 * fr * r2;
+        ++cvv;
+      }
+    }
+  }
+  pe = group_sum<TPP>(pe);
+  pew = group_sum<TPP>(pew);
+  vir = group_sum<TPP>(vir);
+  virw = group_sum<TPP>(virw);
+  d2w = group_min<TPP>(d2w);
+  cvv = group_sum<TPP>(cvv);
+  cvw = group_sum<TPP>(cvw);
+  if (!live || sub != 0) return;
+  a.pe_i[i] = pe;
+  a.pevw_i[i] = pew;
+  a.vir_i[i] = vir;
+  a.virw_i[i] = virw;
+  a.d2w_i[i] = d2w;
+  a.cnt_vv_i[i] = cvv;
+  a.cnt_vw_i[i] = cvw;
+}
+
+// f_i = (half-list sum) - (forces of the pairs held by lower partners, read contiguously from i's
+// pairbuf row in i's back-region order); with
+// KICK the second half-kick (Fig. 3) follows
+template <bool KICK, int TPP>
+__global__ void k_gather(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a)) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = g / TPP, sub = g & (TPP - 1);
+  const int N = a.n_total;
+  const bool live = i < N;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  if (live) {
+    const int m = min(a.n_back[i], p.cap_v);
+    const dvec4* __restrict__ pb = a.pairbuf + (size_t)i * p.cap_v;
+#pragma unroll 4
+    for (int q = sub; q < m; q += TPP) {
+      const dvec4 b = pb[q];
+      fx += b.x;
+      fy += b.y;
+      fz += b.z;
+    }
+  }
+  fx = group_sum<TPP>(fx);
+  fy = group_sum<TPP>(fy);
+  fz = group_sum<TPP>(fz);
+  if (!live || sub != 0) return;
+  dvec4 f = a.fpart[i];
+  f.x -= fx;
+  f.y -= fy;
+  f.z -= fz;
+  f.w = 0.0;
+  a.frc[i] = f;
+  if (KICK) {
+    const RepDev& R = a.reps[a.rep[i]];
+    dvec4 v = a.vel[i];
+    const double h = 0.5 * R.dt * p.inv_mass;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    a.vel[i] = v;
+  }
+}
+
+// Mixed precision, full list (front + back of the row): pair terms in FP32 from the cell-local FP32
+// offsets (the displacement is (l_i - l_j) - dc * cell side, all terms small, so the rounding is
+// relative to the cell size rather than the box), per-lane sums in compensated FP32 (TwoSum), the
+// lanes of a molecule combined in FP64. Pairs whose FP32 r^2 lies within a relative 1e-5 of the
+// cutoff are decided in FP64 from the FP64 positions, so the set of interacting pairs is the FP64
+// one. The observable pass accumulates energies and virials in FP64 and measures wall distances in
+// FP64.
+
+template <bool STATS, bool KICK, int TPP>
+__global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lpt) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.force_rebuild = 0;
+  }
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
+  int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    double pe = 0.0, vir = 0.0, pew = 0.0, virw = 0.0;
+    double d2w = __longlong_as_double(0x7ff0000000000000ll);
+    int cvv = 0, cvw = 0, i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const float4 li = a.lpos[i];
+      const dvec4 xi = a.pos[i];
+      const int nf = a.n_front[i], n = nf + a.n_back[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      for (int q = sub; q < n; q += TPP) {
+        const uint32_t e = row[q < nf ? q : cap - 1 - (q - nf)];
+        const int j = (int)(e & kIndexMask);
+        const bool wall = j >= N;
+        const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
+        const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
+        const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
+        const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
+        bool in = r2 < lo;
+        if (!in && r2 < hi) {
+          const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+          const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+          const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+          const double ez = xi.z - xj.z;
+          in = ex * ex + ey * ey + ez * ez < (wall ? p.rcw2 : p.rc2);
+        }
+        if (in) {
+          const float a12 = wall ? p.a12wf : p.a12f, b6 = wall ? p.b6wf : p.b6f;
+          const float inv2 = __frcp_rn(r2);
+          const float inv6 = inv2 * inv2 * inv2;
+          const float fr = inv2 * inv6 * fmaf(a12, inv6, -b6);
+          two_sum_acc(sx, cx, fr * dx);
+          two_sum_acc(sy, cy, fr * dy);
+          two_sum_acc(sz, cz, fr * dz);
+          if (STATS) {
+            const double u = (double)(inv6 * fmaf(wall ? p.e12wf : p.e12f, inv6,
+                                                 -(wall ? p.e6wf : p.e6f)));
+            if (wall) {
+              const dvec4 xj = a.wpos[j - N];
+              const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+              const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+              const double ez = xi.z - xj.z;
+              pew += u - p.ushift_w;
+              virw += (double)(fr * r2);
+              d2w = fmin(d2w, ex * ex + ey * ey + ez * ez);
+              ++cvw;
+            } else {
+              pe += 0.5 * (u - p.ushift);
+              vir += 0.5 * (double)(fr * r2);
+              ++cvv;
+            }
+          } else {
+            cnt += wall ? 2 : 1;  // vapour pairs are seen from both ends
+          }
         }
       }
     }
-    a.frc[i] = make_dvec4((double)sx + (double)cx, (double)sy + (double)cy,
-                            (double)sz + (double)cz, 0.0);
+    double fx = group_sum<TPP>((double)sx + (double)cx);
+    double fy = group_sum<TPP>((double)sy + (double)cy);
+    double fz = group_sum<TPP>((double)sz + (double)cz);
     if (STATS) {
-      a.pe_i[i] = pe;
-      a.pevw_i[i] = pew;
-      a.vir_i[i] = vir;
-      a.virw_i[i] = virw;
-      a.d2w_i[i] = d2w;
-      a.cnt_vv_i[i] = cnt;
-      a.cnt_vw_i[i] = cvw;
+      pe = group_sum<TPP>(pe);
+      pew = group_sum<TPP>(pew);
+      vir = group_sum<TPP>(vir);
+      virw = group_sum<TPP>(virw);
+      d2w = group_min<TPP>(d2w);
+      cvv = group_sum<TPP>(cvv);
+      cvw = group_sum<TPP>(cvw);
     }
-    cnt += 2 * cvw;
+    if (live && sub == 0) {
+      if (!STATS) a.frc[i] = make_dvec4(fx, fy, fz, 0.0);  // the observable pass leaves forces
+      if (KICK) {  // Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+        const RepDev& R = a.reps[a.rep[i]];
+        dvec4 v = a.vel[i];
+        const double h = 0.5 * R.dt * p.inv_mass;
+        v.x += h * fx;
+        v.y += h * fy;
+        v.z += h * fz;
+        a.vel[i] = v;
+      }
+      if (STATS) {
+        a.pe_i[i] = pe;
+        a.pevw_i[i] = pew;
+        a.vir_i[i] = vir;
+        a.virw_i[i] = virw;
+        a.d2w_i[i] = d2w;
+        a.cnt_vv_i[i] = cvv;
+        a.cnt_vw_i[i] = cvw;
+      }
+    }
   }
   if (!STATS) {
-    unsigned long long c = warp_sum((unsigned long long)cnt);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.pair_count, c);
+    const unsigned long long c = warp_sum((unsigned long long)cnt);
+    if (lane == 0 && c) atomicAdd(a.pair_count, c);
   }
+  finish_chunks(a);
 }
 
 // ------------------------------------------------------------------------------------------------
 // observables: pore assignment, occupancy, adsorbed count, axial profile (integer atomics: exact)
 
 __global__ void k_observe(Arrays a, PotDev p) {
+  count_launch(a);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total) return;
   const RepDev& R = a.reps[a.rep[i]];
@@ -639,13 +1011,16 @@ __global__ void k_observe(Arrays a, PotDev p) {
   atomicAdd(&a.prof[(size_t)R.prof_off + (size_t)g * R.n_bins + b], 1ull);
 }
 
-// per-replica sums in a fixed order (one block per replica): ke, pe_vv, pe_vw, vir_vv, vir_vw,
-// ordered vapour pair count, wall pair count
-__global__ void k_rep_sums(Arrays a, PotDev p) {
-  const int r = blockIdx.x;
+// per-replica sums in a fixed order: blocks (replica, chunk of 1024 molecules) write partials,
+// one block per replica adds them in chunk order. Quantities: ke, pe_vv, pe_vw, vir_vv, vir_vw,
+// ordered vapour pair count, wall pair count.
+__global__ void __launch_bounds__(256) k_rep_partial(Arrays a, PotDev p) {
+  count_launch(a);
+  const int r = blockIdx.x / a.rep_chunks, ch = blockIdx.x % a.rep_chunks;
   const RepDev& R = a.reps[r];
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int k = threadIdx.x; k < R.n_vap; k += blockDim.x) {
+  const int k0 = ch * 1024, k1 = min(R.n_vap, k0 + 1024);
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int i = R.vap_off + k;
     const dvec4 v = a.vel[i];
     acc[0] += v.x * v.x + v.y * v.y + v.z * v.z;
@@ -656,75 +1031,167 @@ __global__ void k_rep_sums(Arrays a, PotDev p) {
     acc[5] += (double)a.cnt_vv_i[i];
     acc[6] += (double)a.cnt_vw_i[i];
   }
-  __shared__ double sh[7][32];
+  __shared__ double sh[7][8];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     const double w = warp_sum(acc[q]);
     if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = w;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      double t = threadIdx.x < (blockDim.x >> 5) ? sh[q][threadIdx.x] : 0.0;
-      t = warp_sum(t);
-      if (threadIdx.x == 0) a.rep_sums[r * 8 + q] = (q == 0 ? 0.5 * p.mass * t : t);
-    }
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+    a.rep_part[(size_t)blockIdx.x * 8 + threadIdx.x] = t;
   }
 }
 
-inline int nblocks(long long n, int b) { return n > 0 ? (int)((n + b - 1) / b) : 1; }
+__global__ void k_rep_final(Arrays a, PotDev p) {
+  count_launch(a);
+  const int r = blockIdx.x;
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int ch = 0; ch < a.rep_chunks; ++ch)
+      t += a.rep_part[((size_t)r * a.rep_chunks + ch) * 8 + threadIdx.x];
+    a.rep_sums[r * 8 + threadIdx.x] = threadIdx.x == 0 ? 0.5 * p.mass * t : t;
+  }
+}
+
+// virial pressure per pore (Sec. 2): P_q = (sum m v^2 + sum W_i) / (3 V_q) over the molecules
+// inside pore q (the occupancy predicate), W_i = vir_i + virw_i. Blocks (replica, chunk) write
+// partial sums for every pore of the replica, one thread per pore adds them in chunk order.
+__global__ void __launch_bounds__(256) k_pore_partial(Arrays a, PotDev p) {
+  count_launch(a);
+  const int r = blockIdx.x / a.rep_chunks, ch = blockIdx.x % a.rep_chunks;
+  const RepDev& R = a.reps[r];
+  if (R.n_pores == 0) return;
+  __shared__ double sh[8];
+  const int k0 = ch * 1024, k1 = min(R.n_vap, k0 + 1024);
+  for (int q = 0; q < R.n_pores; ++q) {
+    const PoreDev& P = a.pores[R.pore_off + q];
+    double acc = 0.0;
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int i = R.vap_off + k;
+      const dvec4 x = a.pos[i];
+      if (!(fabs(x.z) < R.slab_half)) continue;
+      const double dx = wrap_diff(x.x - P.cx, R.Lx, R.hx);
+      const double dy = wrap_diff(x.y - P.cy, R.Ly, R.hy);
+      if (!in_pore(P.kind, P.r0, P.r1, P.r_cavity, P.width, dx, dy, x.z, R.slab_half)) continue;
+      const dvec4 v = a.vel[i];
+      acc += p.mass * (v.x * v.x + v.y * v.y + v.z * v.z) + a.vir_i[i] + a.virw_i[i];
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      a.pore_part[(size_t)blockIdx.x * a.max_pores + q] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_pore_final(Arrays a) {
+  count_launch(a);
+  const int r = blockIdx.x;
+  const RepDev& R = a.reps[r];
+  for (int q = threadIdx.x; q < R.n_pores; q += blockDim.x) {
+    double t = 0.0;
+    for (int ch = 0; ch < a.rep_chunks; ++ch)
+      t += a.pore_part[((size_t)r * a.rep_chunks + ch) * a.max_pores + q];
+    const double vol = a.pores[R.pore_off + q].vol;
+    a.pore_press[R.pore_off + q] = vol > 0.0 ? t / (3.0 * vol) : 0.0;
+  }
+}
 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
 // launchers
 
-void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, cudaStream_t s) {
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
+                            cudaStream_t s) {
   const int b = 256;
   if (mixed)
-    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p);
+    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c);
   else
-    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p);
+    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c);
 }
 
-void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, const int32_t* cell_rep,
-                    cudaStream_t s) {
+int rebuild_kernel_count(bool mixed) { return mixed ? 10 : 11; }
+
+void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s) {
   const int b = 256;
   const int nt = nblocks(a.n_total, b);
   const int ntiles = nblocks(a.n_cells, 4096);
-  k_cell_count<<<nt, b, 0, s>>>(a, p, cell_rep);
-  k_scan_tiles<<<ntiles, 1024, 0, s>>>(a, p);
-  k_scan_top<<<1, 1024, 0, s>>>(a, p, ntiles);
-  k_scan_add<<<ntiles, 1024, 0, s>>>(a, p);
+  const int half = mixed ? 0 : 1, lpt = t.lpt;
+  k_cell_count<<<nt, b, 0, s>>>(a, p);
+  if (ntiles <= 16) {
+    k_scan_single<<<1, 1024, 0, s>>>(a, p);
+  } else {
+    k_scan_tiles<<<ntiles, 1024, 0, s>>>(a, p);
+    k_scan_top<<<1, 1024, 0, s>>>(a, p, ntiles);
+    k_scan_add<<<ntiles, 1024, 0, s>>>(a, p);
+  }
   k_scatter<<<nt, b, 0, s>>>(a, p);
   k_permute<<<nt, b, 0, s>>>(a, p);
   k_copyback<<<nt, b, 0, s>>>(a, p);
-  const int lb = t.list_block;
-  const int warps = lb / 32;
-  k_list_build<<<nblocks(a.n_cells, warps), lb, warps * 64 * sizeof(int), s>>>(a, p, cell_rep);
+  k_list_build<<<nblocks(a.n_cells, kListWarps), kListWarps * 32, 0, s>>>(a, p, half, lpt);
+  if (lpt) {
+    k_order_scan<<<1, 1024, 0, s>>>(a, p);
+    k_order_assign<<<nt, b, 0, s>>>(a, p, half);
+  }
+  if (half) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
-void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, const Tuning& t,
-                   cudaStream_t s) {
+template <int TPP>
+void launch_forces_tpp(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
+                       const Tuning& t, cudaStream_t s) {
   const int b = t.force_block;
-  const int g = nblocks(a.n_total, b);
+  const int per_sm = mixed ? t.force_blocks_per_sm_mixed : t.force_blocks_per_sm_fp64;
+  const long long threads = (long long)a.n_total * TPP;
+  const int g = std::min(nblocks(threads, b), std::max(1, t.sm_count * per_sm));
   if (mixed) {
-    if (stats) k_forces_mixed<true><<<g, b, 0, s>>>(a, p);
-    else k_forces_mixed<false><<<g, b, 0, s>>>(a, p);
-  } else {
-    if (stats) k_forces_fp64<true><<<g, b, 0, s>>>(a, p);
-    else k_forces_fp64<false><<<g, b, 0, s>>>(a, p);
+    if (stats) k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+    else if (kick) k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+    else k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+    return;
+  }
+  if (stats) {
+    k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p);
+    return;
+  }
+  k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  const int gb = nblocks((long long)a.n_total * t.gather_tpp, 256);
+  switch (t.gather_tpp) {
+    case 1:
+      if (kick) k_gather<true, 1><<<gb, 256, 0, s>>>(a, p);
+      else k_gather<false, 1><<<gb, 256, 0, s>>>(a, p);
+      break;
+    case 2:
+      if (kick) k_gather<true, 2><<<gb, 256, 0, s>>>(a, p);
+      else k_gather<false, 2><<<gb, 256, 0, s>>>(a, p);
+      break;
+    default:
+      if (kick) k_gather<true, 4><<<gb, 256, 0, s>>>(a, p);
+      else k_gather<false, 4><<<gb, 256, 0, s>>>(a, p);
+      break;
   }
 }
 
-void launch_integrate_second(const Arrays& a, const PotDev& p, cudaStream_t s) {
-  const int b = 256;
-  k_integrate_second<<<nblocks(a.n_total, b), b, 0, s>>>(a, p);
+void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
+                   const Tuning& t, cudaStream_t s) {
+  switch (mixed ? t.tpp_mixed : t.tpp_fp64) {
+    case 1: launch_forces_tpp<1>(a, p, mixed, stats, kick, t, s); break;
+    case 2: launch_forces_tpp<2>(a, p, mixed, stats, kick, t, s); break;
+    case 8: launch_forces_tpp<8>(a, p, mixed, stats, kick, t, s); break;
+    default: launch_forces_tpp<4>(a, p, mixed, stats, kick, t, s); break;
+  }
 }
 
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s) {
-  k_thermo_reduce<<<a.n_reps, 256, 0, s>>>(a, p);
+  k_thermo_partial<<<a.n_reps * a.rep_chunks, 256, 0, s>>>(a);
+  k_thermo_lambda<<<nblocks(a.n_reps, 8), 256, 0, s>>>(a, p);
   const int b = 256;
   k_thermo_scale<<<nblocks(a.n_total, b), b, 0, s>>>(a);
 }
@@ -732,10 +1199,10 @@ void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s) {
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s) {
   const int b = 256;
   k_observe<<<nblocks(a.n_total, b), b, 0, s>>>(a, p);
-  k_rep_sums<<<a.n_reps, 256, 0, s>>>(a, p);
+  k_rep_partial<<<a.n_reps * a.rep_chunks, 256, 0, s>>>(a, p);
+  k_rep_final<<<a.n_reps, 32, 0, s>>>(a, p);
+  k_pore_partial<<<a.n_reps * a.rep_chunks, 256, 0, s>>>(a, p);
+  k_pore_final<<<a.n_reps, 32, 0, s>>>(a);
 }
-
-int kernels_per_step() { return 1 + 8 + 1 + 1 + 2; }
-int kernels_per_rebuild() { return 8; }
 
 }  // namespace mdk

@@ -61,6 +61,9 @@ def check_observables(sim, r, s, st, pot=POT):
     assert o["virial_vv"] == pytest.approx(stats["vir_vv"], rel=1e-10, abs=1e-10)
     assert o["virial_vw"] == pytest.approx(stats["vir_vw"], rel=1e-10, abs=1e-10)
     assert o["ke"] == pytest.approx(oracle.kinetic(p, st.v), rel=1e-12)
+    wv = oracle.molecule_virials(p, st.x, st.wall, nthreads=0)
+    np.testing.assert_allclose(o["pore_pressure"], oracle.pore_pressure(p, s.pores, st.x, st.v, wv),
+                               rtol=1e-9, atol=1e-12)
     return o
 
 
@@ -140,6 +143,7 @@ def test_generated_wall_matches_generator(shapes):
 def test_graph_replay_is_bitwise_identical_to_plain_launches():
     s = W.cylinder_pore_1k()
     with md.Simulation(s) as a, md.Simulation(s) as b:
+        a.set_tuning(use_graph=2)
         b.set_tuning(use_graph=1, steps_per_graph=5)
         a.step(23)
         b.step(23)
@@ -220,10 +224,11 @@ def test_edge_cases_batch_empty_single_and_wall_free():
             assert prof.sum() == s.n_vapor
 
 
-def test_list_overflow_is_reported():
+@pytest.mark.parametrize("precision", [md.MD_PREC_FP64, md.MD_PREC_MIXED])
+def test_list_overflow_is_reported(precision):
     s = W.cylinder_pore_1k()
     with pytest.raises(md.MDError) as ei:
-        md.Simulation(s, max_neighbors=2)
+        md.Simulation(s, precision=precision, max_neighbors=2, max_wall_neighbors=2)
     assert ei.value.status == md.MD_EOVERFLOW
 
 
@@ -261,8 +266,13 @@ def test_mixed_precision_force_error_small_cylinder():
     s = W.cylinder_pore_1k()
     with md.Simulation(s, precision=md.MD_PREC_MIXED) as sim:
         f = sim.forces()
-        g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+        g, d2, stats = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
         assert rms_rel_err(f, g) <= 1e-5
+        # borderline cutoffs and wall distances are decided in FP64: integer results are exact
+        o, occ, ads, prof = sim.observables()
+        assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+        _, ads_o, _ = oracle.observables(oracle_params(s), s.pores, s.x0, d2)
+        np.testing.assert_array_equal(ads, ads_o)
         st = oracle.State(oracle_params(s), s.x0, s.v0, s.wall)
         errs = []
         for _ in range(10):
@@ -279,6 +289,39 @@ def test_mixed_precision_four_shapes(shapes):
         for r, s in enumerate(shapes):
             g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
             assert rms_rel_err(sim.forces(r), g) <= 1e-5, s.name
+
+
+def test_mixed_precision_error_after_equilibration(shapes):
+    """Hundreds of steps in (condensed, adsorbed layers): the mixed RMS force error against the
+    oracle at the mixed run's own positions stays below 1e-5."""
+    with md.Simulation(shapes, precision=md.MD_PREC_MIXED) as sim:
+        sim.set_tuning(use_graph=1, steps_per_graph=10)
+        sim.step(300)
+        for r, s in enumerate(shapes):
+            x, _ = sim.state(r)
+            g, _, stats = oracle.forces(oracle_params(s), x, s.wall, method=1)
+            assert rms_rel_err(sim.forces(r), g) <= 1e-5, s.name
+            o, *_ = sim.observables(r)
+            assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+
+
+def test_graph_with_conditional_rebuilds_matches_plain_launches_fp64_long():
+    shapes4 = W.pore_shape_systems_20k()
+    with md.Simulation(shapes4) as a, md.Simulation(shapes4) as b:
+        a.set_tuning(use_graph=2)
+        b.set_tuning(use_graph=1, steps_per_graph=7)
+        a.step(70)
+        b.step(70)
+        oa, *_ = a.observables(0)
+        ob, *_ = b.observables(0)
+        assert oa["n_rebuilds"] == ob["n_rebuilds"] > 1
+        for r in range(4):
+            xa, va = a.state(r)
+            xb, vb = b.state(r)
+            np.testing.assert_array_equal(xa, xb)
+            np.testing.assert_array_equal(va, vb)
+        # skipped conditional branches launch nothing
+        assert b.kernel_launches() < a.kernel_launches()
 
 
 # ------------------------------------------------------------------------------------------ large

@@ -1,0 +1,124 @@
+"""GPU parity on the batched and large workloads, and the autotuner.
+
+* an uneven batch of pore systems (the four shapes, radii 2-10, 1,000-20,000 molecules, T* in
+  [0.8, 1.2]) in one context: forces per replica (FP64 <= 1e-10 max/RMS, mixed RMS <= 1e-5),
+  trajectories and observables;
+* the 400 x 400 x 200 array of 16 pores with 2,000,000 molecules and ~6.2 M wall atoms: every
+  force against the oracle, pair counts and the per-pore observables;
+* the autotuner leaves positions unchanged and forces within tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1812_07993_gb300 as md
+from paper_1812_07993_gb300 import autotune
+from paper_1812_07993_gb300 import build as mdbuild
+from paper_1812_07993_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POT = W.Potential()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mdbuild.build()
+    md.load_library()
+
+
+def force_err(f, g):
+    return np.abs(f - g).max() / np.sqrt((g ** 2).sum(1).mean())
+
+
+def rms_rel_err(f, g):
+    return np.sqrt(((f - g) ** 2).sum() / (g ** 2).sum())
+
+
+def wrapped_diff(a, b, s):
+    d = a - b
+    d[:, 0] -= s.Lx * np.round(d[:, 0] / s.Lx)
+    d[:, 1] -= s.Ly * np.round(d[:, 1] / s.Ly)
+    return d
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return W.replica_batch(n_replicas=12, n_max=20000)
+
+
+def test_uneven_batch_forces_and_trajectories(batch):
+    params = [oracle.make_params(s, POT) for s in batch]
+    states = [oracle.State(p, s.x0, s.v0, s.wall, nthreads=0) for p, s in zip(params, batch)]
+    with md.Simulation(batch) as sim:
+        for r, (s, st) in enumerate(zip(batch, states)):
+            assert force_err(sim.forces(r), st.f) <= 1e-10, s.name
+        sim.step(10)
+        for r, (s, st, p) in enumerate(zip(batch, states, params)):
+            st.run(10)
+            x, v = sim.state(r)
+            assert np.abs(wrapped_diff(x, st.x, s)).max() <= 1e-8, s.name
+            assert np.abs(v - st.v).max() <= 1e-8, s.name
+            o, occ, ads, prof = sim.observables(r)
+            g, d2, stats = oracle.forces(p, st.x, s.wall, method=1, nthreads=0)
+            occ_o, ads_o, prof_o = oracle.observables(p, s.pores, st.x, d2)
+            assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+            np.testing.assert_array_equal(occ, occ_o)
+            np.testing.assert_array_equal(ads, ads_o)
+            np.testing.assert_array_equal(prof, prof_o)
+
+
+def test_uneven_batch_mixed_precision(batch):
+    with md.Simulation(batch, precision=md.MD_PREC_MIXED) as sim:
+        sim.step(20)
+        for r, s in enumerate(batch):
+            x, _ = sim.state(r)
+            g, _, _ = oracle.forces(oracle.make_params(s, POT), x, s.wall, method=1, nthreads=0)
+            assert rms_rel_err(sim.forces(r), g) <= 1e-5, s.name
+
+
+@pytest.mark.parametrize("precision,tol", [(md.MD_PREC_FP64, 1e-10), (md.MD_PREC_MIXED, 1e-5)])
+def test_pore_array_2m_every_force_and_per_pore_observables(precision, tol):
+    s = W.pore_array_2m()
+    p = oracle.make_params(s, POT)
+    g, d2, stats = oracle.forces(p, s.x0, s.wall, method=1, nthreads=0)
+    with md.Simulation(s, precision=precision) as sim:
+        f = sim.forces()
+        o, occ, ads, prof = sim.observables()
+    err = force_err(f, g) if precision == md.MD_PREC_FP64 else rms_rel_err(f, g)
+    assert err <= tol
+    assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+    occ_o, ads_o, prof_o = oracle.observables(p, s.pores, s.x0, d2)
+    assert len(occ) == 16
+    wv = oracle.molecule_virials(p, s.x0, s.wall, nthreads=0)
+    P_o = oracle.pore_pressure(p, s.pores, s.x0, s.v0, wv)
+    np.testing.assert_allclose(o["pore_pressure"], P_o,
+                               rtol=1e-9 if precision == md.MD_PREC_FP64 else 1e-4, atol=1e-12)
+    np.testing.assert_array_equal(occ, occ_o)
+    np.testing.assert_array_equal(ads, ads_o)
+    np.testing.assert_array_equal(prof, prof_o)
+
+
+@pytest.mark.parametrize("precision", [md.MD_PREC_FP64, md.MD_PREC_MIXED])
+def test_autotune_keeps_state_and_forces(precision, tmp_path):
+    shapes = W.pore_shape_systems_20k()
+    with md.Simulation(shapes, precision=precision) as sim:
+        sim.step(30)
+        x0, v0 = sim.state(1)
+        res = autotune.tune(sim, trials=3, cache_path=str(tmp_path / "t.json"))
+        t = res["tuning"]
+        assert t["force_tpp"] in (1, 2, 4, 8) and 1 <= t["force_blocks_per_sm"] <= 8
+        assert t["force_block"] in (128, 256) and t["order_by_length"] in (1, 2)
+        assert res["us"] > 0 and not res["cached"]
+        x1, v1 = sim.state(1)
+        np.testing.assert_array_equal(x0, x1)
+        np.testing.assert_array_equal(v0, v1)
+        g, _, _ = oracle.forces(oracle.make_params(shapes[1], POT), x1, shapes[1].wall, method=1)
+        f = sim.forces(1)
+        if precision == md.MD_PREC_FP64:
+            assert force_err(f, g) <= 1e-10
+        else:
+            assert rms_rel_err(f, g) <= 1e-5
+        again = autotune.tune(sim, cache_path=str(tmp_path / "t.json"))
+        assert again["cached"] and again["tuning"] == t
+        sim.step(5)

@@ -34,6 +34,8 @@ def _pin_suite():
         ("periodic_axis", pins.test_pore_offset_axis_and_periodic_image),
         ("adsorbed", pins.test_adsorbed_threshold_and_group_assignment),
         ("bins", pins.test_profile_bin_edges),
+        ("pore_volume", pins.test_pore_volume_closed_forms_and_monte_carlo),
+        ("pressure", pins.test_pore_pressure_kinetic_and_pair_terms),
     ]
 
 
@@ -60,6 +62,10 @@ MUTATIONS = {
     "ink-bottle cavity dropped": ("|| rxy2 + z * z < q->r_cavity * q->r_cavity", "&& rxy2 + z * z < q->r_cavity * q->r_cavity"),
     "adsorbed threshold not squared": ("d2wall[i] < p->r_ads * p->r_ads", "d2wall[i] < p->r_ads"),
     "bins offset by half the box the wrong way": ("floor((zi + 0.5 * p->Lz) / p->bin_width)", "floor((zi - 0.5 * p->Lz) / p->bin_width)"),
+    "pressure drops the kinetic term": ("sum += p->mass * (v[3 * i] * v[3 * i]", "sum += 0.0 * (v[3 * i] * v[3 * i]"),
+    "molecule virial double-counts vapour pairs": ("if (wvir) wvir[i] = acc[i].vir_vv + acc[i].vir_vw;", "if (wvir) wvir[i] = 2.0 * acc[i].vir_vv + acc[i].vir_vw;"),
+    "cone volume uses the radius, not its square": ("return M_PI * R * R;", "return M_PI * R;"),
+    "ink-bottle area takes the smaller disc": ("return M_PI * (c > n2 ? c : n2);", "return M_PI * (c < n2 ? c : n2);"),
     "axis distance ignores periodicity": ("double dx = min_image(xi - pores[q].cx, p->Lx), dy = min_image(yi - pores[q].cy, p->Ly);",
                                           "double dx = xi - pores[q].cx, dy = yi - pores[q].cy;"),
 }

@@ -401,3 +401,54 @@ def test_ideal_gas_occupancy_and_flat_profile():
     expected = n / prof.shape[1]
     chi2 = ((prof[0] - expected) ** 2 / expected).sum()
     assert chi2 < prof.shape[1] + 6 * math.sqrt(2 * prof.shape[1])
+
+
+# ---------------------------------------------------------------- Sec. 2: virial pressure per pore
+
+
+def test_pore_volume_closed_forms_and_monte_carlo():
+    p = P(Lx=40.0, Ly=40.0, Lz=60.0, slab_half=10.0)
+    cyl = W.Pore(W.PORE_CYLINDER, r0=5.0)
+    cone = W.Pore(W.PORE_CONE, r0=3.0, r1=8.0)
+    slit = W.Pore(W.PORE_SLIT, width=6.0)
+    ink = W.Pore(W.PORE_INKBOTTLE, r0=3.0, r_cavity=8.0)
+    assert oracle.pore_volume(p, cyl) == pytest.approx(math.pi * 25 * 20, rel=1e-12)
+    assert oracle.pore_volume(p, cone) == pytest.approx(math.pi / 3 * 20 * (9 + 24 + 64), rel=1e-12)
+    assert oracle.pore_volume(p, slit) == pytest.approx(6.0 * 40.0 * 20.0, rel=1e-12)
+    # ink-bottle: neck cylinder plus the part of the sphere outside it (Monte Carlo, independent)
+    rng = np.random.default_rng(5)
+    n = 2_000_000
+    pts = np.stack([rng.uniform(-9, 9, n), rng.uniform(-9, 9, n), rng.uniform(-10, 10, n)], 1)
+    inside = W.carve_mask(pts, ink, 40.0, 40.0, 10.0)
+    mc = inside.mean() * 18 * 18 * 20
+    assert oracle.pore_volume(p, ink) == pytest.approx(mc, rel=5e-3)
+
+
+def test_pore_pressure_kinetic_and_pair_terms():
+    L, h = 20.0, 5.0
+    pore = W.Pore(W.PORE_CYLINDER, r0=4.0)
+    p = P(Lx=L, Ly=L, Lz=40.0, slab_half=h)
+    V = math.pi * 16 * 2 * h
+    # one molecule moving inside the pore, nothing to interact with: P = m v^2 / (3 V)
+    x = np.array([[0.5, 0.0, 1.0]])
+    v = np.array([[0.3, -1.2, 0.7]])
+    wv = oracle.molecule_virials(p, x, None)
+    assert oracle.pore_pressure(p, [pore], x, v, wv)[0] == pytest.approx(
+        (0.09 + 1.44 + 0.49) / (3 * V), rel=1e-13)
+    # two molecules at rest, both in the pore: P = r F(r) / (3 V); one outside: its half is dropped
+    r = 1.1
+    x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    wv = oracle.molecule_virials(p, x, None)
+    rF = 24.0 * (2 * r ** -12 - r ** -6)
+    assert wv.sum() == pytest.approx(rF, rel=1e-13)
+    assert oracle.pore_pressure(p, [pore], x, np.zeros_like(x), wv)[0] == pytest.approx(
+        rF / (3 * V), rel=1e-13)
+    x2 = np.array([[0.0, 0.0, 4.6], [0.0, 0.0, 4.6 + r]])   # second molecule above the slab
+    wv2 = oracle.molecule_virials(p, x2, None)
+    assert oracle.pore_pressure(p, [pore], x2, np.zeros_like(x2), wv2)[0] == pytest.approx(
+        0.5 * rF / (3 * V), rel=1e-13)
+    # a wall atom acts on the molecule only, fully counted
+    wall = np.array([[1.3, 0.0, 0.0]])
+    x3 = np.array([[0.0, 0.0, 0.0]])
+    wv3 = oracle.molecule_virials(p, x3, wall)
+    assert wv3[0] == pytest.approx(1.5 * 24.0 * (2 * 1.3 ** -12 - 1.3 ** -6), rel=1e-13)
