@@ -358,6 +358,10 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
     c->own_stream = true;
   }
+  {
+    const cudaError_t e = configure_kernels();
+    if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
+  }
   c->n_reps = n_reps;
   c->mixed = pot->precision == MD_PREC_MIXED;
 
@@ -668,8 +672,9 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     else nt.force_blocks_per_sm_fp64 = t->force_blocks_per_sm;
   }
   if (t->force_tpp) {
-    if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8)
-      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4 or 8");
+    if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8 &&
+        !(t->force_tpp == 32 && !c->mixed))
+      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4 or 8 (or 32 at FP64)");
     if (c->mixed) nt.tpp_mixed = t->force_tpp;
     else nt.tpp_fp64 = t->force_tpp;
   }
@@ -715,12 +720,13 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   Tuning bestT = saved;
   double bestv = 1e300;
   md_status st = MD_OK;
-  const int tpps[4] = {1, 2, 4, 8}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
+  const int tpps[5] = {1, 2, 4, 8, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
   for (int lpt = 1; lpt >= 0 && st == MD_OK; --lpt) {
     c->tun = saved;
     c->tun.lpt = lpt;
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
-    for (int tp : tpps)
+    for (int tp : tpps) {
+      if (tp == 32 && c->mixed) continue;  // the packed kernel is the FP64 path's
       for (int bp : bpss)
         for (int bk : blocks) {
           Tuning t = c->tun;
@@ -751,6 +757,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
             bestT = t;
           }
         }
+    }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (st != MD_OK) {

@@ -137,7 +137,8 @@ struct Tuning {
   int force_block = 256;
   int force_blocks_per_sm_fp64 = 1;   // resident blocks per SM of the pair kernels (grid size)
   int force_blocks_per_sm_mixed = 4;
-  int tpp_fp64 = 2;                   // lanes sharing one molecule's list in the pair kernels
+  int tpp_fp64 = 2;                   // lanes sharing one molecule's list in the pair kernels;
+                                      // 32: the FP64 packed kernel (lanes share packed pairs)
   int tpp_mixed = 4;
   int gather_tpp = 2;                 // lanes per molecule in the FP64 reverse gather
   int lpt = 1;                        // process molecules longest list first
@@ -174,6 +175,7 @@ void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const 
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
+cudaError_t configure_kernels();
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s);
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);

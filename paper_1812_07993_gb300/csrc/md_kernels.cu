@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
     a.pos[i] = x;
     a.vel[i] = v;
-    if (MIXED) a.lpos[i] = local_offset(R, x, a.home[i]);
+    a.lpos[i] = local_offset(R, x, a.home[i]);  // FP32 screens of both pair kernels
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
@@ -328,21 +328,64 @@ __global__ void __launch_bounds__(1024) k_scan_add(Arrays a, PotDev p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
 }
 
-// the whole cell scan in one block (small grids): tile after tile with a running carry
+// the whole cell scan in one block (at most 16 x 4096 cells): each thread owns a contiguous
+// segment of whole int4s, sums it, takes its exclusive offset from a block scan of the sums and
+// writes its segment; every load is issued up front, one round trip to memory per pass
 __global__ void __launch_bounds__(1024) k_scan_single(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
-  int carry = 0;
-  for (int base = 0; base < a.n_cells; base += 4096) {
-    const int tot = tile_exclusive_scan(a.vcount, a.vstart, a.n_cells, base);
-    for (int k = threadIdx.x; k < 4096; k += blockDim.x) {
-      const int idx = base + k;
-      if (idx < a.n_cells) a.vstart[idx] += carry;
+  __shared__ int warp_tot[32];
+  const int n = a.n_cells, t = threadIdx.x;
+  const int S = (((n + 1023) >> 10) + 3) & ~3;
+  const int b0 = min(t * S, n), b1 = min(b0 + S, n);
+  const int* __restrict__ in = a.vcount;
+  int sum = 0;
+  for (int k = b0; k < b1; k += 4) {
+    if (k + 3 < b1) {
+      const int4 v = *reinterpret_cast<const int4*>(in + k);
+      sum += v.x + v.y + v.z + v.w;
+    } else {
+      for (int u = k; u < b1; ++u) sum += in[u];
     }
-    carry += tot;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    const int w = warp_tot[t];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, wi, o);
+      if (t >= o) wi += y;
+    }
+    warp_tot[t] = wi - w;
+  }
+  __syncthreads();
+  int run = warp_tot[t >> 5] + incl - sum;
+  for (int k = b0; k < b1; k += 4) {
+    if (k + 3 < b1) {
+      const int4 v = *reinterpret_cast<const int4*>(in + k);
+      int4 o;
+      o.x = run;
+      o.y = o.x + v.x;
+      o.z = o.y + v.y;
+      o.w = o.z + v.z;
+      run = o.w + v.w;
+      *reinterpret_cast<int4*>(a.vstart + k) = o;
+    } else {
+      for (int u = k; u < b1; ++u) {
+        a.vstart[u] = run;
+        run += in[u];
+      }
+    }
+  }
+  if (t == 0) a.vstart[n] = a.n_total;
 }
 
 __global__ void k_scatter(Arrays a, PotDev p) {
@@ -418,8 +461,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
-  __shared__ float4 sh_li[kListWarps][64];
-  __shared__ int sh_f[kListWarps][64], sh_b[kListWarps][64];
+  __shared__ float4 sh_li[kListWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
@@ -450,15 +492,12 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   const int N = a.n_total, cap = p.cap;
   uint32_t* stream = sh_stream[w];
   int max_n = 0;
-  for (int ib = i_begin; ib < i_end; ib += 64) {
-    const int nic = min(64, i_end - ib);
-    // the molecules of this group: offsets and front / back counts in shared memory
-    for (int q = lane; q < 64; q += 32) {
-      sh_li[w][q] = q < nic ? a.lpos[ib + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      sh_f[w][q] = 0;
-      sh_b[w][q] = 0;
-    }
-    int vh0 = 0, vh1 = 0;
+  for (int ib = i_begin; ib < i_end; ib += 32) {
+    const int nic = min(32, i_end - ib);
+    // the molecules of this group: FP32 offsets in shared memory; lane il keeps molecule il's
+    // front and back counts in registers
+    sh_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int cf = 0, cb = 0, vh = 0;
     __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
       const bool wallpass = pass == 1;
@@ -498,35 +537,30 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
             const bool back = hit && !front;
             const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
             if (bf | bb) {
+              const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
               if (front) {
-                const int slot = sh_f[w][il] + __popc(bf & lt);
+                const int slot = f0 + __popc(bf & lt);
                 if (slot < cap) a.nbr[(size_t)i * cap + slot] = entry;
               } else if (back) {
-                const int slot = cap - 1 - (sh_b[w][il] + __popc(bb & lt));
+                const int slot = cap - 1 - (b0 + __popc(bb & lt));
                 if (slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
               }
-              __syncwarp();
-              if (lane == 0) {
-                sh_f[w][il] += __popc(bf);
-                sh_b[w][il] += __popc(bb);
+              if (lane == il) {
+                cf += __popc(bf);
+                cb += __popc(bb);
               }
-              __syncwarp();
             }
           }
         }
         __syncwarp();
       }
-      if (!wallpass) {
-        vh0 = sh_f[w][lane];
-        vh1 = sh_f[w][lane + 32];
-      }
+      if (!wallpass) vh = cf;
     }
     // counts, overflow, processing-order histogram
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int i = ib + g * 32 + lane;
-      const bool own = g * 32 + lane < nic;
-      const int nf = sh_f[w][g * 32 + lane], nb = sh_b[w][g * 32 + lane], nvh = g ? vh1 : vh0;
+    {
+      const int i = ib + lane;
+      const bool own = lane < nic;
+      const int nf = cf, nb = cb, nvh = vh;
       if (own) {
         if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
           atomicOr(a.status, kStatusOverflow);
@@ -748,6 +782,143 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
     fy = group_sum<TPP>(fy);
     fz = group_sum<TPP>(fz);
     if (live && sub == 0) a.fpart[i] = make_dvec4(fx, fy, fz, 0.0);
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
+// FP64, half list, packed: a warp owns 32 molecules (one lane each). Per window of kPackT list
+// slots, an FP32 screen on the cell-local offsets drops the entries that are surely beyond the
+// cutoff (FP32 r^2 at or above rc^2 (1 + 1e-5); the FP32 error is ~1e-7 of rc^2) and packs the
+// others, molecule after molecule, into a per-warp queue; the FP64 pair terms then run over the
+// queue with every lane busy, whatever the lanes' hit counts; finally each lane adds its own
+// molecule's pair forces in list order (deterministic). Dropped vapour slots store a zero force
+// for the partner's gather.
+constexpr int kPackT = 8;
+constexpr int kPackCap = 32 * kPackT;
+
+struct PackWarp {
+  dvec4 xi[32];                              // FP64 positions of the warp's molecules
+  double rx[kPackCap], ry[kPackCap], rz[kPackCap];
+  uint32_t qe[kPackCap];                     // list entry of each packed slot
+  int32_t mi[32], mv[32], mr[32];            // molecule, vapour front length, replica
+  uint16_t qmk[kPackCap];                    // (owner lane << 10) | list slot
+};
+
+__global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, int lpt) {
+  extern __shared__ __align__(32) unsigned char pack_smem[];
+  PackWarp& S = reinterpret_cast<PackWarp*>(pack_smem)[threadIdx.x >> 5];
+  count_launch(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.force_rebuild = 0;
+  }
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap, capv = p.cap_v;
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  for (int chunk = next_chunk<32>(a); chunk >= 0; chunk = next_chunk<32>(a)) {
+    const int t = chunk * 32 + lane;
+    const bool live = t < N;
+    int i = 0, n = 0, nvh = 0, r = 0;
+    float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      n = a.n_front[i];
+      nvh = a.n_vh[i];
+      r = a.rep[i];
+      li = a.lpos[i];
+      S.xi[lane] = a.pos[i];
+    }
+    S.mi[lane] = i;
+    S.mv[lane] = nvh;
+    S.mr[lane] = r;
+    const RepDev& R = a.reps[r];
+    const float lcx = R.lcxf, lcy = R.lcyf, lcz = R.lczf;
+    const int nmax = __reduce_max_sync(kFull, n);
+    const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+    const uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    __syncwarp();
+    for (int t0 = 0; t0 < nmax; t0 += kPackT) {
+      // FP32 screen of the lane's own slots t0 .. t0 + kPackT - 1
+      uint32_t e[kPackT];
+      unsigned hm = 0;
+#pragma unroll
+      for (int s = 0; s < kPackT; ++s) {
+        const int k = t0 + s;
+        e[s] = 0u;
+        if (k < n) {
+          e[s] = row[k];
+          const int j = (int)(e[s] & kIndexMask);
+          const bool wall = j >= N;
+          const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
+          const float dx = (li.x - b.x) - (float)((int)((e[s] >> 26) & 3u) - 1) * lcx;
+          const float dy = (li.y - b.y) - (float)((int)((e[s] >> 28) & 3u) - 1) * lcy;
+          const float dz = (li.z - b.z) - (float)((int)(e[s] >> 30) - 1) * lcz;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < (wall ? p.rcw2f_hi : p.rc2f_hi)) hm |= 1u << s;
+          else if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        }
+      }
+      // pack: the lane's survivors go to [seg, seg + c) of the queue, in slot order
+      const int c = __popc(hm);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int Q = __shfl_sync(kFull, incl, 31);
+      const int seg = incl - c;
+      int q = seg;
+#pragma unroll
+      for (int s = 0; s < kPackT; ++s) {
+        if ((hm >> s) & 1u) {
+          S.qe[q] = e[s];
+          S.qmk[q] = (uint16_t)((lane << 10) | (t0 + s));
+          ++q;
+        }
+      }
+      __syncwarp();
+      // FP64 pair terms over the queue: every lane takes a packed entry of any molecule
+      for (int u = lane; u < Q; u += 32) {
+        const uint32_t en = S.qe[u];
+        const int mk = S.qmk[u];
+        const int m = mk >> 10, k = mk & 1023;
+        const dvec4 xm = S.xi[m];
+        const RepDev& Rm = a.reps[S.mr[m]];
+        const int j = (int)(en & kIndexMask);
+        const bool wall = j >= N;
+        const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+        const double dx = image_hi(xm.x - xj.x, Rm.Lx, Rm.hi_thr_x);
+        const double dy = image_hi(xm.y - xj.y, Rm.Ly, Rm.hi_thr_y);
+        const double dz = xm.z - xj.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
+        const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+        const double inv2 = rcp_nr(r2);
+        const double inv6 = inv2 * inv2 * inv2;
+        const double fr = in ? inv2 * inv6 * fma(a12, inv6, -b6) : 0.0;
+        const double px = fr * dx, py = fr * dy, pz = fr * dz;
+        S.rx[u] = px;
+        S.ry[u] = py;
+        S.rz[u] = pz;
+        if (!wall && k < S.mv[m])
+          a.pairbuf[a.fwd[(size_t)S.mi[m] * capv + k]] = make_dvec4(px, py, pz, 0.0);
+        cnt += in ? 1 : 0;
+      }
+      __syncwarp();
+      // the lane's own molecule, in list order
+      for (int u = seg; u < seg + c; ++u) {
+        fx += S.rx[u];
+        fy += S.ry[u];
+        fz += S.rz[u];
+      }
+      __syncwarp();
+    }
+    if (live) a.fpart[i] = make_dvec4(fx, fy, fz, 0.0);
+    __syncwarp();
   }
   const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
   if (lane == 0 && c) atomicAdd(a.pair_count, c);
@@ -1144,24 +1315,34 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   if (half) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
+// grid of the pair kernels: at most SMs x blocks per SM; warps fetch chunks of molecules
+int pair_grid(long long threads, int block, int per_sm, const Tuning& t) {
+  return std::min(nblocks(threads, block), std::max(1, t.sm_count * per_sm));
+}
+
 template <int TPP>
-void launch_forces_tpp(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
-                       const Tuning& t, cudaStream_t s) {
+void launch_mixed(const Arrays& a, const PotDev& p, bool stats, bool kick, const Tuning& t,
+                  cudaStream_t s) {
   const int b = t.force_block;
-  const int per_sm = mixed ? t.force_blocks_per_sm_mixed : t.force_blocks_per_sm_fp64;
-  const long long threads = (long long)a.n_total * TPP;
-  const int g = std::min(nblocks(threads, b), std::max(1, t.sm_count * per_sm));
-  if (mixed) {
-    if (stats) k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-    else if (kick) k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-    else k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-    return;
+  const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_mixed, t);
+  if (stats) k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  else if (kick) k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  else k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+}
+
+// FP64: half-list pass (TPP lanes per molecule, or the packed kernel for TPP = 32), then the
+// gather (with the second half-kick when KICK)
+template <int TPP>
+void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cudaStream_t s) {
+  const int b = t.force_block;
+  const int per_sm = t.force_blocks_per_sm_fp64;
+  if constexpr (TPP == 32) {
+    const size_t sm = (size_t)(b / 32) * sizeof(PackWarp);
+    k_forces_half_packed<<<pair_grid(a.n_total, b, per_sm, t), b, sm, s>>>(a, p, t.lpt);
+  } else {
+    k_forces_half<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0, s>>>(a, p,
+                                                                                       t.lpt);
   }
-  if (stats) {
-    k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p);
-    return;
-  }
-  k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
   const int gb = nblocks((long long)a.n_total * t.gather_tpp, 256);
   switch (t.gather_tpp) {
     case 1:
@@ -1181,12 +1362,32 @@ void launch_forces_tpp(const Arrays& a, const PotDev& p, bool mixed, bool stats,
 
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s) {
-  switch (mixed ? t.tpp_mixed : t.tpp_fp64) {
-    case 1: launch_forces_tpp<1>(a, p, mixed, stats, kick, t, s); break;
-    case 2: launch_forces_tpp<2>(a, p, mixed, stats, kick, t, s); break;
-    case 8: launch_forces_tpp<8>(a, p, mixed, stats, kick, t, s); break;
-    default: launch_forces_tpp<4>(a, p, mixed, stats, kick, t, s); break;
+  if (mixed) {
+    switch (t.tpp_mixed) {
+      case 1: launch_mixed<1>(a, p, stats, kick, t, s); break;
+      case 2: launch_mixed<2>(a, p, stats, kick, t, s); break;
+      case 8: launch_mixed<8>(a, p, stats, kick, t, s); break;
+      default: launch_mixed<4>(a, p, stats, kick, t, s); break;
+    }
+    return;
   }
+  if (stats) {  // FP64 observables: a full-row pass that leaves the forces untouched
+    k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p);
+    return;
+  }
+  switch (t.tpp_fp64) {
+    case 1: launch_fp64<1>(a, p, kick, t, s); break;
+    case 2: launch_fp64<2>(a, p, kick, t, s); break;
+    case 8: launch_fp64<8>(a, p, kick, t, s); break;
+    case 32: launch_fp64<32>(a, p, kick, t, s); break;
+    default: launch_fp64<4>(a, p, kick, t, s); break;
+  }
+}
+
+// one-time kernel attributes (before any launch or capture)
+cudaError_t configure_kernels() {
+  return cudaFuncSetAttribute(k_forces_half_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(8 * sizeof(PackWarp)));
 }
 
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s) {

@@ -131,6 +131,33 @@ def test_four_pore_shapes_batched_trajectory_and_observables(shapes):
             check_observables(sim, r, s, st)
 
 
+@pytest.fixture(scope="module")
+def shapes_after_ten(shapes):
+    states = [oracle.State(oracle_params(s), s.x0, s.v0, s.wall) for s in shapes]
+    for st in states:
+        st.run(10)
+    return states
+
+
+@pytest.mark.parametrize("tpp,block,lpt", [(1, 128, 1), (2, 256, 1), (4, 128, 2), (8, 256, 1),
+                                           (32, 128, 1), (32, 256, 1), (32, 128, 2)])
+def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, lpt):
+    """Every pair-kernel variant (lanes per molecule, the packed kernel, block size, processing
+    order) gives the oracle's forces and 10-step trajectories, pair counts and observables."""
+    with md.Simulation(shapes) as sim:
+        sim.set_tuning(force_tpp=tpp, force_block=block, force_blocks_per_sm=2, order_by_length=lpt)
+        sim.compute_forces()
+        for r, s in enumerate(shapes):
+            g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            assert force_err(sim.forces(r), g) <= FORCE_TOL, s.name
+        sim.step(10)
+        for r, (s, st) in enumerate(zip(shapes, shapes_after_ten)):
+            x, v = sim.state(r)
+            assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL, s.name
+            assert np.abs(v - st.v).max() <= TRAJ_TOL, s.name
+            check_observables(sim, r, s, st)
+
+
 def test_generated_wall_matches_generator(shapes):
     with md.Simulation(shapes, generate_wall=True) as sim:
         for r, s in enumerate(shapes):
