@@ -83,6 +83,9 @@ WORKLOADS = {
                           "N log-uniform [1k,50k], T*~U[0.8,1.2], density 0.02 outside |z|<8"),
     "pore_array_2m": ("400x400x200 box, 4x4 pores (cylinder/cone/ink-bottle, R~U[4,10]) in slab "
                       "|z|<20, 2,000,000 vapour, T*=0.85"),
+    "drying_pore_6k": ("drying of a filled pore: 40x40x80 box, slab |z|<10, cylinder r8 holding "
+                       "1,000 molecules, 4,800 outside at a fifth of that density, T*=1.0, "
+                       "Berendsen tau_B=0.5"),
 }
 
 
@@ -96,6 +99,8 @@ def make_workload(name: str):
         return W.replica_batch(256), name
     if name == "pore_array_2m":
         return [W.pore_array_2m()], name
+    if name == "drying_pore_6k":
+        return [W.drying_cylinder_pore()], name
     return W.pore_shape_systems_20k(), "pore_shapes_4x20k"
 
 

@@ -122,6 +122,12 @@ typedef struct {
   int32_t order_by_length; /* 1: process molecules longest list first; 2: in cell order */
   int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 2: plain launches */
   int32_t steps_per_graph; /* MD steps captured per graph replay */
+  int32_t force_accumulate; /* FP64 only. 1: deterministic -- each vapour pair's force is stored
+                              in the partner's slot and every molecule sums its slots in list
+                              order (bit-for-bit reproducible); 2: the reaction forces go to the
+                              partners by FP64 atomic adds (no gather; the summation order varies
+                              from run to run, so results agree with mode 1 to rounding only).
+                              Changing it rebuilds the lists (synchronises). */
 } md_tuning;
 
 typedef struct {

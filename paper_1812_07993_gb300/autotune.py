@@ -43,7 +43,7 @@ def tune(sim: Simulation, trials: int = 15, cache_path: Optional[str] = None,
     """Apply the cached launch shape of the simulation's size class, or run ``md_autotune`` and
     cache its choice. Returns {"tuning": ..., "us": ..., "cached": bool, "seconds": ...}."""
     path = cache_path or default_cache_path()
-    key = size_class(sim.systems, sim.precision)
+    key = size_class(sim.systems, sim.precision) + f"-acc{sim.tuning()['force_accumulate']}"
     cache = _load(path) if use_cache else {}
     t0 = time.perf_counter()
     if key in cache:

@@ -236,10 +236,13 @@ md_status sync_status(md_ctx* c) {
   return MD_OK;
 }
 
+// the FP64 atomic pair pass adds into the forces: k_integrate_first clears them after its kick
+bool zero_forces(const md_ctx* c) { return !c->mixed && c->tun.atomic_acc; }
+
 // One step with plain launches: the rebuild and thermostat kernels always launch and return at
 // once when the device decides they have nothing to do.
 void enqueue_step(md_ctx* c) {
-  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, c->stream);
+  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, zero_forces(c), c->stream);
   launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
   launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
   launch_thermostat(c->a, c->pot, c->stream);
@@ -308,7 +311,7 @@ md_status build_graph(md_ctx* c, int steps) {
     if (e == cudaSuccess)
       e = cudaGraphConditionalHandleCreate(&sc.thermo, g, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) break;
-    launch_integrate_first(c->a, c->pot, c->mixed, sc, c->stream);
+    launch_integrate_first(c->a, c->pot, c->mixed, sc, zero_forces(c), c->stream);
     e = add_conditional(c, g, sc.rebuild, [&](cudaStream_t s) {
       launch_rebuild(c->a, c->pot, c->tun, c->mixed, s);
     });
@@ -683,8 +686,17 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->use_graph < 0 || t->use_graph > 2)
     return fail(c, MD_EINVAL, "use_graph must be 0 (keep), 1 (graph) or 2 (plain launches)");
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
-  const bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
+  if (t->force_accumulate < 0 || t->force_accumulate > 2)
+    return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
+  if (c->mixed && t->force_accumulate == 2)
+    return fail(c, MD_EINVAL, "atomic accumulation is an FP64-path option");
+  const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
+  if (at && nt.tpp_fp64 == 32)
+    return fail(c, MD_EINVAL, "the packed kernel (force_tpp 32) has no atomic form");
+  bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
+  relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
+  nt.atomic_acc = at;
   c->tun = nt;
   if (t->use_graph) c->use_graph = t->use_graph == 1 ? 1 : 0;
   if (t->steps_per_graph) c->steps_per_graph = t->steps_per_graph;
@@ -702,6 +714,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->order_by_length = c->tun.lpt ? 1 : 2;
   t->use_graph = c->use_graph ? 1 : 2;
   t->steps_per_graph = c->steps_per_graph;
+  t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
   return MD_OK;
 }
 
@@ -726,7 +739,8 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     c->tun.lpt = lpt;
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
     for (int tp : tpps) {
-      if (tp == 32 && c->mixed) continue;  // the packed kernel is the FP64 path's
+      // the packed kernel is the FP64 path's, in its deterministic form
+      if (tp == 32 && (c->mixed || c->tun.atomic_acc)) continue;
       for (int bp : bpss)
         for (int bk : blocks) {
           Tuning t = c->tun;

@@ -142,6 +142,7 @@ struct Tuning {
   int tpp_mixed = 4;
   int gather_tpp = 2;                 // lanes per molecule in the FP64 reverse gather
   int lpt = 1;                        // process molecules longest list first
+  int atomic_acc = 0;                 // FP64: reaction forces by atomic adds (no gather)
   int sm_count = 152;
 };
 
@@ -171,7 +172,7 @@ struct StepConds {
 
 // ---- launchers (md_kernels.cu); all enqueue on `s` and never synchronise
 void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
-                            cudaStream_t s);
+                            bool zero_f, cudaStream_t s);
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces

@@ -72,12 +72,23 @@ __device__ __forceinline__ float4 local_offset(const RepDev& R, const dvec4& x, 
   return l;
 }
 
-// 1/x by one Newton-Raphson step y <- y (2 - x y) from the correctly rounded FP32 reciprocal:
-// the relative error of the seed (<= 2^-24) is squared, ~4e-15 after the step.
+// 1/x for a positive normal double x in [2^-126, 2^127] (squared distances), without an FP64
+// conversion: x's exponent and leading 20 mantissa bits are rebuilt as an FP32 number with integer
+// operations, its correctly rounded FP32 reciprocal (relative error < 2^-19.9) is widened back to
+// FP64 the same way, and one third-order Newton step y + y (e + e^2), e = 1 - x y, cubes the error
+// (within an ulp of 1/x). Three FP64 FMAs in all.
 __device__ __forceinline__ double rcp_nr(double x) {
-  const double y = (double)__frcp_rn((float)x);
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const float xf = __uint_as_float((hi << 3) - (896u << 23));  // exponent bias 1023 -> 127
+  const unsigned yb = __float_as_uint(__frcp_rn(xf));
+  const double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
   const double e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  return fma(y, fma(e, e, e), y);
+}
+
+// -x by flipping the sign bit (an integer operation)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
 // error-free transformation s + x = t + e (Knuth's TwoSum); the error is collected in c
@@ -101,7 +112,8 @@ inline int nblocks(long long n, int b) { return n > 0 ? (int)((n + b - 1) / b) :
 // ------------------------------------------------------------------------------------------------
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc) {
+__global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc,
+                                                         int zero_f) {
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.step += 1;
@@ -141,6 +153,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
     a.pos[i] = x;
     a.vel[i] = v;
+    if (zero_f) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);  // the atomic pair pass adds into it
     a.lpos[i] = local_offset(R, x, a.home[i]);  // FP32 screens of both pair kernels
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
@@ -788,6 +801,95 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
   finish_chunks(a);
 }
 
+// FP64, half list, reaction forces by atomics: as k_forces_half, but each vapour pair's reaction
+// goes straight to the partner's force with FP64 atomic adds (executed in L2, not on the SM's FP64
+// pipe), and the molecule adds its own half-list sum the same way; no pair buffer, no gather. The
+// forces must be zero beforehand. The order of the atomic adds varies from run to run, so the
+// forces agree with the deterministic form to rounding, not bit for bit.
+template <int TPP>
+__global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, int lpt) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.force_rebuild = 0;
+  }
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
+  int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    int i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const dvec4 xi = a.pos[i];
+      const int n = a.n_front[i], nvh = a.n_vh[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      for (int k = sub; k < n; k += TPP) {
+        const int j = (int)(row[k] & kIndexMask);
+        const bool wall = j >= N;
+        const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+        const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+        const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+        const double dz = xi.z - xj.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (lt_pos(r2, wall ? p.rcw2 : p.rc2)) {
+          const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+          const double inv2 = rcp_nr(r2);
+          const double inv6 = inv2 * inv2 * inv2;
+          const double fr = inv2 * inv6 * fma(a12, inv6, -b6);
+          const double px = fr * dx, py = fr * dy, pz = fr * dz;
+          fx += px;
+          fy += py;
+          fz += pz;
+          if (k < nvh) {  // Newton's third law: the partner receives -p
+            atomicAdd(&a.frc[j].x, neg_bits(px));
+            atomicAdd(&a.frc[j].y, neg_bits(py));
+            atomicAdd(&a.frc[j].z, neg_bits(pz));
+          }
+          ++cnt;
+        }
+      }
+    }
+    fx = group_sum<TPP>(fx);
+    fy = group_sum<TPP>(fy);
+    fz = group_sum<TPP>(fz);
+    if (live && sub == 0) {
+      atomicAdd(&a.frc[i].x, fx);
+      atomicAdd(&a.frc[i].y, fy);
+      atomicAdd(&a.frc[i].z, fz);
+    }
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
+// second half-kick (Fig. 3) after the atomic pair pass: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+__global__ void k_kick(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_total) return;
+  const RepDev& R = a.reps[a.rep[i]];
+  dvec4 v = a.vel[i];
+  const dvec4 f = a.frc[i];
+  const double h = 0.5 * R.dt * p.inv_mass;
+  v.x += h * f.x;
+  v.y += h * f.y;
+  v.z += h * f.z;
+  a.vel[i] = v;
+}
+
+__global__ void k_zero_forces(Arrays a) {
+  count_launch(a);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_total) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+}
+
 // FP64, half list, packed: a warp owns 32 molecules (one lane each). Per window of kPackT list
 // slots, an FP32 screen on the cell-local offsets drops the entries that are surely beyond the
 // cutoff (FP32 r^2 at or above rc^2 (1 + 1e-5); the FP32 error is ~1e-7 of rc^2) and packs the
@@ -1280,13 +1382,13 @@ __global__ void k_pore_final(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 
-void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c, bool zero_f,
                             cudaStream_t s) {
   const int b = 256;
   if (mixed)
-    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c);
+    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, zero_f ? 1 : 0);
   else
-    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c);
+    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, zero_f ? 1 : 0);
 }
 
 int rebuild_kernel_count(bool mixed) { return mixed ? 10 : 11; }
@@ -1312,7 +1414,7 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
     k_order_scan<<<1, 1024, 0, s>>>(a, p);
     k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   }
-  if (half) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
+  if (half && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
 // grid of the pair kernels: at most SMs x blocks per SM; warps fetch chunks of molecules
@@ -1336,6 +1438,14 @@ template <int TPP>
 void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cudaStream_t s) {
   const int b = t.force_block;
   const int per_sm = t.force_blocks_per_sm_fp64;
+  if (t.atomic_acc && TPP != 32) {
+    // forces start from zero: k_integrate_first clears them on the way through a step
+    if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+    k_forces_half_atomic<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0, s>>>(
+        a, p, t.lpt);
+    if (kick) k_kick<<<nblocks(a.n_total, 256), 256, 0, s>>>(a, p);
+    return;
+  }
   if constexpr (TPP == 32) {
     const size_t sm = (size_t)(b / 32) * sizeof(PackWarp);
     k_forces_half_packed<<<pair_grid(a.n_total, b, per_sm, t), b, sm, s>>>(a, p, t.lpt);

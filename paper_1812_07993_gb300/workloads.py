@@ -210,6 +210,53 @@ def rsa_vapor(rng: np.random.Generator, n: int, Lx: float, Ly: float, Lz: float,
     return np.ascontiguousarray(accepted)
 
 
+def rsa_in_pores(rng: np.random.Generator, n: int, pores: Sequence[Pore], Lx: float, Ly: float,
+                 Lz: float, slab_half: float, obstacles: np.ndarray, min_sep: float = 0.9,
+                 max_attempt_factor: int = 1000) -> np.ndarray:
+    """Random sequential addition of ``n`` points uniform in the carved regions of ``pores`` within
+    the slab ``|z| < slab_half``, each at least ``min_sep`` from the obstacle points (wall atoms)
+    and from each other. Candidates are drawn uniform in the slab and kept where a pore's
+    predicate holds (rejection), in batches as in ``rsa_vapor``."""
+    from scipy.spatial import cKDTree
+    if n == 0:
+        return np.zeros((0, 3))
+    obs_tree, oq = (None, None)
+    if len(obstacles):
+        obs_tree, oq = _periodic_tree(obstacles, Lx, Ly, Lz)
+    accepted = np.zeros((0, 3))
+    attempts = 0
+    while len(accepted) < n:
+        need = n - len(accepted)
+        k = max(4096, 16 * need)
+        attempts += k
+        if attempts > max_attempt_factor * 16 * n:
+            raise RuntimeError("random sequential addition in the pores did not converge")
+        cand = np.stack([rng.uniform(-0.5 * Lx, 0.5 * Lx, k), rng.uniform(-0.5 * Ly, 0.5 * Ly, k),
+                         rng.uniform(-slab_half, slab_half, k)], axis=1)
+        inside = np.zeros(k, dtype=bool)
+        for p in pores:
+            inside |= carve_mask(cand, p, Lx, Ly, slab_half)
+        cand = cand[inside]
+        ok = np.ones(len(cand), dtype=bool)
+        if obs_tree is not None and len(cand):
+            d, _ = obs_tree.query(oq(cand), k=1, distance_upper_bound=min_sep)
+            ok &= ~(d < min_sep)
+        if len(accepted) and len(cand):
+            acc_tree, aq = _periodic_tree(accepted, Lx, Ly, Lz)
+            d, _ = acc_tree.query(aq(cand), k=1, distance_upper_bound=min_sep)
+            ok &= ~(d < min_sep)
+        idx = np.flatnonzero(ok)
+        if len(idx) > 1:
+            btree, _ = _periodic_tree(cand[idx], Lx, Ly, Lz)
+            pairs = btree.query_pairs(min_sep, output_type="ndarray")
+            if len(pairs):
+                keep = np.ones(len(idx), dtype=bool)
+                keep[np.unique(pairs.max(axis=1))] = False
+                idx = idx[keep]
+        accepted = np.concatenate([accepted, cand[idx[:need]]], axis=0)
+    return np.ascontiguousarray(accepted)
+
+
 def maxwell_velocities(rng: np.random.Generator, n: int, T0: float, mass: float = 1.0) -> np.ndarray:
     if n == 0:
         return np.zeros((0, 3))
@@ -336,6 +383,27 @@ def pore_array_2m(seed: int = 5, n_vapor: int = 2_000_000, pitch: float = 100.0)
             pores.append(p)
             k += 1
     return make_system("pore_array_2m", L, L, Lz, h, pores, n_vapor, 0.85, seed + 1)
+
+
+def drying_cylinder_pore(seed: int = 7, n_in: int = 1000, n_out: int = 4800, R: float = 8.0,
+                         T0: float = 1.0, tau_B: float = 0.5) -> System:
+    """Drying of a pore (the paper's 3D scenario, Sec. 5: a pore filled with saturated vapour
+    empties into surroundings at 20 % saturation), in reduced units: a 40x40x80 box, wall slab
+    |z|<10 with a cylinder of radius R on the axis; n_in molecules start inside the pore
+    (density ~0.25) and n_out outside the slab (~0.05, a fifth of it); T*=1.0, Berendsen
+    coupling with tau_B = 0.5 applied every 10 steps. Seed ``seed`` draws the outer molecules,
+    ``seed + 1`` the pore filling, ``seed + 2`` the velocities."""
+    L, Lz, h = 40.0, 80.0, 10.0
+    pore = Pore(PORE_CYLINDER, r0=R)
+    wall = sc_wall(L, L, Lz, h, 1.0, [pore])
+    inner = rsa_in_pores(np.random.default_rng(seed + 1), n_in, [pore], L, L, Lz, h, wall)
+    outer = rsa_vapor(np.random.default_rng(seed), n_out, L, L, Lz, h, 0.5 * Lz,
+                      np.concatenate([wall, inner], axis=0))
+    x0 = np.ascontiguousarray(np.concatenate([inner, outer], axis=0))
+    v0 = maxwell_velocities(np.random.default_rng(seed + 2), len(x0), T0)
+    return System(name="drying_cylinder_pore", Lx=L, Ly=L, Lz=Lz, slab_half=h, lattice_a=1.0,
+                  pores=[pore], x0=x0, v0=v0, wall=wall, T0=T0, dt=0.005, tau_B=tau_B,
+                  thermostat_every=10, seed=seed)
 
 
 def vapor_only_box(n: int, L: float, Lz: float, T0: float, seed: int, min_sep: float = 0.9) -> System:

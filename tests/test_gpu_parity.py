@@ -139,13 +139,18 @@ def shapes_after_ten(shapes):
     return states
 
 
-@pytest.mark.parametrize("tpp,block,lpt", [(1, 128, 1), (2, 256, 1), (4, 128, 2), (8, 256, 1),
-                                           (32, 128, 1), (32, 256, 1), (32, 128, 2)])
-def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, lpt):
+@pytest.mark.parametrize("tpp,block,lpt,acc", [
+    (1, 128, 1, 1), (2, 256, 1, 1), (4, 128, 2, 1), (8, 256, 1, 1), (32, 128, 1, 1),
+    (32, 256, 1, 1), (32, 128, 2, 1), (1, 256, 1, 2), (2, 128, 1, 2), (4, 256, 2, 2),
+    (8, 128, 1, 2)])
+def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, lpt, acc):
     """Every pair-kernel variant (lanes per molecule, the packed kernel, block size, processing
-    order) gives the oracle's forces and 10-step trajectories, pair counts and observables."""
+    order, deterministic or atomic accumulation) gives the oracle's forces and 10-step
+    trajectories, pair counts and observables."""
     with md.Simulation(shapes) as sim:
-        sim.set_tuning(force_tpp=tpp, force_block=block, force_blocks_per_sm=2, order_by_length=lpt)
+        sim.set_tuning(force_tpp=tpp, force_block=block, force_blocks_per_sm=2, order_by_length=lpt,
+                       force_accumulate=acc)
+        assert sim.tuning()["force_accumulate"] == acc
         sim.compute_forces()
         for r, s in enumerate(shapes):
             g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
@@ -156,6 +161,24 @@ def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, b
             assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL, s.name
             assert np.abs(v - st.v).max() <= TRAJ_TOL, s.name
             check_observables(sim, r, s, st)
+
+
+def test_atomic_accumulation_agrees_with_deterministic_to_rounding(shapes):
+    """The atomic form sums the same FP64 pair forces in another order: forces agree to a few
+    ulps of the force scale, trajectories over 20 steps to round-off growth."""
+    with md.Simulation(shapes) as a, md.Simulation(shapes) as b:
+        b.set_tuning(force_accumulate=2)
+        for r in range(len(shapes)):
+            assert force_err(b.forces(r), a.forces(r)) <= 1e-13
+        a.step(20)
+        b.step(20)
+        for r, s in enumerate(shapes):
+            xa, va = a.state(r)
+            xb, vb = b.state(r)
+            assert np.abs(wrapped_diff(xa, xb, s)).max() <= 1e-10
+            assert np.abs(va - vb).max() <= 1e-10
+        with pytest.raises(md.MDError):
+            b.set_tuning(force_tpp=32)
 
 
 def test_generated_wall_matches_generator(shapes):

@@ -5,7 +5,9 @@
   trajectories and observables;
 * the 400 x 400 x 200 array of 16 pores with 2,000,000 molecules and ~6.2 M wall atoms: every
   force against the oracle, pair counts and the per-pore observables;
-* the autotuner leaves positions unchanged and forces within tolerance.
+* the autotuner leaves positions unchanged and forces within tolerance;
+* the drying of an initially filled pore with general Berendsen coupling: 10-step parity and the
+  occupancy decay over 2,000 steps against the oracle's, over four seeds.
 """
 import numpy as np
 import pytest
@@ -122,3 +124,54 @@ def test_autotune_keeps_state_and_forces(precision, tmp_path):
         again = autotune.tune(sim, cache_path=str(tmp_path / "t.json"))
         assert again["cached"] and again["tuning"] == t
         sim.step(5)
+
+
+# ------------------------------------------------------------------ drying of a filled pore
+
+
+def test_drying_run_ten_steps_general_berendsen():
+    """A filled pore with Berendsen coupling tau_B = 0.5 (not plain rescaling): 10 steps, exact
+    occupancy and adsorbed counts, trajectories within 1e-8 of the oracle."""
+    s = W.drying_cylinder_pore()
+    p = oracle.make_params(s, POT)
+    st = oracle.State(p, s.x0, s.v0, s.wall)
+    with md.Simulation(s) as sim:
+        sim.step(10)
+        st.run(10)
+        x, v = sim.state()
+        d = x - st.x
+        d[:, :2] -= 40.0 * np.round(d[:, :2] / 40.0)
+        assert np.abs(d).max() <= 1e-8
+        assert np.abs(v - st.v).max() <= 1e-8
+        o, occ, ads, prof = sim.observables()
+        occ_o, ads_o, prof_o = oracle.observables(p, s.pores, st.x, st.d2wall)
+        np.testing.assert_array_equal(occ, occ_o)
+        np.testing.assert_array_equal(ads, ads_o)
+        np.testing.assert_array_equal(prof, prof_o)
+
+
+def test_drying_run_occupancy_decay_matches_oracle():
+    """Pore occupancy over 2,000 steps of drying, four seeds: the GPU and oracle means at every
+    checkpoint agree within the seed-to-seed standard error, and the pore empties."""
+    seeds = [7, 17, 27, 37]
+    systems = [W.drying_cylinder_pore(seed=sd) for sd in seeds]
+    every, nck = 250, 8
+    gpu = np.zeros((len(seeds), nck))
+    with md.Simulation(systems) as sim:
+        for c in range(nck):
+            sim.step(every)
+            for r in range(len(seeds)):
+                gpu[r, c] = sim.observables(r)[1].sum()
+    ora = np.zeros_like(gpu)
+    for r, s in enumerate(systems):
+        p = oracle.make_params(s, POT)
+        st = oracle.State(p, s.x0, s.v0, s.wall, nthreads=0)
+        for c in range(nck):
+            st.run(every)
+            ora[r, c] = oracle.observables(p, s.pores, st.x, st.d2wall)[0].sum()
+    k = len(seeds)
+    se = np.sqrt(gpu.var(0, ddof=1) / k + ora.var(0, ddof=1) / k) + 1.0
+    z = (gpu.mean(0) - ora.mean(0)) / se
+    print("occupancy GPU", gpu.mean(0), "oracle", ora.mean(0), "z", z)
+    assert np.abs(z).max() <= 4.0
+    assert gpu.mean(0)[-1] < 0.9 * 1000 and ora.mean(0)[-1] < 0.9 * 1000

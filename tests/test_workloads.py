@@ -53,3 +53,18 @@ def test_replica_specs_ranges():
         assert s["n"] / (L * L * (2 * L - 16)) == pytest.approx(0.02, rel=1e-6)
         assert 2 <= s["R"] <= 10 and 0.8 <= s["T0"] <= 1.2 and s["kind"] in (1, 2, 3, 4)
     assert specs == W.replica_batch_specs(256, seed=4)
+
+
+def test_drying_pore_filled_inside_dilute_outside():
+    s = W.drying_cylinder_pore()
+    assert s.n_vapor == 5800 and s.tau_B == 0.5 and s.thermostat_every == 10
+    inside = W.carve_mask(s.x0, s.pores[0], s.Lx, s.Ly, s.slab_half) & (np.abs(s.x0[:, 2]) < 10)
+    outside = np.abs(s.x0[:, 2]) > 10
+    assert inside.sum() == 1000 and outside.sum() == 4800
+    assert min_periodic_distance(s.x0, s.x0, 40, 40, same=True) >= 0.9
+    assert min_periodic_distance(s.x0[inside], s.wall, 40, 40) >= 0.9
+    rho_in = 1000 / (np.pi * 8.0 ** 2 * 20.0)
+    rho_out = 4800 / (40.0 * 40.0 * 60.0)
+    assert rho_out / rho_in == pytest.approx(0.2, abs=0.02)
+    b = W.drying_cylinder_pore()
+    np.testing.assert_array_equal(s.x0, b.x0)
