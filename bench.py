@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--roofline-launches", type=int, default=50)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
+                    help="FP64 reaction forces: FP64 atomic adds, or the bit-reproducible "
+                         "slot-and-gather form")
     return ap.parse_args()
 
 
@@ -254,6 +257,8 @@ def time_steps(sim, torch, stream, flush, steps):
 def measure_precision(md, systems, precision, args, torch, stream, flush):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
+    if precision == md.MD_PREC_FP64:
+        sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
     sim.tune_info = None
     if not args.no_autotune:
         sim.tune_info = autotune.tune(sim, trials=9, use_cache=False)
@@ -270,22 +275,25 @@ def measure_precision(md, systems, precision, args, torch, stream, flush):
     return sim, ms, p1 - p0, launches
 
 
-def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision):
+def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate):
     evs = []
     for _ in range(nlaunch):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sim.compute_forces()
+        sim.pair_pass()          # the pair kernel alone
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
+    sim.compute_forces()         # complete forces again
+    sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in evs) / nlaunch
     flops = pairs_per_launch * FLOPS_PER_PAIR
     achieved = flops / (ms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
-    kname = "k_forces_fp64" if precision == "fp64" else "k_forces_mixed"
+    kname = "k_forces_mixed" if precision != "fp64" else (
+        "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half")
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == kernel_sha() else None
     return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
@@ -361,7 +369,7 @@ def run_ours(args):
     if rank == 0:
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
-                                     args.precision)
+                                     args.precision, args.accumulate)
         extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step)
         if not args.no_mixed and args.precision == "fp64":
             import oracle
@@ -403,6 +411,8 @@ def run_ours(args):
                            "n_vapor": sum(s.n_vapor for s in systems),
                            "n_wall": sum(s.n_wall for s in systems),
                            "precision": args.precision,
+                           "force_accumulate": (args.accumulate if args.precision == "fp64"
+                                                else "per-molecule sums (full list)"),
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "md_steps_per_s": 1e3 / ms_per_step,

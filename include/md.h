@@ -128,6 +128,10 @@ typedef struct {
                               partners by FP64 atomic adds (no gather; the summation order varies
                               from run to run, so results agree with mode 1 to rounding only).
                               Changing it rebuilds the lists (synchronises). */
+  int32_t pair_method;     /* FP64 only. 1: Verlet lists (default); 2: every pair every step, one
+                              thread per molecule summing over all molecules and wall atoms of
+                              its replica (the paper's F1 form, Sec. 3, Fig. 1; O(N^2), for small
+                              systems). Same pair set and forces; no list rebuilds while on. */
 } md_tuning;
 
 typedef struct {
@@ -171,8 +175,8 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 /* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 2 and 8): time
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
  * force_tpp {1,2,4,8, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
- * x order_by_length {on,off} -- with CUDA events on the context's stream (median of `trials` launches each, trials
- * clamped to [3, 101]), then apply the fastest. Positions and velocities are unchanged; forces are
+ * x order_by_length {on,off} -- with CUDA events on the context's stream (median of `trials`
+ * launches each, trials clamped to [3, 101]), then apply the fastest. Positions and velocities are unchanged; forces are
  * recomputed at the same positions. *best and *best_us (either may be NULL) receive the chosen
  * shape and its median time in microseconds. Synchronises. */
 md_status md_autotune(md_ctx* ctx, int32_t trials, md_tuning* best, double* best_us);
@@ -196,6 +200,13 @@ md_status md_set_state(md_ctx* ctx, int32_t replica, const double* x, const doub
  * and launch shape the step uses (Eq. 2, Fig. 1), without moving molecules or rebuilding lists.
  * Asynchronous; meant for timing the pair kernel in isolation. */
 md_status md_compute_forces(md_ctx* ctx);
+
+/* Enqueue the pair kernel alone -- the dominant kernel of the step (the FP64 half-list or atomic
+ * pass, the all-pairs pass, or the mixed-precision pass) -- with no clearing, gather or kick, so
+ * that its duration can be timed with events on the context's stream. It leaves the forces
+ * incomplete (or, in the atomic form, added twice): call md_compute_forces afterwards before
+ * reading forces or stepping. Asynchronous. */
+md_status md_pair_pass(md_ctx* ctx);
 
 /* Host<->device bytes the library has copied for this context since creation (state uploads,
  * read-backs, status words). Either pointer may be NULL. */

@@ -60,7 +60,7 @@ class md_tuning(ctypes.Structure):
     _fields_ = [("force_block", ctypes.c_int32), ("force_blocks_per_sm", ctypes.c_int32),
                 ("force_tpp", ctypes.c_int32), ("order_by_length", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32),
-                ("force_accumulate", ctypes.c_int32)]
+                ("force_accumulate", ctypes.c_int32), ("pair_method", ctypes.c_int32)]
 
 
 class md_obs(ctypes.Structure):
@@ -98,6 +98,7 @@ _SIGNATURES = {
     "md_set_state": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP, _DP]),
     "md_get_forces": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP]),
     "md_compute_forces": (ctypes.c_int, [_CTX]),
+    "md_pair_pass": (ctypes.c_int, [_CTX]),
     "md_transfer_bytes": (ctypes.c_int, [_CTX, _I64P, _I64P]),
     "md_observables": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(md_obs), _I64P, _I64P,
                                       _I64P, _DP]),
@@ -281,12 +282,13 @@ class Simulation:
         return d, occ[:npores], ads, prof
 
     def set_tuning(self, force_block=0, force_blocks_per_sm=0, force_tpp=0, order_by_length=0,
-                   use_graph=0, steps_per_graph=0, force_accumulate=0):
+                   use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0):
         """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
-        deterministic gather, 2 atomic reaction forces."""
+        deterministic gather, 2 atomic reaction forces; pair_method (FP64): 1 Verlet lists,
+        2 all pairs."""
         t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
-                      steps_per_graph, force_accumulate)
+                      steps_per_graph, force_accumulate, pair_method)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)
 
     def autotune(self, trials: int = 15):
@@ -306,6 +308,11 @@ class Simulation:
     def compute_forces(self):
         """Enqueue one pair-force evaluation at the current positions (asynchronous)."""
         _check(load_library().md_compute_forces(self.ctx), self.ctx)
+
+    def pair_pass(self):
+        """Enqueue the pair kernel alone, for timing it (md_pair_pass); call compute_forces
+        before reading forces or stepping again."""
+        _check(load_library().md_pair_pass(self.ctx), self.ctx)
 
     def transfer_bytes(self):
         h, d = ctypes.c_int64(), ctypes.c_int64()

@@ -236,14 +236,20 @@ md_status sync_status(md_ctx* c) {
   return MD_OK;
 }
 
-// the FP64 atomic pair pass adds into the forces: k_integrate_first clears them after its kick
-bool zero_forces(const md_ctx* c) { return !c->mixed && c->tun.atomic_acc; }
+// what the first half-kick does besides Fig. 2: clear the forces for the FP64 atomic pair pass;
+// refresh the FP32 cell-local offsets for the kernels that screen or compute with them
+int integrate_flags(const md_ctx* c) {
+  int f = 0;
+  if (!c->mixed && c->tun.atomic_acc) f |= kIntZeroForces;
+  if (c->mixed || c->tun.tpp_fp64 == 32) f |= kIntLocalOffsets;
+  return f;
+}
 
 // One step with plain launches: the rebuild and thermostat kernels always launch and return at
 // once when the device decides they have nothing to do.
 void enqueue_step(md_ctx* c) {
-  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, zero_forces(c), c->stream);
-  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, integrate_flags(c), c->stream);
+  if (!c->tun.all_pairs) launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
   launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
   launch_thermostat(c->a, c->pot, c->stream);
 }
@@ -307,14 +313,17 @@ md_status build_graph(md_ctx* c, int steps) {
   for (int k = 0; k < steps && e == cudaSuccess; ++k) {
     StepConds sc;
     sc.use = 1;
-    e = cudaGraphConditionalHandleCreate(&sc.rebuild, g, 0, cudaGraphCondAssignDefault);
+    sc.has_rebuild = c->tun.all_pairs ? 0 : 1;
+    if (sc.has_rebuild)
+      e = cudaGraphConditionalHandleCreate(&sc.rebuild, g, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess)
       e = cudaGraphConditionalHandleCreate(&sc.thermo, g, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) break;
-    launch_integrate_first(c->a, c->pot, c->mixed, sc, zero_forces(c), c->stream);
-    e = add_conditional(c, g, sc.rebuild, [&](cudaStream_t s) {
-      launch_rebuild(c->a, c->pot, c->tun, c->mixed, s);
-    });
+    launch_integrate_first(c->a, c->pot, c->mixed, sc, integrate_flags(c), c->stream);
+    if (sc.has_rebuild)
+      e = add_conditional(c, g, sc.rebuild, [&](cudaStream_t s) {
+        launch_rebuild(c->a, c->pot, c->tun, c->mixed, s);
+      });
     if (e != cudaSuccess) break;
     launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
     e = add_conditional(c, g, sc.thermo, [&](cudaStream_t s) { launch_thermostat(c->a, c->pot, s); });
@@ -690,12 +699,20 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
   if (c->mixed && t->force_accumulate == 2)
     return fail(c, MD_EINVAL, "atomic accumulation is an FP64-path option");
+  if (t->pair_method < 0 || t->pair_method > 2)
+    return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists) or 2 (all pairs)");
+  if (c->mixed && t->pair_method == 2)
+    return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
+  if (t->pair_method) nt.all_pairs = t->pair_method == 2 ? 1 : 0;
   const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
   if (at && nt.tpp_fp64 == 32)
     return fail(c, MD_EINVAL, "the packed kernel (force_tpp 32) has no atomic form");
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
+  relist = relist || nt.all_pairs != c->tun.all_pairs;  // lists fresh when they come back
+  // the packed kernel screens with the FP32 cell-local offsets: refresh them on the way in
+  relist = relist || (!c->mixed && (nt.tpp_fp64 == 32) != (c->tun.tpp_fp64 == 32));
   nt.atomic_acc = at;
   c->tun = nt;
   if (t->use_graph) c->use_graph = t->use_graph == 1 ? 1 : 0;
@@ -715,6 +732,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->use_graph = c->use_graph ? 1 : 2;
   t->steps_per_graph = c->steps_per_graph;
   t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
+  t->pair_method = c->tun.all_pairs ? 2 : 1;
   return MD_OK;
 }
 
@@ -743,6 +761,9 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
       if (tp == 32 && (c->mixed || c->tun.atomic_acc)) continue;
       for (int bp : bpss)
         for (int bk : blocks) {
+          // the all-pairs kernel has a fixed shape: time it once
+          if (c->tun.all_pairs && (tp != tpps[0] || bp != bpss[0] || bk != blocks[0] || !lpt))
+            continue;
           Tuning t = c->tun;
           t.force_block = bk;
           if (c->mixed) {
@@ -970,6 +991,15 @@ md_status md_compute_forces(md_ctx* c) {
   md_status prev = device_status(c);
   if (prev != MD_OK) return prev;
   launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  return MD_OK;
+}
+
+md_status md_pair_pass(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  md_status prev = device_status(c);
+  if (prev != MD_OK) return prev;
+  launch_pair_pass(c->a, c->pot, c->mixed, c->tun, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   return MD_OK;
 }

@@ -143,6 +143,7 @@ struct Tuning {
   int gather_tpp = 2;                 // lanes per molecule in the FP64 reverse gather
   int lpt = 1;                        // process molecules longest list first
   int atomic_acc = 0;                 // FP64: reaction forces by atomic adds (no gather)
+  int all_pairs = 0;                  // FP64: every pair each step, no lists (the paper's F1)
   int sm_count = 152;
 };
 
@@ -168,15 +169,23 @@ __host__ __device__ inline int cell_coord(double u, double half, double l, int n
 struct StepConds {
   cudaGraphConditionalHandle rebuild = 0, thermo = 0;
   int use = 0;
+  int has_rebuild = 1;              // 0: no rebuild node (all-pairs mode)
 };
 
 // ---- launchers (md_kernels.cu); all enqueue on `s` and never synchronise
+// flags of the first half-kick: clear the forces (the atomic pair pass adds into them); refresh
+// the FP32 cell-local offsets (read by the mixed pair kernel and the packed FP64 kernel's screen)
+constexpr int kIntZeroForces = 1;
+constexpr int kIntLocalOffsets = 2;
 void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
-                            bool zero_f, cudaStream_t s);
+                            int flags, cudaStream_t s);
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
 cudaError_t configure_kernels();
+// the pair kernel alone (no clearing, gather or kick): for timing the dominant kernel
+void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
+                      cudaStream_t s);
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s);
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);

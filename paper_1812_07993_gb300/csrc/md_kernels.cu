@@ -113,7 +113,7 @@ inline int nblocks(long long n, int b) { return n > 0 ? (int)((n + b - 1) / b) :
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc,
-                                                         int zero_f) {
+                                                         int flags) {
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.step += 1;
@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
     a.pos[i] = x;
     a.vel[i] = v;
-    if (zero_f) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);  // the atomic pair pass adds into it
-    a.lpos[i] = local_offset(R, x, a.home[i]);  // FP32 screens of both pair kernels
+    if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    if (flags & kIntLocalOffsets) a.lpos[i] = local_offset(R, x, a.home[i]);
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   if (threadIdx.x == 0) {
     *a.blk_done = 0u;
     const bool rb = !halt && atomicAdd(a.force_rebuild, 0) != 0;
-    cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
+    if (sc.has_rebuild) cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
     cudaGraphSetConditional(sc.thermo, (!halt && th) ? 1u : 0u);
   }
 }
@@ -746,6 +746,31 @@ __device__ __forceinline__ bool lt_pos(double x, double y) {
 // FP64, half list: molecule i walks the front of its row; each vapour pair's force goes to the
 // partner's back slot in pairbuf (fwd), where the partner's gather reads it in list order.
 
+// One FP64 pair term, branch-free: the force on i from list entry e, p = F(r)/r * (r_i - r_j), or
+// zero beyond the cutoff (the FP64 pipe costs a warp the same whether or not its lanes are
+// predicated off, so computing every entry and masking keeps the two chains of the unrolled loop
+// independent and free of divergence). Returns whether the pair is within the cutoff.
+__device__ __forceinline__ bool pair_term(const Arrays& a, const PotDev& p, const RepDev& R,
+                                          const dvec4& xi, uint32_t e, int N, double& px,
+                                          double& py, double& pz) {
+  const int j = (int)(e & kIndexMask);
+  const bool wall = j >= N;
+  const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+  const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+  const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+  const double dz = xi.z - xj.z;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
+  const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+  const double inv2 = rcp_nr(r2);
+  const double inv6 = inv2 * inv2 * inv2;
+  const double fr = in ? inv2 * inv6 * fma(a12, inv6, -b6) : 0.0;
+  px = fr * dx;
+  py = fr * dy;
+  pz = fr * dz;
+  return in;
+}
+
 template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt) {
   constexpr int MPW = 32 / TPP;
@@ -769,26 +794,25 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
       const uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
-      for (int k = sub; k < n; k += TPP) {
-        const int j = (int)(row[k] & kIndexMask);
-        const bool wall = j >= N;
-        const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
-        const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-        const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
-        const double dz = xi.z - xj.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        double fr = 0.0;
-        if (lt_pos(r2, wall ? p.rcw2 : p.rc2)) {
-          const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
-          const double inv2 = rcp_nr(r2);
-          const double inv6 = inv2 * inv2 * inv2;
-          fr = inv2 * inv6 * fma(a12, inv6, -b6);
-          fx = fma(fr, dx, fx);
-          fy = fma(fr, dy, fy);
-          fz = fma(fr, dz, fz);
-          ++cnt;
+      // two entries per iteration: independent FP64 chains, added in list order
+      for (int k = sub; k < n; k += 2 * TPP) {
+        const int k2 = k + TPP;
+        const bool has2 = k2 < n;
+        const uint32_t e1 = row[k], e2 = row[has2 ? k2 : k];
+        double p1x, p1y, p1z, p2x, p2y, p2z;
+        const bool in1 = pair_term(a, p, R, xi, e1, N, p1x, p1y, p1z);
+        const bool in2 = pair_term(a, p, R, xi, e2, N, p2x, p2y, p2z) && has2;
+        fx += p1x;
+        fy += p1y;
+        fz += p1z;
+        if (has2) {
+          fx += p2x;
+          fy += p2y;
+          fz += p2z;
         }
-        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(fr * dx, fr * dy, fr * dz, 0.0);
+        cnt += (in1 ? 1 : 0) + (in2 ? 1 : 0);
+        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(p1x, p1y, p1z, 0.0);
+        if (has2 && k2 < nvh) a.pairbuf[fw[k2]] = make_dvec4(p2x, p2y, p2z, 0.0);
       }
     }
     fx = group_sum<TPP>(fx);
@@ -828,30 +852,35 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
-      for (int k = sub; k < n; k += TPP) {
-        const int j = (int)(row[k] & kIndexMask);
-        const bool wall = j >= N;
-        const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
-        const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-        const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
-        const double dz = xi.z - xj.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (lt_pos(r2, wall ? p.rcw2 : p.rc2)) {
-          const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
-          const double inv2 = rcp_nr(r2);
-          const double inv6 = inv2 * inv2 * inv2;
-          const double fr = inv2 * inv6 * fma(a12, inv6, -b6);
-          const double px = fr * dx, py = fr * dy, pz = fr * dz;
-          fx += px;
-          fy += py;
-          fz += pz;
-          if (k < nvh) {  // Newton's third law: the partner receives -p
-            atomicAdd(&a.frc[j].x, neg_bits(px));
-            atomicAdd(&a.frc[j].y, neg_bits(py));
-            atomicAdd(&a.frc[j].z, neg_bits(pz));
-          }
-          ++cnt;
+      for (int k = sub; k < n; k += 2 * TPP) {
+        const int k2 = k + TPP;
+        const bool has2 = k2 < n;
+        const uint32_t e1 = row[k], e2 = row[has2 ? k2 : k];
+        double p1x, p1y, p1z, p2x, p2y, p2z;
+        const bool in1 = pair_term(a, p, R, xi, e1, N, p1x, p1y, p1z);
+        const bool in2 = pair_term(a, p, R, xi, e2, N, p2x, p2y, p2z) && has2;
+        fx += p1x;
+        fy += p1y;
+        fz += p1z;
+        if (has2) {
+          fx += p2x;
+          fy += p2y;
+          fz += p2z;
         }
+        // Newton's third law: the partner receives -p (vapour partners within the cutoff)
+        if (in1 && k < nvh) {
+          const int j = (int)(e1 & kIndexMask);
+          atomicAdd(&a.frc[j].x, neg_bits(p1x));
+          atomicAdd(&a.frc[j].y, neg_bits(p1y));
+          atomicAdd(&a.frc[j].z, neg_bits(p1z));
+        }
+        if (in2 && k2 < nvh) {
+          const int j = (int)(e2 & kIndexMask);
+          atomicAdd(&a.frc[j].x, neg_bits(p2x));
+          atomicAdd(&a.frc[j].y, neg_bits(p2y));
+          atomicAdd(&a.frc[j].z, neg_bits(p2z));
+        }
+        cnt += (in1 ? 1 : 0) + (in2 ? 1 : 0);
       }
     }
     fx = group_sum<TPP>(fx);
@@ -888,6 +917,92 @@ __global__ void k_zero_forces(Arrays a) {
   count_launch(a);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n_total) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+}
+
+// FP64, every pair, no lists (the paper's F1 form, Fig. 1): one thread per molecule sums over every
+// other vapour molecule and every wall atom of its replica, in index order. Pairs beyond the
+// cutoff contribute nothing, so the pair set and the forces are those of the list path; the work
+// is O(N^2) per replica (small systems). STATS computes the observable pass instead of forces.
+template <bool STATS, bool KICK>
+__global__ void __launch_bounds__(128) k_allpairs(Arrays a, PotDev p) {
+  count_launch(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !STATS) {
+    *a.force_rebuild = 0;
+  }
+  if (halted(a)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = a.n_total;
+  const bool live = i < N;
+  double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0, vir = 0.0, pew = 0.0, virw = 0.0;
+  double d2w = __longlong_as_double(0x7ff0000000000000ll);
+  int cvv = 0, cvw = 0;
+  if (live) {
+    const RepDev& R = a.reps[a.rep[i]];
+    const dvec4 xi = a.pos[i];
+    for (int j = R.vap_off; j < R.vap_off + R.n_vap; ++j) {
+      if (j == i) continue;
+      const dvec4 xj = a.pos[j];
+      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+      const double dz = xi.z - xj.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!lt_pos(r2, p.rc2)) continue;
+      const double inv2 = rcp_nr(r2), inv6 = inv2 * inv2 * inv2;
+      const double fr = inv2 * inv6 * fma(p.a12, inv6, -p.b6);
+      if (STATS) {
+        pe += 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift);
+        vir += 0.5 * fr * r2;
+      } else {
+        fx = fma(fr, dx, fx);
+        fy = fma(fr, dy, fy);
+        fz = fma(fr, dz, fz);
+      }
+      ++cvv;
+    }
+    for (int w = R.wall_off; w < R.wall_off + R.n_wall; ++w) {
+      const dvec4 xj = a.wpos[w];
+      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+      const double dz = xi.z - xj.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!lt_pos(r2, p.rcw2)) continue;
+      const double inv2 = rcp_nr(r2), inv6 = inv2 * inv2 * inv2;
+      const double fr = inv2 * inv6 * fma(p.a12w, inv6, -p.b6w);
+      if (STATS) {
+        pew += inv6 * fma(p.e12w, inv6, -p.e6w) - p.ushift_w;
+        virw += fr * r2;
+        d2w = fmin(d2w, r2);
+      } else {
+        fx = fma(fr, dx, fx);
+        fy = fma(fr, dy, fy);
+        fz = fma(fr, dz, fz);
+      }
+      ++cvw;
+    }
+    if (STATS) {
+      a.pe_i[i] = pe;
+      a.pevw_i[i] = pew;
+      a.vir_i[i] = vir;
+      a.virw_i[i] = virw;
+      a.d2w_i[i] = d2w;
+      a.cnt_vv_i[i] = cvv;
+      a.cnt_vw_i[i] = cvw;
+    } else {
+      a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
+      if (KICK) {  // Fig. 3
+        dvec4 v = a.vel[i];
+        const double h = 0.5 * R.dt * p.inv_mass;
+        v.x += h * fx;
+        v.y += h * fy;
+        v.z += h * fz;
+        a.vel[i] = v;
+      }
+    }
+  }
+  if (!STATS) {  // vapour pairs are seen from both ends, wall pairs once: count 2 per pair
+    const unsigned long long c = warp_sum((unsigned long long)(cvv + 2 * cvw));
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.pair_count, c);
+  }
 }
 
 // FP64, half list, packed: a warp owns 32 molecules (one lane each). Per window of kPackT list
@@ -1382,13 +1497,13 @@ __global__ void k_pore_final(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 
-void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c, bool zero_f,
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c, int flags,
                             cudaStream_t s) {
   const int b = 256;
   if (mixed)
-    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, zero_f ? 1 : 0);
+    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, flags);
   else
-    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, zero_f ? 1 : 0);
+    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, flags);
 }
 
 int rebuild_kernel_count(bool mixed) { return mixed ? 10 : 11; }
@@ -1481,6 +1596,13 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
     }
     return;
   }
+  if (t.all_pairs) {
+    const int g = nblocks(a.n_total, 128);
+    if (stats) k_allpairs<true, false><<<g, 128, 0, s>>>(a, p);
+    else if (kick) k_allpairs<false, true><<<g, 128, 0, s>>>(a, p);
+    else k_allpairs<false, false><<<g, 128, 0, s>>>(a, p);
+    return;
+  }
   if (stats) {  // FP64 observables: a full-row pass that leaves the forces untouched
     k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p);
     return;
@@ -1491,6 +1613,41 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
     case 8: launch_fp64<8>(a, p, kick, t, s); break;
     case 32: launch_fp64<32>(a, p, kick, t, s); break;
     default: launch_fp64<4>(a, p, kick, t, s); break;
+  }
+}
+
+template <int TPP>
+void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t, cudaStream_t s) {
+  const int b = t.force_block;
+  if (mixed) {
+    k_forces_mixed<false, false, TPP><<<pair_grid((long long)a.n_total * TPP, b,
+                                                  t.force_blocks_per_sm_mixed, t), b, 0, s>>>(
+        a, p, t.lpt);
+    return;
+  }
+  const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
+  if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  else k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+}
+
+void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
+                      cudaStream_t s) {
+  if (!mixed && t.all_pairs) {
+    k_allpairs<false, false><<<nblocks(a.n_total, 128), 128, 0, s>>>(a, p);
+    return;
+  }
+  const int tpp = mixed ? t.tpp_mixed : t.tpp_fp64;
+  if (!mixed && tpp == 32) {
+    const size_t sm = (size_t)(t.force_block / 32) * sizeof(PackWarp);
+    k_forces_half_packed<<<pair_grid(a.n_total, t.force_block, t.force_blocks_per_sm_fp64, t),
+                           t.force_block, sm, s>>>(a, p, t.lpt);
+    return;
+  }
+  switch (tpp) {
+    case 1: pair_pass_tpp<1>(a, p, mixed, t, s); break;
+    case 2: pair_pass_tpp<2>(a, p, mixed, t, s); break;
+    case 8: pair_pass_tpp<8>(a, p, mixed, t, s); break;
+    default: pair_pass_tpp<4>(a, p, mixed, t, s); break;
   }
 }
 

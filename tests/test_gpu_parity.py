@@ -181,6 +181,41 @@ def test_atomic_accumulation_agrees_with_deterministic_to_rounding(shapes):
             b.set_tuning(force_tpp=32)
 
 
+def test_all_pairs_method_small_cylinder():
+    """The paper's F1 form (every pair each step, no lists): forces, 10-step trajectory with the
+    thermostat, pair counts and observables equal the oracle's; switching back to lists gives the
+    same forces."""
+    s = W.cylinder_pore_1k()
+    st = oracle.State(oracle_params(s), s.x0, s.v0, s.wall)
+    with md.Simulation(s) as sim:
+        sim.set_tuning(pair_method=2)
+        assert sim.tuning()["pair_method"] == 2
+        g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=0)
+        assert force_err(sim.forces(), g) <= FORCE_TOL
+        sim.step(10)
+        st.run(10)
+        x, v = sim.state()
+        assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL
+        assert np.abs(v - st.v).max() <= TRAJ_TOL
+        check_observables(sim, 0, s, st)
+        f_all = sim.forces()
+        sim.set_tuning(pair_method=1)
+        assert force_err(sim.forces(), f_all) <= 1e-13
+    with md.Simulation(s, precision=md.MD_PREC_MIXED) as m, pytest.raises(md.MDError):
+        m.set_tuning(pair_method=2)
+
+
+def test_all_pairs_method_four_shapes(shapes):
+    with md.Simulation(shapes) as sim:
+        sim.set_tuning(pair_method=2, use_graph=2)
+        for r, s in enumerate(shapes):
+            g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            assert force_err(sim.forces(r), g) <= FORCE_TOL, s.name
+        sim.step(3)
+        o, *_ = sim.observables(0)
+        assert o["step"] == 3
+
+
 def test_generated_wall_matches_generator(shapes):
     with md.Simulation(shapes, generate_wall=True) as sim:
         for r, s in enumerate(shapes):
