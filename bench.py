@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--roofline-launches", type=int, default=50)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-mode", choices=["graph", "plain"], default="graph",
+                    help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
+                         "launch lists)")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
                     help="FP64 reaction forces: FP64 atomic adds, or the bit-reproducible "
                          "slot-and-gather form")
@@ -228,6 +231,21 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------ GPU leg
 
 
+def nvtx_push(torch, name):
+    """Mark a region for ncu's --nvtx-include filter (a no-op where NVTX is unavailable)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop(torch):
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def pair_total(sim, nrep):
     return sim.observables(0)[0]["pair_evals_total"]
 
@@ -262,14 +280,16 @@ def measure_precision(md, systems, precision, args, torch, stream, flush):
     sim.tune_info = None
     if not args.no_autotune:
         sim.tune_info = autotune.tune(sim, trials=9, use_cache=False)
-    sim.set_tuning(use_graph=1, steps_per_graph=1)
+    sim.set_tuning(use_graph=1 if args.launch_mode == "graph" else 2, steps_per_graph=1)
     for _ in range(args.warmup):
         flush.zero_()
         sim.step(1)
     sim.sync()
     p0 = pair_total(sim, len(systems))
     l0 = sim.kernel_launches()
+    nvtx_push(torch, "timed_steps")
     ms = time_steps(sim, torch, stream, flush, args.steps)
+    nvtx_pop(torch)
     launches = sim.kernel_launches() - l0
     p1 = pair_total(sim, len(systems))
     return sim, ms, p1 - p0, launches
@@ -277,6 +297,7 @@ def measure_precision(md, systems, precision, args, torch, stream, flush):
 
 def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate):
     evs = []
+    nvtx_push(torch, "roofline")
     for _ in range(nlaunch):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -286,6 +307,7 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
+    nvtx_pop(torch)
     sim.compute_forces()         # complete forces again
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in evs) / nlaunch
@@ -304,23 +326,29 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
             "flops_per_pair": FLOPS_PER_PAIR}
 
 
-def e2e(sim, systems, nsteps, pairs_per_step):
-    import numpy as np
-    states = [sim.state(r) for r in range(len(systems))]
+def e2e(sim, systems, nsteps, pairs_per_step, torch):
+    """Whole-job steps through the public API with host buffers: every step uploads the state of
+    every replica from pinned host memory (md_set_state, replica -1: lists rebuilt, forces
+    evaluated), runs one MD step and reads every force back (md_get_forces, replica -1)."""
+    n = sum(s.n_vapor for s in systems)
+    bufs = [torch.empty((n, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
+    x, v, f = (b.numpy() for b in bufs)
+    sim.state(-1, out=(x, v))
+    sim.set_state(-1, x, v)
+    sim.step(1)
+    sim.forces(-1, out=f)                      # warm-up of the same path
     h0, d0 = sim.transfer_bytes()
     t0 = time.perf_counter()
     for _ in range(nsteps):
-        for r, (x, v) in enumerate(states):
-            sim.set_state(r, x, v)
+        sim.set_state(-1, x, v)
         sim.step(1)
-        for r in range(len(systems)):
-            sim.forces(r)
+        sim.forces(-1, out=f)
     el = time.perf_counter() - t0
     h1, d1 = sim.transfer_bytes()
     return {"value": pairs_per_step * nsteps / el, "unit": UNIT,
             "h2d_bytes_per_step": (h1 - h0) // nsteps, "d2h_bytes_per_step": (d1 - d0) // nsteps,
             "ms_per_step": 1e3 * el / nsteps,
-            "path": "md_set_state (host arrays) + md_step(1) + md_get_forces per replica"}
+            "path": "md_set_state(-1) from pinned host arrays + md_step(1) + md_get_forces(-1)"}
 
 
 def run_ours(args):
@@ -370,7 +398,7 @@ def run_ours(args):
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
                                      args.precision, args.accumulate)
-        extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step)
+        extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step, torch)
         if not args.no_mixed and args.precision == "fp64":
             import oracle
             from paper_1812_07993_gb300 import workloads as W
@@ -414,6 +442,7 @@ def run_ours(args):
                            "force_accumulate": (args.accumulate if args.precision == "fp64"
                                                 else "per-molecule sums (full list)"),
                            "l2": "flushed between timed steps (256 MB write outside the events)",
+                           "launch_mode": args.launch_mode,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "md_steps_per_s": 1e3 / ms_per_step,
                 "replica_steps_per_s": nrep * 1e3 / ms_per_step,

@@ -189,11 +189,17 @@ md_status md_step(md_ctx* ctx, int64_t n);
 md_status md_sync(md_ctx* ctx);
 
 /* Copy replica state to caller-owned host arrays (3*n_vapor each, caller's molecule order).
- * x: positions wrapped into the box; v: velocities; either may be NULL. Synchronises. */
+ * replica = -1 copies every replica, concatenated in replica order (3 * total vapour each).
+ * x: positions wrapped into the box; v: velocities; either may be NULL. The rows are put into
+ * caller order on the device and copied with one cudaMemcpyAsync per array (pinned host memory
+ * makes it a DMA at full link speed). Synchronises. */
 md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
 
 /* Overwrite replica state from host arrays (3*n_vapor each, caller's order; positions must lie
- * inside the box). Forces are re-evaluated and lists rebuilt. The step counter is unchanged. */
+ * inside the box, checked on the host before anything is copied: MD_EINVAL leaves the state
+ * untouched). replica = -1 sets every replica from arrays concatenated in replica order. One
+ * copy per array into device staging rows, then a kernel writes the records; forces are
+ * re-evaluated and lists rebuilt. The step counter is unchanged. */
 md_status md_set_state(md_ctx* ctx, int32_t replica, const double* x, const double* v);
 
 /* Enqueue one evaluation of the forces at the current positions with the same pair-force kernel
@@ -212,7 +218,8 @@ md_status md_pair_pass(md_ctx* ctx);
  * read-backs, status words). Either pointer may be NULL. */
 md_status md_transfer_bytes(const md_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
-/* Copy the forces of the last evaluation (at the current positions) to host f (3*n_vapor). */
+/* Copy the forces of the last evaluation (at the current positions) to host f (3*n_vapor; with
+ * replica = -1, every replica concatenated in replica order). Synchronises. */
 md_status md_get_forces(md_ctx* ctx, int32_t replica, double* f);
 
 /* Observables of one replica at the current state. Fills *out; when non-NULL the arrays receive

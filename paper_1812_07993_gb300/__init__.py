@@ -168,6 +168,14 @@ def _as3(a) -> np.ndarray:
     return a
 
 
+def _as_out(a, n: int) -> np.ndarray:
+    """An output array must already be (n, 3) float64 and C-contiguous (it is written in place)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (n, 3)
+            and a.flags.c_contiguous and a.flags.writeable):
+        raise ValueError(f"output must be a writeable C-contiguous float64 array of shape ({n}, 3)")
+    return a
+
+
 class Simulation:
     """One context: a batch of replicas advanced together on the GPU.
 
@@ -238,23 +246,37 @@ class Simulation:
                                            ctypes.byref(ng), ctypes.byref(nb)), self.ctx)
         return nv.value, nw.value, ng.value, nb.value
 
-    def state(self, r: int = 0):
-        n = self.sizes(r)[0]
-        x = np.zeros((n, 3))
-        v = np.zeros((n, 3))
-        _check(load_library().md_get_state(self.ctx, r, x.ctypes.data_as(_DP),
-                                           v.ctypes.data_as(_DP)), self.ctx)
+    def n_molecules(self, r: int = 0) -> int:
+        """Vapour molecules of replica r, or of the whole context for r = -1."""
+        if r == -1:
+            return sum(s.n_vapor for s in self.systems)
+        return self.sizes(r)[0]
+
+    def state(self, r: int = 0, out=None):
+        """(x, v) of replica r (r = -1: every replica, concatenated in replica order). ``out`` may
+        supply the two (n, 3) float64 C-contiguous arrays to fill (e.g. pinned host memory)."""
+        n = self.n_molecules(r)
+        x, v = out if out is not None else (np.zeros((n, 3)), np.zeros((n, 3)))
+        _check(load_library().md_get_state(self.ctx, r, _as_out(x, n).ctypes.data_as(_DP),
+                                           _as_out(v, n).ctypes.data_as(_DP)), self.ctx)
         return x, v
 
     def set_state(self, r: int, x, v):
+        """Overwrite the state of replica r (r = -1: every replica, concatenated)."""
         x, v = _as3(x), _as3(v)
+        n = self.n_molecules(r)
+        if x.shape[0] != n or v.shape[0] != n:
+            raise ValueError(f"set_state({r}): expected {n} molecules, got {x.shape[0]}, "
+                             f"{v.shape[0]}")
         _check(load_library().md_set_state(self.ctx, r, x.ctypes.data_as(_DP),
                                            v.ctypes.data_as(_DP)), self.ctx)
 
-    def forces(self, r: int = 0):
-        n = self.sizes(r)[0]
-        f = np.zeros((n, 3))
-        _check(load_library().md_get_forces(self.ctx, r, f.ctypes.data_as(_DP)), self.ctx)
+    def forces(self, r: int = 0, out=None):
+        """Forces of replica r (r = -1: every replica, concatenated), into ``out`` if given."""
+        n = self.n_molecules(r)
+        f = out if out is not None else np.zeros((n, 3))
+        _check(load_library().md_get_forces(self.ctx, r, _as_out(f, n).ctypes.data_as(_DP)),
+               self.ctx)
         return f
 
     def wall(self, r: int = 0):

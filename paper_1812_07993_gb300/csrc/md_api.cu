@@ -44,6 +44,7 @@ struct md_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_steps = 0;
   size_t prof_total = 0, groups_total = 0, pores_total = 0;
+  double *stage_x = nullptr, *stage_v = nullptr;  // caller-order xyz rows (3 n_total each)
 };
 
 namespace {
@@ -540,6 +541,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.pos, N); ALLOC(A.vel, N); ALLOC(A.frc, N); ALLOC(A.pos_ref, N);
   ALLOC(A.pos_alt, N); ALLOC(A.vel_alt, N); ALLOC(A.frc_alt, N);
   ALLOC(A.lpos, N);
+  ALLOC(c->stage_x, 3 * N); ALLOC(c->stage_v, 3 * N);
   ALLOC(A.home, N); ALLOC(A.id, N); ALLOC(A.rep, N); ALLOC(A.id_alt, N);
   ALLOC(A.cell_tmp, N); ALLOC(A.slot_tmp, N); ALLOC(A.perm_tmp, N);
   ALLOC(A.nbr, N * (size_t)P.cap);
@@ -847,75 +849,81 @@ md_status md_sync(md_ctx* c) {
   return sync_status(c);
 }
 
-static md_status fetch_permuted(md_ctx* c, int32_t r, const dvec4* dsrc, double* out) {
-  const RepDev& R = c->reps[r];
-  const size_t n = (size_t)R.n_vap;
-  std::vector<dvec4> buf(n);
-  std::vector<int32_t> id(n);
-  if (n) {
-    CUDA_TRY(c, cudaMemcpyAsync(buf.data(), dsrc + R.vap_off, n * sizeof(dvec4),
-                                cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(id.data(), c->a.id + R.vap_off, n * sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, c->stream));
+// molecules of replica r (or of every replica, r = -1): first record and count
+static void replica_range(const md_ctx* c, int32_t r, int* off, int* n) {
+  if (r < 0) {
+    *off = 0;
+    *n = c->a.n_total;
+  } else {
+    *off = c->reps[r].vap_off;
+    *n = c->reps[r].n_vap;
   }
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  c->bytes_d2h += (int64_t)(n * (sizeof(dvec4) + sizeof(int32_t)));
-  for (size_t k = 0; k < n; ++k) {
-    const int i = id[k];
-    out[3 * i] = buf[k].x;
-    out[3 * i + 1] = buf[k].y;
-    out[3 * i + 2] = buf[k].z;
-  }
+}
+
+static bool check_replica_or_all(md_ctx* c, int32_t r) { return c && r >= -1 && r < c->n_reps; }
+
+// records -> caller-order rows on the device -> one copy into the caller's array
+static md_status fetch_rows(md_ctx* c, int32_t r, const dvec4* dsrc, double* stage, double* out) {
+  int off, n;
+  replica_range(c, r, &off, &n);
+  launch_store_rows(c->a, dsrc, stage, off, n, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  if (n)
+    CUDA_TRY(c, cudaMemcpyAsync(out, stage + 3 * (size_t)off, 3 * (size_t)n * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  c->bytes_d2h += (int64_t)(3 * (size_t)n * sizeof(double));
   return MD_OK;
 }
 
 md_status md_get_state(md_ctx* c, int32_t r, double* x, double* v) {
-  if (!check_replica(c, r)) return fail(c, MD_EINVAL, "bad replica");
+  if (!check_replica_or_all(c, r)) return fail(c, MD_EINVAL, "bad replica");
   md_status s = sync_status(c);
   if (s != MD_OK && s != MD_EOVERFLOW && s != MD_EUNSTABLE && s != MD_ETIMEOUT) return s;
   md_status t;
-  if (x && (t = fetch_permuted(c, r, c->a.pos, x)) != MD_OK) return t;
-  if (v && (t = fetch_permuted(c, r, c->a.vel, v)) != MD_OK) return t;
+  if (x && (t = fetch_rows(c, r, c->a.pos, c->stage_x, x)) != MD_OK) return t;
+  if (v && (t = fetch_rows(c, r, c->a.vel, c->stage_v, v)) != MD_OK) return t;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return s;
 }
 
 md_status md_get_forces(md_ctx* c, int32_t r, double* f) {
-  if (!check_replica(c, r) || !f) return fail(c, MD_EINVAL, "bad replica or NULL output");
+  if (!check_replica_or_all(c, r) || !f) return fail(c, MD_EINVAL, "bad replica or NULL output");
   md_status s = sync_status(c);
   if (s == MD_ECUDA) return s;
-  md_status t = fetch_permuted(c, r, c->a.frc, f);
-  return t != MD_OK ? t : s;
+  md_status t = fetch_rows(c, r, c->a.frc, c->stage_x, f);
+  if (t != MD_OK) return t;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return s;
 }
 
 md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
-  if (!check_replica(c, r) || !x || !v) return fail(c, MD_EINVAL, "bad replica or NULL input");
+  if (!check_replica_or_all(c, r) || !x || !v)
+    return fail(c, MD_EINVAL, "bad replica or NULL input");
   md_status s = sync_status(c);
   if (s != MD_OK) return s;
-  const RepDev& R = c->reps[r];
-  const size_t n = (size_t)R.n_vap;
-  std::vector<dvec4> pos(n), vel(n), zero(n, make_dvec4(0, 0, 0, 0));
-  std::vector<int32_t> id(n);
-  for (size_t i = 0; i < n; ++i) {
-    const double* q = x + 3 * i;
-    if (!(q[0] >= -R.hx && q[0] < R.hx && q[1] >= -R.hy && q[1] < R.hy && q[2] >= -R.hz &&
-          q[2] <= R.hz))
-      return fail(c, MD_EINVAL, "molecule " + std::to_string(i) + " outside the box");
-    pos[i] = make_dvec4(q[0], q[1], q[2], 0.0);
-    vel[i] = make_dvec4(v[3 * i], v[3 * i + 1], v[3 * i + 2], 0.0);
-    id[i] = (int32_t)i;
+  int off, n;
+  replica_range(c, r, &off, &n);
+  // every position inside its replica's box, checked before anything is copied
+  for (int rr = (r < 0 ? 0 : r); rr < (r < 0 ? c->n_reps : r + 1); ++rr) {
+    const RepDev& R = c->reps[rr];
+    const double* xr = x + 3 * (size_t)(R.vap_off - off);
+    for (int i = 0; i < R.n_vap; ++i) {
+      const double* q = xr + 3 * (size_t)i;
+      if (!(q[0] >= -R.hx && q[0] < R.hx && q[1] >= -R.hy && q[1] < R.hy && q[2] >= -R.hz &&
+            q[2] <= R.hz))
+        return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
+                                      std::to_string(i) + " outside the box");
+    }
   }
   if (n) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->a.pos + R.vap_off, pos.data(), n * sizeof(dvec4),
-                                cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->a.pos_ref + R.vap_off, pos.data(), n * sizeof(dvec4),
-                                cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->a.vel + R.vap_off, vel.data(), n * sizeof(dvec4),
-                                cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->a.frc + R.vap_off, zero.data(), n * sizeof(dvec4),
-                                cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->a.id + R.vap_off, id.data(), n * sizeof(int32_t),
-                                cudaMemcpyHostToDevice, c->stream));
-    c->bytes_h2d += (int64_t)(n * (4 * sizeof(dvec4) + sizeof(int32_t)));
+    const size_t bytes = 3 * (size_t)n * sizeof(double);
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage_x + 3 * (size_t)off, x, bytes, cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage_v + 3 * (size_t)off, v, bytes, cudaMemcpyHostToDevice,
+                                c->stream));
+    c->bytes_h2d += (int64_t)(2 * bytes);
+    launch_load_state(c->a, c->stage_x, c->stage_v, off, n, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
   }
   return rebuild_and_forces(c);
 }

@@ -183,6 +183,11 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
 cudaError_t configure_kernels();
+// state transfer through device staging rows (caller order, xyz interleaved)
+void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
+                       cudaStream_t s);
+void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,
+                       cudaStream_t s);
 // the pair kernel alone (no clearing, gather or kick): for timing the dominant kernel
 void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
                       cudaStream_t s);

@@ -746,10 +746,10 @@ __device__ __forceinline__ bool lt_pos(double x, double y) {
 // FP64, half list: molecule i walks the front of its row; each vapour pair's force goes to the
 // partner's back slot in pairbuf (fwd), where the partner's gather reads it in list order.
 
-// One FP64 pair term, branch-free: the force on i from list entry e, p = F(r)/r * (r_i - r_j), or
-// zero beyond the cutoff (the FP64 pipe costs a warp the same whether or not its lanes are
-// predicated off, so computing every entry and masking keeps the two chains of the unrolled loop
-// independent and free of divergence). Returns whether the pair is within the cutoff.
+// One FP64 pair term: whether list entry e is within the cutoff of i and, if so, the force on i,
+// p = F(r)/r * (r_i - r_j). The LJ part sits behind the cutoff branch: a warp whose lanes are all
+// beyond the cutoff skips it, which a masked (branch-free) form cannot (measured: the masked
+// two-entry form took ~9 % more FP64-pipe cycles).
 __device__ __forceinline__ bool pair_term(const Arrays& a, const PotDev& p, const RepDev& R,
                                           const dvec4& xi, uint32_t e, int N, double& px,
                                           double& py, double& pz) {
@@ -760,15 +760,15 @@ __device__ __forceinline__ bool pair_term(const Arrays& a, const PotDev& p, cons
   const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
   const double dz = xi.z - xj.z;
   const double r2 = dx * dx + dy * dy + dz * dz;
-  const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
+  if (!lt_pos(r2, wall ? p.rcw2 : p.rc2)) return false;
   const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
   const double inv2 = rcp_nr(r2);
   const double inv6 = inv2 * inv2 * inv2;
-  const double fr = in ? inv2 * inv6 * fma(a12, inv6, -b6) : 0.0;
+  const double fr = inv2 * inv6 * fma(a12, inv6, -b6);
   px = fr * dx;
   py = fr * dy;
   pz = fr * dz;
-  return in;
+  return true;
 }
 
 template <int TPP>
@@ -794,25 +794,17 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
       const uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
-      // two entries per iteration: independent FP64 chains, added in list order
-      for (int k = sub; k < n; k += 2 * TPP) {
-        const int k2 = k + TPP;
-        const bool has2 = k2 < n;
-        const uint32_t e1 = row[k], e2 = row[has2 ? k2 : k];
-        double p1x, p1y, p1z, p2x, p2y, p2z;
-        const bool in1 = pair_term(a, p, R, xi, e1, N, p1x, p1y, p1z);
-        const bool in2 = pair_term(a, p, R, xi, e2, N, p2x, p2y, p2z) && has2;
-        fx += p1x;
-        fy += p1y;
-        fz += p1z;
-        if (has2) {
-          fx += p2x;
-          fy += p2y;
-          fz += p2z;
+      for (int k = sub; k < n; k += TPP) {
+        const uint32_t e = row[k];
+        double px = 0.0, py = 0.0, pz = 0.0;
+        // warps whose lanes are all beyond the cutoff skip the pair term (a branch, not a mask)
+        if (pair_term(a, p, R, xi, e, N, px, py, pz)) {
+          fx += px;
+          fy += py;
+          fz += pz;
+          ++cnt;
         }
-        cnt += (in1 ? 1 : 0) + (in2 ? 1 : 0);
-        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(p1x, p1y, p1z, 0.0);
-        if (has2 && k2 < nvh) a.pairbuf[fw[k2]] = make_dvec4(p2x, p2y, p2z, 0.0);
+        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(px, py, pz, 0.0);
       }
     }
     fx = group_sum<TPP>(fx);
@@ -852,35 +844,21 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
-      for (int k = sub; k < n; k += 2 * TPP) {
-        const int k2 = k + TPP;
-        const bool has2 = k2 < n;
-        const uint32_t e1 = row[k], e2 = row[has2 ? k2 : k];
-        double p1x, p1y, p1z, p2x, p2y, p2z;
-        const bool in1 = pair_term(a, p, R, xi, e1, N, p1x, p1y, p1z);
-        const bool in2 = pair_term(a, p, R, xi, e2, N, p2x, p2y, p2z) && has2;
-        fx += p1x;
-        fy += p1y;
-        fz += p1z;
-        if (has2) {
-          fx += p2x;
-          fy += p2y;
-          fz += p2z;
+      for (int k = sub; k < n; k += TPP) {
+        const uint32_t e = row[k];
+        double px, py, pz;
+        if (pair_term(a, p, R, xi, e, N, px, py, pz)) {
+          fx += px;
+          fy += py;
+          fz += pz;
+          if (k < nvh) {  // Newton's third law: the partner receives -p
+            const int j = (int)(e & kIndexMask);
+            atomicAdd(&a.frc[j].x, neg_bits(px));
+            atomicAdd(&a.frc[j].y, neg_bits(py));
+            atomicAdd(&a.frc[j].z, neg_bits(pz));
+          }
+          ++cnt;
         }
-        // Newton's third law: the partner receives -p (vapour partners within the cutoff)
-        if (in1 && k < nvh) {
-          const int j = (int)(e1 & kIndexMask);
-          atomicAdd(&a.frc[j].x, neg_bits(p1x));
-          atomicAdd(&a.frc[j].y, neg_bits(p1y));
-          atomicAdd(&a.frc[j].z, neg_bits(p1z));
-        }
-        if (in2 && k2 < nvh) {
-          const int j = (int)(e2 & kIndexMask);
-          atomicAdd(&a.frc[j].x, neg_bits(p2x));
-          atomicAdd(&a.frc[j].y, neg_bits(p2y));
-          atomicAdd(&a.frc[j].z, neg_bits(p2z));
-        }
-        cnt += (in1 ? 1 : 0) + (in2 ? 1 : 0);
       }
     }
     fx = group_sum<TPP>(fx);
@@ -1649,6 +1627,50 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
     case 8: pair_pass_tpp<8>(a, p, mixed, t, s); break;
     default: pair_pass_tpp<4>(a, p, mixed, t, s); break;
   }
+}
+
+// ------------------------------------------------------------------------------------------------
+// state transfer: caller-order xyz arrays <-> cell-sorted device records
+
+// molecules [off, off + n) take the caller-order rows xin/vin (xyz interleaved, same offset); the
+// stored order restarts as the caller's (id = index within the replica), forces cleared
+__global__ void k_load_state(Arrays a, const double* __restrict__ xin,
+                             const double* __restrict__ vin, int off, int n) {
+  count_launch(a);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = off + k;
+  const dvec4 x = make_dvec4(xin[3 * (size_t)i], xin[3 * (size_t)i + 1], xin[3 * (size_t)i + 2],
+                             0.0);
+  a.pos[i] = x;
+  a.pos_ref[i] = x;
+  a.vel[i] = make_dvec4(vin[3 * (size_t)i], vin[3 * (size_t)i + 1], vin[3 * (size_t)i + 2], 0.0);
+  a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+  a.id[i] = i - a.reps[a.rep[i]].vap_off;
+}
+
+// out rows (caller order, xyz interleaved) of molecules [off, off + n) from the records src
+__global__ void k_store_rows(Arrays a, const dvec4* __restrict__ src, double* __restrict__ out,
+                             int off, int n) {
+  count_launch(a);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = off + k;
+  const size_t row = (size_t)a.reps[a.rep[i]].vap_off + (size_t)a.id[i];
+  const dvec4 v = src[i];
+  out[3 * row] = v.x;
+  out[3 * row + 1] = v.y;
+  out[3 * row + 2] = v.z;
+}
+
+void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
+                       cudaStream_t s) {
+  if (n > 0) k_load_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n);
+}
+
+void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,
+                       cudaStream_t s) {
+  if (n > 0) k_store_rows<<<nblocks(n, 256), 256, 0, s>>>(a, src, out, off, n);
 }
 
 // one-time kernel attributes (before any launch or capture)

@@ -216,6 +216,34 @@ def test_all_pairs_method_four_shapes(shapes):
         assert o["step"] == 3
 
 
+def test_whole_context_transfers_match_per_replica(shapes):
+    """replica -1 reads and writes every replica at once, concatenated in replica order."""
+    with md.Simulation(shapes) as sim:
+        sim.step(7)
+        x, v = sim.state(-1)
+        f = sim.forces(-1)
+        per = [sim.state(r) for r in range(len(shapes))]
+        np.testing.assert_array_equal(x, np.concatenate([p[0] for p in per]))
+        np.testing.assert_array_equal(v, np.concatenate([p[1] for p in per]))
+        np.testing.assert_array_equal(f, np.concatenate([sim.forces(r) for r in range(len(shapes))]))
+        h0, d0 = sim.transfer_bytes()
+        sim.set_state(-1, x, v)
+        h1, _ = sim.transfer_bytes()
+        assert h1 - h0 >= 48 * len(x)
+        x2, v2 = sim.state(-1)
+        np.testing.assert_array_equal(x2, x)
+        np.testing.assert_array_equal(v2, v)
+        # forces re-evaluated at the same positions (lists rebuilt): equal to rounding
+        assert force_err(sim.forces(-1), f) <= 1e-13
+        bad = x.copy()
+        bad[len(shapes[0].x0) + 5, 2] = 1e3
+        with pytest.raises(md.MDError):
+            sim.set_state(-1, bad, v)
+        np.testing.assert_array_equal(sim.state(-1)[0], x)  # untouched by the rejected call
+        with pytest.raises(ValueError):
+            sim.set_state(-1, x[:-1], v[:-1])
+
+
 def test_generated_wall_matches_generator(shapes):
     with md.Simulation(shapes, generate_wall=True) as sim:
         for r, s in enumerate(shapes):
