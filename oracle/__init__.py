@@ -37,7 +37,8 @@ class Params(ctypes.Structure):
                 ("thermostat_every", ctypes.c_int32), ("dt", ctypes.c_double),
                 ("T0", ctypes.c_double), ("tau_B", ctypes.c_double),
                 ("slab_half", ctypes.c_double), ("r_ads", ctypes.c_double),
-                ("bin_width", ctypes.c_double)]
+                ("bin_width", ctypes.c_double), ("dims", ctypes.c_int32),
+                ("hard_walls", ctypes.c_int32)]
 
 
 class PoreC(ctypes.Structure):
@@ -80,6 +81,13 @@ def _load(path: str):
                           _D, _I64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _D, _D, _D,
                           ctypes.POINTER(Stats)]
     L.orc_run.restype = ctypes.c_int
+    L.orc_run_geom.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(PoreC), ctypes.c_int,
+                               ctypes.c_int64, _D, _D, _D, ctypes.c_int64, _D, _I64,
+                               ctypes.c_int64, ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                               ctypes.POINTER(Stats)]
+    L.orc_run_geom.restype = ctypes.c_int
+    L.orc_in_solid.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(PoreC), ctypes.c_int, _D]
+    L.orc_in_solid.restype = ctypes.c_int
     L.orc_observables.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(PoreC), ctypes.c_int,
                                   ctypes.c_int64, _D, _D, _I64, _I64, _I64, ctypes.c_int]
     L.orc_observables.restype = ctypes.c_int
@@ -150,7 +158,7 @@ def make_params(system=None, potential=None, **over) -> Params:
     """Build oracle parameters from a ``workloads.System`` and ``workloads.Potential``."""
     d = dict(Lx=10.0, Ly=10.0, Lz=10.0, eps=1.0, sigma=1.0, mass=1.0, rc=2.5, eps_w=1.5,
              sigma_w=1.0, rc_w=2.5, shift_energy=1, thermostat_every=0, dt=0.005, T0=1.0,
-             tau_B=0.0, slab_half=0.0, r_ads=1.5, bin_width=0.5)
+             tau_B=0.0, slab_half=0.0, r_ads=1.5, bin_width=0.5, dims=3, hard_walls=0)
     if potential is not None:
         for k in ("eps", "sigma", "mass", "rc", "eps_w", "sigma_w", "rc_w", "shift_energy",
                   "r_ads", "bin_width"):
@@ -158,6 +166,8 @@ def make_params(system=None, potential=None, **over) -> Params:
     if system is not None:
         for k in ("Lx", "Ly", "Lz", "dt", "T0", "tau_B", "thermostat_every", "slab_half"):
             d[k] = getattr(system, k)
+        d["dims"] = getattr(system, "dims", 3) or 3
+        d["hard_walls"] = 1 if getattr(system, "wall_model", 0) == 1 else 0
     d.update(over)
     return Params(**d)
 
@@ -191,8 +201,11 @@ def kinetic(p: Params, v) -> float:
 class State:
     """An oracle trajectory: positions, velocities, forces and the step counter."""
 
-    def __init__(self, p: Params, x, v, wall=None, method: int = 1, nthreads: int = 1):
+    def __init__(self, p: Params, x, v, wall=None, method: int = 1, nthreads: int = 1,
+                 pores: Sequence = ()):
         self.p = p
+        self.pores = list(pores)
+        self._pc = _pores_c(self.pores)
         self.x = _c3(x).copy()
         self.v = _c3(v).copy()
         self.wall = _c3(wall if wall is not None else np.zeros((0, 3)))
@@ -207,16 +220,31 @@ class State:
         pe = np.zeros(max(nsteps, 1))
         step = ctypes.c_int64(self.step)
         st = Stats()
-        rc = lib().orc_run(ctypes.byref(self.p), n, _dp(self.x), _dp(self.v), _dp(self.f),
-                           len(self.wall), _dp(self.wall), ctypes.byref(step), nsteps,
-                           self.method, self.nthreads, _dp(ke), _dp(pe), _dp(self.d2wall),
-                           ctypes.byref(st))
+        rc = lib().orc_run_geom(ctypes.byref(self.p), self._pc, len(self.pores), n, _dp(self.x),
+                                _dp(self.v), _dp(self.f), len(self.wall), _dp(self.wall),
+                                ctypes.byref(step), nsteps, self.method, self.nthreads, _dp(ke),
+                                _dp(pe), _dp(self.d2wall), ctypes.byref(st))
         if rc != 0:
             raise ValueError("oracle run failed")
         self.step = step.value
         if nsteps > 0:
             self.stats = st.as_dict()
         return ke[:nsteps], pe[:nsteps]
+
+
+def _pores_c(pores):
+    arr = (PoreC * max(len(pores), 1))()
+    for k, q in enumerate(pores):
+        arr[k] = PoreC(q.kind, q.cx, q.cy, q.r0, q.r1, q.r_cavity, q.width)
+    return arr
+
+
+def in_solid(p: Params, pores: Sequence, x) -> np.ndarray:
+    """Per point: 1 if it lies in the solid of a hard-wall system."""
+    x = _c3(x)
+    pc = _pores_c(pores)
+    return np.array([lib().orc_in_solid(ctypes.byref(p), pc, len(pores), _dp(np.ascontiguousarray(r)))
+                     for r in x], dtype=np.int64)
 
 
 def nbins(p: Params) -> int:
@@ -241,13 +269,6 @@ def observables(p: Params, pores: Sequence, x, d2wall):
     if rc != 0:
         raise ValueError("oracle observables failed")
     return occ[:npores], ads, prof
-
-
-def _pores_c(pores):
-    arr = (PoreC * max(len(pores), 1))()
-    for k, q in enumerate(pores):
-        arr[k] = PoreC(q.kind, q.cx, q.cy, q.r0, q.r1, q.r_cavity, q.width)
-    return arr
 
 
 def molecule_virials(p: Params, x, wall=None, method: int = 1, nthreads: int = 1):

@@ -243,8 +243,8 @@ double orc_kinetic(const orc_params* p, int64_t n, const double* v) {
   return 0.5 * p->mass * s;
 }
 
-/* specular reflection at z = +-Lz/2, then periodic wrap of x and y into [-L/2, L/2) */
-static void apply_boundaries(const orc_params* p, double* r, double* v) {
+/* specular reflection at z = +-Lz/2 */
+static void reflect_box_z(const orc_params* p, double* r, double* v) {
   const double hz = 0.5 * p->Lz;
   if (r[2] > hz) {
     r[2] = p->Lz - r[2];
@@ -253,6 +253,10 @@ static void apply_boundaries(const orc_params* p, double* r, double* v) {
     r[2] = -p->Lz - r[2];
     v[2] = -v[2];
   }
+}
+
+/* periodic wrap of x and y into [-L/2, L/2) */
+static void wrap_xy(const orc_params* p, double* r) {
   if (r[0] >= 0.5 * p->Lx) r[0] -= p->Lx;
   else if (r[0] < -0.5 * p->Lx) r[0] += p->Lx;
   if (r[1] >= 0.5 * p->Ly) r[1] -= p->Ly;
@@ -262,16 +266,93 @@ static void apply_boundaries(const orc_params* p, double* r, double* v) {
 int orc_run(const orc_params* p, int64_t n, double* x, double* v, double* f, int64_t nw,
             const double* w, int64_t* step, int64_t nsteps, int method, int nthreads,
             double* ke_log, double* pe_log, double* d2wall, orc_stats* last) {
+  if (p->hard_walls) return -1; /* hard walls need the pore geometry: orc_run_geom */
+  return orc_run_geom(p, NULL, 0, n, x, v, f, nw, w, step, nsteps, method, nthreads, ke_log,
+                      pe_log, d2wall, last);
+}
+
+/* floor of a prism pore: z = h - depth for a blind pore (0 < depth < 2h), else below the slab */
+static double prism_floor(const orc_pore* q, double h) {
+  return (q->width > 0.0 && q->width < 2.0 * h) ? h - q->width : -2.0 * h;
+}
+
+/* carved region of a pore at a point (dx, dy = offset from the axis, z) */
+static int in_pore(const orc_pore* q, double dx, double dy, double z, double h) {
+  double rxy2 = dx * dx + dy * dy;
+  switch (q->kind) {
+    case 1: return rxy2 < q->r0 * q->r0;
+    case 2: return sqrt(rxy2) < q->r0 + (q->r1 - q->r0) * (z + h) / (2.0 * h);
+    case 3: return fabs(dy) < 0.5 * q->width;
+    case 4: return rxy2 < q->r0 * q->r0 || rxy2 + z * z < q->r_cavity * q->r_cavity;
+    case 5: return fabs(dx) < q->r0 && fabs(dy) < q->r1 && z > prism_floor(q, h);
+    default: return 0;
+  }
+}
+
+int orc_in_solid(const orc_params* p, const orc_pore* pores, int npores, const double* r) {
+  const double h = p->slab_half;
+  if (!(fabs(r[2]) < h)) return 0;
+  for (int q = 0; q < npores; ++q) {
+    double dx = min_image(r[0] - pores[q].cx, p->Lx), dy = min_image(r[1] - pores[q].cy, p->Ly);
+    if (in_pore(&pores[q], dx, dy, r[2], h)) return 0;
+  }
+  return 1;
+}
+
+/* Hard walls: a molecule that ended the drift inside the solid is reflected off the face it
+ * crossed. From outside the slab (|z_old| >= h) that is the slab face on its side; from inside a
+ * pore it is each side wall (|dx| >= r0 or |dy| >= r1, slit: |dy| >= width/2) it passed and the
+ * floor (z <= floor). Specular: the coordinate is mirrored in the face, that velocity component
+ * reversed. */
+static void reflect_solid(const orc_params* p, const orc_pore* pores, int npores,
+                          const double* r_old, double* r, double* v) {
+  const double h = p->slab_half;
+  if (!orc_in_solid(p, pores, npores, r)) return;
+  if (fabs(r_old[2]) >= h) {
+    const double face = r_old[2] > 0.0 ? h : -h;
+    r[2] = 2.0 * face - r[2];
+    v[2] = -v[2];
+    return;
+  }
+  for (int q = 0; q < npores; ++q) {
+    const orc_pore* P = &pores[q];
+    double dx0 = min_image(r_old[0] - P->cx, p->Lx), dy0 = min_image(r_old[1] - P->cy, p->Ly);
+    if (!in_pore(P, dx0, dy0, r_old[2], h)) continue;
+    double dx = min_image(r[0] - P->cx, p->Lx), dy = min_image(r[1] - P->cy, p->Ly);
+    if (P->kind == 5) {
+      if (dx >= P->r0) { r[0] += 2.0 * (P->r0 - dx); v[0] = -v[0]; }
+      else if (dx <= -P->r0) { r[0] += 2.0 * (-P->r0 - dx); v[0] = -v[0]; }
+      if (dy >= P->r1) { r[1] += 2.0 * (P->r1 - dy); v[1] = -v[1]; }
+      else if (dy <= -P->r1) { r[1] += 2.0 * (-P->r1 - dy); v[1] = -v[1]; }
+      const double fl = prism_floor(P, h);
+      if (r[2] <= fl) { r[2] = 2.0 * fl - r[2]; v[2] = -v[2]; }
+    } else if (P->kind == 3) {
+      const double hw = 0.5 * P->width;
+      if (dy >= hw) { r[1] += 2.0 * (hw - dy); v[1] = -v[1]; }
+      else if (dy <= -hw) { r[1] += 2.0 * (-hw - dy); v[1] = -v[1]; }
+    }
+    return;
+  }
+}
+
+int orc_run_geom(const orc_params* p, const orc_pore* pores, int npores, int64_t n, double* x,
+                 double* v, double* f, int64_t nw, const double* w, int64_t* step, int64_t nsteps,
+                 int method, int nthreads, double* ke_log, double* pe_log, double* d2wall,
+                 orc_stats* last) {
   const double dt = p->dt, m = p->mass;
+  const double dof = p->dims == 2 ? 2.0 : 3.0;
   for (int64_t s = 0; s < nsteps; ++s) {
     /* Fig. 2: r(t+dt) = r(t) + v(t) dt + a(t) dt^2 / 2 ;  v(t+dt/2) = v(t) + a(t) dt / 2 */
     for (int64_t i = 0; i < n; ++i) {
+      double r_old[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
       for (int c = 0; c < 3; ++c) {
         double a = f[3 * i + c] / m;
         x[3 * i + c] = x[3 * i + c] + v[3 * i + c] * dt + 0.5 * a * dt * dt;
         v[3 * i + c] = v[3 * i + c] + 0.5 * a * dt;
       }
-      apply_boundaries(p, &x[3 * i], &v[3 * i]);
+      reflect_box_z(p, &x[3 * i], &v[3 * i]);
+      if (p->hard_walls) reflect_solid(p, pores, npores, r_old, &x[3 * i], &v[3 * i]);
+      wrap_xy(p, &x[3 * i]);
     }
     /* Fig. 1: a(t+dt) from the interaction potential at r(t+dt) */
     orc_stats st;
@@ -285,7 +366,7 @@ int orc_run(const orc_params* p, int64_t n, double* x, double* v, double* f, int
     if (last) *last = st;
     /* Fig. 4: Berendsen scaling v <- lambda v on every n_th-th step */
     if (p->thermostat_every > 0 && (*step % p->thermostat_every) == 0 && n > 0) {
-      double T = 2.0 * ke / (3.0 * (double)n);
+      double T = 2.0 * ke / (dof * (double)n);
       double tauB = p->tau_B > 0.0 ? p->tau_B : p->thermostat_every * dt;
       double lambda = 1.0;
       if (T > 0.0) lambda = sqrt(1.0 + (p->thermostat_every * dt / tauB) * (p->T0 / T - 1.0));
@@ -293,18 +374,6 @@ int orc_run(const orc_params* p, int64_t n, double* x, double* v, double* f, int
     }
   }
   return 0;
-}
-
-/* carved region of a pore at a point (dx, dy = offset from the axis, z) */
-static int in_pore(const orc_pore* q, double dx, double dy, double z, double h) {
-  double rxy2 = dx * dx + dy * dy;
-  switch (q->kind) {
-    case 1: return rxy2 < q->r0 * q->r0;
-    case 2: return sqrt(rxy2) < q->r0 + (q->r1 - q->r0) * (z + h) / (2.0 * h);
-    case 3: return fabs(dy) < 0.5 * q->width;
-    case 4: return rxy2 < q->r0 * q->r0 || rxy2 + z * z < q->r_cavity * q->r_cavity;
-    default: return 0;
-  }
 }
 
 int orc_nbins(const orc_params* p) { return (int)ceil(p->Lz / p->bin_width); }
@@ -340,9 +409,13 @@ int orc_observables(const orc_params* p, const orc_pore* pores, int npores, int6
   return 0;
 }
 
-/* cross-section area of a pore's carved region at height z */
+/* cross-section of a pore's carved region at height z: an area, or for dims == 2 a length in x */
 static double pore_area(const orc_params* p, const orc_pore* q, double z) {
   const double h = p->slab_half;
+  if (q->kind == 5) {
+    if (z < prism_floor(q, h)) return 0.0; /* (the floor itself has measure zero) */
+    return p->dims == 2 ? 2.0 * q->r0 : 4.0 * q->r0 * q->r1;
+  }
   switch (q->kind) {
     case 1: return M_PI * q->r0 * q->r0;
     case 2: {
@@ -361,7 +434,10 @@ static double pore_area(const orc_params* p, const orc_pore* q, double z) {
 
 double orc_pore_volume(const orc_params* p, const orc_pore* q) {
   const int m = 20000; /* even */
-  const double a = -p->slab_half, b = p->slab_half, step = (b - a) / m;
+  double a = -p->slab_half;
+  const double b = p->slab_half;
+  if (q->kind == 5 && prism_floor(q, b) > a) a = prism_floor(q, b); /* where the pore is */
+  const double step = (b - a) / m;
   double s = pore_area(p, q, a) + pore_area(p, q, b);
   for (int k = 1; k < m; ++k) s += (k % 2 ? 4.0 : 2.0) * pore_area(p, q, a + k * step);
   return s * step / 3.0;
@@ -381,7 +457,7 @@ int orc_pore_pressure(const orc_params* p, const orc_pore* pores, int npores, in
       sum += wvir[i];
     }
     const double vol = orc_pore_volume(p, &pores[q]);
-    pressure[q] = vol > 0.0 ? sum / (3.0 * vol) : 0.0;
+    pressure[q] = vol > 0.0 ? sum / ((p->dims == 2 ? 2.0 : 3.0) * vol) : 0.0;
   }
   return 0;
 }

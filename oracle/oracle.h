@@ -41,11 +41,17 @@ typedef struct {
   double slab_half;           /* wall slab |z| < slab_half (occupancy window) */
   double r_ads;               /* adsorbed when the nearest wall atom is closer than r_ads */
   double bin_width;           /* axial profile bin width */
+  int32_t dims;               /* 3, or 2: a planar system in x-z (y = 0, vy = 0), T = m sum v^2 / (2N) */
+  int32_t hard_walls;         /* 1: no wall atoms; the slab |z| < slab_half minus the pores is a solid
+                                 that reflects molecules specularly (the paper's reflecting pore
+                                 walls, Sec. 4 and Sec. 5); needs orc_run_geom */
 } orc_params;
 
 typedef struct {
-  int32_t kind;               /* 1 cylinder, 2 cone, 3 slit, 4 ink-bottle */
+  int32_t kind;               /* 1 cylinder, 2 cone, 3 slit, 4 ink-bottle, 5 rectangular prism */
   double cx, cy, r0, r1, r_cavity, width;
+  /* prism: |x - cx| < r0, |y - cy| < r1, open at the slab's top face z = +slab_half and closed by
+     a floor at z = slab_half - width when 0 < width < 2 slab_half (otherwise a through-pore) */
 } orc_pore;
 
 typedef struct {
@@ -75,11 +81,13 @@ int orc_forces_w(const orc_params* p, int64_t n, const double* x, int64_t nw, co
 
 /* Volume of a pore's carved region inside the slab |z| < slab_half: the integral over z of the
  * cross-section area (cylinder pi r0^2, cone pi R(z)^2, slit width * Lx, ink-bottle
- * pi max(r0^2, r_cav^2 - z^2)), by composite Simpson quadrature on 20000 intervals. */
+ * pi max(r0^2, r_cav^2 - z^2), prism 4 r0 r1 above its floor), by composite Simpson quadrature on
+ * 20000 intervals over the z range the pore occupies. For dims == 2 the measure is the area in the
+ * x-z plane: the cross-section is the length 2 r0 (prism). */
 double orc_pore_volume(const orc_params* p, const orc_pore* q);
 
-/* Virial pressure in each pore (Sec. 2): P_q = (sum m v_i^2 + sum W_i) / (3 V_q) over the molecules
- * inside pore q (the occupancy predicate), W_i from orc_forces_w. */
+/* Virial pressure in each pore (Sec. 2): P_q = (sum m v_i^2 + sum W_i) / (dims V_q) over the
+ * molecules inside pore q (the occupancy predicate), W_i from orc_forces_w. */
 int orc_pore_pressure(const orc_params* p, const orc_pore* pores, int npores, int64_t n,
                       const double* x, const double* v, const double* wvir, double* pressure);
 
@@ -94,6 +102,19 @@ double orc_kinetic(const orc_params* p, int64_t n, const double* v);
 int orc_run(const orc_params* p, int64_t n, double* x, double* v, double* f, int64_t nw,
             const double* w, int64_t* step, int64_t nsteps, int method, int nthreads,
             double* ke_log, double* pe_log, double* d2wall, orc_stats* last);
+
+/* As orc_run, with the pore geometry that hard walls need: after the drift and the z reflection at
+ * the box, a molecule that ends inside the solid (p->hard_walls) is reflected specularly off the
+ * face it crossed -- the slab face z = +-slab_half if it came from outside the slab, else the side
+ * walls or the floor of the pore it came from (axis-aligned faces: prism and slit pores) -- and
+ * x, y are then wrapped. The thermostat uses T = m sum v^2 / (dims N). */
+int orc_run_geom(const orc_params* p, const orc_pore* pores, int npores, int64_t n, double* x,
+                 double* v, double* f, int64_t nw, const double* w, int64_t* step, int64_t nsteps,
+                 int method, int nthreads, double* ke_log, double* pe_log, double* d2wall,
+                 orc_stats* last);
+
+/* 1 if point x (3) lies in the solid of a hard-wall system: |z| < slab_half outside every pore. */
+int orc_in_solid(const orc_params* p, const orc_pore* pores, int npores, const double* x);
 
 /* Per-pore observables at positions x with nearest-wall distances d2wall (from orc_forces).
  * Groups: one per pore (a molecule belongs to the pore whose axis is nearest in xy; ties go to

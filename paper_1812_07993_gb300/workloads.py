@@ -19,6 +19,11 @@ Geometry conventions
     - SLIT:      |dy| < width / 2                                       (spans the whole x extent)
     - INKBOTTLE: dx^2 + dy^2 < r0^2  or  dx^2 + dy^2 + z^2 < r_cavity^2 (neck through the slab,
                  spherical cavity at the slab centre)
+    - PRISM:     |dx| < r0 and |dy| < r1 and z > h - width   (rectangular pore open at the slab's top
+                 face; a floor at z = h - width when 0 < width < 2h, else through the slab)
+* Wall models: 0 = fixed LJ wall atoms (the lattice above); 1 = hard walls -- no atoms, the slab
+  minus the pores is a solid that reflects molecules specularly (the paper's reflecting pore walls).
+* Planar systems (dims = 2): every molecule at y = 0 with vy = 0, moving in the x-z plane.
 * Vapour: random sequential addition, uniform in ``slab_half < |z| < Lz/2``, at least ``min_sep``
   from every wall atom and from every other vapour molecule (periodic in x, y). Pores start empty.
 * Velocities: each component drawn from N(0, T0/m), then the mean (centre-of-mass) velocity removed.
@@ -31,9 +36,9 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-PORE_NONE, PORE_CYLINDER, PORE_CONE, PORE_SLIT, PORE_INKBOTTLE = 0, 1, 2, 3, 4
+PORE_NONE, PORE_CYLINDER, PORE_CONE, PORE_SLIT, PORE_INKBOTTLE, PORE_PRISM = 0, 1, 2, 3, 4, 5
 PORE_KIND_NAMES = {PORE_CYLINDER: "cylinder", PORE_CONE: "cone", PORE_SLIT: "slit",
-                   PORE_INKBOTTLE: "inkbottle"}
+                   PORE_INKBOTTLE: "inkbottle", PORE_PRISM: "prism"}
 
 
 @dataclasses.dataclass
@@ -41,10 +46,10 @@ class Pore:
     kind: int
     cx: float = 0.0
     cy: float = 0.0
-    r0: float = 0.0        # cylinder radius / cone radius at z=-h / ink-bottle neck radius
-    r1: float = 0.0        # cone radius at z=+h
+    r0: float = 0.0        # cylinder radius / cone radius at z=-h / ink-bottle neck / prism half-side x
+    r1: float = 0.0        # cone radius at z=+h / prism half-side y
     r_cavity: float = 0.0  # ink-bottle cavity radius
-    width: float = 0.0     # slit width
+    width: float = 0.0     # slit width / prism depth from the top face (<= 0 or >= 2h: through)
 
 
 @dataclasses.dataclass
@@ -80,6 +85,8 @@ class System:
     tau_B: float = 0.0       # 0 -> thermostat_every * dt (plain velocity rescaling)
     thermostat_every: int = 10
     seed: int = 0
+    dims: int = 3            # 2: planar system in x-z (y = 0, vy = 0)
+    wall_model: int = 0      # 0 LJ wall atoms, 1 hard reflecting walls (no atoms)
 
     @property
     def n_vapor(self) -> int:
@@ -117,6 +124,10 @@ def carve_mask(points: np.ndarray, pore: Pore, Lx: float, Ly: float, slab_half: 
         return np.abs(dy) < 0.5 * pore.width
     if pore.kind == PORE_INKBOTTLE:
         return (rxy2 < pore.r0 * pore.r0) | (rxy2 + z * z < pore.r_cavity * pore.r_cavity)
+    if pore.kind == PORE_PRISM:
+        h = slab_half
+        floor = h - pore.width if 0.0 < pore.width < 2.0 * h else -2.0 * h
+        return (np.abs(dx) < pore.r0) & (np.abs(dy) < pore.r1) & (z > floor)
     raise ValueError(f"unknown pore kind {pore.kind}")
 
 
@@ -163,7 +174,8 @@ def _shift_query(q: np.ndarray, Lx: float, Ly: float, Lz: float) -> np.ndarray:
 
 def rsa_vapor(rng: np.random.Generator, n: int, Lx: float, Ly: float, Lz: float, z_lo: float,
               z_hi: float, wall: np.ndarray, min_sep: float = 0.9,
-              max_attempt_factor: int = 1000) -> np.ndarray:
+              max_attempt_factor: int = 1000, planar: bool = False,
+              upper_only: bool = False) -> np.ndarray:
     """Random sequential addition of ``n`` points uniform in ``z_lo < |z| < z_hi`` (x, y periodic),
     each at least ``min_sep`` from the wall points and from each other.
 
@@ -188,7 +200,9 @@ def rsa_vapor(rng: np.random.Generator, n: int, Lx: float, Ly: float, Lz: float,
         y = rng.uniform(-0.5 * Ly, 0.5 * Ly, k)
         az = rng.uniform(z_lo, z_hi, k)
         sgn = np.where(rng.uniform(0.0, 1.0, k) < 0.5, -1.0, 1.0)
-        cand = np.stack([x, y, sgn * az], axis=1)
+        if upper_only:
+            sgn[:] = 1.0
+        cand = np.stack([x, 0.0 * y if planar else y, sgn * az], axis=1)
         ok = np.ones(k, dtype=bool)
         if wall_tree is not None:
             d, _ = wall_tree.query(wq(cand), k=1, distance_upper_bound=min_sep)
@@ -212,7 +226,8 @@ def rsa_vapor(rng: np.random.Generator, n: int, Lx: float, Ly: float, Lz: float,
 
 def rsa_in_pores(rng: np.random.Generator, n: int, pores: Sequence[Pore], Lx: float, Ly: float,
                  Lz: float, slab_half: float, obstacles: np.ndarray, min_sep: float = 0.9,
-                 max_attempt_factor: int = 1000) -> np.ndarray:
+                 max_attempt_factor: int = 1000, planar: bool = False,
+              upper_only: bool = False) -> np.ndarray:
     """Random sequential addition of ``n`` points uniform in the carved regions of ``pores`` within
     the slab ``|z| < slab_half``, each at least ``min_sep`` from the obstacle points (wall atoms)
     and from each other. Candidates are drawn uniform in the slab and kept where a pore's
@@ -233,6 +248,8 @@ def rsa_in_pores(rng: np.random.Generator, n: int, pores: Sequence[Pore], Lx: fl
             raise RuntimeError("random sequential addition in the pores did not converge")
         cand = np.stack([rng.uniform(-0.5 * Lx, 0.5 * Lx, k), rng.uniform(-0.5 * Ly, 0.5 * Ly, k),
                          rng.uniform(-slab_half, slab_half, k)], axis=1)
+        if planar:
+            cand[:, 1] = 0.0
         inside = np.zeros(k, dtype=bool)
         for p in pores:
             inside |= carve_mask(cand, p, Lx, Ly, slab_half)
@@ -257,10 +274,13 @@ def rsa_in_pores(rng: np.random.Generator, n: int, pores: Sequence[Pore], Lx: fl
     return np.ascontiguousarray(accepted)
 
 
-def maxwell_velocities(rng: np.random.Generator, n: int, T0: float, mass: float = 1.0) -> np.ndarray:
+def maxwell_velocities(rng: np.random.Generator, n: int, T0: float, mass: float = 1.0,
+                       planar: bool = False) -> np.ndarray:
     if n == 0:
         return np.zeros((0, 3))
     v = rng.normal(0.0, math.sqrt(T0 / mass), size=(n, 3))
+    if planar:
+        v[:, 1] = 0.0
     v -= v.mean(axis=0, keepdims=True)
     return np.ascontiguousarray(v)
 
@@ -404,6 +424,55 @@ def drying_cylinder_pore(seed: int = 7, n_in: int = 1000, n_out: int = 4800, R: 
     return System(name="drying_cylinder_pore", Lx=L, Ly=L, Lz=Lz, slab_half=h, lattice_a=1.0,
                   pores=[pore], x0=x0, v0=v0, wall=wall, T0=T0, dt=0.005, tau_B=tau_B,
                   thermostat_every=10, seed=seed)
+
+
+def paper_prism_pore(seed: int = 11, n_in: int = 250, n_out: int = 450, side: float = 5.0,
+                     depth: float = 50.0, T0: float = 1.0, tau_B: float = 0.5) -> System:
+    """The paper's 3D drying geometry (Sec. 5) in reduced units, with its reflecting walls: a
+    rectangular prism pore of cross-section side x side and depth ``depth`` (the paper's 10:1:1
+    prism), closed on five faces, its top face open into an outer space nine times the pore volume
+    (3 side x 3 side x depth above the slab; periodic in x, y, reflecting at the box top); hard walls,
+    no wall atoms. n_in molecules start in the pore and n_out outside, at a fifth of the pore
+    density (the paper's saturated pore and 20 % saturated surroundings), T*=1.0, Berendsen
+    tau_B = 0.5. Seeds: ``seed`` outer placement, ``seed + 1`` pore filling, ``seed + 2``
+    velocities."""
+    L = 3.0 * side
+    h = 0.5 * depth + 1.0                  # floor at z = h - depth = 1 - depth / 2
+    Lz = 2.0 * (h + depth)
+    pore = Pore(PORE_PRISM, r0=0.5 * side, r1=0.5 * side, width=depth)
+    none = np.zeros((0, 3))
+    inner = rsa_in_pores(np.random.default_rng(seed + 1), n_in, [pore], L, L, Lz, h, none)
+    outer = rsa_vapor(np.random.default_rng(seed), n_out, L, L, Lz, h, 0.5 * Lz, inner,
+                      upper_only=True)
+    x0 = np.ascontiguousarray(np.concatenate([inner, outer], axis=0))
+    v0 = maxwell_velocities(np.random.default_rng(seed + 2), len(x0), T0)
+    return System(name="paper_prism_pore", Lx=L, Ly=L, Lz=Lz, slab_half=h, lattice_a=1.0,
+                  pores=[pore], x0=x0, v0=v0, wall=none, T0=T0, dt=0.005, tau_B=tau_B,
+                  thermostat_every=10, seed=seed, dims=3, wall_model=1)
+
+
+def paper_pore_2d(seed: int = 13, n_in: int = 84, n_out: int = 352, lx: float = 20.0,
+                  ly: float = 20.0, k: int = 3, T0: float = 1.0, tau_B: float = 0.5) -> System:
+    """The paper's 2D geometry (Sec. 4, Fig. 5) in reduced units: a planar system (dims = 2, the x-z
+    plane at y = 0) with a pore lx deep and ly wide, reflecting walls on three sides, open into an
+    outer space k lx high and (2k + 1) ly wide (21 times the pore for k = 3; periodic in x,
+    reflecting at the box top). n_in molecules start in the pore and n_out outside, at a fifth of
+    the pore density, T*=1.0, Berendsen tau_B = 0.5. Ly = 9 only spaces the (empty) periodic
+    images in y. Seeds: ``seed`` outer, ``seed + 1`` pore, ``seed + 2`` velocities."""
+    Lx, Ly = (2 * k + 1) * ly, 9.0
+    h = 0.5 * lx + 1.0
+    Lz = 2.0 * (h + k * lx)
+    pore = Pore(PORE_PRISM, r0=0.5 * ly, r1=1.0e6, width=lx)
+    none = np.zeros((0, 3))
+    inner = rsa_in_pores(np.random.default_rng(seed + 1), n_in, [pore], Lx, Ly, Lz, h, none,
+                         planar=True)
+    outer = rsa_vapor(np.random.default_rng(seed), n_out, Lx, Ly, Lz, h, 0.5 * Lz, inner,
+                      planar=True, upper_only=True)
+    x0 = np.ascontiguousarray(np.concatenate([inner, outer], axis=0))
+    v0 = maxwell_velocities(np.random.default_rng(seed + 2), len(x0), T0, planar=True)
+    return System(name="paper_pore_2d", Lx=Lx, Ly=Ly, Lz=Lz, slab_half=h, lattice_a=1.0,
+                  pores=[pore], x0=x0, v0=v0, wall=none, T0=T0, dt=0.005, tau_B=tau_B,
+                  thermostat_every=10, seed=seed, dims=2, wall_model=1)
 
 
 def vapor_only_box(n: int, L: float, Lz: float, T0: float, seed: int, min_sep: float = 0.9) -> System:

@@ -36,6 +36,12 @@ def _pin_suite():
         ("bins", pins.test_profile_bin_edges),
         ("pore_volume", pins.test_pore_volume_closed_forms_and_monte_carlo),
         ("pressure", pins.test_pore_pressure_kinetic_and_pair_terms),
+        ("prism_ballistic", pins.test_prism_pore_ballistic_reflections_off_sides_and_floor),
+        ("slab_top", pins.test_molecule_above_the_slab_reflects_off_its_top_face),
+        ("hard_gas3", lambda: pins.test_hard_walls_keep_molecules_out_of_the_solid_and_conserve_energy(3)),
+        ("planar_T", pins.test_planar_thermostat_uses_2n_degrees_of_freedom),
+        ("prism_volume", pins.test_prism_volume_area_and_occupancy),
+        ("planar_pressure", pins.test_planar_pore_pressure_divides_by_2_area),
     ]
 
 
@@ -57,7 +63,15 @@ MUTATIONS = {
     "reflection keeps the velocity": ("r[2] = p->Lz - r[2];\n    v[2] = -v[2];", "r[2] = p->Lz - r[2];\n    v[2] = v[2];"),
     "lambda without square root": ("lambda = sqrt(1.0 + (p->thermostat_every * dt / tauB) * (p->T0 / T - 1.0));",
                                    "lambda = 1.0 + (p->thermostat_every * dt / tauB) * (p->T0 / T - 1.0);"),
-    "temperature with 2N degrees of freedom": ("double T = 2.0 * ke / (3.0 * (double)n);", "double T = 2.0 * ke / (2.0 * (double)n);"),
+    "temperature with 2N degrees of freedom in 3D": ("const double dof = p->dims == 2 ? 2.0 : 3.0;", "const double dof = 2.0;"),
+    "planar temperature with 3N degrees of freedom": ("const double dof = p->dims == 2 ? 2.0 : 3.0;", "const double dof = 3.0;"),
+    "prism side wall keeps the velocity": ("if (dx >= P->r0) { r[0] += 2.0 * (P->r0 - dx); v[0] = -v[0]; }", "if (dx >= P->r0) { r[0] += 2.0 * (P->r0 - dx); }"),
+    "prism reflected about the wrong face": ("else if (dy <= -P->r1) { r[1] += 2.0 * (-P->r1 - dy); v[1] = -v[1]; }", "else if (dy <= -P->r1) { r[1] += 2.0 * (P->r1 - dy); v[1] = -v[1]; }"),
+    "prism floor ignored": ("if (r[2] <= fl) { r[2] = 2.0 * fl - r[2]; v[2] = -v[2]; }", "if (0) { r[2] = 2.0 * fl - r[2]; v[2] = -v[2]; }"),
+    "slab top face reflects about the wrong side": ("const double face = r_old[2] > 0.0 ? h : -h;", "const double face = r_old[2] > 0.0 ? -h : h;"),
+    "prism floor at the wrong depth": ("return (q->width > 0.0 && q->width < 2.0 * h) ? h - q->width : -2.0 * h;", "return (q->width > 0.0 && q->width < 2.0 * h) ? -h + q->width : -2.0 * h;"),
+    "planar pressure divides by 3": ("pressure[q] = vol > 0.0 ? sum / ((p->dims == 2 ? 2.0 : 3.0) * vol) : 0.0;", "pressure[q] = vol > 0.0 ? sum / (3.0 * vol) : 0.0;"),
+    "prism volume uses half-sides": ("return p->dims == 2 ? 2.0 * q->r0 : 4.0 * q->r0 * q->r1;", "return p->dims == 2 ? q->r0 : q->r0 * q->r1;"),
     "cone narrow end at the top": ("q->r0 + (q->r1 - q->r0) * (z + h) / (2.0 * h)", "q->r0 + (q->r1 - q->r0) * (h - z) / (2.0 * h)"),
     "ink-bottle cavity dropped": ("|| rxy2 + z * z < q->r_cavity * q->r_cavity", "&& rxy2 + z * z < q->r_cavity * q->r_cavity"),
     "adsorbed threshold not squared": ("d2wall[i] < p->r_ads * p->r_ads", "d2wall[i] < p->r_ads"),

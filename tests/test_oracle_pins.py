@@ -452,3 +452,102 @@ def test_pore_pressure_kinetic_and_pair_terms():
     x3 = np.array([[0.0, 0.0, 0.0]])
     wv3 = oracle.molecule_virials(p, x3, wall)
     assert wv3[0] == pytest.approx(1.5 * 24.0 * (2 * 1.3 ** -12 - 1.3 ** -6), rel=1e-13)
+
+
+# ------------------------------------------------ hard walls, prism pores, planar systems
+# The paper's reflecting pore walls (Sec. 4 and Sec. 5): the slab minus the pores is a solid that
+# reflects molecules specularly. Pinned by free flight between parallel mirrors (closed form),
+# by never entering the solid, by energy conservation, and by the planar system's invariants.
+
+def unfold(x0, v, t, a, b):
+    """Free flight between specular walls at a and b: position and the sign of the velocity."""
+    L = b - a
+    u = np.mod(x0 - a + v * t, 2.0 * L)
+    return (a + u, 1.0) if u <= L else (a + 2.0 * L - u, -1.0)
+
+
+PRISM = W.Pore(W.PORE_PRISM, cx=1.0, cy=-2.0, r0=3.0, r1=2.0, width=12.0)
+
+
+def test_prism_pore_ballistic_reflections_off_sides_and_floor():
+    """One molecule in a blind prism pore (slab |z| < 8, floor at z = -4), no forces: x and y fold
+    between the side walls, z between the floor and (not reached) the top."""
+    dt, n = 0.005, 400
+    p = P(Lx=30.0, Ly=30.0, Lz=40.0, dt=dt, slab_half=8.0, hard_walls=1)
+    x0 = np.array([[1.5, -1.2, 0.0]])
+    v0 = np.array([[7.3, -5.1, -3.3]])
+    st = oracle.State(p, x0, v0, None, pores=[PRISM])
+    st.run(n)
+    t = n * dt
+    ex, sx = unfold(1.5, 7.3, t, -2.0, 4.0)
+    ey, sy = unfold(-1.2, -5.1, t, -4.0, 0.0)
+    ez, sz = unfold(0.0, -3.3, t, -4.0, 1e6)
+    np.testing.assert_allclose(st.x[0], [ex, ey, ez], atol=1e-10)
+    np.testing.assert_allclose(st.v[0], [7.3 * sx, -5.1 * sy, -3.3 * sz], rtol=1e-14)
+
+
+def test_molecule_above_the_slab_reflects_off_its_top_face():
+    dt, n = 0.005, 600
+    p = P(Lx=30.0, Ly=30.0, Lz=40.0, dt=dt, slab_half=8.0, hard_walls=1)
+    x0 = np.array([[-10.0, 5.0, 12.0]])
+    v0 = np.array([[0.5, 0.2, -6.1]])
+    st = oracle.State(p, x0, v0, None, pores=[PRISM])
+    st.run(n)
+    t = n * dt
+    ez, sz = unfold(12.0, -6.1, t, 8.0, 20.0)       # slab top face and the box wall
+    np.testing.assert_allclose(st.x[0], [-10.0 + 0.5 * t, 5.0 + 0.2 * t, ez], atol=1e-10)
+    assert st.v[0, 2] == pytest.approx(-6.1 * sz, rel=1e-14)
+
+
+def hard_wall_gas(dims, seed, n_in=60, n_out=90):
+    s = (W.paper_pore_2d(seed=seed, n_in=n_in, n_out=n_out) if dims == 2 else
+         W.paper_prism_pore(seed=seed, n_in=n_in, n_out=n_out))
+    return s, oracle.make_params(s, W.Potential(), thermostat_every=0)
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_hard_walls_keep_molecules_out_of_the_solid_and_conserve_energy(dims):
+    s, p = hard_wall_gas(dims, 31)
+    assert oracle.in_solid(p, s.pores, s.x0).sum() == 0
+    st = oracle.State(p, s.x0, s.v0, None, pores=s.pores)
+    e0 = oracle.kinetic(p, st.v) + st.stats["pe_vv"]
+    emax = 0.0
+    for _ in range(20):
+        ke, pe = st.run(100)
+        assert oracle.in_solid(p, s.pores, st.x).sum() == 0
+        emax = max(emax, np.abs(ke + pe - e0).max() / len(st.x))
+    assert emax < 2e-3                                 # reflections conserve kinetic energy
+    if dims == 2:
+        assert (st.x[:, 1] == 0.0).all() and (st.v[:, 1] == 0.0).all() and (st.f[:, 1] == 0.0).all()
+
+
+def test_planar_thermostat_uses_2n_degrees_of_freedom():
+    s, _ = hard_wall_gas(2, 33)
+    p = oracle.make_params(s, W.Potential(), thermostat_every=10, T0=0.7, tau_B=0.0)
+    assert p.dims == 2
+    st = oracle.State(p, s.x0, s.v0, None, pores=s.pores)
+    st.run(10)
+    assert (st.v ** 2).sum() / (2 * len(st.v)) == pytest.approx(0.7, rel=1e-13)
+
+
+def test_prism_volume_area_and_occupancy():
+    p3 = P(Lx=30.0, Ly=30.0, Lz=40.0, slab_half=8.0)
+    assert oracle.pore_volume(p3, PRISM) == pytest.approx(6.0 * 4.0 * 12.0, rel=1e-12)
+    through = W.Pore(W.PORE_PRISM, r0=3.0, r1=2.0, width=0.0)
+    assert oracle.pore_volume(p3, through) == pytest.approx(6.0 * 4.0 * 16.0, rel=1e-12)
+    p2 = P(Lx=30.0, Ly=9.0, Lz=40.0, slab_half=8.0, dims=2)
+    assert oracle.pore_volume(p2, PRISM) == pytest.approx(6.0 * 12.0, rel=1e-12)
+    inside = [[1.0, -2.0, 0.0], [3.9, -0.1, -3.9], [-1.9, -3.9, 7.9]]
+    outside = [[1.0, -2.0, -4.1], [4.1, -2.0, 0.0], [1.0, 0.1, 0.0], [1.0, -2.0, 8.1]]
+    occ, _, _ = obs_for(inside + outside, [PRISM], Lx=30.0, Ly=30.0, Lz=40.0, slab_half=8.0)
+    assert occ[0] == len(inside)
+
+
+def test_planar_pore_pressure_divides_by_2_area():
+    """A free planar gas inside a 2D pore: P = sum m v^2 / (2 A)."""
+    p = P(Lx=30.0, Ly=9.0, Lz=40.0, slab_half=8.0, dims=2)
+    x = np.array([[0.5, 0.0, 0.0], [2.0, 0.0, -3.0], [20.0, 0.0, 12.0]])
+    v = np.array([[1.0, 0.0, 2.0], [-0.5, 0.0, 0.3], [3.0, 0.0, 3.0]])
+    planar = W.Pore(W.PORE_PRISM, cx=1.0, cy=0.0, r0=3.0, r1=1e6, width=12.0)
+    press = oracle.pore_pressure(p, [planar], x, v, np.zeros(3))
+    assert press[0] == pytest.approx((5.0 + 0.34) / (2.0 * 6.0 * 12.0), rel=1e-12)
