@@ -89,6 +89,12 @@ WORKLOADS = {
                           "N log-uniform [1k,50k], T*~U[0.8,1.2], density 0.02 outside |z|<8"),
     "pore_array_2m": ("400x400x200 box, 4x4 pores (cylinder/cone/ink-bottle, R~U[4,10]) in slab "
                       "|z|<20, 2,000,000 vapour, T*=0.85"),
+    "paper_prism_pore": ("the paper's 3D geometry in reduced units: a 5x5x50 prism pore closed on "
+                         "five faces by hard reflecting walls, open into a space 9 times its "
+                         "volume, 250 molecules inside and 450 outside, T*=1.0"),
+    "paper_pore_2d": ("the paper's 2D geometry in reduced units: a planar 20x20 pore with "
+                      "reflecting walls on three sides, outer space k=3 (21 times the pore), 84 "
+                      "molecules inside and 352 outside, T*=1.0"),
     "drying_pore_6k": ("drying of a filled pore: 40x40x80 box, slab |z|<10, cylinder r8 holding "
                        "1,000 molecules, 4,800 outside at a fifth of that density, T*=1.0, "
                        "Berendsen tau_B=0.5"),
@@ -107,6 +113,10 @@ def make_workload(name: str):
         return [W.pore_array_2m()], name
     if name == "drying_pore_6k":
         return [W.drying_cylinder_pore()], name
+    if name == "paper_prism_pore":
+        return [W.paper_prism_pore()], name
+    if name == "paper_pore_2d":
+        return [W.paper_pore_2d()], name
     return W.pore_shape_systems_20k(), "pore_shapes_4x20k"
 
 
@@ -176,7 +186,7 @@ def oracle_rate(systems, seconds: float, nthreads: int = 0):
     from paper_1812_07993_gb300 import workloads as W
     pot = W.Potential()
     states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1,
-                           nthreads=nthreads) for s in systems]
+                           nthreads=nthreads, pores=s.pores) for s in systems]
     steps = pairs = 0
     t0 = time.perf_counter()
     while True:
@@ -199,8 +209,8 @@ def run_reference(args):
     from paper_1812_07993_gb300 import workloads as W
     systems, wname = make_workload(args.workload)
     pot = W.Potential()
-    states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1, nthreads=0)
-              for s in systems]
+    states = [oracle.State(oracle.make_params(s, pot), s.x0, s.v0, s.wall, method=1, nthreads=0,
+                           pores=s.pores) for s in systems]
     for k in range(args.warmup):
         states[k % len(states)].run(1)
     pairs = 0

@@ -5,7 +5,8 @@
  * What one MD step computes (per replica, reduced Lennard-Jones units, sigma = eps = m = k_B = 1):
  *   1. first half-kick and drift (Sec. 2 velocity Verlet; Fig. 2):
  *        v <- v + (dt/2) f/m ;  r <- r + dt v
- *      then specular reflection at z = +-Lz/2 and periodic wrap of x, y into [-L/2, L/2);
+ *      then specular reflection at z = +-Lz/2, off the solid for hard walls (md_wall_model),
+ *      and periodic wrap of x, y into [-L/2, L/2);
  *   2. neighbour-list maintenance: when any molecule has moved more than skin/2 since the last
  *      build, particles are binned into cells (counting sort) and Verlet lists rebuilt;
  *   3. forces at r(t+dt) (Sec. 2, Eq. 2; Fig. 1): f_i = -dU/dr_i with U the Lennard-Jones 12-6
@@ -14,7 +15,7 @@
  *   4. second half-kick (Fig. 3): v <- v + (dt/2) f/m;
  *   5. Berendsen scaling (Sec. 2; Fig. 4) when the step counter reaches a multiple of
  *      thermostat_every: v <- lambda v, lambda = sqrt(1 + (n_th dt / tau_B)(T0/T - 1)),
- *      T = m sum v^2 / (3 N).
+ *      T = m sum v^2 / (d N), d = 3 (or 2 for a planar system).
  * Observables (on demand): kinetic / potential energy, the pair virial sum_{pairs} r_ij . F_ij
  * (the sum in the virial pressure of Sec. 2), pairs within the cutoff, pore occupancy, adsorbed
  * count and axial density profile per pore.
@@ -61,8 +62,23 @@ typedef enum {
   MD_PORE_CYLINDER = 1,   /* dx^2 + dy^2 < r0^2 */
   MD_PORE_CONE = 2,       /* sqrt(dx^2 + dy^2) < r0 + (r1 - r0)(z + h)/(2h), narrow end at z = -h */
   MD_PORE_SLIT = 3,       /* |dy| < width/2, spanning the whole x extent */
-  MD_PORE_INKBOTTLE = 4   /* dx^2 + dy^2 < r0^2  or  dx^2 + dy^2 + z^2 < r_cavity^2 */
+  MD_PORE_INKBOTTLE = 4,  /* dx^2 + dy^2 < r0^2  or  dx^2 + dy^2 + z^2 < r_cavity^2 */
+  MD_PORE_PRISM = 5       /* |dx| < r0 and |dy| < r1 and z > h - width: a rectangular pore open at
+                             the slab's top face z = +h with a floor at z = h - width when
+                             0 < width < 2h (otherwise through the slab) -- the paper's pore shape
+                             (Sec. 4 and Sec. 5) */
 } md_pore_kind;
+
+typedef enum {
+  MD_WALL_ATOMS = 0,      /* fixed Lennard-Jones wall atoms (the default) */
+  MD_WALL_HARD = 1        /* no wall atoms: the slab |z| < h minus the pores is a solid that
+                             reflects molecules specularly (the paper's reflecting pore walls,
+                             Sec. 4). A molecule that ends a drift inside the solid is mirrored in
+                             the face it crossed: the slab face on its side if it came from outside
+                             the slab, else the side walls (prism |dx| = r0, |dy| = r1; slit
+                             |dy| = width/2) and the floor of the pore it came from. Pores must be
+                             prisms or slits (axis-aligned faces). */
+} md_wall_model;
 
 /* One pore carved through the wall slab |z| < h. (dx, dy) is the minimum-image offset of a point
  * from the pore axis (cx, cy). The carve predicates above decide which wall sites are removed
@@ -70,9 +86,10 @@ typedef enum {
 typedef struct {
   int32_t kind;            /* md_pore_kind */
   double cx, cy;           /* axis position */
-  double r0, r1;           /* radius (cylinder, neck), cone radii at z = -h and z = +h */
+  double r0, r1;           /* radius (cylinder, neck), cone radii at z = -h and z = +h;
+                              prism half-sides in x and y */
   double r_cavity;         /* ink-bottle cavity radius */
-  double width;            /* slit width */
+  double width;            /* slit width; prism depth from the top face */
 } md_pore;
 
 /* One independent system (replica). */
@@ -92,6 +109,11 @@ typedef struct {
   int64_t n_wall;          /* length of wall_xyz (ignored when wall_xyz is NULL) */
   const md_pore* pores;    /* host, n_pores pores (may be NULL when n_pores == 0) */
   int32_t n_pores;
+  int32_t dims;            /* 0 or 3: three-dimensional; 2: planar system in the x-z plane (every
+                              molecule at y = 0 with vy = 0; needs wall_model MD_WALL_HARD and
+                              prism pores), temperature T = m sum v^2 / (2N) -- the paper's 2D
+                              simulation (Sec. 4) */
+  int32_t wall_model;      /* md_wall_model */
 } md_system;
 
 /* Interaction, list and observable parameters shared by every replica of a context. */

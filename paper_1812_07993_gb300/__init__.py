@@ -44,7 +44,8 @@ class md_system(ctypes.Structure):
                 ("dt", ctypes.c_double), ("tau_B", ctypes.c_double),
                 ("thermostat_every", ctypes.c_int32), ("slab_half", ctypes.c_double),
                 ("lattice_a", ctypes.c_double), ("wall_xyz", _DP), ("n_wall", ctypes.c_int64),
-                ("pores", ctypes.POINTER(md_pore)), ("n_pores", ctypes.c_int32)]
+                ("pores", ctypes.POINTER(md_pore)), ("n_pores", ctypes.c_int32),
+                ("dims", ctypes.c_int32), ("wall_model", ctypes.c_int32)]
 
 
 class md_potential(ctypes.Structure):
@@ -203,7 +204,8 @@ class Simulation:
                                v0.ctypes.data_as(_DP), s.T0, s.dt, s.tau_B, s.thermostat_every,
                                s.slab_half, s.lattice_a,
                                None if generate_wall else wall.ctypes.data_as(_DP),
-                               0 if generate_wall else len(wall), pores, len(s.pores))
+                               0 if generate_wall else len(wall), pores, len(s.pores),
+                               getattr(s, "dims", 3), getattr(s, "wall_model", 0))
         pot = md_potential_from(self.potential, precision, max_neighbors, max_wall_neighbors)
         ctx = _CTX()
         st = lib.md_create_batch(arr, len(self.systems), ctypes.byref(pot),

@@ -127,9 +127,30 @@ md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
     return fail(c, MD_EINVAL, who + "lattice_a must be > 0 to generate the wall");
   for (int q = 0; q < s->n_pores; ++q) {
     const md_pore& P = s->pores[q];
-    if (P.kind < 1 || P.kind > 4) return fail(c, MD_EINVAL, who + "unknown pore kind");
+    if (P.kind < 1 || P.kind > 5) return fail(c, MD_EINVAL, who + "unknown pore kind");
     if (P.kind == MD_PORE_CONE && !(s->slab_half > 0))
       return fail(c, MD_EINVAL, who + "a cone needs slab_half > 0");
+    if (P.kind == MD_PORE_PRISM && !(P.r0 > 0 && P.r1 > 0))
+      return fail(c, MD_EINVAL, who + "a prism needs half-sides r0, r1 > 0");
+    if (s->wall_model == MD_WALL_HARD && P.kind != MD_PORE_PRISM && P.kind != MD_PORE_SLIT)
+      return fail(c, MD_EINVAL, who + "hard walls need prism or slit pores (axis-aligned faces)");
+  }
+  if (s->wall_model != MD_WALL_ATOMS && s->wall_model != MD_WALL_HARD)
+    return fail(c, MD_EINVAL, who + "unknown wall model");
+  if (s->wall_model == MD_WALL_HARD && s->wall_xyz && s->n_wall > 0)
+    return fail(c, MD_EINVAL, who + "hard walls take no wall atoms");
+  if (s->dims != 0 && s->dims != 2 && s->dims != 3)
+    return fail(c, MD_EINVAL, who + "dims must be 0 (3), 2 or 3");
+  if (s->dims == 2) {
+    if (s->wall_model != MD_WALL_HARD)
+      return fail(c, MD_EINVAL, who + "a planar system needs hard walls");
+    for (int q = 0; q < s->n_pores; ++q)
+      if (s->pores[q].kind != MD_PORE_PRISM)
+        return fail(c, MD_EINVAL, who + "a planar system needs prism pores");
+    for (int64_t i = 0; i < s->n_vapor; ++i)
+      if (s->x0[3 * i + 1] != 0.0 || s->v0[3 * i + 1] != 0.0)
+        return fail(c, MD_EINVAL, who + "a planar system needs y = 0 and vy = 0 for molecule " +
+                                      std::to_string(i));
   }
   const double hx = 0.5 * s->Lx, hy = 0.5 * s->Ly, hz = 0.5 * s->Lz;
   for (int64_t i = 0; i < s->n_vapor; ++i) {
@@ -148,8 +169,9 @@ md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
   return MD_OK;
 }
 
-// volume of a pore's carved region inside the slab |z| < h (closed forms)
-double pore_volume(const md_pore& q, double Lx, double h) {
+// volume of a pore's carved region inside the slab |z| < h (closed forms); for a planar system
+// (dims 2) the area in the x-z plane
+double pore_volume(const md_pore& q, double Lx, double h, int dims) {
   const double pi = 3.14159265358979323846;
   switch (q.kind) {
     case MD_PORE_CYLINDER: return pi * q.r0 * q.r0 * 2.0 * h;
@@ -164,6 +186,11 @@ double pore_volume(const md_pore& q, double Lx, double h) {
         v += 2.0 * pi * (a2 * zt - zt * zt * zt / 3.0);
       }
       return v;
+    }
+    case MD_PORE_PRISM: {
+      const double depth = h - prism_floor(q.width, h) < 2.0 * h ? h - prism_floor(q.width, h)
+                                                                   : 2.0 * h;
+      return (dims == 2 ? 2.0 * q.r0 : 4.0 * q.r0 * q.r1) * depth;
     }
     default: return 0.0;
   }
@@ -424,7 +451,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   for (int r = 0; r < n_reps; ++r) {
     const md_system* s = &systems[r];
     ReplicaHost& H = c->rh[r];
-    if (s->wall_xyz)
+    if (s->wall_model == MD_WALL_HARD)
+      H.wall.clear();
+    else if (s->wall_xyz)
       H.wall.assign(s->wall_xyz, s->wall_xyz + 3 * s->n_wall);
     else
       H.wall = generate_wall(s);
@@ -461,10 +490,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     R.n_groups = H.n_groups;
     R.n_bins = H.n_bins;
     R.prof_off = (int32_t)prof;
+    R.dims = s->dims == 2 ? 2 : 3;
+    R.hard = s->wall_model == MD_WALL_HARD ? 1 : 0;
     for (int q = 0; q < s->n_pores; ++q) {
       const md_pore& Q = s->pores[q];
       pores.push_back(PoreDev{Q.kind, Q.cx, Q.cy, Q.r0, Q.r1, Q.r_cavity, Q.width,
-                              pore_volume(Q, s->Lx, s->slab_half)});
+                              pore_volume(Q, s->Lx, s->slab_half, R.dims)});
     }
     n_tot += H.n_vap;
     nw_tot += H.n_wall;
@@ -913,6 +944,9 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
             q[2] <= R.hz))
         return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
                                       std::to_string(i) + " outside the box");
+      if (R.dims == 2 && (q[1] != 0.0 || v[3 * (size_t)(R.vap_off - off + i) + 1] != 0.0))
+        return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
+                                      std::to_string(i) + " leaves the plane y = 0");
     }
   }
   if (n) {
@@ -970,7 +1004,7 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   out->pe_vv = sums[1];
   out->pe_vw = sums[2];
   out->pe = sums[1] + sums[2];
-  out->T = H.n_vap ? 2.0 * sums[0] / (3.0 * (double)H.n_vap) : 0.0;
+  out->T = H.n_vap ? 2.0 * sums[0] / ((double)c->reps[r].dims * (double)H.n_vap) : 0.0;
   out->virial_vv = sums[3];
   out->virial_vw = sums[4];
   out->pairs_vv = (int64_t)std::llround(sums[5]) / 2;

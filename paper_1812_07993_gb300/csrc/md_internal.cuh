@@ -62,6 +62,8 @@ struct RepDev {
   int32_t group_off, n_groups;      // adsorbed counters / profile rows
   int32_t n_bins;
   int32_t prof_off;                 // first profile counter of this replica
+  int32_t dims;                     // 3, or 2 for a planar system (temperature with 2N)
+  int32_t hard;                     // 1: hard reflecting walls (no wall atoms)
 };
 
 struct PoreDev {
@@ -148,6 +150,11 @@ struct Tuning {
 };
 
 // carve predicate of a pore at offset (dx, dy) from its axis and height z (slab half-thickness h)
+// floor of a prism pore: z = h - depth for a blind pore (0 < depth < 2h), else below the slab
+__host__ __device__ inline double prism_floor(double depth, double h) {
+  return (depth > 0.0 && depth < 2.0 * h) ? h - depth : -2.0 * h;
+}
+
 __host__ __device__ inline bool in_pore(int kind, double r0, double r1, double rcav, double width,
                                         double dx, double dy, double z, double h) {
   double rxy2 = dx * dx + dy * dy;
@@ -156,6 +163,7 @@ __host__ __device__ inline bool in_pore(int kind, double r0, double r1, double r
     case 2: return sqrt(rxy2) < r0 + (r1 - r0) * (z + h) / (2.0 * h);
     case 3: return fabs(dy) < 0.5 * width;
     case 4: return rxy2 < r0 * r0 || rxy2 + z * z < rcav * rcav;
+    case 5: return fabs(dx) < r0 && fabs(dy) < r1 && z > prism_floor(width, h);
     default: return false;
   }
 }

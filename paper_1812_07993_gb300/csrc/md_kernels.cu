@@ -110,6 +110,70 @@ __device__ __forceinline__ T warp_sum(T v) {
 inline int nblocks(long long n, int b) { return n > 0 ? (int)((n + b - 1) / b) : 1; }
 
 // ------------------------------------------------------------------------------------------------
+// Hard walls (the paper's reflecting pore walls, Sec. 4 and Sec. 5): the slab |z| < h minus the
+// pores is solid. A molecule that ended the drift inside it (r, from r0) is mirrored in the face it
+// crossed: the slab face on its side when it came from outside the slab, else the side walls and
+// the floor of the pore it came from (prism |dx| = r0, |dy| = r1, z = floor; slit |dy| = w/2).
+__device__ bool in_any_pore(const Arrays& a, const RepDev& R, double x, double y, double z) {
+  for (int q = 0; q < R.n_pores; ++q) {
+    const PoreDev& P = a.pores[R.pore_off + q];
+    if (in_pore(P.kind, P.r0, P.r1, P.r_cavity, P.width, wrap_diff(x - P.cx, R.Lx, R.hx),
+                wrap_diff(y - P.cy, R.Ly, R.hy), z, R.slab_half))
+      return true;
+  }
+  return false;
+}
+
+__device__ void reflect_solid(const Arrays& a, const RepDev& R, const dvec4& r0, dvec4& r,
+                              dvec4& v) {
+  const double h = R.slab_half;
+  if (!(fabs(r.z) < h) || in_any_pore(a, R, r.x, r.y, r.z)) return;
+  if (fabs(r0.z) >= h) {
+    const double face = r0.z > 0.0 ? h : -h;
+    r.z = 2.0 * face - r.z;
+    v.z = -v.z;
+    return;
+  }
+  for (int q = 0; q < R.n_pores; ++q) {
+    const PoreDev& P = a.pores[R.pore_off + q];
+    const double dx0 = wrap_diff(r0.x - P.cx, R.Lx, R.hx), dy0 = wrap_diff(r0.y - P.cy, R.Ly, R.hy);
+    if (!in_pore(P.kind, P.r0, P.r1, P.r_cavity, P.width, dx0, dy0, r0.z, h)) continue;
+    const double dx = wrap_diff(r.x - P.cx, R.Lx, R.hx), dy = wrap_diff(r.y - P.cy, R.Ly, R.hy);
+    if (P.kind == 5) {
+      if (dx >= P.r0) {
+        r.x += 2.0 * (P.r0 - dx);
+        v.x = -v.x;
+      } else if (dx <= -P.r0) {
+        r.x += 2.0 * (-P.r0 - dx);
+        v.x = -v.x;
+      }
+      if (dy >= P.r1) {
+        r.y += 2.0 * (P.r1 - dy);
+        v.y = -v.y;
+      } else if (dy <= -P.r1) {
+        r.y += 2.0 * (-P.r1 - dy);
+        v.y = -v.y;
+      }
+      const double fl = prism_floor(P.width, h);
+      if (r.z <= fl) {
+        r.z = 2.0 * fl - r.z;
+        v.z = -v.z;
+      }
+    } else if (P.kind == 3) {
+      const double hw = 0.5 * P.width;
+      if (dy >= hw) {
+        r.y += 2.0 * (hw - dy);
+        v.y = -v.y;
+      } else if (dy <= -hw) {
+        r.y += 2.0 * (-hw - dy);
+        v.y = -v.y;
+      }
+    }
+    return;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc,
@@ -125,6 +189,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   if (!halt && i < a.n_total) {
     const RepDev& R = a.reps[a.rep[i]];
     dvec4 x = a.pos[i], v = a.vel[i];
+    const dvec4 x_old = x;
     const dvec4 f = a.frc[i];
     const double h = 0.5 * R.dt * p.inv_mass;
     v.x += h * f.x;
@@ -140,6 +205,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
       x.z = -R.Lz - x.z;
       v.z = -v.z;
     }
+    if (R.hard) reflect_solid(a, R, x_old, x, v);
     if (x.x >= R.hx) x.x -= R.Lx;
     else if (x.x < -R.hx) x.x += R.Lx;
     if (x.y >= R.hy) x.y -= R.Ly;
@@ -231,7 +297,7 @@ __global__ void k_thermo_lambda(Arrays a, PotDev p) {
   for (int ch = lane; ch < nch; ch += 32) t += a.rep_part[((size_t)r * a.rep_chunks + ch) * 8];
   t = warp_sum(t);  // fixed butterfly: deterministic
   if (lane == 0) {
-    const double T = p.mass * t / (3.0 * (double)R.n_vap);
+    const double T = p.mass * t / ((double)R.dims * (double)R.n_vap);
     double lam = 1.0;
     if (T > 0.0) lam = sqrt(1.0 + R.lam_coef * (R.T0 / T - 1.0));
     a.lambda[r] = lam;
@@ -1422,7 +1488,7 @@ __global__ void k_rep_final(Arrays a, PotDev p) {
   }
 }
 
-// virial pressure per pore (Sec. 2): P_q = (sum m v^2 + sum W_i) / (3 V_q) over the molecules
+// virial pressure per pore (Sec. 2): P_q = (sum m v^2 + sum W_i) / (d V_q) over the molecules
 // inside pore q (the occupancy predicate), W_i = vir_i + virw_i. Blocks (replica, chunk) write
 // partial sums for every pore of the replica, one thread per pore adds them in chunk order.
 __global__ void __launch_bounds__(256) k_pore_partial(Arrays a, PotDev p) {
@@ -1466,7 +1532,7 @@ __global__ void k_pore_final(Arrays a) {
     for (int ch = 0; ch < a.rep_chunks; ++ch)
       t += a.pore_part[((size_t)r * a.rep_chunks + ch) * a.max_pores + q];
     const double vol = a.pores[R.pore_off + q].vol;
-    a.pore_press[R.pore_off + q] = vol > 0.0 ? t / (3.0 * vol) : 0.0;
+    a.pore_press[R.pore_off + q] = vol > 0.0 ? t / ((double)R.dims * vol) : 0.0;
   }
 }
 
