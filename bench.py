@@ -305,6 +305,32 @@ def measure_precision(md, systems, precision, args, torch, stream, flush):
     return sim, ms, p1 - p0, launches
 
 
+def steady_state(sim, torch, stream, flush, steps, nrep, per_replay=10):
+    """The same steps run back to back as CUDA-graph replays of ``per_replay`` steps each (how a
+    long run executes), with the L2 flush between replays, not between steps."""
+    sim.set_tuning(use_graph=1, steps_per_graph=per_replay)
+    sim.step(per_replay)
+    sim.sync()
+    p0 = pair_total(sim, nrep)
+    reps = max(1, steps // per_replay)
+    evs = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(per_replay)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    pairs = pair_total(sim, nrep) - p0
+    sim.set_tuning(steps_per_graph=1)
+    return {"value": pairs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / (reps * per_replay),
+            "steps": reps * per_replay, "steps_per_replay": per_replay,
+            "l2": "flushed between graph replays"}
+
+
 def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate):
     evs = []
     nvtx_push(torch, "roofline")
@@ -404,6 +430,9 @@ def run_ours(args):
 
     sim_tune = sim.tune_info
     extra = {}
+    if rank == 0 and args.launch_mode == "graph":
+        extra["steady_state"] = steady_state(sim, torch, stream, flush, args.steps,
+                                             len(systems))
     if rank == 0:
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,

@@ -602,6 +602,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.any_scale, 1);
   ALLOC(A.step, 1);
   ALLOC(A.force_rebuild, 1);
+  ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1);
   ALLOC(A.status, 1);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);
@@ -911,6 +912,7 @@ md_status md_get_state(md_ctx* c, int32_t r, double* x, double* v) {
   md_status s = sync_status(c);
   if (s != MD_OK && s != MD_EOVERFLOW && s != MD_EUNSTABLE && s != MD_ETIMEOUT) return s;
   md_status t;
+  if (v) launch_settle_kick(c->a, c->pot, c->stream);
   if (x && (t = fetch_rows(c, r, c->a.pos, c->stage_x, x)) != MD_OK) return t;
   if (v && (t = fetch_rows(c, r, c->a.vel, c->stage_v, v)) != MD_OK) return t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -949,6 +951,8 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
                                       std::to_string(i) + " leaves the plane y = 0");
     }
   }
+  // the other replicas' owed kicks are paid before the load resets the flag
+  launch_settle_kick(c->a, c->pot, c->stream);
   if (n) {
     const size_t bytes = 3 * (size_t)n * sizeof(double);
     CUDA_TRY(c, cudaMemcpyAsync(c->stage_x + 3 * (size_t)off, x, bytes, cudaMemcpyHostToDevice,
@@ -971,6 +975,7 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   CUDA_TRY(c, cudaMemsetAsync(A.occ, 0, std::max<size_t>(c->pores_total, 1) * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.ads, 0, c->groups_total * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.prof, 0, std::max<size_t>(c->prof_total, 1) * 8, c->stream));
+  launch_settle_kick(A, c->pot, c->stream);  // kinetic energy at v(t+dt)
   launch_forces(A, c->pot, c->mixed, true, false, c->tun, c->stream);
   launch_observables(A, c->pot, c->stream);
   CUDA_TRY(c, cudaGetLastError());

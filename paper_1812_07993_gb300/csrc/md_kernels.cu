@@ -9,7 +9,10 @@
 //                         k_list_build (warp per cell) [-> FP64 half-list preparation]
 //   pair forces         Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) and the second half-kick
 //                       (Fig. 3): FP64 half list + reverse gather with the kick fused into the
-//                       gather, or mixed precision on the full list with the kick fused in
+//                       gather; FP64 half list with atomic reaction forces, the kick deferred into
+//                       the next first half-kick (k_kick_pending settles it before the thermostat
+//                       or any read of the velocities); or mixed precision on the full list with
+//                       the kick fused in
 //   k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on thermostat steps
 //                       (Fig. 4)
 // No kernel spins or waits on another block.
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     *a.any_scale = 0;
   }
   const bool halt = halted(a);
+  const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d2 = 0.0;
   if (!halt && i < a.n_total) {
@@ -192,6 +196,11 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     const dvec4 x_old = x;
     const dvec4 f = a.frc[i];
     const double h = 0.5 * R.dt * p.inv_mass;
+    if (pend) {  // the previous step's second half-kick (Fig. 3), deferred to here
+      v.x += h * f.x;
+      v.y += h * f.y;
+      v.z += h * f.z;
+    }
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
@@ -534,13 +543,23 @@ __device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
 }
 
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
-constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
+constexpr int kListWin = 256;      // candidates staged in shared memory per window and warp
 
+// Verlet list, warp per cell (the cell's molecules in groups of up to 32). The candidate stream --
+// the 27 neighbour cells in stencil order, molecules in index order, then their wall atoms -- is
+// staged window by window in shared memory together with the candidates' FP32 cell-local offsets;
+// the warp then takes the group's molecules one after another, its lanes testing 32 candidates at
+// a time: (l_i - l_j) - dc * cell (exactly antisymmetric, so the lists are symmetric) against the
+// padded list radius. Hits go to the front (j > i, wall atoms) or, from the end, the back (j < i) of
+// the molecule's row in stream order; the running counts are warp-uniform.
 __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half, int lpt) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
-  __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
-  __shared__ float4 sh_li[kListWarps][32];
+  __shared__ uint32_t s_ent[kListWarps][kListWin];
+  __shared__ float4 s_pos[kListWarps][kListWin];
+  __shared__ float4 s_off[kListWarps][64];
+  __shared__ float4 s_li[kListWarps][32];
+  __shared__ int s_f[kListWarps][32], s_b[kListWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
@@ -551,6 +570,10 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   const RepDev& R = a.reps[a.cell_rep[c]];
   const int local = c - R.cell_off;
   const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
+  // offset of a neighbour cell by the 6-bit code in bits 26-31 of a list entry
+  for (int k = lane; k < 64; k += 32)
+    s_off[w][k] = make_float4((float)((k & 3) - 1) * R.lcxf, (float)(((k >> 2) & 3) - 1) * R.lcyf,
+                              (float)((k >> 4) - 1) * R.lczf, 0.f);
   // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
   int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
   uint32_t code = 0;
@@ -569,14 +592,15 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   }
   const unsigned lt = (1u << lane) - 1u;
   const int N = a.n_total, cap = p.cap;
-  uint32_t* stream = sh_stream[w];
+  uint32_t* __restrict__ ent = s_ent[w];
+  float4* __restrict__ pos = s_pos[w];
   int max_n = 0;
   for (int ib = i_begin; ib < i_end; ib += 32) {
     const int nic = min(32, i_end - ib);
-    // the molecules of this group: FP32 offsets in shared memory; lane il keeps molecule il's
-    // front and back counts in registers
-    sh_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int cf = 0, cb = 0, vh = 0;
+    s_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    s_f[w][lane] = 0;
+    s_b[w][lane] = 0;
+    int vh = 0;
     __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
       const bool wallpass = pass == 1;
@@ -590,56 +614,55 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
       }
       const int T = __shfl_sync(kFull, incl, 31);
       const int excl = incl - tot;
-      for (int W0 = 0; W0 < T; W0 += kStreamWin) {
-        const int W1 = min(T, W0 + kStreamWin);
+      for (int W0 = 0; W0 < T; W0 += kListWin) {
+        const int W1 = min(T, W0 + kListWin), nwin = W1 - W0;
         // lane l writes the part of its cell's candidates that falls in this window
         for (int m = max(0, W0 - excl); m < tot && excl + m < W1; ++m)
-          stream[excl + m - W0] = (base_idx + (uint32_t)m) | code;
+          ent[excl + m - W0] = (base_idx + (uint32_t)m) | code;
         __syncwarp();
-        for (int base = W0; base < W1; base += 32) {
-          const int q = base + lane;
-          const bool valid = q < W1;
-          const uint32_t entry = valid ? stream[q - W0] : 0u;
-          const int jj = (int)(entry & kIndexMask);
-          const int j = wallpass ? jj - N : jj;
-          float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
-          const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
-          const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
-          const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
-          for (int il = 0; il < nic; ++il) {
-            const int i = ib + il;
-            const float4 li = sh_li[w][il];
-            const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
-            const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
-            const bool front = hit && (wallpass || j > i);
-            const bool back = hit && !front;
-            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
-            if (bf | bb) {
-              const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
-              if (front) {
-                const int slot = f0 + __popc(bf & lt);
-                if (slot < cap) a.nbr[(size_t)i * cap + slot] = entry;
-              } else if (back) {
-                const int slot = cap - 1 - (b0 + __popc(bb & lt));
-                if (slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
-              }
-              if (lane == il) {
-                cf += __popc(bf);
-                cb += __popc(bb);
-              }
+        for (int q = lane; q < nwin; q += 32) {
+          const int jj = (int)(ent[q] & kIndexMask);
+          pos[q] = wallpass ? a.wlpos[jj - N] : a.lpos[jj];
+        }
+        __syncwarp();
+        for (int il = 0; il < nic; ++il) {
+          const int i = ib + il;
+          const float4 li = s_li[w][il];
+          int f = s_f[w][il], b = s_b[w][il];  // warp-uniform running counts
+          uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+          for (int q0 = 0; q0 < nwin; q0 += 32) {
+            const int q = q0 + lane;
+            const bool valid = q < nwin;
+            const uint32_t e = valid ? ent[q] : 0u;
+            const float4 bp = pos[valid ? q : 0];
+            const float4 o = s_off[w][e >> 26];
+            const float dx = (li.x - bp.x) - o.x, dy = (li.y - bp.y) - o.y, dz = (li.z - bp.z) - o.z;
+            const int jj = (int)(e & kIndexMask);
+            const bool hit = valid && (wallpass || jj != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
+            const bool front = hit && (wallpass || jj > i);
+            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, hit && !front);
+            if (hit) {
+              const int slot = front ? f + __popc(bf & lt) : cap - 1 - (b + __popc(bb & lt));
+              if (front ? slot < cap : slot >= 0) row[slot] = e;
             }
+            f += __popc(bf);
+            b += __popc(bb);
           }
+          if (lane == 0) {
+            s_f[w][il] = f;
+            s_b[w][il] = b;
+          }
+          __syncwarp();
         }
         __syncwarp();
       }
-      if (!wallpass) vh = cf;
+      if (!wallpass) vh = s_f[w][lane];
     }
     // counts, overflow, processing-order histogram
     {
       const int i = ib + lane;
       const bool own = lane < nic;
-      const int nf = cf, nb = cb, nvh = vh;
+      const int nf = s_f[w][lane], nb = s_b[w][lane], nvh = vh;
       if (own) {
         if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
           atomicOr(a.status, kStatusOverflow);
@@ -889,11 +912,14 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
 // forces must be zero beforehand. The order of the atomic adds varies from run to run, so the
 // forces agree with the deterministic form to rounding, not bit for bit.
 template <int TPP>
-__global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, int lpt) {
+__global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, int lpt,
+                                                            int owe_kick) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.force_rebuild = 0;
+    // in a step, the second half-kick is owed: the next first half-kick (or k_kick_pending) pays it
+    if (owe_kick) *a.kick_pending = 1;
   }
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap;
@@ -941,20 +967,34 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
   finish_chunks(a);
 }
 
-// second half-kick (Fig. 3) after the atomic pair pass: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
-__global__ void k_kick(Arrays a, PotDev p) {
+// The owed second half-kick (Fig. 3), v(t+dt) = v(t+dt/2) + a(t+dt) dt/2, when the FP64 atomic form
+// deferred it: applied before the thermostat, the observables or a state read. Every block reads
+// the flag before its first thread reports in; the last block to report clears it.
+__global__ void k_kick_pending(Arrays a, PotDev p) {
   count_launch(a);
-  if (halted(a)) return;
+  const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total) return;
-  const RepDev& R = a.reps[a.rep[i]];
-  dvec4 v = a.vel[i];
-  const dvec4 f = a.frc[i];
-  const double h = 0.5 * R.dt * p.inv_mass;
-  v.x += h * f.x;
-  v.y += h * f.y;
-  v.z += h * f.z;
-  a.vel[i] = v;
+  if (pend && !halted(a) && i < a.n_total) {
+    const RepDev& R = a.reps[a.rep[i]];
+    dvec4 v = a.vel[i];
+    const dvec4 f = a.frc[i];
+    const double h = 0.5 * R.dt * p.inv_mass;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    a.vel[i] = v;
+  }
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(a.kick_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *a.kick_pending = 0;
+    *a.kick_done = 0u;
+  }
 }
 
 __global__ void k_zero_forces(Arrays a) {
@@ -972,6 +1012,7 @@ __global__ void __launch_bounds__(128) k_allpairs(Arrays a, PotDev p) {
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0 && !STATS) {
     *a.force_rebuild = 0;
+    if (KICK) *a.kick_pending = 0;  // this step kicks itself
   }
   if (halted(a)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1252,6 +1293,7 @@ __global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p) {
 template <bool KICK, int TPP>
 __global__ void k_gather(Arrays a, PotDev p) {
   count_launch(a);
+  if (KICK && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 0;  // this step kicks itself
   if (halted(a)) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = g / TPP, sub = g & (TPP - 1);
@@ -1304,6 +1346,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.force_rebuild = 0;
+    if (KICK) *a.kick_pending = 0;  // this step kicks itself
   }
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap;
@@ -1600,9 +1643,9 @@ void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, c
   if (t.atomic_acc && TPP != 32) {
     // forces start from zero: k_integrate_first clears them on the way through a step
     if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+    // in a step the second half-kick is deferred into the next first half-kick
     k_forces_half_atomic<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0, s>>>(
-        a, p, t.lpt);
-    if (kick) k_kick<<<nblocks(a.n_total, 256), 256, 0, s>>>(a, p);
+        a, p, t.lpt, kick ? 1 : 0);
     return;
   }
   if constexpr (TPP == 32) {
@@ -1670,7 +1713,7 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
-  if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
   else k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
 }
 
@@ -1713,6 +1756,7 @@ __global__ void k_load_state(Arrays a, const double* __restrict__ xin,
   a.vel[i] = make_dvec4(vin[3 * (size_t)i], vin[3 * (size_t)i + 1], vin[3 * (size_t)i + 2], 0.0);
   a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
   a.id[i] = i - a.reps[a.rep[i]].vap_off;
+  if (k == 0) *a.kick_pending = 0;  // owed kicks were settled before the load
 }
 
 // out rows (caller order, xyz interleaved) of molecules [off, off + n) from the records src
@@ -1745,7 +1789,12 @@ cudaError_t configure_kernels() {
                               (int)(8 * sizeof(PackWarp)));
 }
 
+void launch_settle_kick(const Arrays& a, const PotDev& p, cudaStream_t s) {
+  k_kick_pending<<<nblocks(a.n_total, 256), 256, 0, s>>>(a, p);
+}
+
 void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s) {
+  launch_settle_kick(a, p, s);  // the thermostat reads v(t+dt)
   k_thermo_partial<<<a.n_reps * a.rep_chunks, 256, 0, s>>>(a);
   k_thermo_lambda<<<nblocks(a.n_reps, 8), 256, 0, s>>>(a, p);
   const int b = 256;
