@@ -94,6 +94,19 @@ __device__ __forceinline__ double neg_bits(double x) {
   return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
+// comparisons against a positive threshold t by bit patterns (integer instructions): finite IEEE
+// doubles order like their patterns read as signed 64-bit integers when t > 0
+__device__ __forceinline__ bool gt_pos(double x, double t) {
+  return __double_as_longlong(x) > __double_as_longlong(t);
+}
+__device__ __forceinline__ bool ge_pos(double x, double t) {
+  return __double_as_longlong(x) >= __double_as_longlong(t);
+}
+// |x| <= t; false for NaN
+__device__ __forceinline__ bool abs_le(double x, double t) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffll) <= __double_as_longlong(t);
+}
+
 // error-free transformation s + x = t + e (Knuth's TwoSum); the error is collected in c
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   const float t = s + x;
@@ -207,23 +220,28 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     x.x += R.dt * v.x;
     x.y += R.dt * v.y;
     x.z += R.dt * v.z;
-    if (x.z > R.hz) {
+    // the boundary tests compare bit patterns (integer instructions; the FP64 pipe does only the
+    // arithmetic, and the adds behind the tests run only where a molecule crosses)
+    if (gt_pos(x.z, R.hz)) {
       x.z = R.Lz - x.z;
       v.z = -v.z;
-    } else if (x.z < -R.hz) {
+    } else if (gt_pos(neg_bits(x.z), R.hz)) {
       x.z = -R.Lz - x.z;
       v.z = -v.z;
     }
     if (R.hard) reflect_solid(a, R, x_old, x, v);
-    if (x.x >= R.hx) x.x -= R.Lx;
-    else if (x.x < -R.hx) x.x += R.Lx;
-    if (x.y >= R.hy) x.y -= R.Ly;
-    else if (x.y < -R.hy) x.y += R.Ly;
-    const bool bad = !(fabs(x.x) <= R.hx && fabs(x.y) <= R.hy && fabs(x.z) <= R.hz);
+    if (ge_pos(x.x, R.hx)) x.x -= R.Lx;
+    else if (gt_pos(neg_bits(x.x), R.hx)) x.x += R.Lx;
+    if (ge_pos(x.y, R.hy)) x.y -= R.Ly;
+    else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
+    const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
     if (bad) atomicOr(a.status, kStatusUnstable);
     const dvec4 r0 = a.pos_ref[i];
-    const double dx = wrap_diff(x.x - r0.x, R.Lx, R.hx);
-    const double dy = wrap_diff(x.y - r0.y, R.Ly, R.hy);
+    double dx = x.x - r0.x, dy = x.y - r0.y;
+    if (ge_pos(dx, R.hx)) dx -= R.Lx;
+    else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
+    if (ge_pos(dy, R.hy)) dy -= R.Ly;
+    else if (gt_pos(neg_bits(dy), R.hy)) dy += R.Ly;
     const double dz = x.z - r0.z;
     d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
     a.pos[i] = x;
@@ -233,7 +251,8 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
-  if (__syncthreads_or(d2 >= p.half_skin2) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
+  if (__syncthreads_or(ge_pos(d2, p.half_skin2)) && threadIdx.x == 0)
+    atomicExch(a.force_rebuild, 1);
   if (!sc.use) return;
   // the last block to finish decides this step's branches of the captured graph
   __shared__ int is_last;
@@ -543,23 +562,13 @@ __device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
 }
 
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
-constexpr int kListWin = 256;      // candidates staged in shared memory per window and warp
+constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
 
-// Verlet list, warp per cell (the cell's molecules in groups of up to 32). The candidate stream --
-// the 27 neighbour cells in stencil order, molecules in index order, then their wall atoms -- is
-// staged window by window in shared memory together with the candidates' FP32 cell-local offsets;
-// the warp then takes the group's molecules one after another, its lanes testing 32 candidates at
-// a time: (l_i - l_j) - dc * cell (exactly antisymmetric, so the lists are symmetric) against the
-// padded list radius. Hits go to the front (j > i, wall atoms) or, from the end, the back (j < i) of
-// the molecule's row in stream order; the running counts are warp-uniform.
 __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half, int lpt) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
-  __shared__ uint32_t s_ent[kListWarps][kListWin];
-  __shared__ float4 s_pos[kListWarps][kListWin];
-  __shared__ float4 s_off[kListWarps][64];
-  __shared__ float4 s_li[kListWarps][32];
-  __shared__ int s_f[kListWarps][32], s_b[kListWarps][32];
+  __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
+  __shared__ float4 sh_li[kListWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
@@ -570,10 +579,6 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   const RepDev& R = a.reps[a.cell_rep[c]];
   const int local = c - R.cell_off;
   const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
-  // offset of a neighbour cell by the 6-bit code in bits 26-31 of a list entry
-  for (int k = lane; k < 64; k += 32)
-    s_off[w][k] = make_float4((float)((k & 3) - 1) * R.lcxf, (float)(((k >> 2) & 3) - 1) * R.lcyf,
-                              (float)((k >> 4) - 1) * R.lczf, 0.f);
   // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
   int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
   uint32_t code = 0;
@@ -592,15 +597,14 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   }
   const unsigned lt = (1u << lane) - 1u;
   const int N = a.n_total, cap = p.cap;
-  uint32_t* __restrict__ ent = s_ent[w];
-  float4* __restrict__ pos = s_pos[w];
+  uint32_t* stream = sh_stream[w];
   int max_n = 0;
   for (int ib = i_begin; ib < i_end; ib += 32) {
     const int nic = min(32, i_end - ib);
-    s_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    s_f[w][lane] = 0;
-    s_b[w][lane] = 0;
-    int vh = 0;
+    // the molecules of this group: FP32 offsets in shared memory; lane il keeps molecule il's
+    // front and back counts in registers
+    sh_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int cf = 0, cb = 0, vh = 0;
     __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
       const bool wallpass = pass == 1;
@@ -614,55 +618,53 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
       }
       const int T = __shfl_sync(kFull, incl, 31);
       const int excl = incl - tot;
-      for (int W0 = 0; W0 < T; W0 += kListWin) {
-        const int W1 = min(T, W0 + kListWin), nwin = W1 - W0;
+      for (int W0 = 0; W0 < T; W0 += kStreamWin) {
+        const int W1 = min(T, W0 + kStreamWin);
         // lane l writes the part of its cell's candidates that falls in this window
         for (int m = max(0, W0 - excl); m < tot && excl + m < W1; ++m)
-          ent[excl + m - W0] = (base_idx + (uint32_t)m) | code;
+          stream[excl + m - W0] = (base_idx + (uint32_t)m) | code;
         __syncwarp();
-        for (int q = lane; q < nwin; q += 32) {
-          const int jj = (int)(ent[q] & kIndexMask);
-          pos[q] = wallpass ? a.wlpos[jj - N] : a.lpos[jj];
-        }
-        __syncwarp();
-        for (int il = 0; il < nic; ++il) {
-          const int i = ib + il;
-          const float4 li = s_li[w][il];
-          int f = s_f[w][il], b = s_b[w][il];  // warp-uniform running counts
-          uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
-          for (int q0 = 0; q0 < nwin; q0 += 32) {
-            const int q = q0 + lane;
-            const bool valid = q < nwin;
-            const uint32_t e = valid ? ent[q] : 0u;
-            const float4 bp = pos[valid ? q : 0];
-            const float4 o = s_off[w][e >> 26];
-            const float dx = (li.x - bp.x) - o.x, dy = (li.y - bp.y) - o.y, dz = (li.z - bp.z) - o.z;
-            const int jj = (int)(e & kIndexMask);
-            const bool hit = valid && (wallpass || jj != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
-            const bool front = hit && (wallpass || jj > i);
-            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, hit && !front);
-            if (hit) {
-              const int slot = front ? f + __popc(bf & lt) : cap - 1 - (b + __popc(bb & lt));
-              if (front ? slot < cap : slot >= 0) row[slot] = e;
+        for (int base = W0; base < W1; base += 32) {
+          const int q = base + lane;
+          const bool valid = q < W1;
+          const uint32_t entry = valid ? stream[q - W0] : 0u;
+          const int jj = (int)(entry & kIndexMask);
+          const int j = wallpass ? jj - N : jj;
+          float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
+          const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
+          const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
+          const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
+          for (int il = 0; il < nic; ++il) {
+            const int i = ib + il;
+            const float4 li = sh_li[w][il];
+            const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
+            const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
+            const bool front = hit && (wallpass || j > i);
+            const bool back = hit && !front;
+            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
+            if (bf | bb) {
+              const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
+              if (hit) {  // front from the start of the row, back from its end, in stream order
+                const int slot = front ? f0 + __popc(bf & lt) : cap - 1 - (b0 + __popc(bb & lt));
+                if (front ? slot < cap : slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
+              }
+              if (lane == il) {
+                cf += __popc(bf);
+                cb += __popc(bb);
+              }
             }
-            f += __popc(bf);
-            b += __popc(bb);
           }
-          if (lane == 0) {
-            s_f[w][il] = f;
-            s_b[w][il] = b;
-          }
-          __syncwarp();
         }
         __syncwarp();
       }
-      if (!wallpass) vh = s_f[w][lane];
+      if (!wallpass) vh = cf;
     }
     // counts, overflow, processing-order histogram
     {
       const int i = ib + lane;
       const bool own = lane < nic;
-      const int nf = s_f[w][lane], nb = s_b[w][lane], nvh = vh;
+      const int nf = cf, nb = cb, nvh = vh;
       if (own) {
         if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
           atomicOr(a.status, kStatusOverflow);
