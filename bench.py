@@ -71,8 +71,8 @@ def parse():
                     help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
                          "launch lists)")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
-                    help="FP64 reaction forces: FP64 atomic adds, or the bit-reproducible "
-                         "slot-and-gather form")
+                    help="reaction forces by FP64 atomic adds (half list, both precisions), or "
+                         "the bit-reproducible forms (FP64 slot-and-gather, mixed full list)")
     return ap.parse_args()
 
 
@@ -285,8 +285,7 @@ def time_steps(sim, torch, stream, flush, steps):
 def measure_precision(md, systems, precision, args, torch, stream, flush):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
-    if precision == md.MD_PREC_FP64:
-        sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
+    sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
     sim.tune_info = None
     if not args.no_autotune:
         sim.tune_info = autotune.tune(sim, trials=9, use_cache=False)
@@ -350,8 +349,10 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
     flops = pairs_per_launch * FLOPS_PER_PAIR
     achieved = flops / (ms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
-    kname = "k_forces_mixed" if precision != "fp64" else (
-        "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half")
+    if precision == "fp64":
+        kname = "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
+    else:
+        kname = "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == kernel_sha() else None
     return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
@@ -478,8 +479,7 @@ def run_ours(args):
                            "n_vapor": sum(s.n_vapor for s in systems),
                            "n_wall": sum(s.n_wall for s in systems),
                            "precision": args.precision,
-                           "force_accumulate": (args.accumulate if args.precision == "fp64"
-                                                else "per-molecule sums (full list)"),
+                           "force_accumulate": args.accumulate,
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "launch_mode": args.launch_mode,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},

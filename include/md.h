@@ -144,12 +144,14 @@ typedef struct {
   int32_t order_by_length; /* 1: process molecules longest list first; 2: in cell order */
   int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 2: plain launches */
   int32_t steps_per_graph; /* MD steps captured per graph replay */
-  int32_t force_accumulate; /* FP64 only. 1: deterministic -- each vapour pair's force is stored
-                              in the partner's slot and every molecule sums its slots in list
-                              order (bit-for-bit reproducible); 2: the reaction forces go to the
-                              partners by FP64 atomic adds (no gather; the summation order varies
-                              from run to run, so results agree with mode 1 to rounding only).
-                              Changing it rebuilds the lists (synchronises). */
+  int32_t force_accumulate; /* 1: deterministic (bit-for-bit reproducible) -- FP64: each vapour
+                              pair's force is stored in the partner's slot and every molecule sums
+                              its slots in list order; mixed: every molecule sums its whole row.
+                              2: each vapour pair is evaluated once and its reaction goes to the
+                              partner by an FP64 atomic add (no gather; the second half-kick of a
+                              step is deferred into the next step's first); the summation order
+                              varies from run to run, so results agree with mode 1 to rounding
+                              only. Changing it rebuilds the lists (synchronises). */
   int32_t pair_method;     /* FP64 only. 1: Verlet lists (default); 2: every pair every step, one
                               thread per molecule summing over all molecules and wall atoms of
                               its replica (the paper's F1 form, Sec. 3, Fig. 1; O(N^2), for small

@@ -268,7 +268,7 @@ md_status sync_status(md_ctx* c) {
 // refresh the FP32 cell-local offsets for the kernels that screen or compute with them
 int integrate_flags(const md_ctx* c) {
   int f = 0;
-  if (!c->mixed && c->tun.atomic_acc) f |= kIntZeroForces;
+  if (c->tun.atomic_acc) f |= kIntZeroForces;
   if (c->mixed || c->tun.tpp_fp64 == 32) f |= kIntLocalOffsets;
   return f;
 }
@@ -731,8 +731,6 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
   if (t->force_accumulate < 0 || t->force_accumulate > 2)
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
-  if (c->mixed && t->force_accumulate == 2)
-    return fail(c, MD_EINVAL, "atomic accumulation is an FP64-path option");
   if (t->pair_method < 0 || t->pair_method > 2)
     return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists) or 2 (all pairs)");
   if (c->mixed && t->pair_method == 2)

@@ -1458,6 +1458,86 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
   finish_chunks(a);
 }
 
+// Mixed precision, half list, reaction forces by atomics: the pair terms of k_forces_mixed (FP32 on
+// the cell-local offsets, the FP64 cutoff decision near rc) for the front of each row only -- every
+// vapour pair once -- with the molecule's own sum in compensated FP32 and each pair's reaction
+// (the FP32 pair force widened to FP64) sent to the partner by an FP64 atomic add. The forces must be
+// zero beforehand; the summation order of the atomic adds varies from run to run.
+template <int TPP>
+__global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p, int lpt,
+                                                             int owe_kick) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.force_rebuild = 0;
+    if (owe_kick) *a.kick_pending = 1;
+  }
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
+  int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    int i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const float4 li = a.lpos[i];
+      const dvec4 xi = a.pos[i];
+      const int n = a.n_front[i], nvh = a.n_vh[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      for (int q = sub; q < n; q += TPP) {
+        const uint32_t e = row[q];
+        const int j = (int)(e & kIndexMask);
+        const bool wall = j >= N;
+        const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
+        const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
+        const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
+        const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
+        bool in = r2 < lo;
+        if (!in && r2 < hi) {
+          const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+          const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+          const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+          const double ez = xi.z - xj.z;
+          in = ex * ex + ey * ey + ez * ez < (wall ? p.rcw2 : p.rc2);
+        }
+        if (in) {
+          const float a12 = wall ? p.a12wf : p.a12f, b6 = wall ? p.b6wf : p.b6f;
+          const float inv2 = __frcp_rn(r2);
+          const float inv6 = inv2 * inv2 * inv2;
+          const float fr = inv2 * inv6 * fmaf(a12, inv6, -b6);
+          const float px = fr * dx, py = fr * dy, pz = fr * dz;
+          two_sum_acc(sx, cx, px);
+          two_sum_acc(sy, cy, py);
+          two_sum_acc(sz, cz, pz);
+          if (q < nvh) {  // Newton's third law: the partner receives -p
+            atomicAdd(&a.frc[j].x, -(double)px);
+            atomicAdd(&a.frc[j].y, -(double)py);
+            atomicAdd(&a.frc[j].z, -(double)pz);
+          }
+          ++cnt;
+        }
+      }
+    }
+    const double fx = group_sum<TPP>((double)sx + (double)cx);
+    const double fy = group_sum<TPP>((double)sy + (double)cy);
+    const double fz = group_sum<TPP>((double)sz + (double)cz);
+    if (live && sub == 0) {
+      atomicAdd(&a.frc[i].x, fx);
+      atomicAdd(&a.frc[i].y, fy);
+      atomicAdd(&a.frc[i].z, fz);
+    }
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
 // ------------------------------------------------------------------------------------------------
 // observables: pore assignment, occupancy, adsorbed count, axial profile (integer atomics: exact)
 
@@ -1601,7 +1681,9 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   const int b = 256;
   const int nt = nblocks(a.n_total, b);
   const int ntiles = nblocks(a.n_cells, 4096);
-  const int half = mixed ? 0 : 1, lpt = t.lpt;
+  // the pair kernel walks the front of each row (FP64, or mixed with atomic reaction forces) or the
+  // whole row (mixed, deterministic): the processing order sorts by that length
+  const int half = (!mixed || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
   k_cell_count<<<nt, b, 0, s>>>(a, p);
   if (ntiles <= 16) {
     k_scan_single<<<1, 1024, 0, s>>>(a, p);
@@ -1618,7 +1700,7 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
     k_order_scan<<<1, 1024, 0, s>>>(a, p);
     k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   }
-  if (half && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
+  if (!mixed && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
 // grid of the pair kernels: at most SMs x blocks per SM; warps fetch chunks of molecules
@@ -1631,6 +1713,13 @@ void launch_mixed(const Arrays& a, const PotDev& p, bool stats, bool kick, const
                   cudaStream_t s) {
   const int b = t.force_block;
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_mixed, t);
+  if (!stats && t.atomic_acc) {
+    // forces start from zero (k_integrate_first clears them in a step); the second half-kick of
+    // a step is deferred into the next first half-kick
+    if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+    k_forces_mixed_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
+    return;
+  }
   if (stats) k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
   else if (kick) k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
   else k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
@@ -1709,9 +1798,9 @@ template <int TPP>
 void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t, cudaStream_t s) {
   const int b = t.force_block;
   if (mixed) {
-    k_forces_mixed<false, false, TPP><<<pair_grid((long long)a.n_total * TPP, b,
-                                                  t.force_blocks_per_sm_mixed, t), b, 0, s>>>(
-        a, p, t.lpt);
+    const int gm = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_mixed, t);
+    if (t.atomic_acc) k_forces_mixed_atomic<TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0);
+    else k_forces_mixed<false, false, TPP><<<gm, b, 0, s>>>(a, p, t.lpt);
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);

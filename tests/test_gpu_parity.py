@@ -181,6 +181,29 @@ def test_atomic_accumulation_agrees_with_deterministic_to_rounding(shapes):
             b.set_tuning(force_tpp=32)
 
 
+@pytest.mark.parametrize("tpp", [1, 2, 4, 8])
+def test_mixed_atomic_half_list_matches_oracle(shapes, shapes_after_ten, tpp):
+    """The mixed form with atomic reaction forces (each vapour pair once): RMS force error <= 1e-5
+    against the oracle and close to the full-list mixed form; 10-step trajectories and the
+    integer observables as the other mixed tests."""
+    with md.Simulation(shapes, precision=md.MD_PREC_MIXED) as a, \
+            md.Simulation(shapes, precision=md.MD_PREC_MIXED) as b:
+        b.set_tuning(force_accumulate=2, force_tpp=tpp)
+        assert b.tuning()["force_accumulate"] == 2
+        for r, s in enumerate(shapes):
+            g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            fb = b.forces(r)
+            assert rms_rel_err(fb, g) <= 1e-5
+            assert rms_rel_err(fb, a.forces(r)) <= 2e-6
+        b.step(10)
+        for r, (s, st) in enumerate(zip(shapes, shapes_after_ten)):
+            x, v = b.state(r)
+            assert np.abs(wrapped_diff(x, st.x, s)).max() <= 1e-5
+            assert np.abs(v - st.v).max() <= 1e-4
+            o, occ, ads, prof = b.observables(r)
+            assert o["step"] == 10
+
+
 def test_all_pairs_method_small_cylinder():
     """The paper's F1 form (every pair each step, no lists): forces, 10-step trajectory with the
     thermostat, pair counts and observables equal the oracle's; switching back to lists gives the
