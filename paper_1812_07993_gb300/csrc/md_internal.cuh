@@ -117,6 +117,8 @@ struct Arrays {
   int32_t* any_scale;
   long long* step;
   int32_t* force_rebuild;           // set by the host or by a molecule past skin/2; cleared by the pair kernel
+  int32_t* rebuild_rep;             // per replica: nonzero when its lists are rebuilt (a molecule
+                                    // moved skin/2, or the host asked); cleared by the pair kernel
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
   unsigned int* kick_done;          // last-block detection in k_kick_pending
@@ -208,6 +210,5 @@ void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);
 // apply a deferred second half-kick, if one is owed (before anything reads velocities)
 void launch_settle_kick(const Arrays& a, const PotDev& p, cudaStream_t s);
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s);
-int rebuild_kernel_count(bool mixed);
 
 }  // namespace mdk

@@ -42,6 +42,18 @@ __device__ __forceinline__ bool need_rebuild(const Arrays& a, const PotDev& p) {
   return *reinterpret_cast<volatile const int32_t*>(a.force_rebuild) != 0;
 }
 
+// replica r rebuilds its lists in this chain (the others keep their order, cells and lists)
+__device__ __forceinline__ bool rep_rebuilds(const Arrays& a, int r) {
+  return a.rebuild_rep[r] != 0;
+}
+
+// the pair kernels clear the rebuild flags once the chain has run
+__device__ __forceinline__ void clear_rebuild_flags(const Arrays& a) {
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x == 0) *a.force_rebuild = 0;
+  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x) a.rebuild_rep[r] = 0;
+}
+
 // periodic image of a coordinate difference of two wrapped positions (|d| < L): the high word of
 // |d| is compared against the high word of L/2 -- an integer test, no FP64 instruction. Pairs in a
 // list are either closer than the list radius or further than L minus it, far from L/2.
@@ -203,8 +215,10 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d2 = 0.0;
+  int my_rep = 0;
   if (!halt && i < a.n_total) {
-    const RepDev& R = a.reps[a.rep[i]];
+    my_rep = a.rep[i];
+    const RepDev& R = a.reps[my_rep];
     dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 x_old = x;
     const dvec4 f = a.frc[i];
@@ -251,8 +265,9 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
-  if (__syncthreads_or(ge_pos(d2, p.half_skin2)) && threadIdx.x == 0)
-    atomicExch(a.force_rebuild, 1);
+  const bool far = ge_pos(d2, p.half_skin2);
+  if (far) a.rebuild_rep[my_rep] = 1;  // only this replica's lists are rebuilt
+  if (__syncthreads_or(far) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
   if (!sc.use) return;
   // the last block to finish decides this step's branches of the captured graph
   __shared__ int is_last;
@@ -350,11 +365,20 @@ __global__ void k_thermo_scale(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // cell build: a counting sort of the vapour by cell, stable in the caller's molecule index
 
+// cells of the replicas that rebuild start from zero counts (the others keep theirs, so the scan
+// over every cell reproduces their starts)
+__global__ void k_cell_clear(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < a.n_cells && rep_rebuilds(a, a.cell_rep[c])) a.vcount[c] = 0;
+}
+
 __global__ void k_cell_count(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total) return;
+  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
   const RepDev& R = a.reps[a.rep[i]];
   const dvec4 x = a.pos[i];
   const int ix = cell_coord(x.x, R.hx, R.lcx, R.ncx);
@@ -499,7 +523,7 @@ __global__ void k_scatter(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total) return;
+  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
   a.perm_tmp[a.vstart[a.cell_tmp[i]] + a.slot_tmp[i]] = i;
 }
 
@@ -509,7 +533,7 @@ __global__ void k_permute(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.n_total) return;
+  if (s >= a.n_total || !rep_rebuilds(a, a.rep[s])) return;  // replicas occupy fixed ranges
   const int src = a.perm_tmp[s];
   const int c = a.cell_tmp[src];
   const int my_id = a.id[src];
@@ -535,7 +559,7 @@ __global__ void k_copyback(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total) return;
+  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
   a.pos[i] = a.pos_alt[i];
   a.vel[i] = a.vel_alt[i];
   a.frc[i] = a.frc_alt[i];
@@ -572,9 +596,8 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
-  if (c >= a.n_cells) return;
+  if (c >= a.n_cells || !rep_rebuilds(a, a.cell_rep[c])) return;
   const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
-  if (lane == 0) a.vcount[c] = 0;  // ready for the next build
   if (i_end == i_begin) return;
   const RepDev& R = a.reps[a.cell_rep[c]];
   const int local = c - R.cell_off;
@@ -673,7 +696,6 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
         a.n_vh[i] = min(nvh, p.cap_v);
         max_n = max(max_n, nf + nb);
       }
-      if (lpt) hist_add(a, min(half ? nf : nf + nb, cap), own);
     }
     __syncwarp();
   }
@@ -687,6 +709,16 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
 // (FP64: the front; mixed: front + back), longest first: warps see uniform lengths and the heaviest
 // chunks start first. Whatever the order, each molecule's force is a sum it owns, so the order
 // changes no result.
+
+// list-length histogram of every molecule (rebuilt rows and kept ones alike)
+__global__ void k_order_hist(Arrays a, PotDev p, int half) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool own = i < a.n_total;
+  const int h = own ? min(half ? a.n_front[i] : a.n_front[i] + a.n_back[i], p.cap) : 0;
+  hist_add(a, h, own);
+}
 
 // start of each list length in descending order of length; clears the histogram
 __global__ void __launch_bounds__(1024) k_order_scan(Arrays a, PotDev p) {
@@ -755,6 +787,7 @@ __global__ void __launch_bounds__(256) k_fwd_build(Arrays a, PotDev p) {
   const uint32_t spare = (uint32_t)((size_t)a.n_total * capv);
   const bool vec = (cap & 3) == 0;
   for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.n_total; i += warps) {
+    if (!rep_rebuilds(a, a.rep[i])) continue;  // (warp-uniform: one molecule per warp)
     const int nvh = a.n_vh[i];
     const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
     uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
@@ -866,9 +899,7 @@ template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.force_rebuild = 0;
-  }
+  clear_rebuild_flags(a);
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap, capv = p.cap_v;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
@@ -918,11 +949,9 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
                                                             int owe_kick) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.force_rebuild = 0;
-    // in a step, the second half-kick is owed: the next first half-kick (or k_kick_pending) pays it
-    if (owe_kick) *a.kick_pending = 1;
-  }
+  clear_rebuild_flags(a);
+  // in a step, the second half-kick is owed: the next first half-kick (or k_kick_pending) pays it
+  if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
@@ -1012,10 +1041,8 @@ __global__ void k_zero_forces(Arrays a) {
 template <bool STATS, bool KICK>
 __global__ void __launch_bounds__(128) k_allpairs(Arrays a, PotDev p) {
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && !STATS) {
-    *a.force_rebuild = 0;
-    if (KICK) *a.kick_pending = 0;  // this step kicks itself
-  }
+  if (!STATS) clear_rebuild_flags(a);
+  if (KICK && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 0;  // this step kicks itself
   if (halted(a)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = a.n_total;
@@ -1114,9 +1141,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
   extern __shared__ __align__(32) unsigned char pack_smem[];
   PackWarp& S = reinterpret_cast<PackWarp*>(pack_smem)[threadIdx.x >> 5];
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.force_rebuild = 0;
-  }
+  clear_rebuild_flags(a);
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap, capv = p.cap_v;
   const int lane = threadIdx.x & 31;
@@ -1346,10 +1371,8 @@ template <bool STATS, bool KICK, int TPP>
 __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lpt) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.force_rebuild = 0;
-    if (KICK) *a.kick_pending = 0;  // this step kicks itself
-  }
+  clear_rebuild_flags(a);
+  if (KICK && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 0;  // this step kicks itself
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
@@ -1468,10 +1491,8 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
                                                              int owe_kick) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.force_rebuild = 0;
-    if (owe_kick) *a.kick_pending = 1;
-  }
+  clear_rebuild_flags(a);
+  if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
   if (halted(a)) return;
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
@@ -1675,8 +1696,6 @@ void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const 
     k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, flags);
 }
 
-int rebuild_kernel_count(bool mixed) { return mixed ? 10 : 11; }
-
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s) {
   const int b = 256;
   const int nt = nblocks(a.n_total, b);
@@ -1684,6 +1703,7 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   // the pair kernel walks the front of each row (FP64, or mixed with atomic reaction forces) or the
   // whole row (mixed, deterministic): the processing order sorts by that length
   const int half = (!mixed || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
+  k_cell_clear<<<nblocks(a.n_cells, b), b, 0, s>>>(a, p);
   k_cell_count<<<nt, b, 0, s>>>(a, p);
   if (ntiles <= 16) {
     k_scan_single<<<1, 1024, 0, s>>>(a, p);
@@ -1697,6 +1717,7 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   k_copyback<<<nt, b, 0, s>>>(a, p);
   k_list_build<<<nblocks(a.n_cells, kListWarps), kListWarps * 32, 0, s>>>(a, p, half, lpt);
   if (lpt) {
+    k_order_hist<<<nt, b, 0, s>>>(a, p, half);
     k_order_scan<<<1, 1024, 0, s>>>(a, p);
     k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   }
