@@ -287,8 +287,9 @@ md_status rebuild_and_forces(md_ctx* c) {
   CUDA_TRY(c, cudaMemcpyAsync(c->a.force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
                               c->stream));
   c->bytes_h2d += sizeof(int);
-  // every replica rebuilds (nonzero bytes make a nonzero flag)
-  CUDA_TRY(c, cudaMemsetAsync(c->a.rebuild_rep, 1, sizeof(int32_t) * (size_t)c->n_reps, c->stream));
+  // every replica rebuilds (all-ones bytes: the largest displacement pattern)
+  CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0xff, sizeof(unsigned long long) * (size_t)c->n_reps,
+                              c->stream));
   launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
   launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
   CUDA_TRY(c, cudaGetLastError());
@@ -426,6 +427,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   P.mass = pot->mass;
   P.inv_mass = 1.0 / pot->mass;
   P.half_skin2 = 0.25 * pot->skin * pot->skin;
+  P.group_disp2 = 0.36 * P.half_skin2;  // 0.6 skin/2
   P.r_ads2 = pot->r_ads * pot->r_ads;
   P.rc2f = (float)P.rc2;
   P.rcw2f = (float)P.rcw2;
@@ -605,7 +607,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.step, 1);
   ALLOC(A.force_rebuild, 1);
   ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1);
-  ALLOC(A.rebuild_rep, (size_t)n_reps);
+  ALLOC(A.rep_disp2, (size_t)n_reps);
+  ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.n_act, 1);
   ALLOC(A.status, 1);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);

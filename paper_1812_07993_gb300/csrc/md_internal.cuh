@@ -79,6 +79,7 @@ struct PotDev {
   double ushift, ushift_w;
   double inv_mass, mass;
   double half_skin2;                // rebuild when a displacement^2 reaches this
+  double group_disp2;               // with a rebuild under way, replicas past this rebuild too
   double r_ads2;
   float rc2f, rcw2f, rl2f;          // FP32 cutoffs and the (padded) list radius^2
   float rc2f_lo, rc2f_hi, rcw2f_lo, rcw2f_hi;  // FP32 band around the cutoff decided in FP64
@@ -117,8 +118,12 @@ struct Arrays {
   int32_t* any_scale;
   long long* step;
   int32_t* force_rebuild;           // set by the host or by a molecule past skin/2; cleared by the pair kernel
-  int32_t* rebuild_rep;             // per replica: nonzero when its lists are rebuilt (a molecule
-                                    // moved skin/2, or the host asked); cleared by the pair kernel
+  unsigned long long* rep_disp2;    // per replica: the largest squared displacement since its
+                                    // last build among molecules past the grouping threshold (bit
+                                    // pattern of a double; 0 below it); all-ones bytes when the
+                                    // host asks for a rebuild; cleared by the pair kernel
+  int32_t* act_cells;               // cells with molecules of the replicas being rebuilt
+  int32_t* n_act;                   // their number
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
   unsigned int* kick_done;          // last-block detection in k_kick_pending

@@ -42,16 +42,19 @@ __device__ __forceinline__ bool need_rebuild(const Arrays& a, const PotDev& p) {
   return *reinterpret_cast<volatile const int32_t*>(a.force_rebuild) != 0;
 }
 
-// replica r rebuilds its lists in this chain (the others keep their order, cells and lists)
+// replica r rebuilds its lists in this chain: some molecule of it moved past the grouping
+// threshold (0.6 skin/2) since its last build -- the chain runs only once some molecule somewhere
+// reached skin/2 -- or the host asked. The other replicas keep their order, cells and lists;
+// grouping near-due replicas into the same chain keeps chains rare when replicas are many.
 __device__ __forceinline__ bool rep_rebuilds(const Arrays& a, int r) {
-  return a.rebuild_rep[r] != 0;
+  return a.rep_disp2[r] != 0ull;
 }
 
 // the pair kernels clear the rebuild flags once the chain has run
 __device__ __forceinline__ void clear_rebuild_flags(const Arrays& a) {
   if (blockIdx.x != 0) return;
   if (threadIdx.x == 0) *a.force_rebuild = 0;
-  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x) a.rebuild_rep[r] = 0;
+  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x) a.rep_disp2[r] = 0ull;
 }
 
 // periodic image of a coordinate difference of two wrapped positions (|d| < L): the high word of
@@ -265,9 +268,10 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
-  const bool far = ge_pos(d2, p.half_skin2);
-  if (far) a.rebuild_rep[my_rep] = 1;  // only this replica's lists are rebuilt
-  if (__syncthreads_or(far) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
+  if (ge_pos(d2, p.group_disp2))  // rare: only molecules well into their skin
+    atomicMax(&a.rep_disp2[my_rep], (unsigned long long)__double_as_longlong(d2));
+  if (__syncthreads_or(ge_pos(d2, p.half_skin2)) && threadIdx.x == 0)
+    atomicExch(a.force_rebuild, 1);
   if (!sc.use) return;
   // the last block to finish decides this step's branches of the captured graph
   __shared__ int is_last;
@@ -371,6 +375,7 @@ __global__ void k_cell_clear(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c == 0) *a.n_act = 0;
   if (c < a.n_cells && rep_rebuilds(a, a.cell_rep[c])) a.vcount[c] = 0;
 }
 
@@ -386,7 +391,9 @@ __global__ void k_cell_count(Arrays a, PotDev p) {
   const int iz = cell_coord(x.z, R.hz, R.lcz, R.ncz);
   const int c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
   a.cell_tmp[i] = c;
-  a.slot_tmp[i] = atomicAdd(&a.vcount[c], 1);
+  const int slot = atomicAdd(&a.vcount[c], 1);
+  a.slot_tmp[i] = slot;
+  if (slot == 0) a.act_cells[atomicAdd(a.n_act, 1)] = c;  // the cell's first molecule lists it
 }
 
 // exclusive scan of a 4096-element tile by 1024 threads; returns the tile total
@@ -594,114 +601,118 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
   __shared__ float4 sh_li[kListWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * kListWarps + w;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
-  if (c >= a.n_cells || !rep_rebuilds(a, a.cell_rep[c])) return;
-  const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
-  if (i_end == i_begin) return;
-  const RepDev& R = a.reps[a.cell_rep[c]];
-  const int local = c - R.cell_off;
-  const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
-  // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
-  int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
-  uint32_t code = 0;
-  if (lane < 27) {
-    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
-    const int jz = iz + dz;
-    if (jz >= 0 && jz < R.ncz) {
-      const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
-      const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
-      vj0 = a.vstart[cn];
-      nv = a.vstart[cn + 1] - vj0;
-      wj0 = a.wstart[cn];
-      nw = a.wstart[cn + 1] - wj0;
-    }
-    code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) | ((uint32_t)(dz + 1) << 30);
-  }
-  const unsigned lt = (1u << lane) - 1u;
-  const int N = a.n_total, cap = p.cap;
-  uint32_t* stream = sh_stream[w];
-  int max_n = 0;
-  for (int ib = i_begin; ib < i_end; ib += 32) {
-    const int nic = min(32, i_end - ib);
-    // the molecules of this group: FP32 offsets in shared memory; lane il keeps molecule il's
-    // front and back counts in registers
-    sh_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int cf = 0, cb = 0, vh = 0;
-    __syncwarp();
-    for (int pass = 0; pass < 2; ++pass) {
-      const bool wallpass = pass == 1;
-      const int tot = wallpass ? nw : nv;
-      const uint32_t base_idx = wallpass ? (uint32_t)(N + wj0) : (uint32_t)vj0;
-      int incl = tot;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
+  // a fixed grid; each warp takes the occupied cells of the rebuilding replicas in turn (the rows
+  // it writes are its cell's molecules', so the order of the cells changes nothing)
+  const int n_act = *a.n_act;
+  for (int ac = blockIdx.x * kListWarps + w; ac < n_act; ac += gridDim.x * kListWarps) {
+    const int c = a.act_cells[ac];
+    const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
+    if (i_end == i_begin) continue;
+    const RepDev& R = a.reps[a.cell_rep[c]];
+    const int local = c - R.cell_off;
+    const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
+    // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+    int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
+    uint32_t code = 0;
+    if (lane < 27) {
+      const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+      const int jz = iz + dz;
+      if (jz >= 0 && jz < R.ncz) {
+        const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
+        const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+        vj0 = a.vstart[cn];
+        nv = a.vstart[cn + 1] - vj0;
+        wj0 = a.wstart[cn];
+        nw = a.wstart[cn + 1] - wj0;
       }
-      const int T = __shfl_sync(kFull, incl, 31);
-      const int excl = incl - tot;
-      for (int W0 = 0; W0 < T; W0 += kStreamWin) {
-        const int W1 = min(T, W0 + kStreamWin);
-        // lane l writes the part of its cell's candidates that falls in this window
-        for (int m = max(0, W0 - excl); m < tot && excl + m < W1; ++m)
-          stream[excl + m - W0] = (base_idx + (uint32_t)m) | code;
-        __syncwarp();
-        for (int base = W0; base < W1; base += 32) {
-          const int q = base + lane;
-          const bool valid = q < W1;
-          const uint32_t entry = valid ? stream[q - W0] : 0u;
-          const int jj = (int)(entry & kIndexMask);
-          const int j = wallpass ? jj - N : jj;
-          float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
-          const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
-          const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
-          const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
-          for (int il = 0; il < nic; ++il) {
-            const int i = ib + il;
-            const float4 li = sh_li[w][il];
-            const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
-            const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
-            const bool front = hit && (wallpass || j > i);
-            const bool back = hit && !front;
-            const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
-            if (bf | bb) {
-              const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
-              if (hit) {  // front from the start of the row, back from its end, in stream order
-                const int slot = front ? f0 + __popc(bf & lt) : cap - 1 - (b0 + __popc(bb & lt));
-                if (front ? slot < cap : slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
-              }
-              if (lane == il) {
-                cf += __popc(bf);
-                cb += __popc(bb);
+      code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) | ((uint32_t)(dz + 1) << 30);
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    const int N = a.n_total, cap = p.cap;
+    uint32_t* stream = sh_stream[w];
+    int max_n = 0;
+    for (int ib = i_begin; ib < i_end; ib += 32) {
+      const int nic = min(32, i_end - ib);
+      // the molecules of this group: FP32 offsets in shared memory; lane il keeps molecule il's
+      // front and back counts in registers
+      sh_li[w][lane] = lane < nic ? a.lpos[ib + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      int cf = 0, cb = 0, vh = 0;
+      __syncwarp();
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool wallpass = pass == 1;
+        const int tot = wallpass ? nw : nv;
+        const uint32_t base_idx = wallpass ? (uint32_t)(N + wj0) : (uint32_t)vj0;
+        int incl = tot;
+  #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int T = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - tot;
+        for (int W0 = 0; W0 < T; W0 += kStreamWin) {
+          const int W1 = min(T, W0 + kStreamWin);
+          // lane l writes the part of its cell's candidates that falls in this window
+          for (int m = max(0, W0 - excl); m < tot && excl + m < W1; ++m)
+            stream[excl + m - W0] = (base_idx + (uint32_t)m) | code;
+          __syncwarp();
+          for (int base = W0; base < W1; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < W1;
+            const uint32_t entry = valid ? stream[q - W0] : 0u;
+            const int jj = (int)(entry & kIndexMask);
+            const int j = wallpass ? jj - N : jj;
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
+            const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
+            const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
+            const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
+            for (int il = 0; il < nic; ++il) {
+              const int i = ib + il;
+              const float4 li = sh_li[w][il];
+              const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
+              const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
+              const bool front = hit && (wallpass || j > i);
+              const bool back = hit && !front;
+              const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
+              if (bf | bb) {
+                const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
+                if (hit) {  // front from the start of the row, back from its end, in stream order
+                  const int slot = front ? f0 + __popc(bf & lt) : cap - 1 - (b0 + __popc(bb & lt));
+                  if (front ? slot < cap : slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
+                }
+                if (lane == il) {
+                  cf += __popc(bf);
+                  cb += __popc(bb);
+                }
               }
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
+        if (!wallpass) vh = cf;
       }
-      if (!wallpass) vh = cf;
-    }
-    // counts, overflow, processing-order histogram
-    {
-      const int i = ib + lane;
-      const bool own = lane < nic;
-      const int nf = cf, nb = cb, nvh = vh;
-      if (own) {
-        if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
-          atomicOr(a.status, kStatusOverflow);
-        a.n_front[i] = min(nf, cap);
-        a.n_back[i] = min(nb, cap - min(nf, cap));
-        a.n_vh[i] = min(nvh, p.cap_v);
-        max_n = max(max_n, nf + nb);
+      // counts, overflow, processing-order histogram
+      {
+        const int i = ib + lane;
+        const bool own = lane < nic;
+        const int nf = cf, nb = cb, nvh = vh;
+        if (own) {
+          if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
+            atomicOr(a.status, kStatusOverflow);
+          a.n_front[i] = min(nf, cap);
+          a.n_back[i] = min(nb, cap - min(nf, cap));
+          a.n_vh[i] = min(nvh, p.cap_v);
+          max_n = max(max_n, nf + nb);
+        }
       }
+      __syncwarp();
     }
-    __syncwarp();
+  #pragma unroll
+    for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
+    if (lane == 0) atomicMax(a.max_nb, max_n);
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
-  if (lane == 0) atomicMax(a.max_nb, max_n);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1715,7 +1726,8 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   k_scatter<<<nt, b, 0, s>>>(a, p);
   k_permute<<<nt, b, 0, s>>>(a, p);
   k_copyback<<<nt, b, 0, s>>>(a, p);
-  k_list_build<<<nblocks(a.n_cells, kListWarps), kListWarps * 32, 0, s>>>(a, p, half, lpt);
+  k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
+      a, p, half, lpt);
   if (lpt) {
     k_order_hist<<<nt, b, 0, s>>>(a, p, half);
     k_order_scan<<<1, 1024, 0, s>>>(a, p);
