@@ -451,6 +451,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   c->reps.resize(n_reps);
   c->rh.resize(n_reps);
   std::vector<PoreDev> pores;
+  std::vector<double> ctr;  // cell centres, per replica x then y then z
   long long n_tot = 0, nw_tot = 0, ncell_tot = 0, groups = 0, prof = 0;
   for (int r = 0; r < n_reps; ++r) {
     const md_system* s = &systems[r];
@@ -494,6 +495,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     R.n_groups = H.n_groups;
     R.n_bins = H.n_bins;
     R.prof_off = (int32_t)prof;
+    R.half_dt_m = 0.5 * s->dt * (1.0 / pot->mass);
+    R.dt_m = s->dt * (1.0 / pot->mass);
+    R.ctr_off = (int32_t)ctr.size();
+    for (int k = 0; k < R.ncx; ++k) ctr.push_back(-R.hx + (k + 0.5) * R.lcx);
+    for (int k = 0; k < R.ncy; ++k) ctr.push_back(-R.hy + (k + 0.5) * R.lcy);
+    for (int k = 0; k < R.ncz; ++k) ctr.push_back(-R.hz + (k + 0.5) * R.lcz);
     R.dims = s->dims == 2 ? 2 : 3;
     R.hard = s->wall_model == MD_WALL_HARD ? 1 : 0;
     for (int q = 0; q < s->n_pores; ++q) {
@@ -602,6 +609,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   int32_t* cell_rep_d = nullptr;
   ALLOC(cell_rep_d, (size_t)ncell_tot);
   A.cell_rep = cell_rep_d;
+  double* ctr_d = nullptr;
+  ALLOC(ctr_d, ctr.size());
+  A.cell_ctr = ctr_d;
   ALLOC(A.lambda, (size_t)n_reps);
   ALLOC(A.any_scale, 1);
   ALLOC(A.step, 1);
@@ -670,6 +680,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = up(cell_rep_d, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
     return bail(st);
   if ((st = up(reps_d, c->reps.data(), c->reps.size() * sizeof(RepDev))) != MD_OK) return bail(st);
+  if ((st = up(ctr_d, ctr.data(), ctr.size() * sizeof(double))) != MD_OK) return bail(st);
   if ((st = up(pores_d, pores.data(), pores.size() * sizeof(PoreDev))) != MD_OK) return bail(st);
   // the host staging vectors above die at return: wait for the copies first
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

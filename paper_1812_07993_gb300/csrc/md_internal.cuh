@@ -62,6 +62,8 @@ struct RepDev {
   int32_t group_off, n_groups;      // adsorbed counters / profile rows
   int32_t n_bins;
   int32_t prof_off;                 // first profile counter of this replica
+  double half_dt_m, dt_m;           // dt/(2m) and dt/m
+  int32_t ctr_off;                  // this replica's cell centres in cell_ctr: x, then y, then z
   int32_t dims;                     // 3, or 2 for a planar system (temperature with 2N)
   int32_t hard;                     // 1: hard reflecting walls (no wall atoms)
 };
@@ -112,6 +114,7 @@ struct Arrays {
   int32_t* scan_tiles;              // tile sums of the cell scan
   const int32_t* cell_rep;          // replica of each cell
   const RepDev* reps;
+  const double* cell_ctr;           // per replica: ncx x-centres, ncy y-centres, ncz z-centres
   const PoreDev* pores;
   // per-replica / global scalars
   double* lambda;                   // per replica

@@ -77,17 +77,22 @@ __device__ __forceinline__ int pack_home(int ix, int iy, int iz) {
   return ix | (iy << 10) | (iz << 20);
 }
 
-__device__ __forceinline__ float4 local_offset(const RepDev& R, const dvec4& x, int home) {
+// position relative to the centre of the home cell (centres from the per-replica table), the
+// periodic wrap decided by integer tests; rounded to FP32 for the list test and the mixed terms
+__device__ __forceinline__ float4 local_offset(const Arrays& a, const RepDev& R, const dvec4& x,
+                                               int home) {
   const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
-  const double cx = -R.hx + (ix + 0.5) * R.lcx;
-  const double cy = -R.hy + (iy + 0.5) * R.lcy;
-  const double cz = -R.hz + (iz + 0.5) * R.lcz;
-  float4 l;
-  l.x = (float)wrap_diff(x.x - cx, R.Lx, R.hx);
-  l.y = (float)wrap_diff(x.y - cy, R.Ly, R.hy);
-  l.z = (float)(x.z - cz);
-  l.w = 0.f;
-  return l;
+  const double* __restrict__ ctr = a.cell_ctr + R.ctr_off;
+  double lx = x.x - ctr[ix], ly = x.y - ctr[R.ncx + iy];
+  const double lz = x.z - ctr[R.ncx + R.ncy + iz];
+  // d >= L/2 and d < -L/2 as bit-pattern tests (-d flips the sign bit); L/2 > 0
+  const long long sgn = (long long)0x8000000000000000ull;
+  const long long hxb = __double_as_longlong(R.hx), hyb = __double_as_longlong(R.hy);
+  if (__double_as_longlong(lx) >= hxb) lx -= R.Lx;
+  else if ((__double_as_longlong(lx) ^ sgn) > hxb) lx += R.Lx;
+  if (__double_as_longlong(ly) >= hyb) ly -= R.Ly;
+  else if ((__double_as_longlong(ly) ^ sgn) > hyb) ly += R.Ly;
+  return make_float4((float)lx, (float)ly, (float)lz, 0.f);
 }
 
 // 1/x for a positive normal double x in [2^-126, 2^127] (squared distances), without an FP64
@@ -225,12 +230,9 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 x_old = x;
     const dvec4 f = a.frc[i];
-    const double h = 0.5 * R.dt * p.inv_mass;
-    if (pend) {  // the previous step's second half-kick (Fig. 3), deferred to here
-      v.x += h * f.x;
-      v.y += h * f.y;
-      v.z += h * f.z;
-    }
+    // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
+    // force) owed, both at once
+    const double h = pend ? R.dt_m : R.half_dt_m;
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     a.pos[i] = x;
     a.vel[i] = v;
     if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
-    if (flags & kIntLocalOffsets) a.lpos[i] = local_offset(R, x, a.home[i]);
+    if (flags & kIntLocalOffsets) a.lpos[i] = local_offset(a, R, x, a.home[i]);
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
@@ -559,7 +561,7 @@ __global__ void k_permute(Arrays a, PotDev p) {
   const int home = pack_home(ix, iy, iz);
   a.home[dst] = home;
   a.pos_ref[dst] = x;
-  a.lpos[dst] = local_offset(R, x, home);
+  a.lpos[dst] = local_offset(a, R, x, home);
 }
 
 __global__ void k_copyback(Arrays a, PotDev p) {
@@ -885,12 +887,17 @@ __device__ __forceinline__ bool lt_pos(double x, double y) {
 // p = F(r)/r * (r_i - r_j). The LJ part sits behind the cutoff branch: a warp whose lanes are all
 // beyond the cutoff skips it, which a masked (branch-free) form cannot (measured: the masked
 // two-entry form took ~9 % more FP64-pipe cycles).
+// position of list entry e's partner (a vapour molecule or a wall atom)
+__device__ __forceinline__ dvec4 partner_pos(const Arrays& a, uint32_t e, int N) {
+  const int j = (int)(e & kIndexMask);
+  return j >= N ? a.wpos[j - N] : a.pos[j];
+}
+
 __device__ __forceinline__ bool pair_term(const Arrays& a, const PotDev& p, const RepDev& R,
-                                          const dvec4& xi, uint32_t e, int N, double& px,
-                                          double& py, double& pz) {
+                                          const dvec4& xi, uint32_t e, const dvec4& xj, int N,
+                                          double& px, double& py, double& pz) {
   const int j = (int)(e & kIndexMask);
   const bool wall = j >= N;
-  const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
   const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
   const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
   const double dz = xi.z - xj.z;
@@ -927,17 +934,25 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
       const uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
+      // software-pipelined: the next entry and its partner's position load while this pair's
+      // FP64 chain runs
+      uint32_t e = sub < n ? row[sub] : 0u;
+      dvec4 xj = sub < n ? partner_pos(a, e, N) : xi;
       for (int k = sub; k < n; k += TPP) {
-        const uint32_t e = row[k];
+        const int kn = k + TPP;
+        const uint32_t en = kn < n ? row[kn] : 0u;
+        const dvec4 xn = kn < n ? partner_pos(a, en, N) : xi;
         double px = 0.0, py = 0.0, pz = 0.0;
         // warps whose lanes are all beyond the cutoff skip the pair term (a branch, not a mask)
-        if (pair_term(a, p, R, xi, e, N, px, py, pz)) {
+        if (pair_term(a, p, R, xi, e, xj, N, px, py, pz)) {
           fx += px;
           fy += py;
           fz += pz;
           ++cnt;
         }
         if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(px, py, pz, 0.0);
+        e = en;
+        xj = xn;
       }
     }
     fx = group_sum<TPP>(fx);
@@ -978,10 +993,14 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      uint32_t e = sub < n ? row[sub] : 0u;
+      dvec4 xj = sub < n ? partner_pos(a, e, N) : xi;
       for (int k = sub; k < n; k += TPP) {
-        const uint32_t e = row[k];
+        const int kn = k + TPP;
+        const uint32_t en = kn < n ? row[kn] : 0u;
+        const dvec4 xn = kn < n ? partner_pos(a, en, N) : xi;
         double px, py, pz;
-        if (pair_term(a, p, R, xi, e, N, px, py, pz)) {
+        if (pair_term(a, p, R, xi, e, xj, N, px, py, pz)) {
           fx += px;
           fy += py;
           fz += pz;
@@ -993,6 +1012,8 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
           }
           ++cnt;
         }
+        e = en;
+        xj = xn;
       }
     }
     fx = group_sum<TPP>(fx);
@@ -1020,7 +1041,7 @@ __global__ void k_kick_pending(Arrays a, PotDev p) {
     const RepDev& R = a.reps[a.rep[i]];
     dvec4 v = a.vel[i];
     const dvec4 f = a.frc[i];
-    const double h = 0.5 * R.dt * p.inv_mass;
+    const double h = R.half_dt_m;
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
@@ -1116,7 +1137,7 @@ __global__ void __launch_bounds__(128) k_allpairs(Arrays a, PotDev p) {
       a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
       if (KICK) {  // Fig. 3
         dvec4 v = a.vel[i];
-        const double h = 0.5 * R.dt * p.inv_mass;
+        const double h = R.half_dt_m;
         v.x += h * fx;
         v.y += h * fy;
         v.z += h * fz;
@@ -1362,7 +1383,7 @@ __global__ void k_gather(Arrays a, PotDev p) {
   if (KICK) {
     const RepDev& R = a.reps[a.rep[i]];
     dvec4 v = a.vel[i];
-    const double h = 0.5 * R.dt * p.inv_mass;
+    const double h = R.half_dt_m;
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
@@ -1468,7 +1489,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
       if (KICK) {  // Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
         const RepDev& R = a.reps[a.rep[i]];
         dvec4 v = a.vel[i];
-        const double h = 0.5 * R.dt * p.inv_mass;
+        const double h = R.half_dt_m;
         v.x += h * fx;
         v.y += h * fy;
         v.z += h * fz;
