@@ -172,7 +172,9 @@ typedef struct {
   int64_t n_rebuilds;      /* neighbour-list builds since creation (whole context) */
   int64_t pair_evals_total;/* pairs within cutoff summed over every step run so far
                               (whole context: unique vapour-vapour + vapour-wall) */
-  int32_t max_list_used;   /* longest neighbour list of any build so far (whole context) */
+  int32_t max_list_used;   /* longest neighbour list of any build so far (whole context); with
+                              force_accumulate 2 the rows hold half lists (partners j > i and
+                              wall atoms) */
   int32_t list_capacity;   /* max_neighbors + max_wall_neighbors */
 } md_obs;
 

@@ -597,7 +597,8 @@ __device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
 constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
 
-__global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half, int lpt) {
+__global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half,
+                                                                 int front_only) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
@@ -624,7 +625,9 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
         const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
         const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
         vj0 = a.vstart[cn];
-        nv = a.vstart[cn + 1] - vj0;
+        // half rows: a lower cell holds only lower molecule indices (cell-sorted order), no partner
+        // of a front; its vapour is left out of the stream
+        nv = (front_only && cn < c) ? 0 : a.vstart[cn + 1] - vj0;
         wj0 = a.wstart[cn];
         nw = a.wstart[cn + 1] - wj0;
       }
@@ -676,11 +679,11 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
               const float dx = (li.x - b.x) - ox, dy = (li.y - b.y) - oy, dz = (li.z - b.z) - oz;
               const bool hit = valid && (wallpass || j != i) && dx * dx + dy * dy + dz * dz < p.rl2f;
               const bool front = hit && (wallpass || j > i);
-              const bool back = hit && !front;
+              const bool back = hit && !front && !front_only;
               const unsigned bf = __ballot_sync(kFull, front), bb = __ballot_sync(kFull, back);
               if (bf | bb) {
                 const int f0 = __shfl_sync(kFull, cf, il), b0 = __shfl_sync(kFull, cb, il);
-                if (hit) {  // front from the start of the row, back from its end, in stream order
+                if (front || back) {  // front from the row's start, back from its end, in stream order
                   const int slot = front ? f0 + __popc(bf & lt) : cap - 1 - (b0 + __popc(bb & lt));
                   if (front ? slot < cap : slot >= 0) a.nbr[(size_t)i * cap + slot] = entry;
                 }
@@ -1289,8 +1292,10 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
 // FP64 observable pass over the full row (front + back): per-molecule energy and virial (half of
 // each vapour pair to each end, wall pairs in full), pair counts and nearest wall atom. The forces
 // of the last step are left untouched.
+// With half rows (the atomic forms: no back region), each vapour pair is met once, at its lower
+// end, which adds the partner's halves by atomics; the per-molecule sums start from zero.
 template <int TPP>
-__global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p) {
+__global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p, int half_rows) {
   count_launch(a);
   if (halted(a)) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1323,9 +1328,15 @@ __global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p) {
         ++cvw;
       } else {
         const double fr = inv2 * inv6 * fma(p.a12, inv6, -p.b6);
-        pe += 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift);
-        vir += 0.5 * fr * r2;
+        const double hu = 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift), hv = 0.5 * fr * r2;
+        pe += hu;
+        vir += hv;
         ++cvv;
+        if (half_rows) {  // the partner's halves
+          atomicAdd(&a.pe_i[j], hu);
+          atomicAdd(&a.vir_i[j], hv);
+          atomicAdd(&a.cnt_vv_i[j], 1);
+        }
       }
     }
   }
@@ -1337,12 +1348,18 @@ __global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p) {
   cvv = group_sum<TPP>(cvv);
   cvw = group_sum<TPP>(cvw);
   if (!live || sub != 0) return;
-  a.pe_i[i] = pe;
+  if (half_rows) {
+    atomicAdd(&a.pe_i[i], pe);
+    atomicAdd(&a.vir_i[i], vir);
+    atomicAdd(&a.cnt_vv_i[i], cvv);
+  } else {
+    a.pe_i[i] = pe;
+    a.vir_i[i] = vir;
+    a.cnt_vv_i[i] = cvv;
+  }
   a.pevw_i[i] = pew;
-  a.vir_i[i] = vir;
   a.virw_i[i] = virw;
   a.d2w_i[i] = d2w;
-  a.cnt_vv_i[i] = cvv;
   a.cnt_vw_i[i] = cvw;
 }
 
@@ -1400,7 +1417,8 @@ __global__ void k_gather(Arrays a, PotDev p) {
 // FP64.
 
 template <bool STATS, bool KICK, int TPP>
-__global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lpt) {
+__global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lpt,
+                                                      int half_rows) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
   clear_rebuild_flags(a);
@@ -1462,9 +1480,15 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
               d2w = fmin(d2w, ex * ex + ey * ey + ez * ez);
               ++cvw;
             } else {
-              pe += 0.5 * (u - p.ushift);
-              vir += 0.5 * (double)(fr * r2);
+              const double hu = 0.5 * (u - p.ushift), hv = 0.5 * (double)(fr * r2);
+              pe += hu;
+              vir += hv;
               ++cvv;
+              if (half_rows) {  // half rows meet each vapour pair once: the partner's halves
+                atomicAdd(&a.pe_i[j], hu);
+                atomicAdd(&a.vir_i[j], hv);
+                atomicAdd(&a.cnt_vv_i[j], 1);
+              }
             }
           } else {
             cnt += wall ? 2 : 1;  // vapour pairs are seen from both ends
@@ -1496,12 +1520,18 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         a.vel[i] = v;
       }
       if (STATS) {
-        a.pe_i[i] = pe;
+        if (half_rows) {
+          atomicAdd(&a.pe_i[i], pe);
+          atomicAdd(&a.vir_i[i], vir);
+          atomicAdd(&a.cnt_vv_i[i], cvv);
+        } else {
+          a.pe_i[i] = pe;
+          a.vir_i[i] = vir;
+          a.cnt_vv_i[i] = cvv;
+        }
         a.pevw_i[i] = pew;
-        a.vir_i[i] = vir;
         a.virw_i[i] = virw;
         a.d2w_i[i] = d2w;
-        a.cnt_vv_i[i] = cvv;
         a.cnt_vw_i[i] = cvw;
       }
     }
@@ -1747,14 +1777,22 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   k_scatter<<<nt, b, 0, s>>>(a, p);
   k_permute<<<nt, b, 0, s>>>(a, p);
   k_copyback<<<nt, b, 0, s>>>(a, p);
+  // the atomic forms walk only the front of each row: half rows
   k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
-      a, p, half, lpt);
+      a, p, half, t.atomic_acc);
   if (lpt) {
     k_order_hist<<<nt, b, 0, s>>>(a, p, half);
     k_order_scan<<<1, 1024, 0, s>>>(a, p);
     k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   }
   if (!mixed && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
+}
+
+// the per-molecule pair observables that half rows accumulate by atomics start from zero
+void zero_pair_stats(const Arrays& a, cudaStream_t s) {
+  cudaMemsetAsync(a.pe_i, 0, sizeof(double) * (size_t)a.n_total, s);
+  cudaMemsetAsync(a.vir_i, 0, sizeof(double) * (size_t)a.n_total, s);
+  cudaMemsetAsync(a.cnt_vv_i, 0, sizeof(int32_t) * (size_t)a.n_total, s);
 }
 
 // grid of the pair kernels: at most SMs x blocks per SM; warps fetch chunks of molecules
@@ -1774,9 +1812,14 @@ void launch_mixed(const Arrays& a, const PotDev& p, bool stats, bool kick, const
     k_forces_mixed_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
     return;
   }
-  if (stats) k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-  else if (kick) k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-  else k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+  if (stats) {
+    if (t.atomic_acc) zero_pair_stats(a, s);
+    k_forces_mixed<true, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt, t.atomic_acc);
+  } else if (kick) {
+    k_forces_mixed<false, true, TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  } else {
+    k_forces_mixed<false, false, TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  }
 }
 
 // FP64: half-list pass (TPP lanes per molecule, or the packed kernel for TPP = 32), then the
@@ -1836,7 +1879,8 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
     return;
   }
   if (stats) {  // FP64 observables: a full-row pass that leaves the forces untouched
-    k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p);
+    if (t.atomic_acc) zero_pair_stats(a, s);
+    k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p, t.atomic_acc);
     return;
   }
   switch (t.tpp_fp64) {
@@ -1854,7 +1898,7 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
   if (mixed) {
     const int gm = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_mixed, t);
     if (t.atomic_acc) k_forces_mixed_atomic<TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0);
-    else k_forces_mixed<false, false, TPP><<<gm, b, 0, s>>>(a, p, t.lpt);
+    else k_forces_mixed<false, false, TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0);
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);

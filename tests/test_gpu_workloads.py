@@ -175,3 +175,23 @@ def test_drying_run_occupancy_decay_matches_oracle():
     print("occupancy GPU", gpu.mean(0), "oracle", ora.mean(0), "z", z)
     assert np.abs(z).max() <= 4.0
     assert gpu.mean(0)[-1] < 0.9 * 1000 and ora.mean(0)[-1] < 0.9 * 1000
+
+
+def test_batched_replicas_evolve_as_they_would_alone():
+    """Each replica rebuilds its lists on its own schedule (grouped with others near their skin
+    limit): a batch of six uneven systems run together gives every replica the trajectory it has
+    when run alone, to rounding (the rebuild moments differ, the pair sets do not)."""
+    batch = W.replica_batch(6, seed=11, n_min=1000, n_max=8000)
+    with md.Simulation(batch) as sim:
+        sim.step(60)
+        together = [sim.state(r) for r in range(len(batch))]
+        nreb = sim.observables(0)[0]["n_rebuilds"]
+    assert nreb > 3
+    for r, s in enumerate(batch):
+        with md.Simulation(s) as solo:
+            solo.step(60)
+            x, v = solo.state()
+        d = x - together[r][0]
+        d[:, :2] -= np.array([s.Lx, s.Ly]) * np.round(d[:, :2] / np.array([s.Lx, s.Ly]))
+        assert np.abs(d).max() <= 1e-9, s.name
+        assert np.abs(v - together[r][1]).max() <= 1e-9, s.name
