@@ -202,6 +202,12 @@ def test_mixed_atomic_half_list_matches_oracle(shapes, shapes_after_ten, tpp):
             assert np.abs(v - st.v).max() <= 1e-4
             o, occ, ads, prof = b.observables(r)
             assert o["step"] == 10
+            # half rows: the observable pass meets each vapour pair once and hands the partner its
+            # halves -- the pair counts are exact, energies and virial within FP32 pair terms
+            g, d2, stats = oracle.forces(oracle_params(s), x, s.wall, method=1)
+            assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
+            assert o["pe"] == pytest.approx(stats["pe_vv"] + stats["pe_vw"], rel=1e-5)
+            assert o["virial_vv"] == pytest.approx(stats["vir_vv"], rel=1e-4)
 
 
 def test_all_pairs_method_small_cylinder():
