@@ -282,7 +282,28 @@ def time_steps(sim, torch, stream, flush, steps):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def measure_precision(md, systems, precision, args, torch, stream, flush):
+def rank_barrier(world: int):
+    """All ranks meet here (N > 1: a gloo barrier)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def job_totals(ms: float, pairs: float, world: int):
+    """Whole-job figures over the ranks: the slowest rank's timed milliseconds and the pair
+    interactions of every rank (each rank runs its own copy of the workload: replicas only)."""
+    if world <= 1:
+        return ms, float(pairs)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(pairs)], dtype=torch.float64)
+    m = torch.tensor([float(ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(m[0]), float(t[0])
+
+
+def measure_precision(md, systems, precision, args, torch, stream, flush, world=1):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
     sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
@@ -296,9 +317,12 @@ def measure_precision(md, systems, precision, args, torch, stream, flush):
     sim.sync()
     p0 = pair_total(sim, len(systems))
     l0 = sim.kernel_launches()
+    torch.cuda.synchronize()
+    rank_barrier(world)            # the timed region starts on every rank together
     nvtx_push(torch, "timed_steps")
-    ms = time_steps(sim, torch, stream, flush, args.steps)
+    ms = time_steps(sim, torch, stream, flush, args.steps)   # ends with a device synchronize
     nvtx_pop(torch)
+    rank_barrier(world)
     launches = sim.kernel_launches() - l0
     p1 = pair_total(sim, len(systems))
     return sim, ms, p1 - p0, launches
@@ -411,20 +435,12 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     prec = md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED
 
-    if world > 1:
-        dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    sim, ms, pairs, launches = measure_precision(md, systems, prec, args, torch, stream, flush)
+    sim, ms, pairs, launches = measure_precision(md, systems, prec, args, torch, stream, flush,
+                                                 world)
     clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms, float(pairs)], dtype=torch.float64)
-        tmax = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms_job, pairs_job = float(tmax[0]), float(t[1])
-    else:
-        ms_job, pairs_job = ms, float(pairs)
+    ms_job, pairs_job = job_totals(ms, pairs, world)
     value = pairs_job / (ms_job * 1e-3)
     ms_per_step = ms_job / args.steps
     pairs_per_step = pairs / args.steps

@@ -1,0 +1,48 @@
+"""The multi-GPU bench path is replicas only: every rank runs its own copy of the workload and the
+whole-job figures are the slowest rank's time and the sum of every rank's pair interactions. The
+host logic runs here as two gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    assert bench.dist_env() == (rank, world, rank)
+    bench.rank_barrier(world)
+    ms, pairs = bench.job_totals(10.0 + rank, 1000 * (rank + 1), world)
+    out[rank] = (ms, pairs)
+    bench.rank_barrier(world)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_the_sum_of_pairs():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
+        got = dict(out)
+    assert got[0] == got[1] == (11.0, 3000.0)
+
+
+def test_single_rank_is_the_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.job_totals(3.5, 123, 1) == (3.5, 123.0)
