@@ -890,6 +890,12 @@ __device__ __forceinline__ bool lt_pos(double x, double y) {
 // p = F(r)/r * (r_i - r_j). The LJ part sits behind the cutoff branch: a warp whose lanes are all
 // beyond the cutoff skips it, which a masked (branch-free) form cannot (measured: the masked
 // two-entry form took ~9 % more FP64-pipe cycles).
+// FP32 cell-local offset of list entry e's partner (a vapour molecule or a wall atom)
+__device__ __forceinline__ float4 partner_lpos(const Arrays& a, uint32_t e, int N) {
+  const int j = (int)(e & kIndexMask);
+  return j >= N ? a.wlpos[j - N] : a.lpos[j];
+}
+
 // position of list entry e's partner (a vapour molecule or a wall atom)
 __device__ __forceinline__ dvec4 partner_pos(const Arrays& a, uint32_t e, int N) {
   const int j = (int)(e & kIndexMask);
@@ -1441,11 +1447,16 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
       const dvec4 xi = a.pos[i];
       const int nf = a.n_front[i], n = nf + a.n_back[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      // software-pipelined as in the atomic form; slot q of the full row is the front's q-th
+      // entry, then the back's from the end
+      uint32_t e = sub < n ? row[sub < nf ? sub : cap - 1 - (sub - nf)] : 0u;
+      float4 b = sub < n ? partner_lpos(a, e, N) : li;
       for (int q = sub; q < n; q += TPP) {
-        const uint32_t e = row[q < nf ? q : cap - 1 - (q - nf)];
+        const int qn = q + TPP;
+        const uint32_t en = qn < n ? row[qn < nf ? qn : cap - 1 - (qn - nf)] : 0u;
+        const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
         const int j = (int)(e & kIndexMask);
         const bool wall = j >= N;
-        const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
         const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
         const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
         const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
@@ -1494,6 +1505,8 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
             cnt += wall ? 2 : 1;  // vapour pairs are seen from both ends
           }
         }
+        e = en;
+        b = bn;
       }
     }
     double fx = group_sum<TPP>((double)sx + (double)cx);
@@ -1571,11 +1584,15 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
       const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      // software-pipelined: the next entry and its partner's offset load while this pair runs
+      uint32_t e = sub < n ? row[sub] : 0u;
+      float4 b = sub < n ? partner_lpos(a, e, N) : li;
       for (int q = sub; q < n; q += TPP) {
-        const uint32_t e = row[q];
+        const int qn = q + TPP;
+        const uint32_t en = qn < n ? row[qn] : 0u;
+        const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
         const int j = (int)(e & kIndexMask);
         const bool wall = j >= N;
-        const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
         const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
         const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
         const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
@@ -1605,6 +1622,8 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
           }
           ++cnt;
         }
+        e = en;
+        b = bn;
       }
     }
     const double fx = group_sum<TPP>((double)sx + (double)cx);
