@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--roofline-launches", type=int, default=50)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--nve-steps", type=int, default=0,
+                    help="with the mixed comparison, also the NVE energy drift of both GPU forms "
+                         "over this many steps (after 200 thermostatted ones)")
     ap.add_argument("--launch-mode", choices=["graph", "plain"], default="graph",
                     help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
                          "launch lists)")
@@ -387,6 +390,35 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
             "flops_per_pair": FLOPS_PER_PAIR}
 
 
+def nve_drift(md, systems, precision, stream, accumulate, equil=200, steps=2000, every=50):
+    """Energy drift without the thermostat: equilibrate with it, then run ``steps`` NVE steps and
+    fit a line to the total energy per molecule against time (|slope|, in eps per molecule per
+    tau); also the RMS of the residuals (the fluctuation)."""
+    import dataclasses
+    import numpy as np
+    with md.Simulation(systems, precision=precision, stream=stream) as sim:
+        sim.step(equil)
+        states = [sim.state(r) for r in range(len(systems))]
+    nve = [dataclasses.replace(s, x0=x, v0=v, thermostat_every=0)
+           for s, (x, v) in zip(systems, states)]
+    n = sum(s.n_vapor for s in systems)
+    t, e = [], []
+    with md.Simulation(nve, precision=precision, stream=stream) as sim:
+        sim.set_tuning(force_accumulate=2 if accumulate == "atomic" else 1)
+        for k in range(steps // every):
+            sim.step(every)
+            tot = 0.0
+            for r in range(len(nve)):
+                o = sim.observables(r)[0]
+                tot += o["ke"] + o["pe"]
+            t.append((k + 1) * every * nve[0].dt)
+            e.append(tot / n)
+    t, e = np.array(t), np.array(e)
+    fit = np.polyfit(t, e, 1)
+    return {"drift": abs(float(fit[0])), "fluctuation": float(np.std(e - np.polyval(fit, t))),
+            "unit": "eps per molecule per tau", "steps": steps}
+
+
 def e2e(sim, systems, nsteps, pairs_per_step, torch):
     """Whole-job steps through the public API with host buffers: every step uploads the state of
     every replica from pinned host memory (md_set_state, replica -1: lists rebuilt, forces
@@ -473,6 +505,12 @@ def run_ours(args):
                     errs.append((((fm - g) ** 2).sum(), ((f64 - g) ** 2).sum(), (g ** 2).sum()))
             den = sum(e[2] for e in errs)
             vm = pairsm / (msm * 1e-3)
+            if args.nve_steps > 0:
+                extra["nve_drift"] = {
+                    "fp64": nve_drift(md, systems, md.MD_PREC_FP64, stream, args.accumulate,
+                                      steps=args.nve_steps),
+                    "mixed": nve_drift(md, systems, md.MD_PREC_MIXED, stream, args.accumulate,
+                                       steps=args.nve_steps)}
             extra["mixed"] = {"value": vm, "unit": UNIT, "ms_per_step": msm / args.steps,
                               "speedup_vs_fp64": vm / value,
                               "rms_force_err": math.sqrt(sum(e[0] for e in errs) / den),
