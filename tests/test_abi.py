@@ -104,3 +104,37 @@ def test_unknown_pore_kind_rejected(lib):
     with pytest.raises(md.MDError) as ei:
         md.Simulation(s, generate_wall=True)
     assert ei.value.status == md.MD_EINVAL
+
+
+def planar_system(**kw):
+    s = W.paper_pore_2d(n_in=10, n_out=20)
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+@pytest.mark.parametrize("make,fragment", [
+    (lambda: planar_system(wall_model=0), "planar system needs hard walls"),
+    (lambda: planar_system(pores=[W.Pore(W.PORE_SLIT, width=4.0)]), "planar system needs prism"),
+    (lambda: planar_system(x0=np.where(np.arange(30)[:, None] == 3, [0.0, 0.5, 0.0],
+                                       planar_system().x0)), "y = 0"),
+    (lambda: planar_system(dims=4), "dims"),
+    (lambda: small_system(wall_model=1), "prism or slit"),
+    (lambda: small_system(wall_model=7), "unknown wall model"),
+    (lambda: small_system(pores=[W.Pore(W.PORE_PRISM, r0=0.0, r1=2.0, width=3.0)]), "half-sides"),
+])
+def test_invalid_geometry_rejected_before_any_gpu_work(lib, make, fragment):
+    """Planar systems, hard walls and prism pores: the argument checks run before any CUDA call."""
+    s = make()
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s)
+    assert ei.value.status == md.MD_EINVAL
+    assert fragment in str(ei.value)
+
+
+def test_hard_walls_take_no_wall_atoms(lib):
+    s = W.paper_prism_pore(n_in=10, n_out=20)
+    s.wall = np.array([[0.0, 0.0, 0.0]])
+    with pytest.raises(md.MDError) as ei:
+        md.Simulation(s)
+    assert ei.value.status == md.MD_EINVAL and "no wall atoms" in str(ei.value)
