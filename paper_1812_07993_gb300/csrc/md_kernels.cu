@@ -1,20 +1,24 @@
 // md_kernels.cu -- CUDA kernels (sm_103a) of the pore / water-vapour MD step.
 //
 // One MD step (Sec. 2 velocity Verlet, Figs. 1-4 of arXiv:1812.07993), all replicas per launch:
-//   k_integrate_first   half-kick + drift (Fig. 2), z reflection, x/y wrap, skin check; its
-//                       last block decides whether the lists are rebuilt and whether the
-//                       thermostat acts (CUDA-graph conditional nodes)
-//   rebuild chain       only when a molecule moved >= skin/2 since the last build:
-//                         k_cell_count -> k_scan_* -> k_scatter -> k_permute -> k_copyback ->
-//                         k_list_build (warp per cell) [-> FP64 half-list preparation]
+//   k_integrate_first   half-kick + drift (Fig. 2), z reflection, hard-wall reflection, x/y wrap,
+//                       skin check; its last block decides whether lists are rebuilt and whether
+//                       the thermostat acts (CUDA-graph conditional nodes)
+//   rebuild chain       only when a molecule moved >= skin/2 since its replica's last build, and
+//                       only for the replicas near their limit:
+//                         k_cell_clear -> k_cell_count -> k_scan_* -> k_scatter -> k_permute ->
+//                         k_copyback -> k_list_build (warp per cell) -> k_order_hist ->
+//                         k_order_scan -> k_order_assign [-> k_fwd_build]
 //   pair forces         Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) and the second half-kick
-//                       (Fig. 3): FP64 half list + reverse gather with the kick fused into the
-//                       gather; FP64 half list with atomic reaction forces, the kick deferred into
-//                       the next first half-kick (k_kick_pending settles it before the thermostat
-//                       or any read of the velocities); or mixed precision on the full list with
-//                       the kick fused in
-//   k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on thermostat steps
-//                       (Fig. 4)
+//                       (Fig. 3), in one of:
+//                         FP64 half list + slot-and-gather, the kick fused into the gather;
+//                         FP64 half list with atomic reaction forces;
+//                         mixed precision, full list, the kick fused in;
+//                         mixed precision, half list with atomic reaction forces.
+//                       The atomic forms defer the kick into the next first half-kick
+//                       (k_kick_pending settles it before the thermostat or any velocity read).
+//   k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on
+//                       thermostat steps (Fig. 4)
 // No kernel spins or waits on another block.
 #include <algorithm>
 #include <cstdint>

@@ -447,6 +447,27 @@ def test_mixed_precision_error_after_equilibration(shapes):
             assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
 
 
+@pytest.mark.parametrize("precision", [md.MD_PREC_FP64, md.MD_PREC_MIXED])
+def test_atomic_forms_graph_and_plain_launches_agree(shapes, precision):
+    """The atomic forms defer each step's second half-kick into the next first half-kick and pay
+    it before thermostat steps and reads; graph replays (conditional nodes) and plain launches
+    take the same steps, so they agree to rounding over 70 steps with 7 thermostat steps."""
+    with md.Simulation(shapes, precision=precision) as a, \
+            md.Simulation(shapes, precision=precision) as b:
+        a.set_tuning(force_accumulate=2, use_graph=2)
+        b.set_tuning(force_accumulate=2, use_graph=1, steps_per_graph=7)
+        a.step(70)
+        b.step(70)
+        for r, s in enumerate(shapes):
+            xa, va = a.state(r)
+            xb, vb = b.state(r)
+            assert np.abs(wrapped_diff(xa, xb, s)).max() <= 1e-9
+            assert np.abs(va - vb).max() <= 1e-9
+            oa, *_ = a.observables(r)
+            ob, *_ = b.observables(r)
+            assert oa["ke"] == pytest.approx(ob["ke"], rel=1e-10)
+
+
 def test_graph_with_conditional_rebuilds_matches_plain_launches_fp64_long():
     shapes4 = W.pore_shape_systems_20k()
     with md.Simulation(shapes4) as a, md.Simulation(shapes4) as b:
