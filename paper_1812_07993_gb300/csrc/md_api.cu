@@ -754,8 +754,6 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
   if (t->pair_method) nt.all_pairs = t->pair_method == 2 ? 1 : 0;
   const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
-  if (at && nt.tpp_fp64 == 32)
-    return fail(c, MD_EINVAL, "the packed kernel (force_tpp 32) has no atomic form");
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
@@ -806,8 +804,8 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     c->tun.lpt = lpt;
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
     for (int tp : tpps) {
-      // the packed kernel is the FP64 path's, in its deterministic form
-      if (tp == 32 && (c->mixed || c->tun.atomic_acc)) continue;
+      // the packed kernels are the FP64 path's
+      if (tp == 32 && c->mixed) continue;
       for (int bp : bpss)
         for (int bk : blocks) {
           // the all-pairs kernel has a fixed shape: time it once

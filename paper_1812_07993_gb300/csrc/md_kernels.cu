@@ -131,6 +131,38 @@ __device__ __forceinline__ bool abs_le(double x, double t) {
   return (__double_as_longlong(x) & 0x7fffffffffffffffll) <= __double_as_longlong(t);
 }
 
+// (code - 1) * lc for a 2-bit cell-offset code (0, 1, 2: one cell down, the same cell, one cell up),
+// by selects: an int-to-float conversion would run on the FP64 pipe's rate
+__device__ __forceinline__ float cell_shift(uint32_t code, float lc) {
+  return code == 0u ? -lc : (code == 2u ? lc : 0.f);
+}
+
+// exact widening of an FP32 number to FP64 (IEEE 754 binary32 -> binary64) with integer operations
+// only (a hardware conversion runs on the FP64 pipe's rate): sign kept, exponent rebiased by
+// 1023 - 127 = 896, mantissa moved up by 29 bits; zero, subnormals (renormalised), infinities and
+// NaNs handled by their own cases
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sgn = u & 0x80000000u, m = u & 0x7fffffffu;
+  unsigned hi, lo;
+  if (m - 0x00800000u < 0x7f000000u) {  // normal: biased exponent in [1, 254]
+    hi = sgn | ((m >> 3) + (896u << 20));
+    lo = m << 29;
+  } else if (m == 0u) {
+    hi = sgn;
+    lo = 0u;
+  } else if (m >= 0x7f800000u) {        // infinity or NaN: all-ones exponent
+    hi = sgn | 0x7ff00000u | ((m & 0x007fffffu) >> 3);
+    lo = m << 29;
+  } else {                              // subnormal: m * 2^-149, normalised
+    const int sh = __clz(m) - 8;        // moves the leading bit to bit 23
+    const unsigned mn = (m << sh) & 0x007fffffu;
+    hi = sgn | ((unsigned)(897 - sh) << 20) | (mn >> 3);
+    lo = mn << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // error-free transformation s + x = t + e (Knuth's TwoSum); the error is collected in c
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   const float t = s + x;
@@ -674,9 +706,9 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
             const int j = wallpass ? jj - N : jj;
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
-            const float ox = (float)((int)((entry >> 26) & 3u) - 1) * R.lcxf;
-            const float oy = (float)((int)((entry >> 28) & 3u) - 1) * R.lcyf;
-            const float oz = (float)((int)(entry >> 30) - 1) * R.lczf;
+            const float ox = cell_shift((entry >> 26) & 3u, R.lcxf);
+            const float oy = cell_shift((entry >> 28) & 3u, R.lcyf);
+            const float oz = cell_shift(entry >> 30, R.lczf);
             for (int il = 0; il < nic; ++il) {
               const int i = ib + il;
               const float4 li = sh_li[w][il];
@@ -1043,6 +1075,196 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
   finish_chunks(a);
 }
 
+// FP64, half list, reaction forces by atomics, compacted: a warp takes kAqMols molecules, and the
+// kAqLanes lanes of a molecule screen its list slots in FP32 on the cell-local offsets, kAqSub slots
+// each at a time, keeping the entries that may lie within the cutoff (FP32 r^2 below
+// rc^2 (1 + 1e-5); the FP32 error is ~1e-7 of rc^2) in a per-warp queue. When the queue is full
+// enough, or the lists are done, the FP64 pair terms (the arithmetic of pair_term, the cutoff
+// decided in FP64) run over the queue with every lane busy, two independent entries per lane; the
+// reactions go to the partners by FP64 atomic adds; each pair's force is kept in shared memory, and
+// every lane then sums the entries it queued, in slot order, before the molecule's lanes add their
+// sums in a fixed order. A skin entry costs an FP32 screen instead of the FP64 difference and r^2,
+// and no lane idles through another lane's pair term. Small chunks keep the warps balanced when a
+// few molecules (those next to a wall) have rows several times longer than the rest.
+constexpr int kAqLanes = 4;                  // lanes screening one molecule's row
+constexpr int kAqMols = 32 / kAqLanes;       // molecules per warp chunk
+constexpr int kAqSub = 4;                    // slots per lane screened at a time
+constexpr int kAqCap = 256;                  // queue entries per warp
+constexpr int kAqSeg = 4;                    // screened rounds held before a flush
+
+struct AtomicQueue {
+  double ox[kAqMols], oy[kAqMols], oz[kAqMols];  // FP64 positions of the warp's molecules
+  double oLx[kAqMols], oLy[kAqMols];         // their replicas' box sides in x and y
+  uint32_t othx[kAqMols], othy[kAqMols];     // and the high-word image thresholds
+  uint32_t qe[kAqCap];                       // partner index | owner << 27
+  double rx[kAqCap], ry[kAqCap], rz[kAqCap]; // pair force on the owner
+};
+
+// one queued FP64 pair term (slot u): the force on the owner kept in shared memory, the reaction
+// sent to a vapour partner; returns whether the pair lies within the cutoff
+__device__ __forceinline__ bool queued_term(const Arrays& a, const PotDev& p, AtomicQueue& S, int u,
+                                            uint32_t q, const dvec4& xj, int N) {
+  const int j = (int)(q & kIndexMask), m = (int)(q >> 27);
+  const bool wall = j >= N;
+  const double dx = image_hi(S.ox[m] - xj.x, S.oLx[m], S.othx[m]);
+  const double dy = image_hi(S.oy[m] - xj.y, S.oLy[m], S.othy[m]);
+  const double dz = S.oz[m] - xj.z;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
+  const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+  const double inv2 = rcp_nr(r2);
+  const double inv6 = inv2 * inv2 * inv2;
+  const double fr = in ? inv2 * inv6 * fma(a12, inv6, -b6) : 0.0;
+  const double px = fr * dx, py = fr * dy, pz = fr * dz;
+  S.rx[u] = px;
+  S.ry[u] = py;
+  S.rz[u] = pz;
+  if (in && !wall) {  // Newton's third law: the partner receives -p
+    atomicAdd(&a.frc[j].x, neg_bits(px));
+    atomicAdd(&a.frc[j].y, neg_bits(py));
+    atomicAdd(&a.frc[j].z, neg_bits(pz));
+  }
+  return in;
+}
+
+__device__ __forceinline__ dvec4 queued_partner(const Arrays& a, uint32_t q, int N) {
+  const int j = (int)(q & kIndexMask);
+  return j >= N ? a.wpos[j - N] : a.pos[j];
+}
+
+__global__ void __launch_bounds__(256) k_forces_atomic_packed(Arrays a, PotDev p, int lpt,
+                                                              int owe_kick) {
+  extern __shared__ __align__(32) unsigned char aq_smem[];
+  AtomicQueue& S = reinterpret_cast<AtomicQueue*>(aq_smem)[threadIdx.x >> 5];
+  count_launch(a);
+  clear_rebuild_flags(a);
+  if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (kAqLanes - 1), mol = lane / kAqLanes;
+  int cnt = 0;
+  for (int chunk = next_chunk<kAqMols>(a); chunk >= 0; chunk = next_chunk<kAqMols>(a)) {
+    const int t = chunk * kAqMols + mol;
+    const bool live = t < N;
+    int i = 0, n = 0;
+    float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+    float lcx = 0.f, lcy = 0.f, lcz = 0.f;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      n = a.n_front[i];
+      li = a.lpos[i];
+      const RepDev& R = a.reps[a.rep[i]];
+      if (sub == 0) {
+        const dvec4 xi = a.pos[i];
+        S.ox[mol] = xi.x;
+        S.oy[mol] = xi.y;
+        S.oz[mol] = xi.z;
+        S.oLx[mol] = R.Lx;
+        S.oLy[mol] = R.Ly;
+        S.othx[mol] = R.hi_thr_x;
+        S.othy[mol] = R.hi_thr_y;
+      }
+      lcx = R.lcxf;
+      lcy = R.lcyf;
+      lcz = R.lczf;
+    }
+    const int nmax = __reduce_max_sync(kFull, n);
+    const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    int Q = 0, nseg = 0;
+    uint32_t seg[kAqSeg];  // the lane's queued runs: first entry | count << 16
+#pragma unroll
+    for (int g = 0; g < kAqSeg; ++g) seg[g] = 0u;
+    for (int t0 = 0; t0 < nmax; t0 += kAqLanes * kAqSub) {
+      // FP32 screen of the lane's slots t0 + k * kAqLanes + sub (entries, then partner offsets)
+      uint32_t e[kAqSub];
+#pragma unroll
+      for (int k = 0; k < kAqSub; ++k) {
+        const int sl = t0 + k * kAqLanes + sub;
+        e[k] = sl < n ? row[sl] : 0u;
+      }
+      float4 b[kAqSub];
+#pragma unroll
+      for (int k = 0; k < kAqSub; ++k)
+        b[k] = t0 + k * kAqLanes + sub < n ? partner_lpos(a, e[k], N) : li;
+      unsigned hm = 0;
+#pragma unroll
+      for (int k = 0; k < kAqSub; ++k) {
+        const bool wall = (int)(e[k] & kIndexMask) >= N;
+        const float dx = (li.x - b[k].x) - cell_shift((e[k] >> 26) & 3u, lcx);
+        const float dy = (li.y - b[k].y) - cell_shift((e[k] >> 28) & 3u, lcy);
+        const float dz = (li.z - b[k].z) - cell_shift(e[k] >> 30, lcz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (t0 + k * kAqLanes + sub < n && r2 < (wall ? p.rcw2f_hi : p.rc2f_hi)) hm |= 1u << k;
+      }
+      // append: the lane's survivors go to [Q + excl, Q + excl + c), in slot order
+      const int c = __popc(hm);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      int w = Q + incl - c;
+#pragma unroll
+      for (int g = 0; g < kAqSeg; ++g)
+        if (g == nseg) seg[g] = (uint32_t)w | ((uint32_t)c << 16);
+#pragma unroll
+      for (int k = 0; k < kAqSub; ++k)
+        if ((hm >> k) & 1u) S.qe[w++] = (e[k] & kIndexMask) | ((uint32_t)mol << 27);
+      Q += total;
+      ++nseg;
+      if (Q <= kAqCap - 32 * kAqSub && nseg < kAqSeg && t0 + kAqLanes * kAqSub < nmax) continue;
+      __syncwarp();
+      // FP64 pair terms over the queue, two entries per lane while at least 33 remain
+      int u0 = 0;
+      for (; u0 + 32 < Q; u0 += 64) {
+        const int u1 = u0 + lane, u2 = u0 + 32 + lane;
+        const bool v2 = u2 < Q;
+        const uint32_t q1 = S.qe[u1], q2 = v2 ? S.qe[u2] : q1;
+        const dvec4 x1 = queued_partner(a, q1, N);
+        const dvec4 x2 = queued_partner(a, q2, N);
+        cnt += queued_term(a, p, S, u1, q1, x1, N) ? 1 : 0;
+        if (v2) cnt += queued_term(a, p, S, u2, q2, x2, N) ? 1 : 0;
+      }
+      if (u0 < Q && u0 + lane < Q) {
+        const int u1 = u0 + lane;
+        const uint32_t q1 = S.qe[u1];
+        cnt += queued_term(a, p, S, u1, q1, queued_partner(a, q1, N), N) ? 1 : 0;
+      }
+      __syncwarp();
+      // the entries this lane queued, in slot order
+#pragma unroll
+      for (int g = 0; g < kAqSeg; ++g) {
+        if (g < nseg) {
+          const int u_end = (int)(seg[g] & 0xffffu) + (int)(seg[g] >> 16);
+          for (int u = (int)(seg[g] & 0xffffu); u < u_end; ++u) {
+            fx += S.rx[u];
+            fy += S.ry[u];
+            fz += S.rz[u];
+          }
+        }
+      }
+      __syncwarp();
+      Q = 0;
+      nseg = 0;
+    }
+    fx = group_sum<kAqLanes>(fx);
+    fy = group_sum<kAqLanes>(fy);
+    fz = group_sum<kAqLanes>(fz);
+    if (live && sub == 0 && n > 0) {
+      atomicAdd(&a.frc[i].x, fx);
+      atomicAdd(&a.frc[i].y, fy);
+      atomicAdd(&a.frc[i].z, fz);
+    }
+    __syncwarp();
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
 // The owed second half-kick (Fig. 3), v(t+dt) = v(t+dt/2) + a(t+dt) dt/2, when the FP64 atomic form
 // deferred it: applied before the thermostat, the observables or a state read. Every block reads
 // the flag before its first thread reports in; the last block to report clears it.
@@ -1227,9 +1449,9 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
           const int j = (int)(e[s] & kIndexMask);
           const bool wall = j >= N;
           const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
-          const float dx = (li.x - b.x) - (float)((int)((e[s] >> 26) & 3u) - 1) * lcx;
-          const float dy = (li.y - b.y) - (float)((int)((e[s] >> 28) & 3u) - 1) * lcy;
-          const float dz = (li.z - b.z) - (float)((int)(e[s] >> 30) - 1) * lcz;
+          const float dx = (li.x - b.x) - cell_shift((e[s] >> 26) & 3u, lcx);
+          const float dy = (li.y - b.y) - cell_shift((e[s] >> 28) & 3u, lcy);
+          const float dz = (li.z - b.z) - cell_shift(e[s] >> 30, lcz);
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < (wall ? p.rcw2f_hi : p.rc2f_hi)) hm |= 1u << s;
           else if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(0.0, 0.0, 0.0, 0.0);
@@ -1461,9 +1683,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
         const int j = (int)(e & kIndexMask);
         const bool wall = j >= N;
-        const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
-        const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
-        const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
+        const float dx = (li.x - b.x) - cell_shift((e >> 26) & 3u, R.lcxf);
+        const float dy = (li.y - b.y) - cell_shift((e >> 28) & 3u, R.lcyf);
+        const float dz = (li.z - b.z) - cell_shift(e >> 30, R.lczf);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
         bool in = r2 < lo;
@@ -1513,9 +1735,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         b = bn;
       }
     }
-    double fx = group_sum<TPP>((double)sx + (double)cx);
-    double fy = group_sum<TPP>((double)sy + (double)cy);
-    double fz = group_sum<TPP>((double)sz + (double)cz);
+    double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (STATS) {
       pe = group_sum<TPP>(pe);
       pew = group_sum<TPP>(pew);
@@ -1597,9 +1819,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
         const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
         const int j = (int)(e & kIndexMask);
         const bool wall = j >= N;
-        const float dx = (li.x - b.x) - (float)((int)((e >> 26) & 3u) - 1) * R.lcxf;
-        const float dy = (li.y - b.y) - (float)((int)((e >> 28) & 3u) - 1) * R.lcyf;
-        const float dz = (li.z - b.z) - (float)((int)(e >> 30) - 1) * R.lczf;
+        const float dx = (li.x - b.x) - cell_shift((e >> 26) & 3u, R.lcxf);
+        const float dy = (li.y - b.y) - cell_shift((e >> 28) & 3u, R.lcyf);
+        const float dz = (li.z - b.z) - cell_shift(e >> 30, R.lczf);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
         bool in = r2 < lo;
@@ -1620,9 +1842,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
           two_sum_acc(sy, cy, py);
           two_sum_acc(sz, cz, pz);
           if (q < nvh) {  // Newton's third law: the partner receives -p
-            atomicAdd(&a.frc[j].x, -(double)px);
-            atomicAdd(&a.frc[j].y, -(double)py);
-            atomicAdd(&a.frc[j].z, -(double)pz);
+            atomicAdd(&a.frc[j].x, widen_f32(-px));
+            atomicAdd(&a.frc[j].y, widen_f32(-py));
+            atomicAdd(&a.frc[j].z, widen_f32(-pz));
           }
           ++cnt;
         }
@@ -1630,9 +1852,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
         b = bn;
       }
     }
-    const double fx = group_sum<TPP>((double)sx + (double)cx);
-    const double fy = group_sum<TPP>((double)sy + (double)cy);
-    const double fz = group_sum<TPP>((double)sz + (double)cz);
+    const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (live && sub == 0) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
@@ -1851,12 +2073,18 @@ template <int TPP>
 void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cudaStream_t s) {
   const int b = t.force_block;
   const int per_sm = t.force_blocks_per_sm_fp64;
-  if (t.atomic_acc && TPP != 32) {
+  if (t.atomic_acc) {
     // forces start from zero: k_integrate_first clears them on the way through a step
     if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
     // in a step the second half-kick is deferred into the next first half-kick
-    k_forces_half_atomic<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0, s>>>(
-        a, p, t.lpt, kick ? 1 : 0);
+    if constexpr (TPP == 32) {
+      const size_t sm = (size_t)(b / 32) * sizeof(AtomicQueue);
+      k_forces_atomic_packed<<<pair_grid((long long)a.n_total * kAqLanes, b, per_sm, t), b, sm,
+                               s>>>(a, p, t.lpt, kick ? 1 : 0);
+    } else {
+      k_forces_half_atomic<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0,
+                                  s>>>(a, p, t.lpt, kick ? 1 : 0);
+    }
     return;
   }
   if constexpr (TPP == 32) {
@@ -1937,9 +2165,15 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
   }
   const int tpp = mixed ? t.tpp_mixed : t.tpp_fp64;
   if (!mixed && tpp == 32) {
-    const size_t sm = (size_t)(t.force_block / 32) * sizeof(PackWarp);
-    k_forces_half_packed<<<pair_grid(a.n_total, t.force_block, t.force_blocks_per_sm_fp64, t),
-                           t.force_block, sm, s>>>(a, p, t.lpt);
+    const int g = pair_grid((long long)a.n_total * (t.atomic_acc ? kAqLanes : 1), t.force_block,
+                            t.force_blocks_per_sm_fp64, t);
+    if (t.atomic_acc) {
+      const size_t sm = (size_t)(t.force_block / 32) * sizeof(AtomicQueue);
+      k_forces_atomic_packed<<<g, t.force_block, sm, s>>>(a, p, t.lpt, 0);
+    } else {
+      const size_t sm = (size_t)(t.force_block / 32) * sizeof(PackWarp);
+      k_forces_half_packed<<<g, t.force_block, sm, s>>>(a, p, t.lpt);
+    }
     return;
   }
   switch (tpp) {
@@ -1997,8 +2231,11 @@ void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, 
 
 // one-time kernel attributes (before any launch or capture)
 cudaError_t configure_kernels() {
-  return cudaFuncSetAttribute(k_forces_half_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(8 * sizeof(PackWarp)));
+  const cudaError_t e = cudaFuncSetAttribute(
+      k_forces_half_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sizeof(PackWarp)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_forces_atomic_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(8 * sizeof(AtomicQueue)));
 }
 
 void launch_settle_kick(const Arrays& a, const PotDev& p, cudaStream_t s) {

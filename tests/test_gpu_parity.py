@@ -142,7 +142,7 @@ def shapes_after_ten(shapes):
 @pytest.mark.parametrize("tpp,block,lpt,acc", [
     (1, 128, 1, 1), (2, 256, 1, 1), (4, 128, 2, 1), (8, 256, 1, 1), (32, 128, 1, 1),
     (32, 256, 1, 1), (32, 128, 2, 1), (1, 256, 1, 2), (2, 128, 1, 2), (4, 256, 2, 2),
-    (8, 128, 1, 2)])
+    (8, 128, 1, 2), (32, 256, 1, 2), (32, 128, 2, 2)])
 def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, lpt, acc):
     """Every pair-kernel variant (lanes per molecule, the packed kernel, block size, processing
     order, deterministic or atomic accumulation) gives the oracle's forces and 10-step
@@ -177,8 +177,28 @@ def test_atomic_accumulation_agrees_with_deterministic_to_rounding(shapes):
             xb, vb = b.state(r)
             assert np.abs(wrapped_diff(xa, xb, s)).max() <= 1e-10
             assert np.abs(va - vb).max() <= 1e-10
-        with pytest.raises(md.MDError):
-            b.set_tuning(force_tpp=32)
+
+
+@pytest.mark.parametrize("tpp", [2, 32])
+def test_atomic_forms_agree_with_deterministic_on_a_filled_pore(tpp):
+    """A liquid-filled pore (rows of 60-100 entries, the compacted kernel's queue flushing several
+    times per warp): the atomic forms give the deterministic form's forces to rounding and keep the
+    trajectory to round-off growth over 30 steps, with the same pair counts at the end."""
+    s = W.drying_cylinder_pore()
+    with md.Simulation(s) as a, md.Simulation(s) as b:
+        b.set_tuning(force_accumulate=2, force_tpp=tpp)
+        assert force_err(b.forces(), a.forces()) <= 1e-13
+        g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+        assert force_err(b.forces(), g) <= FORCE_TOL
+        a.step(30)
+        b.step(30)
+        xa, va = a.state()
+        xb, vb = b.state()
+        assert np.abs(wrapped_diff(xa, xb, s)).max() <= 1e-9
+        assert np.abs(va - vb).max() <= 1e-9
+        oa, *_ = a.observables()
+        ob, *_ = b.observables()
+        assert oa["pairs_vv"] == ob["pairs_vv"] and oa["pairs_vw"] == ob["pairs_vw"]
 
 
 @pytest.mark.parametrize("tpp", [1, 2, 4, 8])
