@@ -616,7 +616,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.any_scale, 1);
   ALLOC(A.step, 1);
   ALLOC(A.force_rebuild, 1);
-  ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1);
+  ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1); ALLOC(A.chain_done, 1);
   ALLOC(A.rep_disp2, (size_t)n_reps);
   ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.n_act, 1);
   ALLOC(A.status, 1);

@@ -6,20 +6,23 @@
 //                       the thermostat acts (CUDA-graph conditional nodes)
 //   rebuild chain       only when a molecule moved >= skin/2 since its replica's last build, and
 //                       only for the replicas near their limit:
-//                         k_cell_clear -> k_cell_count -> k_scan_* -> k_scatter -> k_permute ->
-//                         k_copyback -> k_list_build (warp per cell) -> k_order_hist ->
-//                         k_order_scan -> k_order_assign [-> k_fwd_build]
+//                         k_cell_clear -> k_cell_count (+ the cell scan, or k_scan_*) ->
+//                         k_scatter -> k_permute ->
+//                         k_list_build (warp per cell; list-length counts, whose scan its last
+//                         block does) -> k_order_assign [-> k_fwd_build]
 //   pair forces         Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) and the second half-kick
 //                       (Fig. 3), in one of:
 //                         FP64 half list + slot-and-gather, the kick fused into the gather;
-//                         FP64 half list with atomic reaction forces;
+//                         FP64 half list with atomic reaction forces (lanes per molecule, or
+//                         the compacted form: FP32 screen, per-warp queue of FP64 pair terms);
 //                         mixed precision, full list, the kick fused in;
 //                         mixed precision, half list with atomic reaction forces.
 //                       The atomic forms defer the kick into the next first half-kick
 //                       (k_kick_pending settles it before the thermostat or any velocity read).
 //   k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on
 //                       thermostat steps (Fig. 4)
-// No kernel spins or waits on another block.
+// No kernel spins or waits on another block: where one block finishes a launch's work (the
+// last-block pattern), it is the one whose report comes in last.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -417,21 +420,115 @@ __global__ void k_cell_clear(Arrays a, PotDev p) {
   if (c < a.n_cells && rep_rebuilds(a, a.cell_rep[c])) a.vcount[c] = 0;
 }
 
-__global__ void k_cell_count(Arrays a, PotDev p) {
+// the whole cell scan by one block (at most 16 x 4096 cells): each thread owns a contiguous
+// segment of whole int4s, sums it, takes its exclusive offset from a block scan of the sums and
+// writes its segment; every load is issued up front, one round trip to memory per pass
+__device__ void cell_scan_block(const Arrays& a) {
+  __shared__ int warp_tot[32];
+  const int n = a.n_cells, t = threadIdx.x, nthr = blockDim.x;
+  const int S = (((n + nthr - 1) / nthr) + 3) & ~3;
+  const int b0 = min(t * S, n), b1 = min(b0 + S, n);
+  const int* __restrict__ in = a.vcount;
+  int sum = 0;
+  for (int k = b0; k < b1; k += 4) {
+    if (k + 3 < b1) {
+      const int4 v = *reinterpret_cast<const int4*>(in + k);
+      sum += v.x + v.y + v.z + v.w;
+    } else {
+      for (int u = k; u < b1; ++u) sum += in[u];
+    }
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    const int w = t < (nthr >> 5) ? warp_tot[t] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, wi, o);
+      if (t >= o) wi += y;
+    }
+    if (t < (nthr >> 5)) warp_tot[t] = wi - w;
+  }
+  __syncthreads();
+  int run = warp_tot[t >> 5] + incl - sum;
+  for (int k = b0; k < b1; k += 4) {
+    if (k + 3 < b1) {
+      const int4 v = *reinterpret_cast<const int4*>(in + k);
+      int4 o;
+      o.x = run;
+      o.y = o.x + v.x;
+      o.z = o.y + v.y;
+      o.w = o.z + v.z;
+      run = o.w + v.w;
+      *reinterpret_cast<int4*>(a.vstart + k) = o;
+    } else {
+      for (int u = k; u < b1; ++u) {
+        a.vstart[u] = run;
+        run += in[u];
+      }
+    }
+  }
+  if (t == 0) a.vstart[n] = a.n_total;
+}
+
+// Each molecule of a rebuilding replica takes its cell and a slot in it, and stages its record in
+// the alternate arrays (same index), from which k_permute writes it to its sorted place. A cell's
+// first molecule lists it among the active cells; the list grows by one atomic per warp (a single
+// shared counter would otherwise see one atomic per occupied cell).
+__global__ void k_cell_count(Arrays a, PotDev p, int scan) {
   count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
+  if (!need_rebuild(a, p)) return;  // (the flag holds still while the chain runs)
+  __shared__ int s_run, s_last;
+  // with `scan`, every block reports in at the end and the last one scans the cell counts, so a
+  // block that finds an error flag raised skips its work but not its report
+  if (threadIdx.x == 0) s_run = !halted(a);
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
-  const RepDev& R = a.reps[a.rep[i]];
-  const dvec4 x = a.pos[i];
-  const int ix = cell_coord(x.x, R.hx, R.lcx, R.ncx);
-  const int iy = cell_coord(x.y, R.hy, R.lcy, R.ncy);
-  const int iz = cell_coord(x.z, R.hz, R.lcz, R.ncz);
-  const int c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
-  a.cell_tmp[i] = c;
-  const int slot = atomicAdd(&a.vcount[c], 1);
-  a.slot_tmp[i] = slot;
-  if (slot == 0) a.act_cells[atomicAdd(a.n_act, 1)] = c;  // the cell's first molecule lists it
+  const bool own = s_run && i < a.n_total && rep_rebuilds(a, a.rep[i]);
+  int c = 0;
+  bool first = false;
+  if (own) {
+    const RepDev& R = a.reps[a.rep[i]];
+    const dvec4 x = a.pos[i];
+    const int ix = cell_coord(x.x, R.hx, R.lcx, R.ncx);
+    const int iy = cell_coord(x.y, R.hy, R.lcy, R.ncy);
+    const int iz = cell_coord(x.z, R.hz, R.lcz, R.ncz);
+    c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
+    a.cell_tmp[i] = c;
+    const int slot = atomicAdd(&a.vcount[c], 1);
+    a.slot_tmp[i] = slot;
+    first = slot == 0;
+    a.pos_alt[i] = x;
+    a.vel_alt[i] = a.vel[i];
+    a.frc_alt[i] = a.frc[i];
+    a.id_alt[i] = a.id[i];
+  }
+  const unsigned fm = __ballot_sync(kFull, first);
+  if (fm) {
+    const int lane = threadIdx.x & 31, leader = __ffs(fm) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(a.n_act, __popc(fm));
+    base = __shfl_sync(kFull, base, leader);
+    if (first) a.act_cells[base + __popc(fm & ((1u << lane) - 1u))] = c;
+  }
+  if (!scan) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.chain_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  cell_scan_block(a);
+  if (threadIdx.x == 0) *a.chain_done = 0u;
 }
 
 // exclusive scan of a 4096-element tile by 1024 threads; returns the tile total
@@ -504,66 +601,6 @@ __global__ void __launch_bounds__(1024) k_scan_add(Arrays a, PotDev p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
 }
 
-// the whole cell scan in one block (at most 16 x 4096 cells): each thread owns a contiguous
-// segment of whole int4s, sums it, takes its exclusive offset from a block scan of the sums and
-// writes its segment; every load is issued up front, one round trip to memory per pass
-__global__ void __launch_bounds__(1024) k_scan_single(Arrays a, PotDev p) {
-  count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
-  __shared__ int warp_tot[32];
-  const int n = a.n_cells, t = threadIdx.x;
-  const int S = (((n + 1023) >> 10) + 3) & ~3;
-  const int b0 = min(t * S, n), b1 = min(b0 + S, n);
-  const int* __restrict__ in = a.vcount;
-  int sum = 0;
-  for (int k = b0; k < b1; k += 4) {
-    if (k + 3 < b1) {
-      const int4 v = *reinterpret_cast<const int4*>(in + k);
-      sum += v.x + v.y + v.z + v.w;
-    } else {
-      for (int u = k; u < b1; ++u) sum += in[u];
-    }
-  }
-  int incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, incl, o);
-    if ((t & 31) >= o) incl += y;
-  }
-  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
-  __syncthreads();
-  if (t < 32) {
-    const int w = warp_tot[t];
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, wi, o);
-      if (t >= o) wi += y;
-    }
-    warp_tot[t] = wi - w;
-  }
-  __syncthreads();
-  int run = warp_tot[t >> 5] + incl - sum;
-  for (int k = b0; k < b1; k += 4) {
-    if (k + 3 < b1) {
-      const int4 v = *reinterpret_cast<const int4*>(in + k);
-      int4 o;
-      o.x = run;
-      o.y = o.x + v.x;
-      o.z = o.y + v.y;
-      o.w = o.z + v.z;
-      run = o.w + v.w;
-      *reinterpret_cast<int4*>(a.vstart + k) = o;
-    } else {
-      for (int u = k; u < b1; ++u) {
-        a.vstart[u] = run;
-        run += in[u];
-      }
-    }
-  }
-  if (t == 0) a.vstart[n] = a.n_total;
-}
-
 __global__ void k_scatter(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
@@ -573,7 +610,8 @@ __global__ void k_scatter(Arrays a, PotDev p) {
 }
 
 // within a cell, molecules are ordered by their caller index: the sorted order depends only on
-// the positions, not on the order in which atomics were served
+// the positions, not on the order in which atomics were served. Records move from the staged copy
+// (k_cell_count) to their sorted place.
 __global__ void k_permute(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
@@ -581,16 +619,16 @@ __global__ void k_permute(Arrays a, PotDev p) {
   if (s >= a.n_total || !rep_rebuilds(a, a.rep[s])) return;  // replicas occupy fixed ranges
   const int src = a.perm_tmp[s];
   const int c = a.cell_tmp[src];
-  const int my_id = a.id[src];
+  const int my_id = a.id_alt[src];
   const int b = a.vstart[c], e = a.vstart[c + 1];
   int rank = 0;
-  for (int t = b; t < e; ++t) rank += a.id[a.perm_tmp[t]] < my_id;
+  for (int t = b; t < e; ++t) rank += a.id_alt[a.perm_tmp[t]] < my_id;
   const int dst = b + rank;
-  const dvec4 x = a.pos[src];
-  a.pos_alt[dst] = x;
-  a.vel_alt[dst] = a.vel[src];
-  a.frc_alt[dst] = a.frc[src];
-  a.id_alt[dst] = my_id;
+  const dvec4 x = a.pos_alt[src];
+  a.pos[dst] = x;
+  a.vel[dst] = a.vel_alt[src];
+  a.frc[dst] = a.frc_alt[src];
+  a.id[dst] = my_id;
   const RepDev& R = a.reps[a.rep[src]];
   const int local = c - R.cell_off;
   const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
@@ -598,17 +636,6 @@ __global__ void k_permute(Arrays a, PotDev p) {
   a.home[dst] = home;
   a.pos_ref[dst] = x;
   a.lpos[dst] = local_offset(a, R, x, home);
-}
-
-__global__ void k_copyback(Arrays a, PotDev p) {
-  count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
-  a.pos[i] = a.pos_alt[i];
-  a.vel[i] = a.vel_alt[i];
-  a.frc[i] = a.frc_alt[i];
-  a.id[i] = a.id_alt[i];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -630,20 +657,75 @@ __device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
   if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.hist[h], __popc(grp));
 }
 
+// Processing order (optional). Molecules sorted by the length of the list the pair kernel walks
+// (FP64: the front; mixed: front + back), longest first: warps see uniform lengths and the heaviest
+// chunks start first. Whatever the order, each molecule's force is a sum it owns, so the order
+// changes no result. The list build counts the lengths; its last block turns the counts into the
+// start of each length, longest first (and clears them); k_order_assign places the molecules.
+__device__ __forceinline__ int order_length(const Arrays& a, const PotDev& p, int i, int half) {
+  return min(half ? a.n_front[i] : a.n_front[i] + a.n_back[i], p.cap);
+}
+
+// exclusive scan of the length histogram in descending order of length, by one whole block
+__device__ void order_scan_block(const Arrays& a, const PotDev& p) {
+  __shared__ int warp_tot[32];
+  const int t = threadIdx.x, nthr = blockDim.x;
+  const int per = (p.cap + nthr) / nthr;  // lengths cap .. 0 (cap + 1 of them), `per` a thread
+  int sum = 0;
+  for (int k = 0; k < per; ++k) {
+    const int b = p.cap - (t * per + k);
+    if (b >= 0) sum += a.hist[b];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    const int w = t < (nthr >> 5) ? warp_tot[t] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, wi, o);
+      if (t >= o) wi += y;
+    }
+    if (t < (nthr >> 5)) warp_tot[t] = wi - w;
+  }
+  __syncthreads();
+  int run = warp_tot[t >> 5] + incl - sum;
+  for (int k = 0; k < per; ++k) {
+    const int b = p.cap - (t * per + k);
+    if (b >= 0) {
+      const int v = a.hist[b];
+      a.hstart[b] = run;
+      run += v;
+      a.hist[b] = 0;
+    }
+  }
+}
+
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
 constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
 
 __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half,
-                                                                 int front_only) {
+                                                                 int front_only, int order) {
   count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
+  if (!need_rebuild(a, p)) return;  // (the flag holds still while the chain runs)
   __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
   __shared__ float4 sh_li[kListWarps][32];
+  __shared__ int s_run, s_last;
+  // every block reports in at the end (the last one scans the length counts), so a block that
+  // finds an error flag raised skips its work but not its report
+  if (threadIdx.x == 0) s_run = !halted(a);
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
   // a fixed grid; each warp takes the occupied cells of the rebuilding replicas in turn (the rows
   // it writes are its cell's molecules', so the order of the cells changes nothing)
-  const int n_act = *a.n_act;
+  const int n_act = s_run ? *a.n_act : 0;
   for (int ac = blockIdx.x * kListWarps + w; ac < n_act; ac += gridDim.x * kListWarps) {
     const int c = a.act_cells[ac];
     const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
@@ -739,14 +821,16 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
         const int i = ib + lane;
         const bool own = lane < nic;
         const int nf = cf, nb = cb, nvh = vh;
+        const int nfc = min(nf, cap), nbc = min(nb, cap - min(nf, cap));
         if (own) {
           if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
             atomicOr(a.status, kStatusOverflow);
-          a.n_front[i] = min(nf, cap);
-          a.n_back[i] = min(nb, cap - min(nf, cap));
+          a.n_front[i] = nfc;
+          a.n_back[i] = nbc;
           a.n_vh[i] = min(nvh, p.cap_v);
           max_n = max(max_n, nf + nb);
         }
+        if (order) hist_add(a, min(half ? nfc : nfc + nbc, cap), own);
       }
       __syncwarp();
     }
@@ -754,65 +838,36 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
     for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
     if (lane == 0) atomicMax(a.max_nb, max_n);
   }
+  if (!order) return;
+  // the kept rows of the replicas that do not rebuild count too
+  if (s_run) {
+    const int nw = gridDim.x * kListWarps;
+    for (int base = (blockIdx.x * kListWarps + w) * 32; base < a.n_total; base += nw * 32) {
+      const int i = base + lane;
+      const bool own = i < a.n_total && !rep_rebuilds(a, a.rep[i]);
+      hist_add(a, own ? order_length(a, p, i, half) : 0, own);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.chain_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  order_scan_block(a, p);
+  if (threadIdx.x == 0) *a.chain_done = 0u;
 }
 
 // ------------------------------------------------------------------------------------------------
-// Processing order (optional). Molecules sorted by the length of the list the pair kernel walks
-// (FP64: the front; mixed: front + back), longest first: warps see uniform lengths and the heaviest
-// chunks start first. Whatever the order, each molecule's force is a sum it owns, so the order
-// changes no result.
-
-// list-length histogram of every molecule (rebuilt rows and kept ones alike)
-__global__ void k_order_hist(Arrays a, PotDev p, int half) {
-  count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool own = i < a.n_total;
-  const int h = own ? min(half ? a.n_front[i] : a.n_front[i] + a.n_back[i], p.cap) : 0;
-  hist_add(a, h, own);
-}
-
-// start of each list length in descending order of length; clears the histogram
-__global__ void __launch_bounds__(1024) k_order_scan(Arrays a, PotDev p) {
-  count_launch(a);
-  if (halted(a) || !need_rebuild(a, p)) return;
-  __shared__ int warp_tot[32];
-  const int t = threadIdx.x;
-  const int b = p.cap - t;  // thread t handles length b (longest first)
-  const int v = b >= 0 ? a.hist[b] : 0;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, incl, o);
-    if ((t & 31) >= o) incl += y;
-  }
-  if ((t & 31) == 31) warp_tot[t >> 5] = incl;
-  __syncthreads();
-  if (t < 32) {
-    const int w = warp_tot[t];
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, wi, o);
-      if (t >= o) wi += y;
-    }
-    warp_tot[t] = wi - w;
-  }
-  __syncthreads();
-  if (b >= 0) {
-    a.hstart[b] = warp_tot[t >> 5] + incl - v;
-    a.hist[b] = 0;
-  }
-}
-
 // processing position of each molecule (warp-aggregated atomics on the length starts)
 __global__ void k_order_assign(Arrays a, PotDev p, int half) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool own = i < a.n_total;
-  int h = 0;
-  if (own) h = min(half ? a.n_front[i] : a.n_front[i] + a.n_back[i], p.cap);
+  const int h = own ? order_length(a, p, i, half) : 0;
   const unsigned act = __ballot_sync(kFull, own);
   if (!own) return;
   const unsigned grp = __match_any_sync(act, h);
@@ -2011,25 +2066,20 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   // whole row (mixed, deterministic): the processing order sorts by that length
   const int half = (!mixed || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
   k_cell_clear<<<nblocks(a.n_cells, b), b, 0, s>>>(a, p);
-  k_cell_count<<<nt, b, 0, s>>>(a, p);
   if (ntiles <= 16) {
-    k_scan_single<<<1, 1024, 0, s>>>(a, p);
+    k_cell_count<<<nt, b, 0, s>>>(a, p, 1);  // its last block scans the counts
   } else {
+    k_cell_count<<<nt, b, 0, s>>>(a, p, 0);
     k_scan_tiles<<<ntiles, 1024, 0, s>>>(a, p);
     k_scan_top<<<1, 1024, 0, s>>>(a, p, ntiles);
     k_scan_add<<<ntiles, 1024, 0, s>>>(a, p);
   }
   k_scatter<<<nt, b, 0, s>>>(a, p);
   k_permute<<<nt, b, 0, s>>>(a, p);
-  k_copyback<<<nt, b, 0, s>>>(a, p);
   // the atomic forms walk only the front of each row: half rows
   k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
-      a, p, half, t.atomic_acc);
-  if (lpt) {
-    k_order_hist<<<nt, b, 0, s>>>(a, p, half);
-    k_order_scan<<<1, 1024, 0, s>>>(a, p);
-    k_order_assign<<<nt, b, 0, s>>>(a, p, half);
-  }
+      a, p, half, t.atomic_acc, lpt);
+  if (lpt) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   if (!mixed && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
