@@ -48,8 +48,9 @@ FLOPS_PER_PAIR = 21
 # peak of the FP64 CUDA-core pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch of the pair kernels from one ncu capture, valid for the kernel source with
-# this SHA-256 (traffic is reported as null once the source has changed)
+# DRAM bytes (read + write) per launch of a pair kernel on a workload, from one ncu capture
+# (the command is in profiles/), valid for the kernel source whose SHA-256 prefix is recorded:
+# traffic is reported as null for any other workload, kernel or source
 NCU_TRAFFIC = {}
 
 
@@ -67,6 +68,11 @@ def parse():
     ap.add_argument("--roofline-launches", type=int, default=50)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--force-tpp", type=int, default=0,
+                    help="pin the pair kernel's lanes per molecule (32: the packed FP64 kernels) "
+                         "instead of the autotuner's choice")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="with --force-tpp, the pair kernel's resident blocks per SM")
     ap.add_argument("--nve-steps", type=int, default=0,
                     help="with the mixed comparison, also the NVE energy drift of both GPU forms "
                          "over this many steps (after 200 thermostatted ones)")
@@ -311,7 +317,11 @@ def measure_precision(md, systems, precision, args, torch, stream, flush, world=
     sim = md.Simulation(systems, precision=precision, stream=stream)
     sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
     sim.tune_info = None
-    if not args.no_autotune:
+    main = precision == (md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED)
+    if args.force_tpp and main:   # the pin is the headline run's; the comparison run is tuned
+        sim.set_tuning(force_tpp=args.force_tpp, force_blocks_per_sm=args.blocks_per_sm)
+        sim.tune_info = {"tuning": sim.tuning(), "pinned": True}
+    elif not args.no_autotune:
         sim.tune_info = autotune.tune(sim, trials=9, use_cache=False)
     sim.set_tuning(use_graph=1 if args.launch_mode == "graph" else 2, steps_per_graph=1)
     for _ in range(args.warmup):
@@ -357,7 +367,20 @@ def steady_state(sim, torch, stream, flush, steps, nrep, per_replay=10):
             "l2": "flushed between graph replays"}
 
 
-def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate):
+def pair_kernel_name(sim, precision, accumulate):
+    """The kernel md_pair_pass launches under the context's current tuning."""
+    tpp = sim.tuning()["force_tpp"]
+    if precision == "fp64":
+        if sim.tuning()["pair_method"] == 2:
+            return "k_allpairs"
+        if tpp == 32:
+            return "k_forces_atomic_packed" if accumulate == "atomic" else "k_forces_half_packed"
+        return "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
+    return "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
+
+
+def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate,
+             workload):
     evs = []
     nvtx_push(torch, "roofline")
     for _ in range(nlaunch):
@@ -376,11 +399,8 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
     flops = pairs_per_launch * FLOPS_PER_PAIR
     achieved = flops / (ms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
-    if precision == "fp64":
-        kname = "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
-    else:
-        kname = "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
-    tr = NCU_TRAFFIC.get(kname)
+    kname = pair_kernel_name(sim, precision, accumulate)
+    tr = NCU_TRAFFIC.get((workload, kname))
     traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == kernel_sha() else None
     return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -485,7 +505,7 @@ def run_ours(args):
     if rank == 0:
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
-                                     args.precision, args.accumulate)
+                                     args.precision, args.accumulate, args.workload)
         extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step, torch)
         if not args.no_mixed and args.precision == "fp64":
             import oracle
