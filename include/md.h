@@ -120,7 +120,8 @@ typedef struct {
 typedef struct {
   double eps, sigma, mass, rc;        /* vapour-vapour Lennard-Jones (cut at rc, strict r < rc) */
   double eps_w, sigma_w, rc_w;        /* vapour-wall Lennard-Jones */
-  double skin;                        /* Verlet skin: lists hold pairs with r < max(rc, rc_w)+skin */
+  double skin;                        /* Verlet skin: lists hold pairs with
+                                         r < max(rc, rc_w) + skin */
   int32_t shift_energy;               /* 1: energy per pair is U(r) - U(cutoff) */
   int32_t precision;                  /* md_precision: FP64 pair terms, or FP32 pair terms with
                                          compensated accumulation and FP64 integration */
@@ -202,9 +203,9 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
  * force_tpp {1,2,4,8, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
  * x order_by_length {on,off} -- with CUDA events on the context's stream (median of `trials`
- * launches each, trials clamped to [3, 101]), then apply the fastest. Positions and velocities are unchanged; forces are
- * recomputed at the same positions. *best and *best_us (either may be NULL) receive the chosen
- * shape and its median time in microseconds. Synchronises. */
+ * launches each, trials clamped to [3, 101]), then apply the fastest. Positions and velocities
+ * are unchanged; forces are recomputed at the same positions. *best and *best_us (either may be
+ * NULL) receive the chosen shape and its median time in microseconds. Synchronises. */
 md_status md_autotune(md_ctx* ctx, int32_t trials, md_tuning* best, double* best_us);
 
 /* Enqueue n velocity-Verlet steps for every replica (asynchronous). Returns a sticky device

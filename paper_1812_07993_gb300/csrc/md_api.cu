@@ -95,7 +95,8 @@ md_status validate_potential(md_ctx* c, const md_potential* p) {
   if (!p) return fail(c, MD_EINVAL, "potential is NULL");
   if (!(p->eps >= 0 && p->sigma > 0 && p->mass > 0 && p->rc > 0 && p->eps_w >= 0 &&
         p->sigma_w > 0 && p->rc_w > 0 && p->skin >= 0 && p->bin_width > 0))
-    return fail(c, MD_EINVAL, "potential: eps, eps_w >= 0; sigma, mass, rc, rc_w, bin_width > 0; skin >= 0");
+    return fail(c, MD_EINVAL,
+                "potential: eps, eps_w >= 0; sigma, mass, rc, rc_w, bin_width > 0; skin >= 0");
   if (p->r_ads > p->rc_w) return fail(c, MD_EINVAL, "r_ads must not exceed rc_w");
   if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED)
     return fail(c, MD_EINVAL, "unknown precision");
@@ -305,7 +306,8 @@ void destroy_graph(md_ctx* c) {
 // Append an IF node on `handle` to the graph being captured on c->stream and capture `body`
 // (launches on the given stream) into its body graph.
 template <typename Body>
-cudaError_t add_conditional(md_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle handle, Body body) {
+cudaError_t add_conditional(md_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle handle,
+                            Body body) {
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
@@ -357,7 +359,8 @@ md_status build_graph(md_ctx* c, int steps) {
       });
     if (e != cudaSuccess) break;
     launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
-    e = add_conditional(c, g, sc.thermo, [&](cudaStream_t s) { launch_thermostat(c->a, c->pot, s); });
+    e = add_conditional(c, g, sc.thermo,
+                        [&](cudaStream_t s) { launch_thermostat(c->a, c->pot, s); });
   }
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
@@ -518,7 +521,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     return bail(fail(c, MD_EINVAL, "more than 2^26 - 1 molecules plus wall atoms in one context"));
   if (ncell_tot > 4096LL * 4096LL) return bail(fail(c, MD_EINVAL, "too many cells"));
   if (!c->mixed && (unsigned long long)n_tot * (unsigned long long)c->pot.cap_v >= 0xffffffffull)
-    return bail(fail(c, MD_EINVAL, "FP64 pair buffer: molecules * max_neighbors must stay below 2^32"));
+    return bail(fail(c, MD_EINVAL,
+                     "FP64 pair buffer: molecules * max_neighbors must stay below 2^32"));
   c->prof_total = (size_t)prof;
   c->groups_total = (size_t)groups;
   c->pores_total = pores.size();
@@ -632,7 +636,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.prof, (size_t)prof);
   {
     long long chunks = 1;
-    for (int r = 0; r < n_reps; ++r) chunks = std::max<long long>(chunks, (c->rh[r].n_vap + 1023) / 1024);
+    for (int r = 0; r < n_reps; ++r)
+      chunks = std::max<long long>(chunks, (c->rh[r].n_vap + 1023) / 1024);
     A.rep_chunks = (int32_t)chunks;
   }
   ALLOC(A.rep_part, (size_t)n_reps * A.rep_chunks * 8);
@@ -773,7 +778,8 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
 md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   if (!c || !t) return MD_EINVAL;
   t->force_block = c->tun.force_block;
-  t->force_blocks_per_sm = c->mixed ? c->tun.force_blocks_per_sm_mixed : c->tun.force_blocks_per_sm_fp64;
+  t->force_blocks_per_sm =
+      c->mixed ? c->tun.force_blocks_per_sm_mixed : c->tun.force_blocks_per_sm_fp64;
   t->force_tpp = c->mixed ? c->tun.tpp_mixed : c->tun.tpp_fp64;
   t->order_by_length = c->tun.lpt ? 1 : 2;
   t->use_graph = c->use_graph ? 1 : 2;
@@ -1000,16 +1006,20 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   int32_t mv = 0;
   std::vector<unsigned long long> occ(std::max(H.n_pores, 1)), ads(H.n_groups),
       prof((size_t)H.n_groups * H.n_bins);
-  CUDA_TRY(c, cudaMemcpyAsync(sums, A.rep_sums + 8 * r, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(sums, A.rep_sums + 8 * r, 8 * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&nreb, A.n_rebuilds, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&pc, A.pair_count, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&step, A.step, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&mv, A.max_nb, 4, cudaMemcpyDeviceToHost, c->stream));
   if (H.n_pores)
-    CUDA_TRY(c, cudaMemcpyAsync(occ.data(), A.occ + R.pore_off, H.n_pores * 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(ads.data(), A.ads + R.group_off, H.n_groups * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(occ.data(), A.occ + R.pore_off, H.n_pores * 8,
+                                cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(ads.data(), A.ads + R.group_off, H.n_groups * 8,
+                              cudaMemcpyDeviceToHost, c->stream));
   if (!prof.empty())
-    CUDA_TRY(c, cudaMemcpyAsync(prof.data(), A.prof + R.prof_off, prof.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(prof.data(), A.prof + R.prof_off, prof.size() * 8,
+                                cudaMemcpyDeviceToHost, c->stream));
   if (pore_pressure && H.n_pores)
     CUDA_TRY(c, cudaMemcpyAsync(pore_pressure, A.pore_press + R.pore_off, H.n_pores * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));

@@ -120,7 +120,8 @@ struct Arrays {
   double* lambda;                   // per replica
   int32_t* any_scale;
   long long* step;
-  int32_t* force_rebuild;           // set by the host or by a molecule past skin/2; cleared by the pair kernel
+  int32_t* force_rebuild;           // set by the host or by a molecule past skin/2; cleared by the
+                                    // pair kernel
   unsigned long long* rep_disp2;    // per replica: the largest squared displacement since its
                                     // last build among molecules past the grouping threshold (bit
                                     // pattern of a double; 0 below it); all-ones bytes when the
@@ -142,7 +143,8 @@ struct Arrays {
   int32_t *cnt_vv_i, *cnt_vw_i;
   unsigned long long *occ, *ads, *prof;  // per pore, per group, per group*bin
   double* rep_part;                 // per (replica, chunk) partial sums, 8 each
-  double* rep_sums;                 // per replica: ke, pe_vv, pe_vw, vir_vv, vir_vw, pairs_vv, pairs_vw
+  double* rep_sums;                 // per replica: ke, pe_vv, pe_vw, vir_vv, vir_vw, pairs_vv,
+                                    // pairs_vw
   double *pore_part, *pore_press;   // per (replica, chunk, pore) partials; per pore pressure
   int32_t max_pores;                // most pores of any replica (>= 1)
   int32_t n_total, n_wall_total, n_cells, n_reps;
