@@ -51,7 +51,16 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of a pair kernel on a workload, from one ncu capture
 # (the command is in profiles/), valid for the kernel source whose SHA-256 prefix is recorded:
 # traffic is reported as null for any other workload, kernel or source
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("pore_shapes_4x20k", "k_forces_half_atomic<2>"):
+        {"bytes_per_launch": 17651968, "source_sha": "1146aa046aa3efd3"},
+    ("pore_shapes_4x20k", "k_forces_mixed_atomic<4>"):
+        {"bytes_per_launch": 18596608, "source_sha": "1146aa046aa3efd3"},
+    ("drying_pore_6k", "k_forces_half_atomic<2>"):
+        {"bytes_per_launch": 1400832, "source_sha": "1146aa046aa3efd3"},
+    ("drying_pore_6k", "k_forces_atomic_packed"):
+        {"bytes_per_launch": 1605376, "source_sha": "1146aa046aa3efd3"},
+}
 
 
 def parse():
@@ -368,15 +377,18 @@ def steady_state(sim, torch, stream, flush, steps, nrep, per_replay=10):
 
 
 def pair_kernel_name(sim, precision, accumulate):
-    """The kernel md_pair_pass launches under the context's current tuning."""
+    """The kernel md_pair_pass launches under the context's current tuning (with its lanes per
+    molecule as the template argument, as ncu names it)."""
     tpp = sim.tuning()["force_tpp"]
     if precision == "fp64":
         if sim.tuning()["pair_method"] == 2:
             return "k_allpairs"
         if tpp == 32:
             return "k_forces_atomic_packed" if accumulate == "atomic" else "k_forces_half_packed"
-        return "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
-    return "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
+        base = "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
+    else:
+        base = "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
+    return f"{base}<{tpp}>"
 
 
 def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate,

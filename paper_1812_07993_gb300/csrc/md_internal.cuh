@@ -131,7 +131,7 @@ struct Arrays {
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
   unsigned int* kick_done;          // last-block detection in k_kick_pending
-  unsigned int* chain_done;         // last-block detection in k_cell_count and k_list_build
+  unsigned int* chain_done;         // last-block detection in k_list_build
   int32_t* status;
   unsigned int* blk_done;           // last-block detection in k_integrate_first
   unsigned long long* n_rebuilds;

@@ -6,8 +6,7 @@
 //                       the thermostat acts (CUDA-graph conditional nodes)
 //   rebuild chain       only when a molecule moved >= skin/2 since its replica's last build, and
 //                       only for the replicas near their limit:
-//                         k_cell_clear -> k_cell_count (+ the cell scan, or k_scan_*) ->
-//                         k_scatter -> k_permute ->
+//                         k_cell_clear -> k_cell_count -> k_scan_* -> k_scatter -> k_permute ->
 //                         k_list_build (warp per cell; list-length counts, whose scan its last
 //                         block does) -> k_order_assign [-> k_fwd_build]
 //   pair forces         Lennard-Jones forces at r(t+dt) (Eq. 2, Fig. 1) and the second half-kick
@@ -410,17 +409,25 @@ __global__ void k_thermo_scale(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // cell build: a counting sort of the vapour by cell, stable in the caller's molecule index
 
-// cells of the replicas that rebuild start from zero counts (the others keep theirs, so the scan
-// over every cell reproduces their starts)
+// cells of the replicas that rebuild start from zero counts. The occupied ones are exactly the
+// home cells of their molecules at the last build (the rest are zero already), so the clear runs
+// over molecules, not cells. The other replicas keep their counts, so the scan over every cell
+// reproduces their starts.
 __global__ void k_cell_clear(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c == 0) *a.n_act = 0;
-  if (c < a.n_cells && rep_rebuilds(a, a.cell_rep[c])) a.vcount[c] = 0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *a.n_act = 0;
+  if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
+  const RepDev& R = a.reps[a.rep[i]];
+  const int h = a.home[i];
+  const int ix = h & 1023, iy = (h >> 10) & 1023, iz = (h >> 20) & 1023;
+  if (ix < R.ncx && iy < R.ncy && iz < R.ncz)
+    a.vcount[R.cell_off + (iz * R.ncy + iy) * R.ncx + ix] = 0;
 }
 
-// the whole cell scan by one block (at most 16 x 4096 cells): each thread owns a contiguous
+// the whole cell scan by one block (at most 16 x 4096 cells; k_scan_single runs it with 1024
+// threads): each thread owns a contiguous
 // segment of whole int4s, sums it, takes its exclusive offset from a block scan of the sums and
 // writes its segment; every load is issued up front, one round trip to memory per pass
 __device__ void cell_scan_block(const Arrays& a) {
@@ -482,16 +489,11 @@ __device__ void cell_scan_block(const Arrays& a) {
 // the alternate arrays (same index), from which k_permute writes it to its sorted place. A cell's
 // first molecule lists it among the active cells; the list grows by one atomic per warp (a single
 // shared counter would otherwise see one atomic per occupied cell).
-__global__ void k_cell_count(Arrays a, PotDev p, int scan) {
+__global__ void k_cell_count(Arrays a, PotDev p) {
   count_launch(a);
-  if (!need_rebuild(a, p)) return;  // (the flag holds still while the chain runs)
-  __shared__ int s_run, s_last;
-  // with `scan`, every block reports in at the end and the last one scans the cell counts, so a
-  // block that finds an error flag raised skips its work but not its report
-  if (threadIdx.x == 0) s_run = !halted(a);
-  __syncthreads();
+  if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool own = s_run && i < a.n_total && rep_rebuilds(a, a.rep[i]);
+  const bool own = i < a.n_total && rep_rebuilds(a, a.rep[i]);
   int c = 0;
   bool first = false;
   if (own) {
@@ -518,17 +520,6 @@ __global__ void k_cell_count(Arrays a, PotDev p, int scan) {
     base = __shfl_sync(kFull, base, leader);
     if (first) a.act_cells[base + __popc(fm & ((1u << lane) - 1u))] = c;
   }
-  if (!scan) return;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(a.chain_done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  cell_scan_block(a);
-  if (threadIdx.x == 0) *a.chain_done = 0u;
 }
 
 // exclusive scan of a 4096-element tile by 1024 threads; returns the tile total
@@ -599,6 +590,12 @@ __global__ void __launch_bounds__(1024) k_scan_add(Arrays a, PotDev p) {
     if (idx < a.n_cells) a.vstart[idx] += add;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.vstart[a.n_cells] = a.n_total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_single(Arrays a, PotDev p) {
+  count_launch(a);
+  if (halted(a) || !need_rebuild(a, p)) return;
+  cell_scan_block(a);
 }
 
 __global__ void k_scatter(Arrays a, PotDev p) {
@@ -951,6 +948,20 @@ __device__ __forceinline__ double group_min(double v) {
 #pragma unroll
   for (int o = TPP / 2; o; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
   return v;
+}
+
+// sum over the TPP lanes of a molecule of compensated FP32 partial sums s + c: the butterfly
+// stays compensated (TwoSum per stage, fixed order) and only the total is widened to FP64, one
+// FP64 add instead of one per stage
+template <int TPP>
+__device__ __forceinline__ double group_sum_comp(float s, float c) {
+#pragma unroll
+  for (int o = TPP / 2; o; o >>= 1) {
+    const float so = __shfl_xor_sync(kFull, s, o), co = __shfl_xor_sync(kFull, c, o);
+    two_sum_acc(s, c, so);
+    c += co;
+  }
+  return widen_f32(s) + widen_f32(c);
 }
 
 __device__ __forceinline__ void finish_chunks(const Arrays& a) {
@@ -1790,9 +1801,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         b = bn;
       }
     }
-    double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
-    double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
-    double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
+    double fx = group_sum_comp<TPP>(sx, cx);
+    double fy = group_sum_comp<TPP>(sy, cy);
+    double fz = group_sum_comp<TPP>(sz, cz);
     if (STATS) {
       pe = group_sum<TPP>(pe);
       pew = group_sum<TPP>(pew);
@@ -1907,9 +1918,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
         b = bn;
       }
     }
-    const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
-    const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
-    const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
+    const double fx = group_sum_comp<TPP>(sx, cx);
+    const double fy = group_sum_comp<TPP>(sy, cy);
+    const double fz = group_sum_comp<TPP>(sz, cz);
     if (live && sub == 0) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
@@ -2065,11 +2076,11 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   // the pair kernel walks the front of each row (FP64, or mixed with atomic reaction forces) or the
   // whole row (mixed, deterministic): the processing order sorts by that length
   const int half = (!mixed || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
-  k_cell_clear<<<nblocks(a.n_cells, b), b, 0, s>>>(a, p);
+  k_cell_clear<<<nt, b, 0, s>>>(a, p);
+  k_cell_count<<<nt, b, 0, s>>>(a, p);
   if (ntiles <= 16) {
-    k_cell_count<<<nt, b, 0, s>>>(a, p, 1);  // its last block scans the counts
+    k_scan_single<<<1, 1024, 0, s>>>(a, p);
   } else {
-    k_cell_count<<<nt, b, 0, s>>>(a, p, 0);
     k_scan_tiles<<<ntiles, 1024, 0, s>>>(a, p);
     k_scan_top<<<1, 1024, 0, s>>>(a, p, ntiles);
     k_scan_add<<<ntiles, 1024, 0, s>>>(a, p);
