@@ -69,10 +69,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
+                    help="fp64; mixed (FP32 pair terms); df64 (an FP64 context whose pair terms "
+                         "run in double-float on the FP32 pipe; atomic reaction forces only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the comparison runs of the mixed and double-float forms")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--roofline-launches", type=int, default=50)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
@@ -321,12 +324,17 @@ def job_totals(ms: float, pairs: float, world: int):
     return float(m[0]), float(t[0])
 
 
+def prec_enum(md, name):
+    return {"fp64": md.MD_PREC_FP64, "mixed": md.MD_PREC_MIXED, "df64": md.MD_PREC_DF64}[name]
+
+
 def measure_precision(md, systems, precision, args, torch, stream, flush, world=1):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
-    sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
+    atomic = args.accumulate == "atomic" or precision == md.MD_PREC_DF64
+    sim.set_tuning(force_accumulate=2 if atomic else 1)
     sim.tune_info = None
-    main = precision == (md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED)
+    main = precision == prec_enum(md, args.precision)
     if args.force_tpp and main:   # the pin is the headline run's; the comparison run is tuned
         sim.set_tuning(force_tpp=args.force_tpp, force_blocks_per_sm=args.blocks_per_sm)
         sim.tune_info = {"tuning": sim.tuning(), "pinned": True}
@@ -380,6 +388,8 @@ def pair_kernel_name(sim, precision, accumulate):
     """The kernel md_pair_pass launches under the context's current tuning (with its lanes per
     molecule as the template argument, as ncu names it)."""
     tpp = sim.tuning()["force_tpp"]
+    if precision == "df64":
+        return f"k_forces_df_atomic<{tpp}>"
     if precision == "fp64":
         if sim.tuning()["pair_method"] == 2:
             return "k_allpairs"
@@ -497,7 +507,9 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    prec = md.MD_PREC_FP64 if args.precision == "fp64" else md.MD_PREC_MIXED
+    if args.precision == "df64" and args.accumulate != "atomic":
+        raise SystemExit("--precision df64 comes with --accumulate atomic only")
+    prec = prec_enum(md, args.precision)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -549,6 +561,32 @@ def run_ours(args):
                               "fp64_rms_force_err": math.sqrt(sum(e[1] for e in errs) / den),
                               "md_steps_per_s": args.steps / (msm * 1e-3)}
             simm.close()
+            # double-float pair terms: the same workload, steps and timing; force error against
+            # the oracle and against the FP64 GPU form at the run's final state
+            simd, msd, pairsd, _ = measure_precision(md, systems, md.MD_PREC_DF64, args, torch,
+                                                     stream, flush)
+            errs, max_vs64 = [], 0.0
+            with md.Simulation(systems, stream=stream) as sim64:
+                sim64.set_tuning(force_accumulate=2)
+                for r, s in enumerate(systems):
+                    x, v = simd.state(r)
+                    sim64.set_state(r, x, v)
+                    g, _, _ = oracle.forces(oracle.make_params(s, W.Potential()), x, s.wall,
+                                            method=1, nthreads=0)
+                    fd = simd.forces(r)
+                    f64 = sim64.forces(r)
+                    errs.append((((fd - g) ** 2).sum(), (g ** 2).sum()))
+                    rms = math.sqrt(float((f64 ** 2).sum(1).mean()))
+                    max_vs64 = max(max_vs64, float(abs(fd - f64).max()) / rms)
+            vd = pairsd / (msd * 1e-3)
+            extra["df64"] = {"value": vd, "unit": UNIT, "ms_per_step": msd / args.steps,
+                             "speedup_vs_fp64": vd / value,
+                             "rms_force_err": math.sqrt(sum(e[0] for e in errs) /
+                                                        sum(e[1] for e in errs)),
+                             "max_force_err_vs_fp64_over_rms": max_vs64,
+                             "md_steps_per_s": args.steps / (msd * 1e-3),
+                             "tuning": (simd.tune_info or {}).get("tuning")}
+            simd.close()
         if not args.no_cpu_baseline:
             v, st, pr, el, thr = oracle_rate(systems, args.cpu_seconds)
             extra["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -559,7 +597,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": wname, "description": WORKLOADS[wname], "replicas": nrep,
                            "n_vapor": sum(s.n_vapor for s in systems),

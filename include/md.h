@@ -56,7 +56,13 @@ typedef enum {
   MD_ETIMEOUT = 6    /* a bounded device spin wait gave up */
 } md_status;
 
-typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 } md_precision;
+/* MD_PREC_DF64: an FP64 context (positions, integration, cutoff decisions, accumulation, observables)
+ * whose pair terms run in double-float arithmetic -- each value a pair of FP32 numbers hi + lo,
+ * combined by error-free transformations (Dekker; Knuth; Joldes, Muller and Popescu 2017) -- on
+ * FP32 cell-local offsets split the same way: ~2^-44 relative per pair term, against 2^-53 for
+ * FP64, with the work on the FP32 pipe. Atomic reaction forces only (force_accumulate 2); no
+ * force_tpp 32 and no all-pairs method. */
+typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1, MD_PREC_DF64 = 2 } md_precision;
 
 typedef enum {
   MD_PORE_CYLINDER = 1,   /* dx^2 + dy^2 < r0^2 */
@@ -123,8 +129,9 @@ typedef struct {
   double skin;                        /* Verlet skin: lists hold pairs with
                                          r < max(rc, rc_w) + skin */
   int32_t shift_energy;               /* 1: energy per pair is U(r) - U(cutoff) */
-  int32_t precision;                  /* md_precision: FP64 pair terms, or FP32 pair terms with
-                                         compensated accumulation and FP64 integration */
+  int32_t precision;                  /* md_precision: FP64 pair terms, FP32 pair terms with
+                                         compensated accumulation and FP64 integration, or
+                                         double-float pair terms in an FP64 context */
   double r_ads;                       /* adsorbed: nearest wall atom closer than r_ads (<= rc_w) */
   double bin_width;                   /* axial density-profile bin width */
   int32_t max_neighbors;              /* vapour neighbours a molecule may hold (0 = default 160) */

@@ -17,14 +17,14 @@ import numpy as np
 from . import workloads
 
 __all__ = ["Simulation", "MDError", "load_library", "library_path", "md_potential_from",
-           "MD_PREC_FP64", "MD_PREC_MIXED"]
+           "MD_PREC_FP64", "MD_PREC_MIXED", "MD_PREC_DF64"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libmd.so")
 _lib = None
 
 MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = range(7)
-MD_PREC_FP64, MD_PREC_MIXED = 0, 1
+MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_DF64 = 0, 1, 2
 STATUS_NAMES = {0: "MD_OK", 1: "MD_EINVAL", 2: "MD_ENOMEM", 3: "MD_ECUDA", 4: "MD_EOVERFLOW",
                 5: "MD_EUNSTABLE", 6: "MD_ETIMEOUT"}
 

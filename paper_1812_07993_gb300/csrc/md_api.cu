@@ -98,7 +98,8 @@ md_status validate_potential(md_ctx* c, const md_potential* p) {
     return fail(c, MD_EINVAL,
                 "potential: eps, eps_w >= 0; sigma, mass, rc, rc_w, bin_width > 0; skin >= 0");
   if (p->r_ads > p->rc_w) return fail(c, MD_EINVAL, "r_ads must not exceed rc_w");
-  if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED)
+  if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED &&
+      p->precision != MD_PREC_DF64)
     return fail(c, MD_EINVAL, "unknown precision");
   if (p->max_neighbors < 0 || p->max_wall_neighbors < 0)
     return fail(c, MD_EINVAL, "negative list capacity");
@@ -271,6 +272,7 @@ int integrate_flags(const md_ctx* c) {
   int f = 0;
   if (c->tun.atomic_acc) f |= kIntZeroForces;
   if (c->mixed || c->tun.tpp_fp64 == 32) f |= kIntLocalOffsets;
+  if (c->tun.df64) f |= kIntLocalOffsets | kIntLocalOffsetsLo;
   return f;
 }
 
@@ -410,6 +412,14 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   }
   c->n_reps = n_reps;
   c->mixed = pot->precision == MD_PREC_MIXED;
+  if (pot->precision == MD_PREC_DF64) {
+    // an FP64 context whose pair terms run in double-float on the FP32 pipe: atomic reaction
+    // forces, and the launch shape of an FP32-pipe kernel until the autotuner says otherwise
+    c->tun.df64 = 1;
+    c->tun.atomic_acc = 1;
+    c->tun.tpp_fp64 = 4;
+    c->tun.force_blocks_per_sm_fp64 = 4;
+  }
 
   // ---- potential constants
   PotDev& P = c->pot;
@@ -439,6 +449,10 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   P.b6f = (float)P.b6;
   P.a12wf = (float)P.a12w;
   P.b6wf = (float)P.b6w;
+  P.a12l = (float)(P.a12 - (double)P.a12f);
+  P.b6l = (float)(P.b6 - (double)P.b6f);
+  P.a12wl = (float)(P.a12w - (double)P.a12wf);
+  P.b6wl = (float)(P.b6w - (double)P.b6wf);
   P.e12f = (float)P.e12;
   P.e6f = (float)P.e6;
   P.e12wf = (float)P.e12w;
@@ -484,6 +498,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     R.ncz = std::max(1, (int)std::floor(s->Lz / rl));
     R.lcx = s->Lx / R.ncx; R.lcy = s->Ly / R.ncy; R.lcz = s->Lz / R.ncz;
     R.lcxf = (float)R.lcx; R.lcyf = (float)R.lcy; R.lczf = (float)R.lcz;
+    R.lcx_lo = (float)(R.lcx - (double)R.lcxf);
+    R.lcy_lo = (float)(R.lcy - (double)R.lcyf);
+    R.lcz_lo = (float)(R.lcz - (double)R.lczf);
     R.hi_thr_x = hi_word(R.hx);
     R.hi_thr_y = hi_word(R.hy);
     R.bin_width = pot->bin_width;
@@ -531,7 +548,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   std::vector<int> wcell(nw_tot);
   std::vector<int32_t> wstart(ncell_tot + 1, 0);
   std::vector<dvec4> wpos(nw_tot);
-  std::vector<float4> wlpos(nw_tot);
+  std::vector<float4> wlpos(nw_tot), wlpos_lo(nw_tot);
   std::vector<int32_t> cell_rep(ncell_tot);
   {
     long long k = 0;
@@ -562,8 +579,11 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
         const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
         const double cx = -R.hx + (ix + 0.5) * R.lcx, cy = -R.hy + (iy + 0.5) * R.lcy,
                      cz = -R.hz + (iz + 0.5) * R.lcz;
-        wlpos[dst] = make_float4((float)min_img(x - cx, R.Lx), (float)min_img(y - cy, R.Ly),
-                                 (float)(z - cz), 0.f);
+        const double lx = min_img(x - cx, R.Lx), ly = min_img(y - cy, R.Ly), lz = z - cz;
+        wlpos[dst] = make_float4((float)lx, (float)ly, (float)lz, 0.f);
+        wlpos_lo[dst] = make_float4((float)(lx - (double)wlpos[dst].x),
+                                    (float)(ly - (double)wlpos[dst].y),
+                                    (float)(lz - (double)wlpos[dst].z), 0.f);
       }
     }
   }
@@ -586,7 +606,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = dalloc(c, &(ptr), (cnt))) != MD_OK) return bail(st)
   ALLOC(A.pos, N); ALLOC(A.vel, N); ALLOC(A.frc, N); ALLOC(A.pos_ref, N);
   ALLOC(A.pos_alt, N); ALLOC(A.vel_alt, N); ALLOC(A.frc_alt, N);
-  ALLOC(A.lpos, N);
+  ALLOC(A.lpos, N); ALLOC(A.lpos_lo, N);
   ALLOC(c->stage_x, 3 * N); ALLOC(c->stage_v, 3 * N);
   ALLOC(A.home, N); ALLOC(A.id, N); ALLOC(A.rep, N); ALLOC(A.id_alt, N);
   ALLOC(A.cell_tmp, N); ALLOC(A.slot_tmp, N); ALLOC(A.perm_tmp, N);
@@ -600,7 +620,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     ALLOC(A.pairbuf, N * (size_t)P.cap_v + 1);
     ALLOC(A.fpart, N);
   }
-  ALLOC(A.wpos, (size_t)nw_tot); ALLOC(A.wlpos, (size_t)nw_tot);
+  ALLOC(A.wpos, (size_t)nw_tot); ALLOC(A.wlpos, (size_t)nw_tot); ALLOC(A.wlpos_lo, (size_t)nw_tot);
   ALLOC(A.wstart, (size_t)ncell_tot + 1);
   ALLOC(A.vcount, (size_t)ncell_tot); ALLOC(A.vstart, (size_t)ncell_tot + 1);
   ALLOC(A.scan_tiles, 4096);
@@ -681,6 +701,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = up(A.rep, rep.data(), N * sizeof(int32_t))) != MD_OK) return bail(st);
   if ((st = up(A.wpos, wpos.data(), wpos.size() * sizeof(dvec4))) != MD_OK) return bail(st);
   if ((st = up(A.wlpos, wlpos.data(), wlpos.size() * sizeof(float4))) != MD_OK) return bail(st);
+  if ((st = up(A.wlpos_lo, wlpos_lo.data(), wlpos_lo.size() * sizeof(float4))) != MD_OK)
+    return bail(st);
   if ((st = up(A.wstart, wstart.data(), wstart.size() * sizeof(int32_t))) != MD_OK) return bail(st);
   if ((st = up(cell_rep_d, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
     return bail(st);
@@ -741,7 +763,7 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   }
   if (t->force_tpp) {
     if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8 &&
-        !(t->force_tpp == 32 && !c->mixed))
+        !(t->force_tpp == 32 && !c->mixed && !c->tun.df64))
       return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4 or 8 (or 32 at FP64)");
     if (c->mixed) nt.tpp_mixed = t->force_tpp;
     else nt.tpp_fp64 = t->force_tpp;
@@ -755,8 +777,10 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
   if (t->pair_method < 0 || t->pair_method > 2)
     return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists) or 2 (all pairs)");
-  if (c->mixed && t->pair_method == 2)
+  if ((c->mixed || c->tun.df64) && t->pair_method == 2)
     return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
+  if (c->tun.df64 && t->force_accumulate == 1)
+    return fail(c, MD_EINVAL, "double-float pair terms come with atomic reaction forces only");
   if (t->pair_method) nt.all_pairs = t->pair_method == 2 ? 1 : 0;
   const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
@@ -811,7 +835,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
     for (int tp : tpps) {
       // the packed kernels are the FP64 path's
-      if (tp == 32 && c->mixed) continue;
+      if (tp == 32 && (c->mixed || c->tun.df64)) continue;
       for (int bp : bpss)
         for (int bk : blocks) {
           // the all-pairs kernel has a fixed shape: time it once

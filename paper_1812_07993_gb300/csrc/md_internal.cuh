@@ -66,6 +66,7 @@ struct RepDev {
   int32_t ctr_off;                  // this replica's cell centres in cell_ctr: x, then y, then z
   int32_t dims;                     // 3, or 2 for a planar system (temperature with 2N)
   int32_t hard;                     // 1: hard reflecting walls (no wall atoms)
+  float lcx_lo, lcy_lo, lcz_lo;     // cell sides minus their FP32 roundings (double-float form)
 };
 
 struct PoreDev {
@@ -86,6 +87,7 @@ struct PotDev {
   float rc2f, rcw2f, rl2f;          // FP32 cutoffs and the (padded) list radius^2
   float rc2f_lo, rc2f_hi, rcw2f_lo, rcw2f_hi;  // FP32 band around the cutoff decided in FP64
   float a12f, b6f, a12wf, b6wf, e12f, e6f, e12wf, e6wf;
+  float a12l, b6l, a12wl, b6wl;     // force constants minus their FP32 roundings (double-float)
   int32_t cap;                      // list capacity per molecule (vapour + wall)
   int32_t cap_v;                    // vapour half-pair / reverse capacity per molecule
 };
@@ -95,6 +97,7 @@ struct Arrays {
   dvec4 *pos, *vel, *frc, *pos_ref;
   dvec4 *pos_alt, *vel_alt, *frc_alt;
   float4* lpos;
+  float4* lpos_lo;                  // double-float pair terms: lpos's remainder, offset - lpos
   int32_t *home, *id, *rep, *id_alt;
   int32_t *cell_tmp, *slot_tmp, *perm_tmp;
   uint32_t* nbr;                    // [molecule * cap + slot]: front (j > i, walls), back (j < i)
@@ -109,6 +112,7 @@ struct Arrays {
   // wall and cells
   dvec4* wpos;
   float4* wlpos;
+  float4* wlpos_lo;                 // and the wall's
   int32_t* wstart;                  // n_cells + 1
   int32_t *vcount, *vstart;         // n_cells, n_cells + 1
   int32_t* scan_tiles;              // tile sums of the cell scan
@@ -162,6 +166,7 @@ struct Tuning {
   int lpt = 1;                        // process molecules longest list first
   int atomic_acc = 0;                 // FP64: reaction forces by atomic adds (no gather)
   int all_pairs = 0;                  // FP64: every pair each step, no lists (the paper's F1)
+  int df64 = 0;                       // FP64 context, pair terms in double-float (FP32 pairs)
   int sm_count = 152;
 };
 
@@ -201,6 +206,7 @@ struct StepConds {
 // the FP32 cell-local offsets (read by the mixed pair kernel and the packed FP64 kernel's screen)
 constexpr int kIntZeroForces = 1;
 constexpr int kIntLocalOffsets = 2;
+constexpr int kIntLocalOffsetsLo = 4;  // also their double-float remainders
 void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
                             int flags, cudaStream_t s);
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);

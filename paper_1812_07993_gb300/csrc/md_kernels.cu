@@ -15,7 +15,9 @@
 //                         FP64 half list with atomic reaction forces (lanes per molecule, or
 //                         the compacted form: FP32 screen, per-warp queue of FP64 pair terms);
 //                         mixed precision, full list, the kick fused in;
-//                         mixed precision, half list with atomic reaction forces.
+//                         mixed precision, half list with atomic reaction forces;
+//                         FP64 context, double-float pair terms, half list with atomic
+//                         reaction forces.
 //                       The atomic forms defer the kick into the next first half-kick
 //                       (k_kick_pending settles it before the thermostat or any velocity read).
 //   k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on
@@ -84,13 +86,14 @@ __device__ __forceinline__ int pack_home(int ix, int iy, int iz) {
 }
 
 // position relative to the centre of the home cell (centres from the per-replica table), the
-// periodic wrap decided by integer tests; rounded to FP32 for the list test and the mixed terms
-__device__ __forceinline__ float4 local_offset(const Arrays& a, const RepDev& R, const dvec4& x,
-                                               int home) {
+// periodic wrap decided by integer tests, in FP64
+__device__ __forceinline__ void local_offset_d(const Arrays& a, const RepDev& R, const dvec4& x,
+                                               int home, double& lx, double& ly, double& lz) {
   const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
   const double* __restrict__ ctr = a.cell_ctr + R.ctr_off;
-  double lx = x.x - ctr[ix], ly = x.y - ctr[R.ncx + iy];
-  const double lz = x.z - ctr[R.ncx + R.ncy + iz];
+  lx = x.x - ctr[ix];
+  ly = x.y - ctr[R.ncx + iy];
+  lz = x.z - ctr[R.ncx + R.ncy + iz];
   // d >= L/2 and d < -L/2 as bit-pattern tests (-d flips the sign bit); L/2 > 0
   const long long sgn = (long long)0x8000000000000000ull;
   const long long hxb = __double_as_longlong(R.hx), hyb = __double_as_longlong(R.hy);
@@ -98,6 +101,13 @@ __device__ __forceinline__ float4 local_offset(const Arrays& a, const RepDev& R,
   else if ((__double_as_longlong(lx) ^ sgn) > hxb) lx += R.Lx;
   if (__double_as_longlong(ly) >= hyb) ly -= R.Ly;
   else if ((__double_as_longlong(ly) ^ sgn) > hyb) ly += R.Ly;
+}
+
+// the offset rounded to FP32, for the list test and the mixed terms
+__device__ __forceinline__ float4 local_offset(const Arrays& a, const RepDev& R, const dvec4& x,
+                                               int home) {
+  double lx, ly, lz;
+  local_offset_d(a, R, x, home, lx, ly, lz);
   return make_float4((float)lx, (float)ly, (float)lz, 0.f);
 }
 
@@ -163,6 +173,70 @@ __device__ __forceinline__ double widen_f32(float f) {
     lo = mn << 29;
   }
   return __hiloint2double((int)hi, (int)lo);
+}
+
+// the offset as a double-float pair: hi = FP32 rounding (lpos), lo = FP32 rounding of the rest
+__device__ __forceinline__ void local_offset_df(const Arrays& a, const RepDev& R, const dvec4& x,
+                                                int home, float4& hi, float4& lo) {
+  double lx, ly, lz;
+  local_offset_d(a, R, x, home, lx, ly, lz);
+  hi = make_float4((float)lx, (float)ly, (float)lz, 0.f);
+  lo = make_float4((float)(lx - widen_f32(hi.x)), (float)(ly - widen_f32(hi.y)),
+                   (float)(lz - widen_f32(hi.z)), 0.f);
+}
+
+// ---- double-float ("double-word") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, two
+// FP32 numbers carrying ~48 significant bits. The building blocks are the error-free
+// transformations of Dekker (1971) and Knuth (TAOCP vol. 2) -- Fast2Sum, TwoSum, TwoProd through
+// an FMA -- combined as in Joldes, Muller and Popescu, "Tight and rigorous error bounds for basic
+// building blocks of double-word arithmetic" (ACM TOMS 44, 2017); every operation runs on the FP32
+// pipe, which issues 64 times the FP64 rate on this part.
+struct dword {
+  float hi, lo;
+};
+// Fast2Sum (Dekker): a + b = s + e exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ dword fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+// TwoSum (Knuth): a + b = s + e exactly, any order of magnitude
+__device__ __forceinline__ dword two_sum(float a, float b) {
+  const float s = a + b;
+  const float bp = s - a;
+  return {s, (a - (s - bp)) + (b - bp)};
+}
+// TwoProd: a * b = p + e exactly, the error from one FMA
+__device__ __forceinline__ dword two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+// double-word + double-word (the "sloppy" sum: error below 2^-46 (|a| + |b|))
+__device__ __forceinline__ dword dw_add(dword a, dword b) {
+  const dword s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+// double-word * double-word (error below 2^-45 |a b|)
+__device__ __forceinline__ dword dw_mul(dword a, dword b) {
+  dword p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dword dw_sqr(dword a) {
+  dword p = two_prod(a.hi, a.hi);
+  p.lo = fmaf(a.hi + a.hi, a.lo, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+// 1/a for a > 0: the correctly rounded FP32 reciprocal y of a.hi, then one Newton step
+// y + y (1 - a y) with the residual 1 - a y formed from an exact product (error ~2^-46)
+__device__ __forceinline__ dword dw_rcp(dword a) {
+  const float y = __frcp_rn(a.hi);
+  const dword p = two_prod(a.hi, y);           // a.hi y = p.hi + p.lo exactly; p.hi ~ 1
+  const float r = ((1.0f - p.hi) - p.lo) - a.lo * y;
+  return fast_two_sum(y, y * r);
+}
+// the double-word value to FP64: both parts widened exactly, one FP64 add
+__device__ __forceinline__ double dw_to_double(dword a) {
+  return widen_f32(a.hi) + widen_f32(a.lo);
 }
 
 // error-free transformation s + x = t + e (Knuth's TwoSum); the error is collected in c
@@ -304,7 +378,14 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     a.pos[i] = x;
     a.vel[i] = v;
     if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
-    if (flags & kIntLocalOffsets) a.lpos[i] = local_offset(a, R, x, a.home[i]);
+    if (flags & kIntLocalOffsetsLo) {
+      float4 hi, lo;
+      local_offset_df(a, R, x, a.home[i], hi, lo);
+      a.lpos[i] = hi;
+      a.lpos_lo[i] = lo;
+    } else if (flags & kIntLocalOffsets) {
+      a.lpos[i] = local_offset(a, R, x, a.home[i]);
+    }
   }
   // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
   // below the threshold (nearly all steps) issue no atomic at all
@@ -632,7 +713,10 @@ __global__ void k_permute(Arrays a, PotDev p) {
   const int home = pack_home(ix, iy, iz);
   a.home[dst] = home;
   a.pos_ref[dst] = x;
-  a.lpos[dst] = local_offset(a, R, x, home);
+  float4 lhi, llo;
+  local_offset_df(a, R, x, home, lhi, llo);
+  a.lpos[dst] = lhi;
+  a.lpos_lo[dst] = llo;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1932,6 +2016,122 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
   finish_chunks(a);
 }
 
+// double-float remainder of list entry e's partner offset
+__device__ __forceinline__ float4 partner_lpos_lo(const Arrays& a, uint32_t e, int N) {
+  const int j = (int)(e & kIndexMask);
+  return j >= N ? a.wlpos_lo[j - N] : a.lpos_lo[j];
+}
+
+// the displacement (l_i - l_j) - shift as a double word, from the hi + lo parts of both offsets
+// and of the cell shift: the hi differences by TwoSum (exact), the remainders added after
+__device__ __forceinline__ dword dw_disp(float lih, float lil, float bh, float bl, float sh,
+                                         float sl) {
+  const dword t = two_sum(lih, -bh);
+  const dword u = two_sum(t.hi, -sh);
+  return two_sum(u.hi, ((t.lo + u.lo) + (lil - bl)) - sl);
+}
+
+// FP64 context with double-float pair terms (MD_PREC_DF64), half list, reaction forces by
+// atomics. The structure is k_forces_mixed_atomic's: the lanes screen with the FP32 offsets and
+// decide the cutoff near rc in FP64, so the pair set is the FP64 one. Within the cutoff, the
+// displacement (l_i - l_j) - dc*cell, r^2, 1/r^2, the LJ factor of Eq. 2 and the pair force run in
+// double-word arithmetic on the offsets' hi + lo parts (~2^-44 relative, against 2^-53 for FP64;
+// the offsets themselves are exact to ~1e-14, like FP64 positions in the box) -- work for the FP32
+// pipe, not the FP64 one. The molecule's own sum is a compensated FP32 pair; each reaction goes to
+// the partner as an FP64 atomic add of the pair force's double-word value.
+template <int TPP>
+__global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, int lpt,
+                                                          int owe_kick) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
+  clear_rebuild_flags(a);
+  if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
+  int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    int i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const float4 li = a.lpos[i], ll = a.lpos_lo[i];
+      const int n = a.n_front[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      // software-pipelined: the next entry and its partner's offsets load while this pair runs
+      uint32_t e = sub < n ? row[sub] : 0u;
+      float4 b = sub < n ? partner_lpos(a, e, N) : li;
+      float4 bl = sub < n ? partner_lpos_lo(a, e, N) : ll;
+      for (int q = sub; q < n; q += TPP) {
+        const int qn = q + TPP;
+        const uint32_t en = qn < n ? row[qn] : 0u;
+        const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
+        const float4 bln = qn < n ? partner_lpos_lo(a, en, N) : ll;
+        const int j = (int)(e & kIndexMask);
+        const bool wall = j >= N;
+        const uint32_t ox = (e >> 26) & 3u, oy = (e >> 28) & 3u, oz = e >> 30;
+        const float shx = cell_shift(ox, R.lcxf), shy = cell_shift(oy, R.lcyf),
+                    shz = cell_shift(oz, R.lczf);
+        const float dxf = (li.x - b.x) - shx, dyf = (li.y - b.y) - shy, dzf = (li.z - b.z) - shz;
+        const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+        const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
+        bool in = r2f < lo;
+        if (!in && r2f < hi) {  // near rc: the FP64 decision, as the FP64 kernels take it
+          const dvec4 xi = a.pos[i];
+          const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+          const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+          const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+          const double ez = xi.z - xj.z;
+          in = lt_pos(ex * ex + ey * ey + ez * ez, wall ? p.rcw2 : p.rc2);
+        }
+        if (in) {
+          const dword dx = dw_disp(li.x, ll.x, b.x, bl.x, shx, cell_shift(ox, R.lcx_lo));
+          const dword dy = dw_disp(li.y, ll.y, b.y, bl.y, shy, cell_shift(oy, R.lcy_lo));
+          const dword dz = dw_disp(li.z, ll.z, b.z, bl.z, shz, cell_shift(oz, R.lcz_lo));
+          const dword r2 = dw_add(dw_add(dw_sqr(dx), dw_sqr(dy)), dw_sqr(dz));
+          const dword inv2 = dw_rcp(r2);
+          const dword inv4 = dw_sqr(inv2);
+          const dword inv6 = dw_mul(inv4, inv2);
+          const dword inv8 = dw_sqr(inv4);
+          const dword A = wall ? dword{p.a12wf, p.a12wl} : dword{p.a12f, p.a12l};
+          const dword B = wall ? dword{-p.b6wf, -p.b6wl} : dword{-p.b6f, -p.b6l};
+          const dword fr = dw_mul(inv8, dw_add(dw_mul(A, inv6), B));
+          const dword px = dw_mul(fr, dx), py = dw_mul(fr, dy), pz = dw_mul(fr, dz);
+          two_sum_acc(sx, cx, px.hi);
+          two_sum_acc(sy, cy, py.hi);
+          two_sum_acc(sz, cz, pz.hi);
+          cx += px.lo;
+          cy += py.lo;
+          cz += pz.lo;
+          if (!wall) {  // Newton's third law: the partner receives -p
+            atomicAdd(&a.frc[j].x, neg_bits(dw_to_double(px)));
+            atomicAdd(&a.frc[j].y, neg_bits(dw_to_double(py)));
+            atomicAdd(&a.frc[j].z, neg_bits(dw_to_double(pz)));
+          }
+          ++cnt;
+        }
+        e = en;
+        b = bn;
+        bl = bln;
+      }
+    }
+    const double fx = group_sum_comp<TPP>(sx, cx);
+    const double fy = group_sum_comp<TPP>(sy, cy);
+    const double fz = group_sum_comp<TPP>(sz, cz);
+    if (live && sub == 0) {
+      atomicAdd(&a.frc[i].x, fx);
+      atomicAdd(&a.frc[i].y, fy);
+      atomicAdd(&a.frc[i].z, fz);
+    }
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
 // ------------------------------------------------------------------------------------------------
 // observables: pore assignment, occupancy, adsorbed count, axial profile (integer atomics: exact)
 
@@ -2172,6 +2372,17 @@ void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, c
   }
 }
 
+// FP64 context with double-float pair terms (atomic reaction forces only)
+template <int TPP>
+void launch_df(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cudaStream_t s) {
+  const int b = t.force_block;
+  const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
+  // forces start from zero (k_integrate_first clears them in a step); the second half-kick of a
+  // step is deferred into the next first half-kick
+  if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+  k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
+}
+
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s) {
   if (mixed) {
@@ -2195,6 +2406,15 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
     k_stats_fp64<4><<<nblocks((long long)a.n_total * 4, 256), 256, 0, s>>>(a, p, t.atomic_acc);
     return;
   }
+  if (t.df64) {
+    switch (t.tpp_fp64) {
+      case 1: launch_df<1>(a, p, kick, t, s); break;
+      case 2: launch_df<2>(a, p, kick, t, s); break;
+      case 8: launch_df<8>(a, p, kick, t, s); break;
+      default: launch_df<4>(a, p, kick, t, s); break;
+    }
+    return;
+  }
   switch (t.tpp_fp64) {
     case 1: launch_fp64<1>(a, p, kick, t, s); break;
     case 2: launch_fp64<2>(a, p, kick, t, s); break;
@@ -2214,7 +2434,8 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
-  if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  if (t.df64) k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  else if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
   else k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
 }
 
