@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
                     help="fp64; mixed (FP32 pair terms); df64 (an FP64 context whose pair terms "
-                         "run in double-float on the FP32 pipe; atomic reaction forces only)")
+                         "run in double-float on the FP32 pipe)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
@@ -331,8 +331,7 @@ def prec_enum(md, name):
 def measure_precision(md, systems, precision, args, torch, stream, flush, world=1):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, precision=precision, stream=stream)
-    atomic = args.accumulate == "atomic" or precision == md.MD_PREC_DF64
-    sim.set_tuning(force_accumulate=2 if atomic else 1)
+    sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
     sim.tune_info = None
     main = precision == prec_enum(md, args.precision)
     if args.force_tpp and main:   # the pin is the headline run's; the comparison run is tuned
@@ -388,17 +387,16 @@ def pair_kernel_name(sim, precision, accumulate):
     """The kernel md_pair_pass launches under the context's current tuning (with its lanes per
     molecule as the template argument, as ncu names it)."""
     tpp = sim.tuning()["force_tpp"]
+    atomic = accumulate == "atomic"
     if precision == "df64":
-        return f"k_forces_df_atomic<{tpp}>"
+        return f"k_forces_df_atomic<{tpp}>" if atomic else f"k_forces_df<0, {tpp}>"
     if precision == "fp64":
         if sim.tuning()["pair_method"] == 2:
-            return "k_allpairs"
+            return "k_allpairs<0, 0>"
         if tpp == 32:
-            return "k_forces_atomic_packed" if accumulate == "atomic" else "k_forces_half_packed"
-        base = "k_forces_half_atomic" if accumulate == "atomic" else "k_forces_half"
-    else:
-        base = "k_forces_mixed_atomic" if accumulate == "atomic" else "k_forces_mixed"
-    return f"{base}<{tpp}>"
+            return "k_forces_atomic_packed" if atomic else "k_forces_half_packed"
+        return f"k_forces_half_atomic<{tpp}>" if atomic else f"k_forces_half<{tpp}>"
+    return f"k_forces_mixed_atomic<{tpp}>" if atomic else f"k_forces_mixed<0, 0, {tpp}>"
 
 
 def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, accumulate,
@@ -507,8 +505,6 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    if args.precision == "df64" and args.accumulate != "atomic":
-        raise SystemExit("--precision df64 comes with --accumulate atomic only")
     prec = prec_enum(md, args.precision)
 
     clocks = ClockSampler(local)

@@ -60,8 +60,9 @@ typedef enum {
  * whose pair terms run in double-float arithmetic -- each value a pair of FP32 numbers hi + lo,
  * combined by error-free transformations (Dekker; Knuth; Joldes, Muller and Popescu 2017) -- on
  * FP32 cell-local offsets split the same way: ~2^-44 relative per pair term, against 2^-53 for
- * FP64, with the work on the FP32 pipe. Atomic reaction forces only (force_accumulate 2); no
- * force_tpp 32 and no all-pairs method. */
+ * FP64, with the work on the FP32 pipe. force_accumulate 2 (the default here): half list with FP64
+ * atomic reaction forces; 1: full list, each pair from both ends, no atomics, bit-for-bit
+ * reproducible. No force_tpp 32 and no all-pairs method. */
 typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1, MD_PREC_DF64 = 2 } md_precision;
 
 typedef enum {

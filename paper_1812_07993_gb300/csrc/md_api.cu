@@ -414,7 +414,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   c->mixed = pot->precision == MD_PREC_MIXED;
   if (pot->precision == MD_PREC_DF64) {
     // an FP64 context whose pair terms run in double-float on the FP32 pipe: atomic reaction
-    // forces, and the launch shape of an FP32-pipe kernel until the autotuner says otherwise
+    // forces by default, and the launch shape of an FP32-pipe kernel until the autotuner says
+    // otherwise
     c->tun.df64 = 1;
     c->tun.atomic_acc = 1;
     c->tun.tpp_fp64 = 4;
@@ -779,8 +780,6 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists) or 2 (all pairs)");
   if ((c->mixed || c->tun.df64) && t->pair_method == 2)
     return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
-  if (c->tun.df64 && t->force_accumulate == 1)
-    return fail(c, MD_EINVAL, "double-float pair terms come with atomic reaction forces only");
   if (t->pair_method) nt.all_pairs = t->pair_method == 2 ? 1 : 0;
   const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);

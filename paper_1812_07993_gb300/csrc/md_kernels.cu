@@ -16,8 +16,8 @@
 //                         the compacted form: FP32 screen, per-warp queue of FP64 pair terms);
 //                         mixed precision, full list, the kick fused in;
 //                         mixed precision, half list with atomic reaction forces;
-//                         FP64 context, double-float pair terms, half list with atomic
-//                         reaction forces.
+//                         FP64 context, double-float pair terms: full list (the kick fused
+//                         in) or half list with atomic reaction forces.
 //                       The atomic forms defer the kick into the next first half-kick
 //                       (k_kick_pending settles it before the thermostat or any velocity read).
 //   k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on
@@ -2031,14 +2031,61 @@ __device__ __forceinline__ dword dw_disp(float lih, float lil, float bh, float b
   return two_sum(u.hi, ((t.lo + u.lo) + (lil - bl)) - sl);
 }
 
-// FP64 context with double-float pair terms (MD_PREC_DF64), half list, reaction forces by
-// atomics. The structure is k_forces_mixed_atomic's: the lanes screen with the FP32 offsets and
-// decide the cutoff near rc in FP64, so the pair set is the FP64 one. Within the cutoff, the
-// displacement (l_i - l_j) - dc*cell, r^2, 1/r^2, the LJ factor of Eq. 2 and the pair force run in
-// double-word arithmetic on the offsets' hi + lo parts (~2^-44 relative, against 2^-53 for FP64;
-// the offsets themselves are exact to ~1e-14, like FP64 positions in the box) -- work for the FP32
-// pipe, not the FP64 one. The molecule's own sum is a compensated FP32 pair; each reaction goes to
-// the partner as an FP64 atomic add of the pair force's double-word value.
+// One double-float pair term (MD_PREC_DF64): whether list entry e (partner offsets b + bl) lies
+// within the cutoff of molecule i (offsets li + ll) and, if so, the force on i as double words.
+// The lanes screen with the FP32 offsets and decide the cutoff near rc in FP64, so the pair set is
+// the FP64 one. Within the cutoff, the displacement (l_i - l_j) - dc*cell, r^2, 1/r^2, the LJ
+// factor of Eq. 2 and the pair force run in double-word arithmetic on the hi + lo parts (~2^-44
+// relative, against 2^-53 for FP64; the offsets themselves are exact to ~1e-14, like FP64
+// positions in the box) -- work for the FP32 pipe, not the FP64 one.
+__device__ __forceinline__ bool df_pair_term(const Arrays& a, const PotDev& p, const RepDev& R,
+                                             int i, const float4& li, const float4& ll,
+                                             uint32_t e, const float4& b, const float4& bl, int N,
+                                             dword& px, dword& py, dword& pz) {
+  const int j = (int)(e & kIndexMask);
+  const bool wall = j >= N;
+  const uint32_t ox = (e >> 26) & 3u, oy = (e >> 28) & 3u, oz = e >> 30;
+  const float shx = cell_shift(ox, R.lcxf), shy = cell_shift(oy, R.lcyf),
+              shz = cell_shift(oz, R.lczf);
+  const float dxf = (li.x - b.x) - shx, dyf = (li.y - b.y) - shy, dzf = (li.z - b.z) - shz;
+  const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+  const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
+  bool in = r2f < lo;
+  if (!in && r2f < hi) {  // near rc: the FP64 decision, as the FP64 kernels take it
+    const dvec4 xi = a.pos[i];
+    const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+    const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+    const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+    const double ez = xi.z - xj.z;
+    in = lt_pos(ex * ex + ey * ey + ez * ez, wall ? p.rcw2 : p.rc2);
+  }
+  if (!in) return false;
+  const dword dx = dw_disp(li.x, ll.x, b.x, bl.x, shx, cell_shift(ox, R.lcx_lo));
+  const dword dy = dw_disp(li.y, ll.y, b.y, bl.y, shy, cell_shift(oy, R.lcy_lo));
+  const dword dz = dw_disp(li.z, ll.z, b.z, bl.z, shz, cell_shift(oz, R.lcz_lo));
+  const dword r2 = dw_add(dw_add(dw_sqr(dx), dw_sqr(dy)), dw_sqr(dz));
+  const dword inv2 = dw_rcp(r2);
+  const dword inv4 = dw_sqr(inv2);
+  const dword inv6 = dw_mul(inv4, inv2);
+  const dword inv8 = dw_sqr(inv4);
+  const dword A = wall ? dword{p.a12wf, p.a12wl} : dword{p.a12f, p.a12l};
+  const dword B = wall ? dword{-p.b6wf, -p.b6wl} : dword{-p.b6f, -p.b6l};
+  const dword fr = dw_mul(inv8, dw_add(dw_mul(A, inv6), B));
+  px = dw_mul(fr, dx);
+  py = dw_mul(fr, dy);
+  pz = dw_mul(fr, dz);
+  return true;
+}
+
+// the molecule's own sum of double-word pair forces: a compensated FP32 pair per component
+__device__ __forceinline__ void df_accumulate(float& s, float& c, const dword& p) {
+  two_sum_acc(s, c, p.hi);
+  c += p.lo;
+}
+
+// Double-float pair terms, half list, reaction forces by atomics: each vapour pair once, its
+// reaction sent to the partner as an FP64 atomic add of the pair force's double-word value. The
+// forces must be zero beforehand.
 template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, int lpt,
                                                           int owe_kick) {
@@ -2070,43 +2117,13 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
         const uint32_t en = qn < n ? row[qn] : 0u;
         const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
         const float4 bln = qn < n ? partner_lpos_lo(a, en, N) : ll;
-        const int j = (int)(e & kIndexMask);
-        const bool wall = j >= N;
-        const uint32_t ox = (e >> 26) & 3u, oy = (e >> 28) & 3u, oz = e >> 30;
-        const float shx = cell_shift(ox, R.lcxf), shy = cell_shift(oy, R.lcyf),
-                    shz = cell_shift(oz, R.lczf);
-        const float dxf = (li.x - b.x) - shx, dyf = (li.y - b.y) - shy, dzf = (li.z - b.z) - shz;
-        const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
-        const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
-        bool in = r2f < lo;
-        if (!in && r2f < hi) {  // near rc: the FP64 decision, as the FP64 kernels take it
-          const dvec4 xi = a.pos[i];
-          const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
-          const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-          const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
-          const double ez = xi.z - xj.z;
-          in = lt_pos(ex * ex + ey * ey + ez * ez, wall ? p.rcw2 : p.rc2);
-        }
-        if (in) {
-          const dword dx = dw_disp(li.x, ll.x, b.x, bl.x, shx, cell_shift(ox, R.lcx_lo));
-          const dword dy = dw_disp(li.y, ll.y, b.y, bl.y, shy, cell_shift(oy, R.lcy_lo));
-          const dword dz = dw_disp(li.z, ll.z, b.z, bl.z, shz, cell_shift(oz, R.lcz_lo));
-          const dword r2 = dw_add(dw_add(dw_sqr(dx), dw_sqr(dy)), dw_sqr(dz));
-          const dword inv2 = dw_rcp(r2);
-          const dword inv4 = dw_sqr(inv2);
-          const dword inv6 = dw_mul(inv4, inv2);
-          const dword inv8 = dw_sqr(inv4);
-          const dword A = wall ? dword{p.a12wf, p.a12wl} : dword{p.a12f, p.a12l};
-          const dword B = wall ? dword{-p.b6wf, -p.b6wl} : dword{-p.b6f, -p.b6l};
-          const dword fr = dw_mul(inv8, dw_add(dw_mul(A, inv6), B));
-          const dword px = dw_mul(fr, dx), py = dw_mul(fr, dy), pz = dw_mul(fr, dz);
-          two_sum_acc(sx, cx, px.hi);
-          two_sum_acc(sy, cy, py.hi);
-          two_sum_acc(sz, cz, pz.hi);
-          cx += px.lo;
-          cy += py.lo;
-          cz += pz.lo;
-          if (!wall) {  // Newton's third law: the partner receives -p
+        dword px, py, pz;
+        if (df_pair_term(a, p, R, i, li, ll, e, b, bl, N, px, py, pz)) {
+          df_accumulate(sx, cx, px);
+          df_accumulate(sy, cy, py);
+          df_accumulate(sz, cz, pz);
+          const int j = (int)(e & kIndexMask);
+          if (j < N) {  // Newton's third law: the partner receives -p
             atomicAdd(&a.frc[j].x, neg_bits(dw_to_double(px)));
             atomicAdd(&a.frc[j].y, neg_bits(dw_to_double(py)));
             atomicAdd(&a.frc[j].z, neg_bits(dw_to_double(pz)));
@@ -2128,6 +2145,73 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
     }
   }
   const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  finish_chunks(a);
+}
+
+// Double-float pair terms, full list (front + back of each row), deterministic: every vapour
+// pair is evaluated from both ends, with no atomics; each molecule sums its own row in slot order
+// and writes its force, with the second half-kick fused when KICK (Fig. 3). The same sum from the
+// same lists every run: bit-for-bit reproducible.
+template <bool KICK, int TPP>
+__global__ void __launch_bounds__(256) k_forces_df(Arrays a, PotDev p, int lpt) {
+  constexpr int MPW = 32 / TPP;
+  count_launch(a);
+  clear_rebuild_flags(a);
+  if (KICK && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 0;  // this step kicks itself
+  if (halted(a)) return;
+  const int N = a.n_total, cap = p.cap;
+  const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
+  int cnt = 0;
+  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int t = chunk * MPW + lane / TPP;
+    const bool live = t < N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    int i = 0;
+    if (live) {
+      i = lpt ? a.order[t] : t;
+      const RepDev& R = a.reps[a.rep[i]];
+      const float4 li = a.lpos[i], ll = a.lpos_lo[i];
+      const int nf = a.n_front[i], n = nf + a.n_back[i];
+      const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      // slot q of the full row is the front's q-th entry, then the back's from the end
+      uint32_t e = sub < n ? row[sub < nf ? sub : cap - 1 - (sub - nf)] : 0u;
+      float4 b = sub < n ? partner_lpos(a, e, N) : li;
+      float4 bl = sub < n ? partner_lpos_lo(a, e, N) : ll;
+      for (int q = sub; q < n; q += TPP) {
+        const int qn = q + TPP;
+        const uint32_t en = qn < n ? row[qn < nf ? qn : cap - 1 - (qn - nf)] : 0u;
+        const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
+        const float4 bln = qn < n ? partner_lpos_lo(a, en, N) : ll;
+        dword px, py, pz;
+        if (df_pair_term(a, p, R, i, li, ll, e, b, bl, N, px, py, pz)) {
+          df_accumulate(sx, cx, px);
+          df_accumulate(sy, cy, py);
+          df_accumulate(sz, cz, pz);
+          cnt += (int)(e & kIndexMask) >= N ? 2 : 1;  // vapour pairs are seen from both ends
+        }
+        e = en;
+        b = bn;
+        bl = bln;
+      }
+    }
+    const double fx = group_sum_comp<TPP>(sx, cx);
+    const double fy = group_sum_comp<TPP>(sy, cy);
+    const double fz = group_sum_comp<TPP>(sz, cz);
+    if (live && sub == 0) {
+      a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
+      if (KICK) {  // Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+        const RepDev& R = a.reps[a.rep[i]];
+        dvec4 v = a.vel[i];
+        const double h = R.half_dt_m;
+        v.x += h * fx;
+        v.y += h * fy;
+        v.z += h * fz;
+        a.vel[i] = v;
+      }
+    }
+  }
+  const unsigned long long c = warp_sum((unsigned long long)cnt);
   if (lane == 0 && c) atomicAdd(a.pair_count, c);
   finish_chunks(a);
 }
@@ -2275,7 +2359,8 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   const int ntiles = nblocks(a.n_cells, 4096);
   // the pair kernel walks the front of each row (FP64, or mixed with atomic reaction forces) or the
   // whole row (mixed, deterministic): the processing order sorts by that length
-  const int half = (!mixed || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
+  // (double-float pair terms in the deterministic form walk the whole row, as mixed does)
+  const int half = ((!mixed && !t.df64) || t.atomic_acc) ? 1 : 0, lpt = t.lpt;
   k_cell_clear<<<nt, b, 0, s>>>(a, p);
   k_cell_count<<<nt, b, 0, s>>>(a, p);
   if (ntiles <= 16) {
@@ -2291,7 +2376,7 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
       a, p, half, t.atomic_acc, lpt);
   if (lpt) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
-  if (!mixed && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
+  if (!mixed && !t.df64 && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
 }
 
 // the per-molecule pair observables that half rows accumulate by atomics start from zero
@@ -2372,11 +2457,16 @@ void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, c
   }
 }
 
-// FP64 context with double-float pair terms (atomic reaction forces only)
+// FP64 context with double-float pair terms: atomic reaction forces, or the full-list form
 template <int TPP>
 void launch_df(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cudaStream_t s) {
   const int b = t.force_block;
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
+  if (!t.atomic_acc) {
+    if (kick) k_forces_df<true, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+    else k_forces_df<false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
+    return;
+  }
   // forces start from zero (k_integrate_first clears them in a step); the second half-kick of a
   // step is deferred into the next first half-kick
   if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
@@ -2434,7 +2524,8 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
-  if (t.df64) k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  if (t.df64 && t.atomic_acc) k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  else if (t.df64) k_forces_df<false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
   else if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
   else k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
 }

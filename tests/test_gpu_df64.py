@@ -1,7 +1,8 @@
 """Double-float pair terms (MD_PREC_DF64) against the FP64 CPU oracle and the FP64 GPU form.
 
 The context is an FP64 one (positions, integration, cutoff decisions near rc, accumulation,
-observables); only the pair terms run in double-word FP32 arithmetic (~2^-44 relative per term).
+observables); only the pair terms run in double-word FP32 arithmetic (~2^-44 relative per term),
+in a half-list form with atomic reaction forces or a full-list form with no atomics.
 The bar is the FP64 path's: per-step forces max_i |F - F_oracle| / RMS(F) <= 1e-10, 10-step
 trajectories |dr|, |dv| <= 1e-8, integer observables exactly equal -- and, closer, the FP64 GPU
 form's forces to 1e-11 of the RMS force.
@@ -57,14 +58,17 @@ def test_small_cylinder_forces_trajectory_and_observables():
         check_observables(sim, 0, s, st)
 
 
-@pytest.mark.parametrize("tpp,block,bps,lpt", [
-    (1, 256, 4, 1), (2, 128, 2, 1), (4, 256, 4, 1), (4, 128, 1, 2), (8, 256, 4, 1)])
-def test_every_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, bps, lpt):
-    """Lanes per molecule, block size, blocks per SM and processing order: the oracle's forces,
-    10-step trajectories (with a thermostat step) and integer observables of four pore shapes."""
+@pytest.mark.parametrize("tpp,block,bps,lpt,acc", [
+    (1, 256, 4, 1, 2), (2, 128, 2, 1, 2), (4, 256, 4, 1, 2), (4, 128, 1, 2, 2), (8, 256, 4, 1, 2),
+    (1, 128, 4, 1, 1), (2, 256, 2, 2, 1), (4, 256, 4, 1, 1), (8, 128, 8, 1, 1)])
+def test_every_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, bps, lpt, acc):
+    """Lanes per molecule, block size, blocks per SM, processing order, and the atomic (half
+    list) or full-list form: the oracle's forces, 10-step trajectories (with a thermostat step)
+    and integer observables of four pore shapes."""
     with md.Simulation(shapes, precision=DF) as sim:
         sim.set_tuning(force_tpp=tpp, force_block=block, force_blocks_per_sm=bps,
-                       order_by_length=lpt)
+                       order_by_length=lpt, force_accumulate=acc)
+        assert sim.tuning()["force_accumulate"] == acc
         sim.compute_forces()
         for r, s in enumerate(shapes):
             g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
@@ -97,6 +101,28 @@ def test_agrees_with_fp64_on_a_filled_pore_over_fifty_steps():
         assert oa["pe"] == pytest.approx(ob["pe"], rel=1e-10)
 
 
+def test_full_list_form_is_bitwise_reproducible(shapes):
+    """The full-list form sums each molecule's own row in a fixed order with no atomics: two runs,
+    and graph replays against plain launches, agree bit for bit; the atomic form agrees with it to
+    rounding."""
+    runs = []
+    for graph in (1, 2, 1):
+        with md.Simulation(shapes, precision=DF) as sim:
+            sim.set_tuning(force_accumulate=1, use_graph=graph, steps_per_graph=5)
+            sim.step(25)
+            runs.append([sim.state(r) + (sim.forces(r),) for r in range(len(shapes))])
+    for r in range(len(shapes)):
+        for k in range(3):
+            np.testing.assert_array_equal(runs[0][r][k], runs[1][r][k])
+            np.testing.assert_array_equal(runs[0][r][k], runs[2][r][k])
+    with md.Simulation(shapes, precision=DF) as sim:
+        sim.step(25)
+        for r, s in enumerate(shapes):
+            x, v = sim.state(r)
+            assert np.abs(wrapped_diff(x, runs[0][r][0], s)).max() <= 1e-9
+            assert np.abs(v - runs[0][r][1]).max() <= 1e-9
+
+
 def test_graph_and_plain_launches_agree(shapes):
     with md.Simulation(shapes, precision=DF) as a, md.Simulation(shapes, precision=DF) as b:
         a.set_tuning(use_graph=2)
@@ -113,7 +139,7 @@ def test_graph_and_plain_launches_agree(shapes):
 def test_options_outside_the_mode_are_rejected():
     s = W.cylinder_pore_1k()
     with md.Simulation(s, precision=DF) as sim:
-        for bad in (dict(force_accumulate=1), dict(force_tpp=32), dict(pair_method=2)):
+        for bad in (dict(force_tpp=32), dict(pair_method=2)):
             with pytest.raises(md.MDError):
                 sim.set_tuning(**bad)
         t, us = sim.autotune(3)
