@@ -146,7 +146,7 @@ typedef struct {
   int32_t force_block;     /* threads per block of the pair-force kernel: 128 or 256 */
   int32_t force_blocks_per_sm; /* resident pair-kernel blocks per SM: the grid is SMs x this and
                               warps fetch chunks of molecules dynamically (1..32) */
-  int32_t force_tpp;       /* lanes that split one molecule's neighbour list: 1, 2, 4 or 8;
+  int32_t force_tpp;       /* lanes that split one molecule's neighbour list: 1, 2, 4, 8 or 16;
                               FP64 also 32: a warp owns 32 molecules, screens their lists in
                               FP32 and packs the surviving pairs so that every lane of the
                               FP64 pair terms is busy */
@@ -209,7 +209,7 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 
 /* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 2 and 8): time
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
- * force_tpp {1,2,4,8, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
+ * force_tpp {1,2,4,8,16, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
  * x order_by_length {on,off} -- with CUDA events on the context's stream (median of `trials`
  * launches each, trials clamped to [3, 101]), then apply the fastest. Positions and velocities
  * are unchanged; forces are recomputed at the same positions. *best and *best_us (either may be

@@ -764,8 +764,8 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   }
   if (t->force_tpp) {
     if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8 &&
-        !(t->force_tpp == 32 && !c->mixed && !c->tun.df64))
-      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4 or 8 (or 32 at FP64)");
+        t->force_tpp != 16 && !(t->force_tpp == 32 && !c->mixed && !c->tun.df64))
+      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4, 8 or 16 (or 32 at FP64)");
     if (c->mixed) nt.tpp_mixed = t->force_tpp;
     else nt.tpp_fp64 = t->force_tpp;
   }
@@ -827,7 +827,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   Tuning bestT = saved;
   double bestv = 1e300;
   md_status st = MD_OK;
-  const int tpps[5] = {1, 2, 4, 8, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
+  const int tpps[6] = {1, 2, 4, 8, 16, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
   for (int lpt = 1; lpt >= 0 && st == MD_OK; --lpt) {
     c->tun = saved;
     c->tun.lpt = lpt;

@@ -2480,6 +2480,7 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
       case 1: launch_mixed<1>(a, p, stats, kick, t, s); break;
       case 2: launch_mixed<2>(a, p, stats, kick, t, s); break;
       case 8: launch_mixed<8>(a, p, stats, kick, t, s); break;
+      case 16: launch_mixed<16>(a, p, stats, kick, t, s); break;
       default: launch_mixed<4>(a, p, stats, kick, t, s); break;
     }
     return;
@@ -2501,6 +2502,7 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
       case 1: launch_df<1>(a, p, kick, t, s); break;
       case 2: launch_df<2>(a, p, kick, t, s); break;
       case 8: launch_df<8>(a, p, kick, t, s); break;
+      case 16: launch_df<16>(a, p, kick, t, s); break;
       default: launch_df<4>(a, p, kick, t, s); break;
     }
     return;
@@ -2509,6 +2511,7 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
     case 1: launch_fp64<1>(a, p, kick, t, s); break;
     case 2: launch_fp64<2>(a, p, kick, t, s); break;
     case 8: launch_fp64<8>(a, p, kick, t, s); break;
+    case 16: launch_fp64<16>(a, p, kick, t, s); break;
     case 32: launch_fp64<32>(a, p, kick, t, s); break;
     default: launch_fp64<4>(a, p, kick, t, s); break;
   }
@@ -2553,6 +2556,7 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
     case 1: pair_pass_tpp<1>(a, p, mixed, t, s); break;
     case 2: pair_pass_tpp<2>(a, p, mixed, t, s); break;
     case 8: pair_pass_tpp<8>(a, p, mixed, t, s); break;
+    case 16: pair_pass_tpp<16>(a, p, mixed, t, s); break;
     default: pair_pass_tpp<4>(a, p, mixed, t, s); break;
   }
 }

@@ -60,7 +60,8 @@ def test_small_cylinder_forces_trajectory_and_observables():
 
 @pytest.mark.parametrize("tpp,block,bps,lpt,acc", [
     (1, 256, 4, 1, 2), (2, 128, 2, 1, 2), (4, 256, 4, 1, 2), (4, 128, 1, 2, 2), (8, 256, 4, 1, 2),
-    (1, 128, 4, 1, 1), (2, 256, 2, 2, 1), (4, 256, 4, 1, 1), (8, 128, 8, 1, 1)])
+    (1, 128, 4, 1, 1), (2, 256, 2, 2, 1), (4, 256, 4, 1, 1), (8, 128, 8, 1, 1), (16, 256, 4, 1, 2),
+    (16, 128, 2, 1, 1)])
 def test_every_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, bps, lpt, acc):
     """Lanes per molecule, block size, blocks per SM, processing order, and the atomic (half
     list) or full-list form: the oracle's forces, 10-step trajectories (with a thermostat step)
@@ -143,6 +144,6 @@ def test_options_outside_the_mode_are_rejected():
             with pytest.raises(md.MDError):
                 sim.set_tuning(**bad)
         t, us = sim.autotune(3)
-        assert t["force_tpp"] in (1, 2, 4, 8) and us > 0
+        assert t["force_tpp"] in (1, 2, 4, 8, 16) and us > 0
         g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
         assert force_err(sim.forces(), g) <= FORCE_TOL

@@ -142,7 +142,7 @@ def shapes_after_ten(shapes):
 @pytest.mark.parametrize("tpp,block,lpt,acc", [
     (1, 128, 1, 1), (2, 256, 1, 1), (4, 128, 2, 1), (8, 256, 1, 1), (32, 128, 1, 1),
     (32, 256, 1, 1), (32, 128, 2, 1), (1, 256, 1, 2), (2, 128, 1, 2), (4, 256, 2, 2),
-    (8, 128, 1, 2), (32, 256, 1, 2), (32, 128, 2, 2)])
+    (8, 128, 1, 2), (32, 256, 1, 2), (32, 128, 2, 2), (16, 256, 1, 1), (16, 128, 1, 2)])
 def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, block, lpt, acc):
     """Every pair-kernel variant (lanes per molecule, the packed kernel, block size, processing
     order, deterministic or atomic accumulation) gives the oracle's forces and 10-step
@@ -201,7 +201,7 @@ def test_atomic_forms_agree_with_deterministic_on_a_filled_pore(tpp):
         assert oa["pairs_vv"] == ob["pairs_vv"] and oa["pairs_vw"] == ob["pairs_vw"]
 
 
-@pytest.mark.parametrize("tpp", [1, 2, 4, 8])
+@pytest.mark.parametrize("tpp", [1, 2, 4, 8, 16])
 def test_mixed_atomic_half_list_matches_oracle(shapes, shapes_after_ten, tpp):
     """The mixed form with atomic reaction forces (each vapour pair once): RMS force error <= 1e-5
     against the oracle and close to the full-list mixed form; 10-step trajectories and the
