@@ -331,17 +331,24 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     *a.step += 1;
     *a.any_scale = 0;
   }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool own = i < a.n_total;
+  // the molecule's records load together with the flags (one round trip to memory, not two)
+  int my_rep = 0;
+  dvec4 x, v, f, r0;
+  if (own) {
+    my_rep = a.rep[i];
+    x = a.pos[i];
+    v = a.vel[i];
+    f = a.frc[i];
+    r0 = a.pos_ref[i];
+  }
   const bool halt = halted(a);
   const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d2 = 0.0;
-  int my_rep = 0;
-  if (!halt && i < a.n_total) {
-    my_rep = a.rep[i];
+  if (!halt && own) {
     const RepDev& R = a.reps[my_rep];
-    dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 x_old = x;
-    const dvec4 f = a.frc[i];
     // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
     // force) owed, both at once
     const double h = pend ? R.dt_m : R.half_dt_m;
@@ -367,7 +374,6 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
     const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
     if (bad) atomicOr(a.status, kStatusUnstable);
-    const dvec4 r0 = a.pos_ref[i];
     double dx = x.x - r0.x, dy = x.y - r0.y;
     if (ge_pos(dx, R.hx)) dx -= R.Lx;
     else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
