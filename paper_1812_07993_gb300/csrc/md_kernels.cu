@@ -331,24 +331,17 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     *a.step += 1;
     *a.any_scale = 0;
   }
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool own = i < a.n_total;
-  // the molecule's records load together with the flags (one round trip to memory, not two)
-  int my_rep = 0;
-  dvec4 x, v, f, r0;
-  if (own) {
-    my_rep = a.rep[i];
-    x = a.pos[i];
-    v = a.vel[i];
-    f = a.frc[i];
-    r0 = a.pos_ref[i];
-  }
   const bool halt = halted(a);
   const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d2 = 0.0;
-  if (!halt && own) {
+  int my_rep = 0;
+  if (!halt && i < a.n_total) {
+    my_rep = a.rep[i];
     const RepDev& R = a.reps[my_rep];
+    dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 x_old = x;
+    const dvec4 f = a.frc[i];
     // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
     // force) owed, both at once
     const double h = pend ? R.dt_m : R.half_dt_m;
@@ -374,6 +367,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
     const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
     if (bad) atomicOr(a.status, kStatusUnstable);
+    const dvec4 r0 = a.pos_ref[i];
     double dx = x.x - r0.x, dy = x.y - r0.y;
     if (ge_pos(dx, R.hx)) dx -= R.Lx;
     else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
@@ -1038,20 +1032,6 @@ __device__ __forceinline__ double group_min(double v) {
 #pragma unroll
   for (int o = TPP / 2; o; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
   return v;
-}
-
-// sum over the TPP lanes of a molecule of compensated FP32 partial sums s + c: the butterfly
-// stays compensated (TwoSum per stage, fixed order) and only the total is widened to FP64, one
-// FP64 add instead of one per stage
-template <int TPP>
-__device__ __forceinline__ double group_sum_comp(float s, float c) {
-#pragma unroll
-  for (int o = TPP / 2; o; o >>= 1) {
-    const float so = __shfl_xor_sync(kFull, s, o), co = __shfl_xor_sync(kFull, c, o);
-    two_sum_acc(s, c, so);
-    c += co;
-  }
-  return widen_f32(s) + widen_f32(c);
 }
 
 __device__ __forceinline__ void finish_chunks(const Arrays& a) {
@@ -1891,9 +1871,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         b = bn;
       }
     }
-    double fx = group_sum_comp<TPP>(sx, cx);
-    double fy = group_sum_comp<TPP>(sy, cy);
-    double fz = group_sum_comp<TPP>(sz, cz);
+    double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (STATS) {
       pe = group_sum<TPP>(pe);
       pew = group_sum<TPP>(pew);
@@ -2008,9 +1988,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
         b = bn;
       }
     }
-    const double fx = group_sum_comp<TPP>(sx, cx);
-    const double fy = group_sum_comp<TPP>(sy, cy);
-    const double fz = group_sum_comp<TPP>(sz, cz);
+    const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (live && sub == 0) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
@@ -2141,9 +2121,9 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
         bl = bln;
       }
     }
-    const double fx = group_sum_comp<TPP>(sx, cx);
-    const double fy = group_sum_comp<TPP>(sy, cy);
-    const double fz = group_sum_comp<TPP>(sz, cz);
+    const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (live && sub == 0) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
@@ -2201,9 +2181,9 @@ __global__ void __launch_bounds__(256) k_forces_df(Arrays a, PotDev p, int lpt) 
         bl = bln;
       }
     }
-    const double fx = group_sum_comp<TPP>(sx, cx);
-    const double fy = group_sum_comp<TPP>(sy, cy);
-    const double fz = group_sum_comp<TPP>(sz, cz);
+    const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
+    const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
+    const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
     if (live && sub == 0) {
       a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
       if (KICK) {  // Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
