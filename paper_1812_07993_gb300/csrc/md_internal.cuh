@@ -7,6 +7,8 @@
 //     pos_ref         positions at the last list build (skin check)
 //     lpos            float4, position relative to the centre of the home cell (FP32 staging for the
 //                     list build and the mixed-precision pair kernel)
+//     lpos_lo         float4, that offset minus lpos, rounded to FP32: with lpos the double-float
+//                     offset of the double-float pair kernels
 //     home, id, rep   int32: home cell (packed ix | iy << 10 | iz << 20), caller index within the
 //                     replica, replica
 //     nbr             Verlet list, one row of `cap` slots per molecule: partners j > i then wall
@@ -19,7 +21,8 @@
 //     pairbuf         forces of the pairs held by lower partners, [molecule * cap_v + back slot],
 //                     plus one spare entry at the end
 //     fpart           partial force of the half-list pass
-//   wall (static, sorted by cell once at creation): wpos double4, wlpos float4, wstart (CSR)
+//   wall (static, sorted by cell once at creation): wpos double4, wlpos and wlpos_lo float4,
+//     wstart (CSR)
 //   cells: per-replica grids of side >= max(rc, rc_w) + skin, at least 3 across x and y.
 // A list entry packs the neighbour index in the low 26 bits -- a vapour molecule below n_total, a
 // wall atom at n_total + its index -- and the neighbour's home-cell offset relative to the
