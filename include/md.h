@@ -230,11 +230,15 @@ md_status md_sync(md_ctx* ctx);
  * makes it a DMA at full link speed). Synchronises. */
 md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
 
-/* Overwrite replica state from host arrays (3*n_vapor each, caller's order; positions must lie
- * inside the box, checked on the host before anything is copied: MD_EINVAL leaves the state
- * untouched). replica = -1 sets every replica from arrays concatenated in replica order. One
- * copy per array into device staging rows, then a kernel writes the records; forces are
- * re-evaluated and lists rebuilt. The step counter is unchanged. */
+/* Overwrite replica state from host arrays (3*n_vapor each, caller's order). Positions must lie
+ * inside the box (x, y in [-L/2, L/2), z in [-Lz/2, Lz/2]; a planar replica's y and vy must be
+ * 0). replica = -1 sets every replica from arrays concatenated in replica order.
+ * - The rows go by one copy per array into device staging rows.
+ * - A kernel checks every row there, then a kernel writes the records only if all rows passed.
+ * - Lists are rebuilt and forces re-evaluated.
+ * A failing row gives MD_EINVAL, with its replica and molecule in md_last_error, and leaves the
+ * positions and velocities as they were (an owed half-kick is still paid). The step counter is
+ * unchanged. Synchronises once at the start and once at the end. */
 md_status md_set_state(md_ctx* ctx, int32_t replica, const double* x, const double* v);
 
 /* Enqueue one evaluation of the forces at the current positions with the same pair-force kernel

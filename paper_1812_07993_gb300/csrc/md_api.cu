@@ -34,7 +34,8 @@ struct md_ctx {
   std::vector<ReplicaHost> rh;
   std::vector<void*> allocs;
   std::string err;
-  int32_t* status_host = nullptr;   // pinned
+  int32_t* status_host = nullptr;   // pinned: [0] device status bits, [1] the state check's row
+  int32_t* bad_row = nullptr;       // device: lowest row a state load's check rejected
   cudaEvent_t status_event = nullptr;
   bool status_pending = false;
   int last_status_bits = 0;
@@ -670,10 +671,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.pore_part, (size_t)n_reps * A.rep_chunks * A.max_pores);
   ALLOC(A.pore_press, std::max<size_t>(pores.size(), 1));
   ALLOC(A.rep_sums, (size_t)n_reps * 8);
+  ALLOC(c->bad_row, 1);
 #undef ALLOC
-  cudaError_t e = cudaMallocHost(&c->status_host, sizeof(int32_t));
+  cudaError_t e = cudaMallocHost(&c->status_host, 2 * sizeof(int32_t));
   if (e != cudaSuccess) return bail(fail(c, MD_ENOMEM, "pinned status word"));
-  *c->status_host = 0;
+  c->status_host[0] = 0;
+  c->status_host[1] = kNoBadRow;
   e = cudaEventCreateWithFlags(&c->status_event, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
 
@@ -978,22 +981,8 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
   if (s != MD_OK) return s;
   int off, n;
   replica_range(c, r, &off, &n);
-  // every position inside its replica's box, checked before anything is copied
-  for (int rr = (r < 0 ? 0 : r); rr < (r < 0 ? c->n_reps : r + 1); ++rr) {
-    const RepDev& R = c->reps[rr];
-    const double* xr = x + 3 * (size_t)(R.vap_off - off);
-    for (int i = 0; i < R.n_vap; ++i) {
-      const double* q = xr + 3 * (size_t)i;
-      if (!(q[0] >= -R.hx && q[0] < R.hx && q[1] >= -R.hy && q[1] < R.hy && q[2] >= -R.hz &&
-            q[2] <= R.hz))
-        return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
-                                      std::to_string(i) + " outside the box");
-      if (R.dims == 2 && (q[1] != 0.0 || v[3 * (size_t)(R.vap_off - off + i) + 1] != 0.0))
-        return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
-                                      std::to_string(i) + " leaves the plane y = 0");
-    }
-  }
-  // the other replicas' owed kicks are paid before the load resets the flag
+  // the owed kicks are paid before the load resets the flag (a state-preserving step, taken
+  // whether or not the rows pass their check)
   launch_settle_kick(c->a, c->pot, c->stream);
   if (n) {
     const size_t bytes = 3 * (size_t)n * sizeof(double);
@@ -1002,10 +991,27 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
     CUDA_TRY(c, cudaMemcpyAsync(c->stage_v + 3 * (size_t)off, v, bytes, cudaMemcpyHostToDevice,
                                 c->stream));
     c->bytes_h2d += (int64_t)(2 * bytes);
-    launch_load_state(c->a, c->stage_x, c->stage_v, off, n, c->stream);
+    // every row is checked on the device (inside its replica's box; planar replicas in the
+    // plane) before the load, which leaves the state untouched if any row fails
+    CUDA_TRY(c, cudaMemsetAsync(c->bad_row, 0x7f, sizeof(int32_t), c->stream));
+    launch_load_state(c->a, c->stage_x, c->stage_v, off, n, c->bad_row, c->stream);
     CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(c->status_host + 1, c->bad_row, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+    c->bytes_d2h += sizeof(int32_t);
   }
-  return rebuild_and_forces(c);
+  const md_status st = rebuild_and_forces(c);   // waits for the stream, the check's row included
+  const int32_t bad = c->status_host[1];
+  c->status_host[1] = kNoBadRow;
+  if (n && bad != kNoBadRow) {
+    const int row = off + (bad >> 1);
+    int rr = 0;
+    while (rr + 1 < c->n_reps && c->reps[rr + 1].vap_off <= row) ++rr;
+    return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
+                                  std::to_string(row - c->reps[rr].vap_off) +
+                                  ((bad & 1) ? " leaves the plane y = 0" : " outside the box"));
+  }
+  return st;
 }
 
 md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, int64_t* adsorbed,

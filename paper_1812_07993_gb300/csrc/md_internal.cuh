@@ -216,9 +216,12 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
 cudaError_t configure_kernels();
-// state transfer through device staging rows (caller order, xyz interleaved)
+// state transfer through device staging rows (caller order, xyz interleaved). The load checks
+// the rows first (positions inside the box, planar replicas in the plane) and loads nothing if
+// any fails; *bad (kNoBadRow beforehand) receives the lowest failing row as 2 k or 2 k + 1.
+constexpr int kNoBadRow = 0x7f7f7f7f;  // the byte pattern 0x7f repeated (a memset)
 void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
-                       cudaStream_t s);
+                       int* bad, cudaStream_t s);
 void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,
                        cudaStream_t s);
 // the pair kernel alone (no clearing, gather or kick): for timing the dominant kernel

@@ -2550,13 +2550,34 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
 // ------------------------------------------------------------------------------------------------
 // state transfer: caller-order xyz arrays <-> cell-sorted device records
 
-// molecules [off, off + n) take the caller-order rows xin/vin (xyz interleaved, same offset); the
-// stored order restarts as the caller's (id = index within the replica), forces cleared
-__global__ void k_load_state(Arrays a, const double* __restrict__ xin,
-                             const double* __restrict__ vin, int off, int n) {
+// caller rows [off, off + n) staged for a state load, checked before they replace anything: every
+// position inside its replica's box (x and y in [-L/2, L/2), z in [-Lz/2, Lz/2]; NaN fails) and,
+// for a planar replica, y = vy = 0. The lowest offending row lands in *bad as 2 k (outside the
+// box) or 2 k + 1 (off the plane); *bad keeps kNoBadRow when every row passes.
+__global__ void k_check_state(Arrays a, const double* __restrict__ xin,
+                              const double* __restrict__ vin, int off, int n, int* bad) {
   count_launch(a);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
+  const int i = off + k;
+  const RepDev& R = a.reps[a.rep[i]];
+  const double x = xin[3 * (size_t)i], y = xin[3 * (size_t)i + 1], z = xin[3 * (size_t)i + 2];
+  int code = -1;
+  if (!(x >= -R.hx && x < R.hx && y >= -R.hy && y < R.hy && z >= -R.hz && z <= R.hz))
+    code = 2 * k;
+  else if (R.dims == 2 && (y != 0.0 || vin[3 * (size_t)i + 1] != 0.0))
+    code = 2 * k + 1;
+  if (code >= 0) atomicMin(bad, code);
+}
+
+// molecules [off, off + n) take the caller-order rows xin/vin (xyz interleaved, same offset); the
+// stored order restarts as the caller's (id = index within the replica), forces cleared. Nothing
+// is loaded when k_check_state found a bad row.
+__global__ void k_load_state(Arrays a, const double* __restrict__ xin,
+                             const double* __restrict__ vin, int off, int n, const int* bad) {
+  count_launch(a);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n || *bad != kNoBadRow) return;
   const int i = off + k;
   const dvec4 x = make_dvec4(xin[3 * (size_t)i], xin[3 * (size_t)i + 1], xin[3 * (size_t)i + 2],
                              0.0);
@@ -2583,8 +2604,10 @@ __global__ void k_store_rows(Arrays a, const dvec4* __restrict__ src, double* __
 }
 
 void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
-                       cudaStream_t s) {
-  if (n > 0) k_load_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n);
+                       int* bad, cudaStream_t s) {
+  if (n <= 0) return;
+  k_check_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n, bad);
+  k_load_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n, bad);
 }
 
 void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,

@@ -343,6 +343,35 @@ def test_set_state_round_trip_and_restart_parity():
         assert np.abs(wrapped_diff(x3, st.x, s)).max() <= TRAJ_TOL
 
 
+def test_rejected_state_names_the_row_and_leaves_the_context_unchanged(shapes):
+    """md_set_state checks the rows on the device before loading: a position outside the box (or
+    NaN) anywhere in a whole-context load is reported with its replica and molecule, nothing is
+    loaded, and the context steps on from where it was."""
+    with md.Simulation(shapes) as sim, md.Simulation(shapes) as ref:
+        sim.step(5)
+        ref.step(5)
+        x, v = sim.state(-1)
+        n0 = shapes[0].n_vapor
+        for bad_value, row in ((shapes[2].Lz, n0 + shapes[1].n_vapor + 17), (np.nan, 3)):
+            xb = x.copy()
+            xb[row, 2] = bad_value
+            with pytest.raises(md.MDError, match="outside the box") as err:
+                sim.set_state(-1, xb, v)
+            rr = 0 if row < n0 else 2
+            first = 0 if rr == 0 else n0 + shapes[1].n_vapor
+            assert f"replica {rr}: molecule {row - first} " in str(err.value)
+        x2, v2 = sim.state(-1)
+        np.testing.assert_array_equal(x2, x)
+        np.testing.assert_array_equal(v2, v)
+        sim.step(5)
+        ref.step(5)
+        for r, s in enumerate(shapes):
+            xa, va = sim.state(r)
+            xb_, vb = ref.state(r)
+            assert np.abs(wrapped_diff(xa, xb_, s)).max() <= 1e-10
+            assert np.abs(va - vb).max() <= 1e-10
+
+
 def place_on(s, axis, value):
     """Move some molecule onto the plane x[axis] = value without creating a close pair."""
     for i in range(s.n_vapor):
