@@ -287,10 +287,8 @@ void enqueue_step(md_ctx* c) {
 }
 
 md_status rebuild_and_forces(md_ctx* c) {
-  const int one = 1;
-  CUDA_TRY(c, cudaMemcpyAsync(c->a.force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
-                              c->stream));
-  c->bytes_h2d += sizeof(int);
+  // the flag only needs to be nonzero: a memset, no copy from pageable host memory
+  CUDA_TRY(c, cudaMemsetAsync(c->a.force_rebuild, 0x01, sizeof(int), c->stream));
   // every replica rebuilds (all-ones bytes: the largest displacement pattern)
   CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0xff, sizeof(unsigned long long) * (size_t)c->n_reps,
                               c->stream));
