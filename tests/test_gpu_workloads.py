@@ -98,6 +98,35 @@ def test_uneven_batch_mixed_precision(batch):
             assert rms_rel_err(sim.forces(r), g) <= 1e-5, s.name
 
 
+def test_replica_batch_256_sampled_replicas_at_full_size():
+    """The bench's batch workload at full size (256 replicas, 3.1 M vapour molecules, 16.8 M wall
+    atoms) in its launch configuration (atomic reaction forces, autotuned launch shape): six
+    replicas spread over the size range -- the smallest, the largest and four between -- against
+    the oracle one by one, forces per step to the FP64 bar and pair counts exact after 10 steps;
+    the double-float form alike, and the mixed form within its RMS bar."""
+    batch = W.replica_batch()
+    order = sorted(range(len(batch)), key=lambda r: batch[r].n_vapor)
+    sample = [order[k] for k in (0, 51, 102, 153, 204, 255)]
+    for precision in (md.MD_PREC_FP64, md.MD_PREC_DF64, md.MD_PREC_MIXED):
+        with md.Simulation(batch, precision=precision) as sim:
+            sim.set_tuning(force_accumulate=2)
+            sim.autotune(3)
+            sim.step(10)
+            for r in sample:
+                s = batch[r]
+                x, _ = sim.state(r)
+                p = oracle.make_params(s, POT)
+                g, _, stats = oracle.forces(p, x, s.wall, method=1, nthreads=0)
+                f = sim.forces(r)
+                if precision == md.MD_PREC_MIXED:
+                    assert rms_rel_err(f, g) <= 1e-5, (precision, s.name)
+                else:
+                    assert force_err(f, g) <= 1e-10, (precision, s.name)
+                    o, *_ = sim.observables(r)
+                    assert o["pairs_vv"] == stats["pairs_vv"], (precision, s.name)
+                    assert o["pairs_vw"] == stats["pairs_vw"], (precision, s.name)
+
+
 @pytest.mark.parametrize("precision,tol", [(md.MD_PREC_FP64, 1e-10), (md.MD_PREC_MIXED, 1e-5),
                                            (md.MD_PREC_DF64, 1e-10)])
 def test_pore_array_2m_every_force_and_per_pore_observables(precision, tol):
