@@ -1164,6 +1164,7 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
   for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     double fx = 0.0, fy = 0.0, fz = 0.0;
@@ -1200,7 +1201,9 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
     fx = group_sum<TPP>(fx);
     fy = group_sum<TPP>(fy);
     fz = group_sum<TPP>(fz);
-    if (live && sub == 0) {
+    // a molecule with no pair within the cutoff adds nothing (dilute vapour: about half of them)
+    const int found = group_sum<TPP>(cnt - cnt0);
+    if (live && sub == 0 && found) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
       atomicAdd(&a.frc[i].z, fz);
@@ -1935,6 +1938,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
   for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
@@ -1991,7 +1995,9 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
     const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
     const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
     const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
-    if (live && sub == 0) {
+    // a molecule with no pair within the cutoff adds nothing (dilute vapour: about half of them)
+    const int found = group_sum<TPP>(cnt - cnt0);
+    if (live && sub == 0 && found) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
       atomicAdd(&a.frc[i].z, fz);
@@ -2084,6 +2090,7 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
   for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+    const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
@@ -2124,7 +2131,9 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
     const double fx = group_sum<TPP>(widen_f32(sx) + widen_f32(cx));
     const double fy = group_sum<TPP>(widen_f32(sy) + widen_f32(cy));
     const double fz = group_sum<TPP>(widen_f32(sz) + widen_f32(cz));
-    if (live && sub == 0) {
+    // a molecule with no pair within the cutoff adds nothing (dilute vapour: about half of them)
+    const int found = group_sum<TPP>(cnt - cnt0);
+    if (live && sub == 0 && found) {
       atomicAdd(&a.frc[i].x, fx);
       atomicAdd(&a.frc[i].y, fy);
       atomicAdd(&a.frc[i].z, fz);
