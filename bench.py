@@ -53,13 +53,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # traffic is reported as null for any other workload, kernel or source
 NCU_TRAFFIC = {
     ("pore_shapes_4x20k", "k_forces_half_atomic<2>"):
-        {"bytes_per_launch": 17652224, "source_sha": "ac27226e2a97abbf"},
+        {"bytes_per_launch": 17651968, "source_sha": "9b0d841deedbbce2"},
     ("pore_shapes_4x20k", "k_forces_atomic_packed"):
-        {"bytes_per_launch": 19108864, "source_sha": "ac27226e2a97abbf"},
+        {"bytes_per_launch": 19108352, "source_sha": "9b0d841deedbbce2"},
     ("pore_shapes_4x20k", "k_forces_mixed_atomic<4>"):
-        {"bytes_per_launch": 18596608, "source_sha": "ac27226e2a97abbf"},
+        {"bytes_per_launch": 18596864, "source_sha": "9b0d841deedbbce2"},
     ("pore_shapes_4x20k", "k_forces_df_atomic<4>"):
-        {"bytes_per_launch": 17561600, "source_sha": "ac27226e2a97abbf"},
+        {"bytes_per_launch": 17542144, "source_sha": "9b0d841deedbbce2"},
 }
 
 
