@@ -23,9 +23,26 @@ def test_small_cylinder_system():
     assert min_periodic_distance(s.x0, s.x0, 20, 20, same=True) >= 0.9
     assert min_periodic_distance(s.x0, s.wall, 20, 20) >= 0.9
     assert np.abs(s.v0.mean(0)).max() < 1e-12
-    assert ((s.v0 ** 2).mean() - 1.0) < 0.1
+    assert abs((s.v0 ** 2).mean() - 1.0) < 0.1
     rxy = np.hypot(s.wall[:, 0], s.wall[:, 1])
     assert rxy.min() >= 4.0 and (np.abs(s.wall[:, 2]) < 5).all()
+
+
+def test_maxwell_velocities_statistics():
+    """Per component N(0, T0/m) minus the sample mean: zero mean exactly, each component's
+    variance within 4 standard errors of T0/m (standard error T0/m sqrt(2/n)), a Gaussian's
+    kurtosis 3 (standard error sqrt(24/n)), uncorrelated components; planar draws have vy = 0."""
+    n, T0, m = 200_000, 0.85, 1.0
+    v = W.maxwell_velocities(np.random.default_rng(11), n, T0, mass=m)
+    assert np.abs(v.mean(0)).max() < 1e-12
+    var = v.var(0)
+    assert np.all(np.abs(var - T0 / m) < 4 * (T0 / m) * np.sqrt(2.0 / n))
+    kurt = (v ** 4).mean(0) / var ** 2
+    assert np.all(np.abs(kurt - 3.0) < 4 * np.sqrt(24.0 / n))
+    c = np.corrcoef(v.T)
+    assert np.abs(c[np.triu_indices(3, 1)]).max() < 4 / np.sqrt(n)
+    vp = W.maxwell_velocities(np.random.default_rng(12), 1000, T0, planar=True)
+    assert (vp[:, 1] == 0.0).all() and np.abs(vp.mean(0)).max() < 1e-12
 
 
 def test_reproducible_by_seed():
