@@ -585,9 +585,14 @@ def run_ours(args):
             simd.close()
         if not args.no_cpu_baseline:
             v, st, pr, el, thr = oracle_rate(systems, args.cpu_seconds)
+            v1, st1, pr1, el1, _ = oracle_rate(systems, max(1.0, args.cpu_seconds / 5), nthreads=1)
             extra["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                                      "sample": f"{st} oracle MD steps (one system per step, in "
-                                               f"turn) in {el:.1f} s, {pr} pair interactions"}
+                                               f"turn) in {el:.1f} s, {pr} pair interactions",
+                                     "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                       "sample": f"{st1} oracle MD steps in "
+                                                                 f"{el1:.1f} s, {pr1} pair "
+                                                                 f"interactions"}}
     sim.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
