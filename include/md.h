@@ -194,7 +194,8 @@ typedef struct md_ctx md_ctx; /* opaque, library-owned */
  * On failure *out is NULL and md_last_error(NULL) describes the failure (per host thread).
  * Copies every host input. Builds (or takes) the wall, bins it once, builds the first lists and
  * evaluates the initial forces. Returns MD_EINVAL for inconsistent parameters (cutoff + skin not
- * below half the periodic box, non-positive sizes, molecules outside the box, r_ads > rc_w). */
+ * below half the periodic box, non-positive sizes, non-finite parameters, molecules outside the
+ * box, r_ads > rc_w). */
 md_status md_create(const md_system* sys, const md_potential* pot, void* stream, md_ctx** out);
 
 /* Create a context holding n_replicas independent systems that advance together: every kernel

@@ -94,6 +94,9 @@ double lj_u(double r2, double eps, double sigma) {
 
 md_status validate_potential(md_ctx* c, const md_potential* p) {
   if (!p) return fail(c, MD_EINVAL, "potential is NULL");
+  for (double q : {p->eps, p->sigma, p->mass, p->rc, p->eps_w, p->sigma_w, p->rc_w, p->skin,
+                   p->r_ads, p->bin_width})
+    if (!std::isfinite(q)) return fail(c, MD_EINVAL, "potential: a parameter is not finite");
   if (!(p->eps >= 0 && p->sigma > 0 && p->mass > 0 && p->rc > 0 && p->eps_w >= 0 &&
         p->sigma_w > 0 && p->rc_w > 0 && p->skin >= 0 && p->bin_width > 0))
     return fail(c, MD_EINVAL,
@@ -112,6 +115,9 @@ md_status validate_potential(md_ctx* c, const md_potential* p) {
 
 md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
   const std::string who = "replica " + std::to_string(r) + ": ";
+  for (double q : {s->Lx, s->Ly, s->Lz, s->dt, s->T0, s->tau_B, s->slab_half, s->lattice_a})
+    if (!std::isfinite(q))
+      return fail(c, MD_EINVAL, who + "box, dt, T0, tau_B, slab_half and lattice_a must be finite");
   if (!(s->Lx > 0 && s->Ly > 0 && s->Lz > 0 && s->dt > 0 && s->T0 >= 0 && s->slab_half >= 0))
     return fail(c, MD_EINVAL, who + "box, dt must be > 0; T0, slab_half >= 0");
   if (s->n_vapor < 0 || s->n_wall < 0 || s->n_pores < 0)
@@ -131,6 +137,8 @@ md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
   for (int q = 0; q < s->n_pores; ++q) {
     const md_pore& P = s->pores[q];
     if (P.kind < 1 || P.kind > 5) return fail(c, MD_EINVAL, who + "unknown pore kind");
+    for (double u : {P.cx, P.cy, P.r0, P.r1, P.r_cavity, P.width})
+      if (!std::isfinite(u)) return fail(c, MD_EINVAL, who + "pore parameters must be finite");
     if (P.kind == MD_PORE_CONE && !(s->slab_half > 0))
       return fail(c, MD_EINVAL, who + "a cone needs slab_half > 0");
     if (P.kind == MD_PORE_PRISM && !(P.r0 > 0 && P.r1 > 0))

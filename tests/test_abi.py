@@ -81,6 +81,10 @@ def small_system(**kw):
     (dict(dt=0.0), "dt"),
     (dict(thermostat_every=10, tau_B=0.01), "tau_B"),
     (dict(x0=np.array([[100.0, 0.0, 0.0]] * 20)), "outside the box"),
+    (dict(dt=float("inf")), "finite"),
+    (dict(T0=float("nan")), "finite"),
+    (dict(tau_B=float("nan")), "finite"),
+    (dict(pores=[W.Pore(W.PORE_CYLINDER, r0=float("nan"))]), "pore parameters must be finite"),
 ])
 def test_invalid_systems_rejected_before_any_gpu_work(lib, change, fragment):
     s = small_system(**change)
@@ -97,6 +101,10 @@ def test_invalid_potential_rejected(lib):
     assert ei.value.status == md.MD_EINVAL and "r_ads" in str(ei.value)
     with pytest.raises(md.MDError):
         md.Simulation(s, W.Potential(sigma=0.0))
+    for bad in (dict(eps=float("inf")), dict(skin=float("nan")), dict(rc=float("inf"))):
+        with pytest.raises(md.MDError) as ei:
+            md.Simulation(s, W.Potential(**bad))
+        assert ei.value.status == md.MD_EINVAL and "not finite" in str(ei.value)
 
 
 def test_unknown_pore_kind_rejected(lib):
