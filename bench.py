@@ -13,9 +13,10 @@ counted exactly by the force kernel over the timed steps -- divided by the summe
 durations of the steps (L2 flushed between steps by a 256 MB write outside the timed events).
 
 Also reported: MD steps/s, the mixed-precision form (FP32 pair terms) with its RMS force error
-against the FP64 form, the pair-force kernel's roofline (timed live with CUDA events), the FP64 CPU
-oracle timed on the host cores (cpu_baseline), and an end-to-end figure through the C ABI with host
-buffers (state upload, one step, force read-back).
+against the FP64 form, the pair-force kernel's roofline (timed live with CUDA events), the rebuild
+chain timed alone beside the list build's ncu DRAM figures, the FP64 CPU oracle timed on the host
+cores (cpu_baseline), and an end-to-end figure through the C ABI with host buffers (state upload,
+one step, force read-back).
 
 --impl reference times the FP64 CPU oracle on the same workload (one system advanced per step, in
 turn) and prints the same JSON line with "impl": "reference".
@@ -60,6 +61,15 @@ NCU_TRAFFIC = {
         {"bytes_per_launch": 18596864, "source_sha": "9b0d841deedbbce2"},
     ("pore_shapes_4x20k", "k_forces_df_atomic<4>"):
         {"bytes_per_launch": 17542144, "source_sha": "9b0d841deedbbce2"},
+}
+
+# k_list_build, the rebuild chain's dominant kernel, from one ncu capture (--set full) of the
+# relist that set_tuning triggers on the FP64 headline run (half rows): DRAM bytes per launch, its
+# duration there and its DRAM throughput as a fraction of the peak. Keyed like NCU_TRAFFIC.
+NCU_LIST_BUILD = {
+    ("pore_shapes_4x20k", "fp64", "atomic"):
+        {"dram_bytes_per_launch": 3202304, "duration_us": 51.7, "dram_frac_of_peak": 0.0078,
+         "source_sha": "9b0d841deedbbce2"},
 }
 
 
@@ -430,6 +440,38 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
             "flops_per_pair": FLOPS_PER_PAIR}
 
 
+def list_build(sim, torch, stream, flush, nlaunch, precision, accumulate, workload):
+    """The rebuild chain alone (md_rebuild_lists: cell sort, Verlet lists, processing order, for
+    every replica), timed with CUDA events on the library's stream, L2 flushed before each; beside
+    it the ncu figures of k_list_build, the chain's dominant kernel. That kernel is bound by
+    instruction issue, not by HBM: its DRAM traffic is a small fraction of the peak."""
+    evs = []
+    nvtx_push(torch, "rebuild")
+    for _ in range(nlaunch):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.rebuild_lists()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    nvtx_pop(torch)
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / nlaunch
+    nc = NCU_LIST_BUILD.get((workload, precision, accumulate))
+    if nc and nc.get("source_sha") != kernel_sha():
+        nc = None
+    return {"kernel": "k_list_build", "bound": "issue", "rebuild_chain_ms": ms,
+            "chains_timed": nlaunch,
+            "chain": "cell clear, count, scan, scatter, permute, list build, order (all replicas)",
+            "ncu": ({"dram_bytes_per_launch": nc["dram_bytes_per_launch"],
+                     "duration_us": nc["duration_us"],
+                     "dram_frac_of_peak": nc["dram_frac_of_peak"],
+                     "source": "profiles/list_build_integrate_pore_shapes_4x20k.md"}
+                    if nc else None)}
+
+
 def nve_drift(md, systems, precision, stream, accumulate, equil=200, steps=2000, every=50):
     """Energy drift without the thermostat: equilibrate with it, then run ``steps`` NVE steps and
     fit a line to the total energy per molecule against time (|slope|, in eps per molecule per
@@ -526,6 +568,10 @@ def run_ours(args):
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
                                      args.precision, args.accumulate, args.workload)
+        if not sim.tuning()["pair_method"] == 2:
+            extra["list_build"] = list_build(sim, torch, stream, flush,
+                                             max(3, args.roofline_launches // 5), args.precision,
+                                             args.accumulate, args.workload)
         extra["e2e"] = e2e(sim, systems, args.e2e_steps, pairs_per_step, torch)
         if not args.no_mixed and args.precision == "fp64":
             import oracle

@@ -254,6 +254,16 @@ md_status md_compute_forces(md_ctx* ctx);
  * reading forces or stepping. Asynchronous. */
 md_status md_pair_pass(md_ctx* ctx);
 
+/* Enqueue the rebuild chain alone for every replica, at the current positions: the counting sort
+ * of the vapour by cell, the Verlet lists with skin and the processing order (the FP64
+ * deterministic form also rebuilds its pair map). No forces are evaluated, and none change: the
+ * molecules' records, forces included, move to their new sorted places together, and every
+ * read-back is in caller order as before. Meant for timing the chain with events on the
+ * context's stream; md_step continues from it as from any rebuild, and n_rebuilds counts it.
+ * Asynchronous. MD_EINVAL in the all-pairs mode (pair_method 2), which keeps no lists; a list
+ * overflow found by the chain is reported by the next synchronising call, as in md_step. */
+md_status md_rebuild_lists(md_ctx* ctx);
+
 /* Host<->device bytes the library has copied for this context since creation (state uploads,
  * read-backs, status words). Either pointer may be NULL. */
 md_status md_transfer_bytes(const md_ctx* ctx, int64_t* h2d, int64_t* d2h);

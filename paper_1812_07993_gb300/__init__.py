@@ -100,6 +100,7 @@ _SIGNATURES = {
     "md_get_forces": (ctypes.c_int, [_CTX, ctypes.c_int32, _DP]),
     "md_compute_forces": (ctypes.c_int, [_CTX]),
     "md_pair_pass": (ctypes.c_int, [_CTX]),
+    "md_rebuild_lists": (ctypes.c_int, [_CTX]),
     "md_transfer_bytes": (ctypes.c_int, [_CTX, _I64P, _I64P]),
     "md_observables": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(md_obs), _I64P, _I64P,
                                       _I64P, _DP]),
@@ -337,6 +338,11 @@ class Simulation:
         """Enqueue the pair kernel alone, for timing it (md_pair_pass); call compute_forces
         before reading forces or stepping again."""
         _check(load_library().md_pair_pass(self.ctx), self.ctx)
+
+    def rebuild_lists(self):
+        """Enqueue the rebuild chain alone (cell sort, Verlet lists, processing order) for every
+        replica at the current positions (md_rebuild_lists); forces are left as they are."""
+        _check(load_library().md_rebuild_lists(self.ctx), self.ctx)
 
     def transfer_bytes(self):
         h, d = ctypes.c_int64(), ctypes.c_int64()

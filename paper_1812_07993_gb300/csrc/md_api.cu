@@ -1109,6 +1109,25 @@ md_status md_pair_pass(md_ctx* c) {
   return MD_OK;
 }
 
+md_status md_rebuild_lists(md_ctx* c) {
+  if (!c) return MD_EINVAL;
+  if (c->tun.all_pairs) return fail(c, MD_EINVAL, "the all-pairs mode keeps no lists");
+  md_status prev = device_status(c);
+  if (prev != MD_OK) return prev;
+  // every replica rebuilds (all-ones bytes: the largest displacement pattern)
+  CUDA_TRY(c, cudaMemsetAsync(c->a.force_rebuild, 0x01, sizeof(int), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0xff, sizeof(unsigned long long) * (size_t)c->n_reps,
+                              c->stream));
+  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+  // the current positions are now every molecule's reference: nothing is due (the flags a pair
+  // kernel clears after a chain)
+  CUDA_TRY(c, cudaMemsetAsync(c->a.force_rebuild, 0, sizeof(int), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0, sizeof(unsigned long long) * (size_t)c->n_reps,
+                              c->stream));
+  CUDA_TRY(c, cudaGetLastError());
+  return MD_OK;
+}
+
 md_status md_transfer_bytes(const md_ctx* c, int64_t* h2d, int64_t* d2h) {
   if (!c) return MD_EINVAL;
   if (h2d) *h2d = c->bytes_h2d;

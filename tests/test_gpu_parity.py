@@ -454,6 +454,51 @@ def test_rebuilds_happen_and_lists_stay_complete():
     assert o["pairs_vv"] == stats["pairs_vv"] and o["pairs_vw"] == stats["pairs_vw"]
 
 
+@pytest.mark.parametrize("precision,acc", [(md.MD_PREC_FP64, 1), (md.MD_PREC_FP64, 2),
+                                           (md.MD_PREC_MIXED, 2), (md.MD_PREC_DF64, 2)])
+def test_rebuild_lists_alone_keeps_the_state_and_the_run_goes_on(shapes, precision, acc):
+    """md_rebuild_lists (the chain the bench times) moves records, not values: state and forces
+    read back bit for bit; the next force evaluation on the new lists matches the oracle, the
+    rebuild is counted, and stepping goes on with forces exact against the oracle."""
+    s = shapes[:2]
+    tol = FORCE_TOL if precision != md.MD_PREC_MIXED else None
+    with md.Simulation(s, precision=precision) as sim:
+        sim.set_tuning(force_accumulate=acc)
+        sim.step(30)
+        x0, v0 = sim.state(-1)
+        f0 = sim.forces(-1)
+        n0 = sim.observables(0)[0]["n_rebuilds"]
+        sim.rebuild_lists()
+        x1, v1 = sim.state(-1)
+        np.testing.assert_array_equal(x1, x0)
+        np.testing.assert_array_equal(v1, v0)
+        np.testing.assert_array_equal(sim.forces(-1), f0)
+        assert sim.observables(0)[0]["n_rebuilds"] == n0 + 1
+        sim.compute_forces()
+        f2 = sim.forces(-1)
+        sim.step(20)
+        x3, _ = sim.state(-1)
+        f3 = sim.forces(-1)
+    k = 0
+    for r, sr in enumerate(s):
+        n = sr.n_vapor
+        for xs, fs in ((x0, f2), (x3, f3)):
+            g, _, _ = oracle.forces(oracle_params(sr), xs[k:k + n], sr.wall, method=1)
+            if tol is None:
+                assert rms_rel_err(fs[k:k + n], g) <= 1e-5
+            else:
+                assert force_err(fs[k:k + n], g) <= tol
+        k += n
+
+
+def test_rebuild_lists_is_refused_in_the_all_pairs_mode():
+    with md.Simulation(W.cylinder_pore_1k()) as sim:
+        sim.set_tuning(pair_method=2)
+        with pytest.raises(md.MDError) as ei:
+            sim.rebuild_lists()
+        assert ei.value.status == md.MD_EINVAL
+
+
 # ------------------------------------------------------------------------------------------ mixed
 
 
