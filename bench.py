@@ -24,6 +24,7 @@ turn) and prints the same JSON line with "impl": "reference".
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -101,6 +102,10 @@ def parse():
     ap.add_argument("--launch-mode", choices=["graph", "plain"], default="graph",
                     help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
                          "launch lists)")
+    ap.add_argument("--skin", default="",
+                    help="Verlet-list skin: a number, or 'auto' for the autotuner's choice "
+                         "(autotune.choose_skin); default: auto for replica_batch_256, whose "
+                         "definition leaves the skin to the autotuner, else 0.3")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
                     help="reaction forces by FP64 atomic adds (half list, both precisions), or "
                          "the bit-reproducible forms (FP64 slot-and-gather, mixed full list)")
@@ -338,9 +343,9 @@ def prec_enum(md, name):
     return {"fp64": md.MD_PREC_FP64, "mixed": md.MD_PREC_MIXED, "df64": md.MD_PREC_DF64}[name]
 
 
-def measure_precision(md, systems, precision, args, torch, stream, flush, world=1):
+def measure_precision(md, systems, precision, args, torch, stream, flush, world=1, potential=None):
     from paper_1812_07993_gb300 import autotune
-    sim = md.Simulation(systems, precision=precision, stream=stream)
+    sim = md.Simulation(systems, potential, precision=precision, stream=stream)
     sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
     sim.tune_info = None
     main = precision == prec_enum(md, args.precision)
@@ -548,11 +553,23 @@ def run_ours(args):
     assert stream.cuda_stream != 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     prec = prec_enum(md, args.precision)
+    from paper_1812_07993_gb300 import workloads as W
+    skin_arg = args.skin or ("auto" if args.workload == "replica_batch_256" else "0.3")
+    skin_choice = None
+    if skin_arg == "auto":
+        # the autotuner times whole MD steps for each candidate skin on fresh contexts (every
+        # candidate gives the same forces and pair counts) and keeps the fastest
+        from paper_1812_07993_gb300 import autotune
+        skin_choice = autotune.choose_skin(systems, precision=prec, stream=stream)
+        skin_choice["by"] = "autotune.choose_skin"
+        pot = dataclasses.replace(W.Potential(), skin=skin_choice["skin"])
+    else:
+        pot = dataclasses.replace(W.Potential(), skin=float(skin_arg))
 
     clocks = ClockSampler(local)
     clocks.start()
     sim, ms, pairs, launches = measure_precision(md, systems, prec, args, torch, stream, flush,
-                                                 world)
+                                                 world, potential=pot)
     clocks.stop()
     ms_job, pairs_job = job_totals(ms, pairs, world)
     value = pairs_job / (ms_job * 1e-3)
@@ -577,7 +594,7 @@ def run_ours(args):
             import oracle
             from paper_1812_07993_gb300 import workloads as W
             simm, msm, pairsm, _ = measure_precision(md, systems, md.MD_PREC_MIXED, args, torch,
-                                                     stream, flush)
+                                                     stream, flush, potential=pot)
             # RMS force error of both GPU forms against the FP64 oracle at the mixed run's state
             errs = []
             with md.Simulation(systems, stream=stream) as sim64:
@@ -606,7 +623,7 @@ def run_ours(args):
             # double-float pair terms: the same workload, steps and timing; force error against
             # the oracle and against the FP64 GPU form at the run's final state
             simd, msd, pairsd, _ = measure_precision(md, systems, md.MD_PREC_DF64, args, torch,
-                                                     stream, flush)
+                                                     stream, flush, potential=pot)
             errs, max_vs64 = [], 0.0
             with md.Simulation(systems, stream=stream) as sim64:
                 sim64.set_tuning(force_accumulate=2)
@@ -651,6 +668,8 @@ def run_ours(args):
                            "n_wall": sum(s.n_wall for s in systems),
                            "precision": args.precision,
                            "force_accumulate": args.accumulate,
+                           "skin": pot.skin,
+                           "skin_choice": skin_choice,
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "launch_mode": args.launch_mode,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},

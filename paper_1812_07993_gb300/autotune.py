@@ -14,7 +14,7 @@ import os
 import time
 from typing import Dict, Optional, Sequence
 
-from . import MD_PREC_FP64, Simulation, workloads
+from . import MD_PREC_FP64, MDError, Simulation, workloads
 
 
 def size_class(systems: Sequence["workloads.System"], precision: int) -> str:
@@ -66,30 +66,31 @@ def tune(sim: Simulation, trials: int = 15, cache_path: Optional[str] = None,
 
 
 def choose_skin(systems: Sequence["workloads.System"], potential: "workloads.Potential" = None,
-                precision: int = MD_PREC_FP64, skins=(0.2, 0.3, 0.4, 0.5), steps: int = 100,
-                warmup: int = 20, stream=None) -> Dict:
+                precision: int = MD_PREC_FP64, skins=(0.2, 0.3, 0.4, 0.5, 0.6, 0.8),
+                steps: int = 100, warmup: int = 20, stream=None) -> Dict:
     """Time ``steps`` MD steps (after ``warmup``) for each candidate skin on a fresh context with an
     autotuned launch shape; returns the skin with the most steps per second and the table. The skin
-    only trades list length against rebuild frequency: every candidate gives the same forces."""
+    only trades list length against rebuild frequency: every candidate gives the same forces. A
+    candidate the context refuses (box too small for its cells) or whose lists overflow their
+    capacity is left out, with its error in the table."""
     pot = potential or workloads.Potential()
     table = []
     for skin in skins:
         p = dataclasses.replace(pot, skin=skin)
         try:
-            sim = Simulation(systems, p, precision=precision, stream=stream)
-        except Exception as e:  # a skin too large for the box is simply not a candidate
+            with Simulation(systems, p, precision=precision, stream=stream) as sim:
+                sim.autotune(7)
+                sim.step(warmup)
+                sim.sync()
+                o0 = sim.observables(0)[0]
+                t0 = time.perf_counter()
+                sim.step(steps)
+                sim.sync()
+                dt = time.perf_counter() - t0
+                o1 = sim.observables(0)[0]
+        except MDError as e:
             table.append({"skin": skin, "error": str(e)})
             continue
-        with sim:
-            sim.autotune(7)
-            sim.step(warmup)
-            sim.sync()
-            o0 = sim.observables(0)[0]
-            t0 = time.perf_counter()
-            sim.step(steps)
-            sim.sync()
-            dt = time.perf_counter() - t0
-            o1 = sim.observables(0)[0]
         table.append({"skin": skin, "steps_per_s": steps / dt,
                       "rebuilds": o1["n_rebuilds"] - o0["n_rebuilds"]})
     ok = [r for r in table if "steps_per_s" in r]

@@ -246,3 +246,26 @@ def test_batched_replicas_evolve_as_they_would_alone():
         d[:, :2] -= np.array([s.Lx, s.Ly]) * np.round(d[:, :2] / np.array([s.Lx, s.Ly]))
         assert np.abs(d).max() <= 1e-9, s.name
         assert np.abs(v - together[r][1]).max() <= 1e-9, s.name
+
+
+def test_skin_choice_changes_speed_not_physics(batch):
+    """The skin is the autotuner's to pick: forces and pair counts do not depend on it (every
+    pair within the cutoff is listed at any skin), a larger skin rebuilds no more often, and
+    choose_skin returns one of the candidates with a timing for each."""
+    import dataclasses
+    systems = batch[:3]
+    forces, pairs = [], []
+    for skin in (0.2, 0.8):
+        pot = dataclasses.replace(W.Potential(), skin=skin)
+        with md.Simulation(systems, pot) as sim:
+            forces.append(sim.forces(-1))
+            o = [sim.observables(r)[0] for r in range(len(systems))]
+            pairs.append([(x["pairs_vv"], x["pairs_vw"]) for x in o])
+    rms = np.sqrt((forces[0] ** 2).sum(1).mean())
+    assert np.abs(forces[0] - forces[1]).max() <= 1e-12 * rms
+    assert pairs[0] == pairs[1]
+    got = autotune.choose_skin(systems, skins=(0.2, 0.8), steps=60, warmup=5)
+    assert got["skin"] in (0.2, 0.8)
+    rows = {r["skin"]: r for r in got["table"]}
+    assert all("steps_per_s" in rows[k] and rows[k]["steps_per_s"] > 0 for k in (0.2, 0.8))
+    assert rows[0.8]["rebuilds"] <= rows[0.2]["rebuilds"]
