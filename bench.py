@@ -104,8 +104,9 @@ def parse():
                          "launch lists)")
     ap.add_argument("--skin", default="",
                     help="Verlet-list skin: a number, or 'auto' for the autotuner's choice "
-                         "(autotune.choose_skin); default: auto for replica_batch_256, whose "
-                         "definition leaves the skin to the autotuner, else 0.3")
+                         "(autotune.choose_skin); default: auto for the workloads whose "
+                         "definition does not fix the skin (200k cylinder, 256-replica batch, "
+                         "2M pore array), else 0.3")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
                     help="reaction forces by FP64 atomic adds (half list, both precisions), or "
                          "the bit-reproducible forms (FP64 slot-and-gather, mixed full list)")
@@ -135,6 +136,10 @@ WORKLOADS = {
                        "1,000 molecules, 4,800 outside at a fifth of that density, T*=1.0, "
                        "Berendsen tau_B=0.5"),
 }
+
+# workloads whose definition leaves the Verlet skin open (the 4x20k pore shapes fix it at 0.3):
+# the bench lets the autotuner pick it
+SKIN_BY_AUTOTUNER = ("cylinder_pore_200k", "replica_batch_256", "pore_array_2m")
 
 
 def make_workload(name: str):
@@ -554,7 +559,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     prec = prec_enum(md, args.precision)
     from paper_1812_07993_gb300 import workloads as W
-    skin_arg = args.skin or ("auto" if args.workload == "replica_batch_256" else "0.3")
+    skin_arg = args.skin or ("auto" if args.workload in SKIN_BY_AUTOTUNER else "0.3")
     skin_choice = None
     if skin_arg == "auto":
         # the autotuner times whole MD steps for each candidate skin on fresh contexts (every
