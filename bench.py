@@ -142,6 +142,22 @@ WORKLOADS = {
 SKIN_BY_AUTOTUNER = ("cylinder_pore_200k", "replica_batch_256", "pore_array_2m")
 
 
+def bench_skin(skin_arg: str, rank: int, world: int, choose):
+    """The Verlet skin of this run and the record of its choice: a number as given (no record), or
+    with "auto" the choice ``choose()`` makes on rank 0, broadcast to every rank so that all
+    replicas run with one skin; 0.3 where no candidate worked."""
+    if skin_arg != "auto":
+        return float(skin_arg), None
+    choice = choose() if rank == 0 else None
+    if world > 1:
+        import torch.distributed as dist
+        box = [choice]
+        dist.broadcast_object_list(box, src=0)
+        choice = box[0]
+    skin = choice["skin"] if choice and choice.get("skin") is not None else 0.3
+    return skin, choice
+
+
 def make_workload(name: str):
     from paper_1812_07993_gb300 import workloads as W
     if name == "cylinder_pore_1k":
@@ -560,16 +576,16 @@ def run_ours(args):
     prec = prec_enum(md, args.precision)
     from paper_1812_07993_gb300 import workloads as W
     skin_arg = args.skin or ("auto" if args.workload in SKIN_BY_AUTOTUNER else "0.3")
-    skin_choice = None
-    if skin_arg == "auto":
+
+    def choose():
         # the autotuner times whole MD steps for each candidate skin on fresh contexts (every
         # candidate gives the same forces and pair counts) and keeps the fastest
         from paper_1812_07993_gb300 import autotune
-        skin_choice = autotune.choose_skin(systems, precision=prec, stream=stream)
-        skin_choice["by"] = "autotune.choose_skin"
-        pot = dataclasses.replace(W.Potential(), skin=skin_choice["skin"])
-    else:
-        pot = dataclasses.replace(W.Potential(), skin=float(skin_arg))
+        return dict(autotune.choose_skin(systems, precision=prec, stream=stream),
+                    by="autotune.choose_skin")
+
+    skin, skin_choice = bench_skin(skin_arg, rank, world, choose)
+    pot = dataclasses.replace(W.Potential(), skin=skin)
 
     clocks = ClockSampler(local)
     clocks.start()

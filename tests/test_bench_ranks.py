@@ -32,6 +32,42 @@ def _rank_main(rank, world, port, out):
     dist.destroy_process_group()
 
 
+def _skin_rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+
+    def choose():
+        if rank != 0:
+            raise AssertionError("only rank 0 runs the skin autotuner")
+        return {"skin": 0.6, "table": [{"skin": 0.6, "steps_per_s": 1.0}]}
+
+    out[rank] = bench.bench_skin("auto", rank, world, choose)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_rank_zeros_skin():
+    """With an autotuned skin, rank 0 chooses and every rank runs its replicas with that skin."""
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_skin_rank_main, args=(world, port, out), nprocs=world, join=True)
+        got = dict(out)
+    assert got[0][0] == got[1][0] == 0.6
+    assert got[0][1] == got[1][1] and got[1][1]["table"][0]["skin"] == 0.6
+
+
+def test_given_skin_and_no_usable_candidate():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.bench_skin("0.45", 0, 1, None) == (0.45, None)
+    skin, rec = bench.bench_skin("auto", 0, 1, lambda: {"skin": None, "table": []})
+    assert skin == 0.3 and rec == {"skin": None, "table": []}
+
+
 def test_two_gloo_ranks_take_the_slowest_time_and_the_sum_of_pairs():
     world = 2
     port = _free_port()
