@@ -189,7 +189,9 @@ typedef struct {
 
 typedef struct md_ctx md_ctx; /* opaque, library-owned */
 
-/* Create a context holding one replica on the current CUDA device.
+/* Create a context holding one replica on the current CUDA device: the system of Sec. 2 (vapour
+ * molecules under the Lennard-Jones potential, Eq. 2) around the pore walls of Sec. 4 (2D) and
+ * Sec. 5 (3D).
  * stream: a cudaStream_t on which all work is enqueued (NULL: a library-owned stream).
  * On failure *out is NULL and md_last_error(NULL) describes the failure (per host thread).
  * Copies every host input. Builds (or takes) the wall, bins it once, builds the first lists and
@@ -199,12 +201,14 @@ typedef struct md_ctx md_ctx; /* opaque, library-owned */
 md_status md_create(const md_system* sys, const md_potential* pot, void* stream, md_ctx** out);
 
 /* Create a context holding n_replicas independent systems that advance together: every kernel
- * launch covers all replicas (uneven sizes allowed). Same rules as md_create per replica. */
+ * launch covers all replicas (uneven sizes allowed). Same rules as md_create per replica. Each
+ * replica is a system of Sec. 2; batching them is not in the paper. */
 md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md_potential* pot,
                           void* stream, md_ctx** out);
 
 /* Replace the launch-shape knobs; takes effect at the next launch. Changing order_by_length
- * rebuilds the lists (synchronises). */
+ * rebuilds the lists (synchronises). The paper picks its threads per block by hand (Sec. 4 and
+ * Sec. 5); these knobs and md_get_tuning have no other counterpart there. */
 md_status md_set_tuning(md_ctx* ctx, const md_tuning* t);
 md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 
@@ -217,23 +221,26 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
  * NULL) receive the chosen shape and its median time in microseconds. Synchronises. */
 md_status md_autotune(md_ctx* ctx, int32_t trials, md_tuning* best, double* best_us);
 
-/* Enqueue n velocity-Verlet steps for every replica (asynchronous). Returns a sticky device
- * status found by earlier work, if any, without waiting for the GPU. */
+/* Enqueue n velocity-Verlet steps (Sec. 2; Figs. 1-4: steps 1-5 above) for every replica
+ * (asynchronous). Returns a sticky device status found by earlier work, if any, without waiting
+ * for the GPU. */
 md_status md_step(md_ctx* ctx, int64_t n);
 
-/* Wait for all enqueued work; returns the sticky device status. */
+/* Wait for all enqueued work; returns the sticky device status (no counterpart in the paper). */
 md_status md_sync(md_ctx* ctx);
 
-/* Copy replica state to caller-owned host arrays (3*n_vapor each, caller's molecule order).
+/* Copy replica state -- the positions and velocities of Sec. 2, Eq. 1 -- to caller-owned host
+ * arrays (3*n_vapor each, caller's molecule order).
  * replica = -1 copies every replica, concatenated in replica order (3 * total vapour each).
  * x: positions wrapped into the box; v: velocities; either may be NULL. The rows are put into
  * caller order on the device and copied with one cudaMemcpyAsync per array (pinned host memory
  * makes it a DMA at full link speed). Synchronises. */
 md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
 
-/* Overwrite replica state from host arrays (3*n_vapor each, caller's order). Positions must lie
- * inside the box (x, y in [-L/2, L/2), z in [-Lz/2, Lz/2]; a planar replica's y and vy must be
- * 0). replica = -1 sets every replica from arrays concatenated in replica order.
+/* Overwrite replica state -- the positions and velocities of Sec. 2, Eq. 1 -- from host arrays
+ * (3*n_vapor each, caller's order). Positions must lie inside the box (x, y in [-L/2, L/2), z in
+ * [-Lz/2, Lz/2]; a planar replica's y and vy must be 0). replica = -1 sets every replica from
+ * arrays concatenated in replica order.
  * - The rows go by one copy per array into device staging rows.
  * - A kernel checks every row there, then a kernel writes the records only if all rows passed.
  * - Lists are rebuilt and forces re-evaluated.
@@ -247,16 +254,17 @@ md_status md_set_state(md_ctx* ctx, int32_t replica, const double* x, const doub
  * Asynchronous; meant for timing the pair kernel in isolation. */
 md_status md_compute_forces(md_ctx* ctx);
 
-/* Enqueue the pair kernel alone -- the dominant kernel of the step (the FP64 half-list or atomic
- * pass, the all-pairs pass, or the mixed-precision pass) -- with no clearing, gather or kick, so
- * that its duration can be timed with events on the context's stream. It leaves the forces
+/* Enqueue the pair kernel alone (F1: Fig. 1, Eq. 2) -- the dominant kernel of the step (the FP64
+ * half-list or atomic pass, the all-pairs pass, or the mixed-precision pass) -- with no clearing,
+ * gather or kick, so that its duration can be timed with events on the context's stream. It leaves the forces
  * incomplete (or, in the atomic form, added twice): call md_compute_forces afterwards before
  * reading forces or stepping. Asynchronous. */
 md_status md_pair_pass(md_ctx* ctx);
 
-/* Enqueue the rebuild chain alone for every replica, at the current positions: the counting sort
- * of the vapour by cell, the Verlet lists with skin and the processing order (the FP64
- * deterministic form also rebuilds its pair map). No forces are evaluated, and none change: the
+/* Enqueue the rebuild chain alone for every replica, at the current positions. The chain is not
+ * in the paper, whose F1 sums over all particles (Fig. 1, Sec. 3): its cell and Verlet lists
+ * replace that sum. The chain is the counting sort of the vapour by cell, the Verlet lists with
+ * skin and the processing order (the FP64 deterministic form also rebuilds its pair map). No forces are evaluated, and none change: the
  * molecules' records, forces included, move to their new sorted places together, and every
  * read-back is in caller order as before. Meant for timing the chain with events on the
  * context's stream; md_step continues from it as from any rebuild, and n_rebuilds counts it.
@@ -265,11 +273,11 @@ md_status md_pair_pass(md_ctx* ctx);
 md_status md_rebuild_lists(md_ctx* ctx);
 
 /* Host<->device bytes the library has copied for this context since creation (state uploads,
- * read-backs, status words). Either pointer may be NULL. */
+ * read-backs, status words). Either pointer may be NULL. No counterpart in the paper. */
 md_status md_transfer_bytes(const md_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
-/* Copy the forces of the last evaluation (at the current positions) to host f (3*n_vapor; with
- * replica = -1, every replica concatenated in replica order). Synchronises. */
+/* Copy the forces of the last evaluation (Eq. 2, Fig. 1; at the current positions) to host f
+ * (3*n_vapor; with replica = -1, every replica concatenated in replica order). Synchronises. */
 md_status md_get_forces(md_ctx* ctx, int32_t replica, double* f);
 
 /* Observables of one replica at the current state. Fills *out; when non-NULL the arrays receive
@@ -305,23 +313,27 @@ md_status md_forces_noalloc(const md_potential* pot, double Lx, double Ly, doubl
                             const double* d_x, int64_t n_vapor, const double* d_wall,
                             int64_t n_wall, double* d_f, void* stream, char* err, int32_t err_len);
 
-/* Copy the wall atoms of a replica (3*n_wall doubles, as generated or given). */
+/* Copy the wall atoms of a replica (3*n_wall doubles, as generated or given): the fixed atoms of
+ * the pore walls of Sec. 4 and Sec. 5. */
 md_status md_get_wall(md_ctx* ctx, int32_t replica, double* wall_xyz);
 
-/* Number of replicas; sizes of one replica. */
+/* Sizes of one replica (no counterpart in the paper). */
 md_status md_get_sizes(const md_ctx* ctx, int32_t replica, int64_t* n_vapor, int64_t* n_wall,
                        int32_t* n_groups, int32_t* n_bins);
 
 /* Kernels the library has launched since creation, counted on the device (kernels inside a
- * graph's skipped conditional branches do not run and are not counted). Synchronises. */
+ * graph's skipped conditional branches do not run and are not counted). Synchronises. No
+ * counterpart in the paper. */
 int64_t md_kernel_launches(const md_ctx* ctx);
 
 /* Human-readable text of a status, and the last error message of a context (never NULL);
- * md_last_error(NULL) gives the last md_create / md_create_batch failure of the calling thread. */
+ * md_last_error(NULL) gives the last md_create / md_create_batch failure of the calling thread.
+ * No counterpart in the paper. */
 const char* md_status_string(md_status s);
 const char* md_last_error(const md_ctx* ctx);
 
-/* Free every resource of the context (synchronises its stream). NULL is ignored. */
+/* Free every resource of the context (synchronises its stream). NULL is ignored. No counterpart
+ * in the paper. */
 void md_destroy(md_ctx* ctx);
 
 #ifdef __cplusplus
