@@ -1,22 +1,25 @@
 #!/usr/bin/env python
-"""Throughput of the pore / water-vapour MD hot path on one GB300.
+"""Throughput and accuracy of the pore / water-vapour MD hot path on one GB300.
 
-Workload: four independent 40 x 40 x 80 sigma systems advanced together in one batch -- cylinder
-(r = 5), cone (r 3 -> 8 across the slab), slit (width 6) and ink-bottle (neck 3, cavity 8) pores
-through a simple-cubic wall slab |z| < 10, 20,000 vapour molecules each, reduced LJ units, rc = 2.5,
-skin 0.3, dt = 0.005, T* = 1.0 with velocity rescaling every 10 steps. One bench step = one MD step
-of all four systems (half-kick/drift/reflect, device-decided list rebuild, pair forces, half-kick,
-thermostat).
+Default workload (the configuration the metric's mixed-vs-FP64 comparison is defined on): one
+cylindrical pore of radius 10 sigma through a simple-cubic wall slab |z| < 30 (1,331,040 fixed wall
+atoms) in a 150 x 150 x 300 sigma box, 200,000 vapour molecules outside the slab, reduced LJ
+units, rc = 2.5, dt = 0.005, T* = 0.9 with velocity rescaling every 10 steps; the Verlet skin,
+which the configuration leaves open, is chosen by the autotuner. One bench step = one MD step
+(half-kick/drift/reflect, device-decided list rebuild, pair forces, half-kick, thermostat).
 
-value: pair interactions per second -- unique vapour-vapour plus vapour-wall pairs with r < rc,
-counted exactly by the force kernel over the timed steps -- divided by the summed CUDA-event
-durations of the steps (L2 flushed between steps by a 256 MB write outside the timed events).
+value: pair interactions per second of the FP64 form -- unique vapour-vapour plus vapour-wall
+pairs with r < rc, counted exactly by the force kernel over the timed steps -- divided by the
+summed CUDA-event durations of the steps (L2 flushed between steps by a 256 MB write outside the
+timed events).
 
-Also reported: MD steps/s, the mixed-precision form (FP32 pair terms) with its RMS force error
-against the FP64 form, the pair-force kernel's roofline (timed live with CUDA events), the rebuild
-chain timed alone beside the list build's ncu DRAM figures, the FP64 CPU oracle timed on the host
-cores (cpu_baseline), and an end-to-end figure through the C ABI with host buffers (state upload,
-one step, force read-back).
+Also reported: MD steps/s; the mixed-precision form (FP32 pair terms) and the double-float form
+with their speed-up over FP64 and their RMS force error against the FP64 oracle; the first ten
+steps from the initial state without thermostat (RMS force error of each form at its own
+positions after every step, total energy against the oracle's own trajectory); the NVE energy
+drift of the FP64 and mixed forms; the pair kernel's roofline (timed live with CUDA events); the
+rebuild chain timed alone; the FP64 CPU oracle timed on the host cores (cpu_baseline); and an
+end-to-end figure through the C ABI with host buffers (state upload, one step, force read-back).
 
 --impl reference times the FP64 CPU oracle on the same workload (one system advanced per step, in
 turn) and prints the same JSON line with "impl": "reference".
@@ -70,7 +73,8 @@ NCU_TRAFFIC = {
 NCU_LIST_BUILD = {
     ("pore_shapes_4x20k", "fp64", "atomic"):
         {"dram_bytes_per_launch": 3202304, "duration_us": 51.7, "dram_frac_of_peak": 0.0078,
-         "source_sha": "9b0d841deedbbce2"},
+         "source_sha": "9b0d841deedbbce2",
+         "source": "profiles/list_build_integrate_pore_shapes_4x20k.md"},
 }
 
 
@@ -89,16 +93,20 @@ def parse():
                     help="skip the comparison runs of the mixed and double-float forms")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--roofline-launches", type=int, default=50)
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pore_shapes_4x20k")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cylinder_pore_200k")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--force-tpp", type=int, default=0,
                     help="pin the pair kernel's lanes per molecule (32: the packed FP64 kernels) "
                          "instead of the autotuner's choice")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="with --force-tpp, the pair kernel's resident blocks per SM")
-    ap.add_argument("--nve-steps", type=int, default=0,
+    ap.add_argument("--nve-steps", type=int, default=2000,
                     help="with the mixed comparison, also the NVE energy drift of both GPU forms "
-                         "over this many steps (after 200 thermostatted ones)")
+                         "over this many steps (after 200 thermostatted ones); 0: skip")
+    ap.add_argument("--first-steps", type=int, default=10,
+                    help="with the mixed comparison, the accuracy of every form over this many "
+                         "steps from the initial state without thermostat, against the oracle; "
+                         "0: skip")
     ap.add_argument("--launch-mode", choices=["graph", "plain"], default="graph",
                     help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
                          "launch lists)")
@@ -494,7 +502,7 @@ def list_build(sim, torch, stream, flush, nlaunch, precision, accumulate, worklo
             "ncu": ({"dram_bytes_per_launch": nc["dram_bytes_per_launch"],
                      "duration_us": nc["duration_us"],
                      "dram_frac_of_peak": nc["dram_frac_of_peak"],
-                     "source": "profiles/list_build_integrate_pore_shapes_4x20k.md"}
+                     "source": nc["source"]}
                     if nc else None)}
 
 
@@ -525,6 +533,50 @@ def nve_drift(md, systems, precision, stream, accumulate, equil=200, steps=2000,
     fit = np.polyfit(t, e, 1)
     return {"drift": abs(float(fit[0])), "fluctuation": float(np.std(e - np.polyval(fit, t))),
             "unit": "eps per molecule per tau", "steps": steps}
+
+
+def first_steps(md, systems, potential, stream, nsteps):
+    """Accuracy over the first ``nsteps`` steps from the initial state with the thermostat off
+    (NVE), per form: after every step, the RMS force error sqrt(sum |F - F_oracle|^2 / sum
+    |F_oracle|^2) against the FP64 oracle's forces at the form's own positions, and the total
+    energy per molecule against the oracle's own NVE trajectory from the same state. Reported:
+    the largest of each over the steps, beside the oracle's own energy change over them."""
+    import numpy as np
+    import oracle
+    nve = [dataclasses.replace(s, thermostat_every=0) for s in systems]
+    n = sum(s.n_vapor for s in nve)
+    params = [oracle.make_params(s, potential) for s in nve]
+    e_or = np.zeros(nsteps)
+    e0 = 0.0
+    for s, p in zip(nve, params):
+        st = oracle.State(p, s.x0, s.v0, s.wall, method=1, nthreads=0, pores=s.pores)
+        e0 += oracle.kinetic(p, s.v0) + st.stats["pe_vv"] + st.stats["pe_vw"]
+        ke, pe = st.run(nsteps)
+        e_or += ke + pe
+    e_or /= n
+    out = {"steps": nsteps, "thermostat": "off",
+           "oracle_energy_change_per_molecule": float(e_or[-1] - e0 / n)}
+    for name, prec in (("fp64", md.MD_PREC_FP64), ("mixed", md.MD_PREC_MIXED),
+                       ("df64", md.MD_PREC_DF64)):
+        errs, dev = [], []
+        with md.Simulation(nve, potential, precision=prec, stream=stream) as sim:
+            sim.set_tuning(force_accumulate=2)
+            for k in range(nsteps):
+                sim.step(1)
+                num = den = etot = 0.0
+                for r, (s, p) in enumerate(zip(nve, params)):
+                    x, _ = sim.state(r)
+                    g, _, _ = oracle.forces(p, x, s.wall, method=1, nthreads=0)
+                    f = sim.forces(r)
+                    num += float(((f - g) ** 2).sum())
+                    den += float((g ** 2).sum())
+                    o = sim.observables(r)[0]
+                    etot += o["ke"] + o["pe"]
+                errs.append(math.sqrt(num / den))
+                dev.append(abs(etot / n - float(e_or[k])))
+        out[name] = {"rms_force_err_max": max(errs), "rms_force_err_last": errs[-1],
+                     "energy_dev_per_molecule_max": max(dev)}
+    return out
 
 
 def e2e(sim, systems, nsteps, pairs_per_step, torch):
@@ -629,6 +681,8 @@ def run_ours(args):
                     errs.append((((fm - g) ** 2).sum(), ((f64 - g) ** 2).sum(), (g ** 2).sum()))
             den = sum(e[2] for e in errs)
             vm = pairsm / (msm * 1e-3)
+            if args.first_steps > 0:
+                extra["first_steps"] = first_steps(md, systems, pot, stream, args.first_steps)
             if args.nve_steps > 0:
                 extra["nve_drift"] = {
                     "fp64": nve_drift(md, systems, md.MD_PREC_FP64, stream, args.accumulate,
@@ -639,7 +693,10 @@ def run_ours(args):
                               "speedup_vs_fp64": vm / value,
                               "rms_force_err": math.sqrt(sum(e[0] for e in errs) / den),
                               "fp64_rms_force_err": math.sqrt(sum(e[1] for e in errs) / den),
-                              "md_steps_per_s": args.steps / (msm * 1e-3)}
+                              "rms_force_err_at": "the mixed run's final state (after the timed "
+                                                  "steps), both GPU forms at the same positions",
+                              "md_steps_per_s": args.steps / (msm * 1e-3),
+                              "tuning": (simm.tune_info or {}).get("tuning")}
             simm.close()
             # double-float pair terms: the same workload, steps and timing; force error against
             # the oracle and against the FP64 GPU form at the run's final state

@@ -10,6 +10,7 @@
 // Limits: n_vapor + n_wall <= kNaMaxAtoms and at most kNaMaxCells cells of side >= max(rc, rc_w)
 // (at least 3 across x and y). Every call reuses the same scratch: calls that overlap on the GPU
 // (on different streams, or from different host threads) race with each other and must not.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -60,9 +61,17 @@ __device__ __forceinline__ int na_coord(double u, double half, double l, int nc)
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// periodic wrap of an x or y coordinate into [-L/2, L/2); a coordinate already inside is returned
+// unchanged (bit for bit), so in-box inputs give the same cells and distances as without the wrap
+__device__ __forceinline__ double na_wrap(double u, double L, double half) {
+  if (u >= half || u < -half) u -= L * floor((u + half) / L);
+  return u;
+}
+
+// cell of a point: x and y wrapped periodically first, z (walls at +-Lz/2) clamped into the grid
 __device__ __forceinline__ int na_cell(const NaGeom& g, const double* p) {
-  const int ix = na_coord(p[0], g.hx, g.lx, g.nx);
-  const int iy = na_coord(p[1], g.hy, g.ly, g.ny);
+  const int ix = na_coord(na_wrap(p[0], g.Lx, g.hx), g.hx, g.lx, g.nx);
+  const int iy = na_coord(na_wrap(p[1], g.Ly, g.hy), g.hy, g.ly, g.ny);
   const int iz = na_coord(p[2], g.hz, g.lz, g.nz);
   return (iz * g.ny + iy) * g.nx + ix;
 }
@@ -143,7 +152,8 @@ __global__ void k_na_forces(NaScratch s, NaGeom g, const double* __restrict__ x,
                             const double* __restrict__ w, double* __restrict__ f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  const double xi = x[3 * (size_t)i], yi = x[3 * (size_t)i + 1], zi = x[3 * (size_t)i + 2];
+  const double xi = na_wrap(x[3 * (size_t)i], g.Lx, g.hx);
+  const double yi = na_wrap(x[3 * (size_t)i + 1], g.Ly, g.hy), zi = x[3 * (size_t)i + 2];
   const int c = s.cell[i];
   const int ix = c % g.nx, iy = (c / g.nx) % g.ny, iz = c / (g.nx * g.ny);
   double fx = 0.0, fy = 0.0, fz = 0.0;
@@ -158,8 +168,8 @@ __global__ void k_na_forces(NaScratch s, NaGeom g, const double* __restrict__ x,
         for (int k = s.start_v[cn]; k < s.start_v[cn + 1]; ++k) {
           const int j = s.sorted[k];
           if (j == i) continue;
-          const double ddx = na_image(xi - x[3 * (size_t)j], g.Lx);
-          const double ddy = na_image(yi - x[3 * (size_t)j + 1], g.Ly);
+          const double ddx = na_image(xi - na_wrap(x[3 * (size_t)j], g.Lx, g.hx), g.Lx);
+          const double ddy = na_image(yi - na_wrap(x[3 * (size_t)j + 1], g.Ly, g.hy), g.Ly);
           const double ddz = zi - x[3 * (size_t)j + 2];
           const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
           if (r2 < g.rc2) {
@@ -172,8 +182,8 @@ __global__ void k_na_forces(NaScratch s, NaGeom g, const double* __restrict__ x,
         }
         for (int k = s.start_w[cn]; k < s.start_w[cn + 1]; ++k) {
           const int j = s.sorted[g.n + k];
-          const double ddx = na_image(xi - w[3 * (size_t)j], g.Lx);
-          const double ddy = na_image(yi - w[3 * (size_t)j + 1], g.Ly);
+          const double ddx = na_image(xi - na_wrap(w[3 * (size_t)j], g.Lx, g.hx), g.Lx);
+          const double ddy = na_image(yi - na_wrap(w[3 * (size_t)j + 1], g.Ly, g.hy), g.Ly);
           const double ddz = zi - w[3 * (size_t)j + 2];
           const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
           if (r2 < g.rcw2) {
@@ -231,8 +241,13 @@ extern "C" md_status md_forces_noalloc(const md_potential* pot, double Lx, doubl
                                        int32_t err_len) {
   if (err && err_len > 0) err[0] = '\0';
   if (!pot) return na_fail(err, err_len, "potential is NULL");
+  // the same rules (and message) as md_create for the fields this entry point reads
+  for (double q : {pot->eps, pot->sigma, pot->mass, pot->rc, pot->eps_w, pot->sigma_w, pot->rc_w})
+    if (!std::isfinite(q)) return na_fail(err, err_len, "potential: a parameter is not finite");
   if (!(pot->sigma > 0 && pot->sigma_w > 0 && pot->rc > 0 && pot->rc_w > 0))
     return na_fail(err, err_len, "sigma, sigma_w, rc, rc_w must be > 0");
+  if (!(std::isfinite(Lx) && std::isfinite(Ly) && std::isfinite(Lz)))
+    return na_fail(err, err_len, "box: a side is not finite");
   if (!(Lx > 0 && Ly > 0 && Lz > 0)) return na_fail(err, err_len, "box must be positive");
   if (n_vapor < 0 || n_wall < 0) return na_fail(err, err_len, "negative count");
   if ((n_vapor > 0 && (!d_x || !d_f)) || (n_wall > 0 && !d_wall))
@@ -280,6 +295,18 @@ extern "C" md_status md_forces_noalloc(const md_potential* pot, double Lx, doubl
   g.b6w = 24.0 * pot->eps_w * w6;
   const NaScratch s = carve(base);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  // an error left by the caller's own earlier work stays theirs: report it without clearing it,
+  // so that the error read after the launches below is this call's
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    if (err && err_len > 0) {
+      char msg[200];
+      std::snprintf(msg, sizeof msg, "a CUDA error was pending before this call (left set): %s",
+                    cudaGetErrorString(pending));
+      na_fail(err, err_len, msg);
+    }
+    return MD_ECUDA;
+  }
   const int atoms = g.n + g.nw;
   k_na_clear<<<(g.ncell + 255) / 256, 256, 0, cs>>>(s, g.ncell);
   k_na_count<<<(atoms + 255) / 256, 256, 0, cs>>>(s, g, d_x, d_wall);
