@@ -115,6 +115,9 @@ def parse():
                          "(autotune.choose_skin); default: auto for the workloads whose "
                          "definition does not fix the skin (200k cylinder, 256-replica batch, "
                          "2M pore array), else 0.3")
+    ap.add_argument("--pair-method", choices=["auto", "lists", "cells"], default="auto",
+                    help="the pair kernel: auto (the autotuner picks between the Verlet-list walk "
+                         "and the cell-tiled kernel, atomic form), lists, or cells")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
                     help="reaction forces by FP64 atomic adds (half list, both precisions), or "
                          "the bit-reproducible forms (FP64 slot-and-gather, mixed full list)")
@@ -376,6 +379,8 @@ def measure_precision(md, systems, precision, args, torch, stream, flush, world=
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, potential, precision=precision, stream=stream)
     sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
+    if args.pair_method != "auto":     # the autotuner then times that method's shapes only
+        sim.set_tuning(pair_method=3 if args.pair_method == "cells" else 1)
     sim.tune_info = None
     main = precision == prec_enum(md, args.precision)
     if args.force_tpp and main:   # the pin is the headline run's; the comparison run is tuned
@@ -432,6 +437,8 @@ def pair_kernel_name(sim, precision, accumulate):
     molecule as the template argument, as ncu names it)."""
     tpp = sim.tuning()["force_tpp"]
     atomic = accumulate == "atomic"
+    if sim.tuning()["pair_method"] == 3:
+        return "k_forces_cells<%d, 0>" % {"fp64": 0, "mixed": 1, "df64": 2}[precision]
     if precision == "df64":
         return f"k_forces_df_atomic<{tpp}>" if atomic else f"k_forces_df<0, {tpp}>"
     if precision == "fp64":
@@ -493,12 +500,15 @@ def list_build(sim, torch, stream, flush, nlaunch, precision, accumulate, worklo
     nvtx_pop(torch)
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in evs) / nlaunch
+    cells = sim.tuning()["pair_method"] == 3
     nc = NCU_LIST_BUILD.get((workload, precision, accumulate))
-    if nc and nc.get("source_sha") != kernel_sha():
+    if cells or (nc and nc.get("source_sha") != kernel_sha()):
         nc = None
-    return {"kernel": "k_list_build", "bound": "issue", "rebuild_chain_ms": ms,
-            "chains_timed": nlaunch,
-            "chain": "cell clear, count, scan, scatter, permute, list build, order (all replicas)",
+    return {"kernel": "k_cell_count" if cells else "k_list_build", "bound": "issue",
+            "rebuild_chain_ms": ms, "chains_timed": nlaunch,
+            "chain": ("cell clear, count, scan, scatter, permute (all replicas; the cell method "
+                      "builds no lists)" if cells else
+                      "cell clear, count, scan, scatter, permute, list build, order (all replicas)"),
             "ncu": ({"dram_bytes_per_launch": nc["dram_bytes_per_launch"],
                      "duration_us": nc["duration_us"],
                      "dram_frac_of_peak": nc["dram_frac_of_peak"],
@@ -658,7 +668,7 @@ def run_ours(args):
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
                                      args.precision, args.accumulate, args.workload)
-        if not sim.tuning()["pair_method"] == 2:
+        if sim.tuning()["pair_method"] != 2:
             extra["list_build"] = list_build(sim, torch, stream, flush,
                                              max(3, args.roofline_launches // 5), args.precision,
                                              args.accumulate, args.workload)

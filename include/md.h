@@ -52,7 +52,9 @@ typedef enum {
   MD_ENOMEM = 2,     /* a device or host allocation failed */
   MD_ECUDA = 3,      /* a CUDA runtime call failed */
   MD_EOVERFLOW = 4,  /* a neighbour list or cell exceeded its capacity */
-  MD_EUNSTABLE = 5,  /* non-finite position or a molecule jumped further than the list skin */
+  MD_EUNSTABLE = 5,  /* a molecule left the box after reflection and wrap, or its position became
+                        non-finite (a molecule that moves more than skin/2 between list builds
+                        is not an error: the lists are rebuilt within the same step) */
   MD_ETIMEOUT = 6    /* a bounded device spin wait gave up */
 } md_status;
 
@@ -161,10 +163,15 @@ typedef struct {
                               step is deferred into the next step's first); the summation order
                               varies from run to run, so results agree with mode 1 to rounding
                               only. Changing it rebuilds the lists (synchronises). */
-  int32_t pair_method;     /* FP64 only. 1: Verlet lists (default); 2: every pair every step, one
+  int32_t pair_method;     /* 1: Verlet lists (default); 2 (FP64 only): every pair every step, one
                               thread per molecule summing over all molecules and wall atoms of
                               its replica (the paper's F1 form, Sec. 3, Fig. 1; O(N^2), for small
-                              systems). Same pair set and forces; no list rebuilds while on. */
+                              systems), no list rebuilds while on; 3: no Verlet lists -- a warp
+                              stages the FP32 offsets of a chunk's 27 neighbour cells in shared
+                              memory, screens every staged candidate, queues the pairs that may lie
+                              within the cutoff and evaluates them with every lane busy, reaction
+                              forces by FP64 atomic adds (force_accumulate 2 only); the rebuild is
+                              then the cell sort alone. Same pair set and forces in every method. */
 } md_tuning;
 
 typedef struct {
@@ -212,13 +219,17 @@ md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md
 md_status md_set_tuning(md_ctx* ctx, const md_tuning* t);
 md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 
-/* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 2 and 8): time
+/* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 7 and 12): time
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
  * force_tpp {1,2,4,8,16, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
- * x order_by_length {on,off} -- with CUDA events on the context's stream (median of `trials`
- * launches each, trials clamped to [3, 101]), then apply the fastest. Positions and velocities
- * are unchanged; forces are recomputed at the same positions. *best and *best_us (either may be
- * NULL) receive the chosen shape and its median time in microseconds. Synchronises. */
+ * x order_by_length {on,off} on the Verlet lists, and, in the atomic form (force_accumulate 2),
+ * the cell method (pair_method 3) x force_blocks_per_sm {1,2,4} x force_block {128,256}. Once the
+ * caller has set pair_method with md_set_tuning, the tuner keeps that method and times its shapes
+ * alone -- with
+ * CUDA events on the context's stream (median of `trials` launches each, trials clamped to
+ * [3, 101]), then apply the fastest. Positions and velocities are unchanged; forces are recomputed
+ * at the same positions. *best and *best_us (either may be NULL) receive the chosen shape and its
+ * median time in microseconds. Synchronises. */
 md_status md_autotune(md_ctx* ctx, int32_t trials, md_tuning* best, double* best_us);
 
 /* Enqueue n velocity-Verlet steps (Sec. 2; Figs. 1-4: steps 1-5 above) for every replica
@@ -239,8 +250,8 @@ md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
 
 /* Overwrite replica state -- the positions and velocities of Sec. 2, Eq. 1 -- from host arrays
  * (3*n_vapor each, caller's order). Positions must lie inside the box (x, y in [-L/2, L/2), z in
- * [-Lz/2, Lz/2]; a planar replica's y and vy must be 0). replica = -1 sets every replica from
- * arrays concatenated in replica order.
+ * [-Lz/2, Lz/2]; a planar replica's y and vy must be 0) and velocities must be finite.
+ * replica = -1 sets every replica from arrays concatenated in replica order.
  * - The rows go by one copy per array into device staging rows.
  * - A kernel checks every row there, then a kernel writes the records only if all rows passed.
  * - Lists are rebuilt and forces re-evaluated.
@@ -264,7 +275,8 @@ md_status md_pair_pass(md_ctx* ctx);
 /* Enqueue the rebuild chain alone for every replica, at the current positions. The chain is not
  * in the paper, whose F1 sums over all particles (Fig. 1, Sec. 3): its cell and Verlet lists
  * replace that sum. The chain is the counting sort of the vapour by cell, the Verlet lists with
- * skin and the processing order (the FP64 deterministic form also rebuilds its pair map). No forces are evaluated, and none change: the
+ * skin and the processing order (the FP64 deterministic form also rebuilds its pair map; the cell
+ * method, pair_method 3, has the counting sort alone). No forces are evaluated, and none change: the
  * molecules' records, forces included, move to their new sorted places together, and every
  * read-back is in caller order as before. Meant for timing the chain with events on the
  * context's stream; md_step continues from it as from any rebuild, and n_rebuilds counts it.
@@ -300,8 +312,12 @@ md_status md_observables(md_ctx* ctx, int32_t replica, md_obs* out, int64_t* occ
  * eps/sigma/rc and eps_w/sigma_w/rc_w of *pot, FP64) on n_vapor molecules at d_x from each other
  * and from n_wall fixed wall atoms at d_wall, in a box Lx x Ly x Lz centred at the origin
  * (periodic x, y). d_x (3*n_vapor), d_wall (3*n_wall) and d_f (3*n_vapor) are caller-owned DEVICE
- * arrays, xyz interleaved; positions must lie inside the box. Work is enqueued on `stream`
- * (NULL = legacy default stream) and is asynchronous.
+ * arrays, xyz interleaved. z must lie in [-Lz/2, Lz/2] (a z outside is binned into the nearest
+ * edge cell); x and y outside [-L/2, L/2) are wrapped periodically before binning and in the
+ * distances. Work is enqueued on `stream` (NULL = legacy default stream) and is asynchronous.
+ * Non-finite box sides or potential parameters give MD_EINVAL. A CUDA error already pending on
+ * the calling thread (from the caller's own earlier work) makes the call return MD_ECUDA before
+ * any launch, and is left set for the caller.
  * Scratch: a fixed array of about 4 MB inside the library, reserved on every GPU that loads the
  * library until the process exits. Limits: n_vapor + n_wall <= 262144 atoms and at most 65536
  * cells of side >= max(rc, rc_w), with at least 3 cells across x and y; larger inputs return

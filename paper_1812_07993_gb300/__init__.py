@@ -310,8 +310,8 @@ class Simulation:
                    use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0):
         """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
-        deterministic gather, 2 atomic reaction forces; pair_method (FP64): 1 Verlet lists,
-        2 all pairs."""
+        deterministic gather, 2 atomic reaction forces; pair_method: 1 Verlet lists, 2 all pairs
+        (FP64), 3 cell-tiled kernel without lists (atomic reaction forces)."""
         t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
                       steps_per_graph, force_accumulate, pair_method)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)

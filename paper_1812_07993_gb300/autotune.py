@@ -3,7 +3,7 @@
 The timing of launch shapes runs in the library (``md_autotune``: CUDA events around the pair-force
 evaluation for every candidate shape); this module keys the result by a size class and caches it in
 a small JSON file, and chooses the skin by timing whole MD steps on fresh contexts. The paper's
-counterpart is its manual scan of threads per block (Sec. 4 and Sec. 5, Figs. 2 and 8).
+counterpart is its manual scan of threads per block (Sec. 4 and Sec. 5, Figs. 7 and 12).
 """
 from __future__ import annotations
 
@@ -49,7 +49,9 @@ def tune(sim: Simulation, trials: int = 15, cache_path: Optional[str] = None,
     if key in cache:
         t = cache[key]["tuning"]
         sim.set_tuning(force_block=t["force_block"], force_blocks_per_sm=t["force_blocks_per_sm"],
-                       force_tpp=t["force_tpp"], order_by_length=t["order_by_length"])
+                       force_tpp=t["force_tpp"], order_by_length=t["order_by_length"],
+                       pair_method=t.get("pair_method", 0) if t.get("pair_method") in (1, 3)
+                       else 0)
         return {"tuning": t, "us": cache[key]["us"], "cached": True,
                 "seconds": time.perf_counter() - t0, "size_class": key}
     t, us = sim.autotune(trials)

@@ -42,6 +42,7 @@ struct md_ctx {
   int64_t steps_done = 0;
   int64_t bytes_h2d = 0, bytes_d2h = 0;
   int use_graph = 1, steps_per_graph = 10;
+  bool method_chosen = false;       // the caller set pair_method: the autotuner keeps it
   cudaGraphExec_t graph_exec = nullptr;
   int graph_steps = 0;
   size_t prof_total = 0, groups_total = 0, pores_total = 0;
@@ -279,19 +280,20 @@ md_status sync_status(md_ctx* c) {
 // refresh the FP32 cell-local offsets for the kernels that screen or compute with them
 int integrate_flags(const md_ctx* c) {
   int f = 0;
-  if (c->tun.atomic_acc) f |= kIntZeroForces;
-  if (c->mixed || c->tun.tpp_fp64 == 32) f |= kIntLocalOffsets;
+  if (c->tun.atomic_acc || c->tun.cells) f |= kIntZeroForces;
+  if (c->mixed || c->tun.tpp_fp64 == 32 || c->tun.cells) f |= kIntLocalOffsets;
   if (c->tun.df64) f |= kIntLocalOffsets | kIntLocalOffsetsLo;
   return f;
 }
 
-// One step with plain launches: the rebuild and thermostat kernels always launch and return at
-// once when the device decides they have nothing to do.
+// One step with plain launches: the rebuild kernels always launch and return at once when the
+// device decides they have nothing to do. A thermostat step's scaling is paid by the next step's
+// first kernel (or by launch_settle before a read).
 void enqueue_step(md_ctx* c) {
-  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, integrate_flags(c), c->stream);
+  launch_integrate_first(c->a, c->pot, c->mixed, StepConds{}, integrate_flags(c), c->tun,
+                         c->stream);
   if (!c->tun.all_pairs) launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
   launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
-  launch_thermostat(c->a, c->pot, c->stream);
 }
 
 md_status rebuild_and_forces(md_ctx* c) {
@@ -341,9 +343,9 @@ cudaError_t add_conditional(md_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle
   return cudaStreamEndCapture(c->aux, &out);
 }
 
-// Capture `steps` MD steps as one graph. The rebuild chain and the thermostat sit in conditional
-// nodes whose condition the last block of k_integrate_first sets, so steps without a rebuild or a
-// thermostat launch only the integrate and force kernels.
+// Capture `steps` MD steps as one graph. The rebuild chain sits in a conditional node whose
+// condition the last block of k_integrate_first sets, so steps without a rebuild launch only the
+// integrate and force kernels; the thermostat lives inside the integrate kernel.
 md_status build_graph(md_ctx* c, int steps) {
   destroy_graph(c);
   if (!c->aux) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
@@ -358,18 +360,14 @@ md_status build_graph(md_ctx* c, int steps) {
     sc.has_rebuild = c->tun.all_pairs ? 0 : 1;
     if (sc.has_rebuild)
       e = cudaGraphConditionalHandleCreate(&sc.rebuild, g, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess)
-      e = cudaGraphConditionalHandleCreate(&sc.thermo, g, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) break;
-    launch_integrate_first(c->a, c->pot, c->mixed, sc, integrate_flags(c), c->stream);
+    launch_integrate_first(c->a, c->pot, c->mixed, sc, integrate_flags(c), c->tun, c->stream);
     if (sc.has_rebuild)
       e = add_conditional(c, g, sc.rebuild, [&](cudaStream_t s) {
         launch_rebuild(c->a, c->pot, c->tun, c->mixed, s);
       });
     if (e != cudaSuccess) break;
     launch_forces(c->a, c->pot, c->mixed, false, true, c->tun, c->stream);
-    e = add_conditional(c, g, sc.thermo,
-                        [&](cudaStream_t s) { launch_thermostat(c->a, c->pot, s); });
   }
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
@@ -414,7 +412,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     c->own_stream = true;
   }
   {
-    const cudaError_t e = configure_kernels();
+    const cudaError_t e = configure_kernels(&c->tun.integrate_blocks_per_sm);
     if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
   }
   c->n_reps = n_reps;
@@ -596,6 +594,30 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     }
   }
 
+  // rows of cells (the cell method's work units) and, per cell, the wall atoms of its 27-cell
+  // neighbourhood (x and y periodic, z bounded)
+  std::vector<int32_t> row_cell, wnear(ncell_tot, 0);
+  for (int r = 0; r < n_reps; ++r) {
+    const RepDev& R = c->reps[r];
+    for (int iz = 0; iz < R.ncz; ++iz)
+      for (int iy = 0; iy < R.ncy; ++iy) {
+        row_cell.push_back(R.cell_off + (iz * R.ncy + iy) * R.ncx);
+        for (int ix = 0; ix < R.ncx; ++ix) {
+          int32_t tot = 0;
+          for (int dz = -1; dz <= 1; ++dz) {
+            const int jz = iz + dz;
+            if (jz < 0 || jz >= R.ncz) continue;
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
+                const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+                tot += wstart[cn + 1] - wstart[cn];
+              }
+          }
+          wnear[R.cell_off + (iz * R.ncy + iy) * R.ncx + ix] = tot;
+        }
+      }
+  }
   {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -641,6 +663,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   int32_t* cell_rep_d = nullptr;
   ALLOC(cell_rep_d, (size_t)ncell_tot);
   A.cell_rep = cell_rep_d;
+  int32_t *row_cell_d = nullptr, *wnear_d = nullptr;
+  ALLOC(row_cell_d, row_cell.size());
+  ALLOC(wnear_d, (size_t)ncell_tot);
+  A.row_cell = row_cell_d;
+  A.wnear = wnear_d;
+  A.n_rows = (int32_t)row_cell.size();
   double* ctr_d = nullptr;
   ALLOC(ctr_d, ctr.size());
   A.cell_ctr = ctr_d;
@@ -649,6 +677,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.step, 1);
   ALLOC(A.force_rebuild, 1);
   ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1); ALLOC(A.chain_done, 1);
+  ALLOC(A.thermo_owed, 1); ALLOC(A.bar_arrive, 1); ALLOC(A.bar_release, 1);
   ALLOC(A.rep_disp2, (size_t)n_reps);
   ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.n_act, 1);
   ALLOC(A.status, 1);
@@ -716,6 +745,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = up(A.wstart, wstart.data(), wstart.size() * sizeof(int32_t))) != MD_OK) return bail(st);
   if ((st = up(cell_rep_d, cell_rep.data(), cell_rep.size() * sizeof(int32_t))) != MD_OK)
     return bail(st);
+  if ((st = up(row_cell_d, row_cell.data(), row_cell.size() * sizeof(int32_t))) != MD_OK)
+    return bail(st);
+  if ((st = up(wnear_d, wnear.data(), wnear.size() * sizeof(int32_t))) != MD_OK) return bail(st);
   if ((st = up(reps_d, c->reps.data(), c->reps.size() * sizeof(RepDev))) != MD_OK) return bail(st);
   if ((st = up(ctr_d, ctr.data(), ctr.size() * sizeof(double))) != MD_OK) return bail(st);
   if ((st = up(pores_d, pores.data(), pores.size() * sizeof(PoreDev))) != MD_OK) return bail(st);
@@ -785,20 +817,30 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
   if (t->force_accumulate < 0 || t->force_accumulate > 2)
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
-  if (t->pair_method < 0 || t->pair_method > 2)
-    return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists) or 2 (all pairs)");
+  if (t->pair_method < 0 || t->pair_method > 3)
+    return fail(c, MD_EINVAL,
+                "pair_method must be 0 (keep), 1 (Verlet lists), 2 (all pairs) or 3 (cells)");
   if ((c->mixed || c->tun.df64) && t->pair_method == 2)
     return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
-  if (t->pair_method) nt.all_pairs = t->pair_method == 2 ? 1 : 0;
-  const int at = t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
+  if (t->pair_method) {
+    nt.all_pairs = t->pair_method == 2 ? 1 : 0;
+    nt.cells = t->pair_method == 3 ? 1 : 0;
+  }
+  const bool chosen = c->method_chosen || t->pair_method != 0;
+  if (nt.cells && t->force_accumulate == 1)
+    return fail(c, MD_EINVAL, "the cell method adds reaction forces by atomics (force_accumulate 2)");
+  const int at = nt.cells ? 1
+                 : t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
   relist = relist || nt.all_pairs != c->tun.all_pairs;  // lists fresh when they come back
+  relist = relist || nt.cells != c->tun.cells;
   // the packed kernel screens with the FP32 cell-local offsets: refresh them on the way in
   relist = relist || (!c->mixed && (nt.tpp_fp64 == 32) != (c->tun.tpp_fp64 == 32));
   nt.atomic_acc = at;
   c->tun = nt;
+  c->method_chosen = chosen;
   if (t->use_graph) c->use_graph = t->use_graph == 1 ? 1 : 0;
   if (t->steps_per_graph) c->steps_per_graph = t->steps_per_graph;
   destroy_graph(c);
@@ -817,7 +859,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->use_graph = c->use_graph ? 1 : 2;
   t->steps_per_graph = c->steps_per_graph;
   t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
-  t->pair_method = c->tun.all_pairs ? 2 : 1;
+  t->pair_method = c->tun.cells ? 3 : (c->tun.all_pairs ? 2 : 1);
   return MD_OK;
 }
 
@@ -837,9 +879,32 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   double bestv = 1e300;
   md_status st = MD_OK;
   const int tpps[6] = {1, 2, 4, 8, 16, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
-  for (int lpt = 1; lpt >= 0 && st == MD_OK; --lpt) {
+  auto time_shape = [&](const Tuning& t) -> bool {
+    launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);  // warm-up
+    for (int k = 0; k < trials; ++k) {
+      cudaEventRecord(ev[2 * k], c->stream);
+      launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);
+      cudaEventRecord(ev[2 * k + 1], c->stream);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      return false;
+    std::vector<float> ms(trials);
+    for (int k = 0; k < trials; ++k) cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]);
+    std::nth_element(ms.begin(), ms.begin() + trials / 2, ms.end());
+    const double us = 1e3 * ms[trials / 2];
+    if (us < bestv) {
+      bestv = us;
+      bestT = t;
+    }
+    return true;
+  };
+  // the method is the caller's once chosen: a context on the cell method times its shapes alone,
+  // one on the Verlet lists times theirs; otherwise both are timed (the cell method in the atomic
+  // form only)
+  for (int lpt = 1; lpt >= 0 && st == MD_OK && !saved.cells; --lpt) {
     c->tun = saved;
     c->tun.lpt = lpt;
+    c->tun.cells = 0;
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
     for (int tp : tpps) {
       // the packed kernels are the FP64 path's
@@ -858,26 +923,31 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
             t.tpp_fp64 = tp;
             t.force_blocks_per_sm_fp64 = bp;
           }
-          launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);  // warm-up
-          for (int k = 0; k < trials; ++k) {
-            cudaEventRecord(ev[2 * k], c->stream);
-            launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);
-            cudaEventRecord(ev[2 * k + 1], c->stream);
-          }
-          if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+          if (!time_shape(t)) {
             st = fail(c, MD_ECUDA, "autotune launch failed");
             break;
           }
-          std::vector<float> ms(trials);
-          for (int k = 0; k < trials; ++k) cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]);
-          std::nth_element(ms.begin(), ms.begin() + trials / 2, ms.end());
-          const double us = 1e3 * ms[trials / 2];
-          if (us < bestv) {
-            bestv = us;
-            bestT = t;
-          }
         }
     }
+  }
+  // the cell method (no lists) is a further form of the atomic half-pair evaluation
+  if (st == MD_OK && !saved.all_pairs &&
+      (saved.cells || (saved.atomic_acc && !c->method_chosen))) {
+    c->tun = saved;
+    c->tun.cells = 1;
+    c->tun.atomic_acc = 1;
+    if ((st = rebuild_and_forces(c)) == MD_OK)
+      for (int bp : {1, 2, 4})
+        for (int bk : blocks) {
+          Tuning t = c->tun;
+          t.force_block = bk;
+          if (c->mixed) t.force_blocks_per_sm_mixed = bp;
+          else t.force_blocks_per_sm_fp64 = bp;
+          if (!time_shape(t)) {
+            st = fail(c, MD_ECUDA, "autotune launch failed");
+            break;
+          }
+        }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (st != MD_OK) {
@@ -963,7 +1033,7 @@ md_status md_get_state(md_ctx* c, int32_t r, double* x, double* v) {
   md_status s = sync_status(c);
   if (s != MD_OK && s != MD_EOVERFLOW && s != MD_EUNSTABLE && s != MD_ETIMEOUT) return s;
   md_status t;
-  if (v) launch_settle_kick(c->a, c->pot, c->stream);
+  if (v) launch_settle(c->a, c->pot, c->stream);
   if (x && (t = fetch_rows(c, r, c->a.pos, c->stage_x, x)) != MD_OK) return t;
   if (v && (t = fetch_rows(c, r, c->a.vel, c->stage_v, v)) != MD_OK) return t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -987,9 +1057,9 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
   if (s != MD_OK) return s;
   int off, n;
   replica_range(c, r, &off, &n);
-  // the owed kicks are paid before the load resets the flag (a state-preserving step, taken
-  // whether or not the rows pass their check)
-  launch_settle_kick(c->a, c->pot, c->stream);
+  // what the last step owes (its second half-kick, its thermostat) is paid before the load resets
+  // the flags (a state-preserving step, taken whether or not the rows pass their check)
+  launch_settle(c->a, c->pot, c->stream);
   if (n) {
     const size_t bytes = 3 * (size_t)n * sizeof(double);
     CUDA_TRY(c, cudaMemcpyAsync(c->stage_x + 3 * (size_t)off, x, bytes, cudaMemcpyHostToDevice,
@@ -1010,12 +1080,13 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
   const int32_t bad = c->status_host[1];
   c->status_host[1] = kNoBadRow;
   if (n && bad != kNoBadRow) {
-    const int row = off + (bad >> 1);
+    const int row = off + bad / 3;
     int rr = 0;
     while (rr + 1 < c->n_reps && c->reps[rr + 1].vap_off <= row) ++rr;
+    static const char* const why[3] = {" outside the box", " leaves the plane y = 0",
+                                       " has a non-finite velocity"};
     return fail(c, MD_EINVAL, "replica " + std::to_string(rr) + ": molecule " +
-                                  std::to_string(row - c->reps[rr].vap_off) +
-                                  ((bad & 1) ? " leaves the plane y = 0" : " outside the box"));
+                                  std::to_string(row - c->reps[rr].vap_off) + why[bad % 3]);
   }
   return st;
 }
@@ -1029,7 +1100,7 @@ md_status md_observables(md_ctx* c, int32_t r, md_obs* out, int64_t* occupancy, 
   CUDA_TRY(c, cudaMemsetAsync(A.occ, 0, std::max<size_t>(c->pores_total, 1) * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.ads, 0, c->groups_total * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(A.prof, 0, std::max<size_t>(c->prof_total, 1) * 8, c->stream));
-  launch_settle_kick(A, c->pot, c->stream);  // kinetic energy at v(t+dt)
+  launch_settle(A, c->pot, c->stream);  // kinetic energy at v(t+dt), after the thermostat
   launch_forces(A, c->pot, c->mixed, true, false, c->tun, c->stream);
   launch_observables(A, c->pot, c->stream);
   CUDA_TRY(c, cudaGetLastError());

@@ -44,6 +44,11 @@ constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kMaxIndex = (1 << kIndexBits) - 1;
 constexpr int kMaxCap = 1023;  // longest list (vapour + wall neighbours) a molecule may hold
 
+// pair-term precision of a kernel (the values of md_precision)
+constexpr int kPrecFP64 = 0;
+constexpr int kPrecMixed = 1;
+constexpr int kPrecDF64 = 2;
+
 // sticky device status bits
 constexpr int kStatusOverflow = 1;
 constexpr int kStatusUnstable = 2;
@@ -120,6 +125,8 @@ struct Arrays {
   int32_t *vcount, *vstart;         // n_cells, n_cells + 1
   int32_t* scan_tiles;              // tile sums of the cell scan
   const int32_t* cell_rep;          // replica of each cell
+  const int32_t* row_cell;          // first cell of each row of cells (fixed iy, iz of a replica)
+  const int32_t* wnear;             // wall atoms in each cell's 27-cell neighbourhood
   const RepDev* reps;
   const double* cell_ctr;           // per replica: ncx x-centres, ncy y-centres, ncz z-centres
   const PoreDev* pores;
@@ -137,6 +144,10 @@ struct Arrays {
   int32_t* n_act;                   // their number
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
+  long long* thermo_owed;           // the step whose Berendsen scaling is still owed (0: none):
+                                    // paid by the next step kernel, or by launch_settle
+  unsigned long long* bar_arrive;   // the step kernel's grid barrier: arrivals (never reset) and
+  unsigned long long* bar_release;  // the last epoch released
   unsigned int* kick_done;          // last-block detection in k_kick_pending
   unsigned int* chain_done;         // last-block detection in k_list_build
   int32_t* status;
@@ -155,6 +166,7 @@ struct Arrays {
   double *pore_part, *pore_press;   // per (replica, chunk, pore) partials; per pore pressure
   int32_t max_pores;                // most pores of any replica (>= 1)
   int32_t n_total, n_wall_total, n_cells, n_reps;
+  int32_t n_rows;                   // rows of cells over every replica
   int32_t rep_chunks;               // partial-sum chunks per replica
 };
 
@@ -169,8 +181,10 @@ struct Tuning {
   int lpt = 1;                        // process molecules longest list first
   int atomic_acc = 0;                 // FP64: reaction forces by atomic adds (no gather)
   int all_pairs = 0;                  // FP64: every pair each step, no lists (the paper's F1)
+  int cells = 0;                      // cell-tiled pair kernel: no Verlet lists (pair_method 3)
   int df64 = 0;                       // FP64 context, pair terms in double-float (FP32 pairs)
   int sm_count = 152;
+  int integrate_blocks_per_sm = 1;    // blocks of the step kernel an SM holds at once
 };
 
 // carve predicate of a pore at offset (dx, dy) from its axis and height z (slab half-thickness h)
@@ -199,7 +213,7 @@ __host__ __device__ inline int cell_coord(double u, double half, double l, int n
 
 // Conditional-node handles of one captured step (unused when launched outside a graph).
 struct StepConds {
-  cudaGraphConditionalHandle rebuild = 0, thermo = 0;
+  cudaGraphConditionalHandle rebuild = 0;
   int use = 0;
   int has_rebuild = 1;              // 0: no rebuild node (all-pairs mode)
 };
@@ -211,14 +225,15 @@ constexpr int kIntZeroForces = 1;
 constexpr int kIntLocalOffsets = 2;
 constexpr int kIntLocalOffsetsLo = 4;  // also their double-float remainders
 void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
-                            int flags, cudaStream_t s);
+                            int flags, const Tuning& t, cudaStream_t s);
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
-cudaError_t configure_kernels();
+cudaError_t configure_kernels(int* integrate_per_sm);
 // state transfer through device staging rows (caller order, xyz interleaved). The load checks
 // the rows first (positions inside the box, planar replicas in the plane) and loads nothing if
-// any fails; *bad (kNoBadRow beforehand) receives the lowest failing row as 2 k or 2 k + 1.
+// any fails; *bad (kNoBadRow beforehand) receives the lowest failing row k as 3 k (outside the
+// box), 3 k + 1 (off the plane) or 3 k + 2 (a non-finite velocity).
 constexpr int kNoBadRow = 0x7f7f7f7f;  // the byte pattern 0x7f repeated (a memset)
 void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
                        int* bad, cudaStream_t s);
@@ -229,9 +244,9 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
                       cudaStream_t s);
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s);
-void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s);
-// apply a deferred second half-kick, if one is owed (before anything reads velocities)
-void launch_settle_kick(const Arrays& a, const PotDev& p, cudaStream_t s);
+// pay what the last step left owed -- its deferred second half-kick and its Berendsen scaling --
+// before anything outside a step reads or replaces velocities
+void launch_settle(const Arrays& a, const PotDev& p, cudaStream_t s);
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s);
 
 }  // namespace mdk

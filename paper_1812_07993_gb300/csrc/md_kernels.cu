@@ -1,9 +1,11 @@
 // md_kernels.cu -- CUDA kernels (sm_103a) of the pore / water-vapour MD step.
 //
 // One MD step (Sec. 2 velocity Verlet, Figs. 1-4 of arXiv:1812.07993), all replicas per launch:
-//   k_integrate_first   half-kick + drift (Fig. 2), z reflection, hard-wall reflection, x/y wrap,
-//                       skin check; its last block decides whether lists are rebuilt and whether
-//                       the thermostat acts (CUDA-graph conditional nodes)
+//   k_integrate_first   the previous step's owed second half-kick (Fig. 3) and Berendsen scaling
+//                       (Fig. 4), then half-kick + drift (Fig. 2), z reflection, hard-wall
+//                       reflection, x/y wrap, skin check; its last block decides whether lists are
+//                       rebuilt (a CUDA-graph conditional node) and whether this step owes a
+//                       thermostat
 //   rebuild chain       only when a molecule moved >= skin/2 since its replica's last build, and
 //                       only for the replicas near their limit:
 //                         k_cell_clear -> k_cell_count -> k_scan_* -> k_scatter -> k_permute ->
@@ -20,10 +22,12 @@
 //                         in) or half list with atomic reaction forces.
 //                       The atomic forms defer the kick into the next first half-kick
 //                       (k_kick_pending settles it before the thermostat or any velocity read).
-//   k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale   Berendsen scaling on
-//                       thermostat steps (Fig. 4)
-// No kernel spins or waits on another block: where one block finishes a launch's work (the
-// last-block pattern), it is the one whose report comes in last.
+//   Berendsen scaling (Fig. 4) of a thermostat step is paid by the next step's k_integrate_first
+//                       (a grid barrier on those steps only), or, before a state read, by
+//                       k_kick_pending / k_thermo_partial / k_thermo_lambda / k_thermo_scale
+// One kernel waits on other blocks: k_integrate_first, at a bounded grid barrier, on steps that
+// owe a thermostat; its grid holds only as many blocks as the SMs keep resident at once. Elsewhere
+// one block finishes a launch's work (the last-block pattern): the one whose report comes in last.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -272,7 +276,7 @@ __device__ bool in_any_pore(const Arrays& a, const RepDev& R, double x, double y
   return false;
 }
 
-__device__ void reflect_solid(const Arrays& a, const RepDev& R, const dvec4& r0, dvec4& r,
+__device__ __noinline__ void reflect_solid(const Arrays& a, const RepDev& R, const dvec4& r0, dvec4& r,
                               dvec4& v) {
   const double h = R.slab_half;
   if (!(fabs(r.z) < h) || in_any_pore(a, R, r.x, r.y, r.z)) return;
@@ -322,32 +326,176 @@ __device__ void reflect_solid(const Arrays& a, const RepDev& R, const dvec4& r0,
 }
 
 // ------------------------------------------------------------------------------------------------
+// The end of a step and the start of the next: the second half-kick (Fig. 3) that the atomic forms
+// owe, the Berendsen scaling (Fig. 4) owed by a thermostat step, and the next first half-kick and
+// drift (Fig. 2). The step kernel pays what is owed on its way through; the settle kernels below pay
+// it before anything outside a step reads velocities. Both routes share these helpers (the same
+// arithmetic in the same order), so they give bit-identical velocities.
+__device__ __forceinline__ void kick_v(dvec4& v, const dvec4& f, double h) {
+  v.x += h * f.x;
+  v.y += h * f.y;
+  v.z += h * f.z;
+}
+
+__device__ __forceinline__ double vsq(const dvec4& v) { return v.x * v.x + v.y * v.y + v.z * v.z; }
+
+// replica R rescales at the end of step s (Fig. 4: every n_th steps)
+__device__ __forceinline__ bool thermo_due(const RepDev& R, long long s) {
+  return s > 0 && R.n_th > 0 && R.n_vap > 0 && (s % R.n_th) == 0;
+}
+
+__device__ __forceinline__ long long thermo_owed(const Arrays& a) {
+  return *reinterpret_cast<volatile const long long*>(a.thermo_owed);
+}
+
+// sum of |v(t+dt)|^2 over molecules [k0, k1) of replica R by the whole block (256 threads), with the
+// owed half-kick applied on the fly: each thread adds its molecules in index order, the warps by a
+// fixed butterfly, thread 0 the warps in order. Returns the sum in thread 0.
+__device__ double thermo_chunk_sum(const Arrays& a, const RepDev& R, int k0, int k1, int pend) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    dvec4 v = a.vel[R.vap_off + k];
+    if (pend) kick_v(v, a.frc[R.vap_off + k], R.half_dt_m);
+    acc += vsq(v);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();  // sh is free again
+  return t;
+}
+
+// lambda of replica r (Fig. 4) from its chunk partial sums, by one warp: the lanes add chunks
+// lane, lane + 32, ... and a fixed butterfly combines them. 1 when the replica is not due.
+__device__ void thermo_lambda_warp(const Arrays& a, const PotDev& p, int r, long long owed) {
+  const int lane = threadIdx.x & 31;
+  const RepDev& R = a.reps[r];
+  if (!thermo_due(R, owed)) {
+    if (lane == 0) a.lambda[r] = 1.0;
+    return;
+  }
+  const int nch = (R.n_vap + 1023) / 1024;
+  double t = 0.0;
+  for (int ch = lane; ch < nch; ch += 32) t += __ldcg(&a.rep_part[((size_t)r * a.rep_chunks + ch) * 8]);
+  t = warp_sum(t);
+  if (lane == 0) {
+    const double T = p.mass * t / ((double)R.dims * (double)R.n_vap);
+    double lam = 1.0;
+    if (T > 0.0) lam = sqrt(1.0 + R.lam_coef * (R.T0 / T - 1.0));
+    a.lambda[r] = lam;
+    *a.any_scale = 1;
+  }
+}
+
+constexpr long long kSpinLimit = 1ll << 22;  // polls of a grid-barrier wait (~0.5 s) before giving up
+
+// Grid barrier of the step kernel on a step that owes a thermostat: every block arrives once its
+// partial sums are written; the last to arrive turns them into lambda for every replica and then
+// releases the others. Arrivals count up without reset, so the k-th barrier of a context (the grid
+// size G is fixed) releases at bar_release = k, and an arrival that returns old reads its epoch as
+// old / G + 1. A wait is bounded: after kSpinLimit polls the block sets the sticky timeout status
+// and gives up. Returns whether the block may go on.
+__device__ bool thermo_barrier(const Arrays& a, const PotDev& p, long long owed) {
+  __shared__ int s_last, s_ok;
+  __shared__ unsigned long long s_epoch;
+  __syncthreads();  // the block's partial sums are written
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long G = gridDim.x;
+    const unsigned long long old = atomicAdd(a.bar_arrive, 1ull);
+    const unsigned long long epoch = old / G + 1;
+    s_epoch = epoch;
+    s_last = (old % G) == G - 1;
+    s_ok = 1;
+    if (!s_last) {
+      long long spins = 0;
+      while (*reinterpret_cast<volatile unsigned long long*>(a.bar_release) < epoch) {
+        if (++spins > kSpinLimit) {
+          atomicOr(a.status, kStatusTimeout);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int r = threadIdx.x >> 5; r < a.n_reps; r += blockDim.x >> 5)
+      thermo_lambda_warp(a, p, r, owed);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicMax(a.bar_release, s_epoch);
+    }
+  }
+  return s_ok != 0;
+}
+
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
+// The first kernel of every step, on a grid of co-resident blocks that walk the molecules with a
+// stride. It pays what the previous step left owed, in this order per molecule: the deferred second
+// half-kick (Fig. 3) v += (dt/2m) f, then -- when that step was a thermostat step of the molecule's
+// replica -- the Berendsen scaling v *= lambda (Fig. 4); then this step's half-kick, drift,
+// reflections, wrap and skin check. lambda needs the replica's sum of v(t+dt)^2 over all of its
+// molecules: on such steps (one in n_th) every block first adds its share in fixed (replica, chunk
+// of 1024 molecules) units and meets the others at thermo_barrier. The last block to finish decides
+// this step's rebuild branch of the captured graph and whether the step owes a thermostat.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, StepConds sc,
-                                                         int flags) {
+__global__ void __launch_bounds__(256, 4) k_integrate_first(Arrays a, PotDev p, StepConds sc,
+                                                            int flags) {
   count_launch(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.step += 1;
     *a.any_scale = 0;
   }
-  const bool halt = halted(a);
+  // uniform within the block (the partial sums below synchronise the block); another block of this
+  // launch may raise a status bit meanwhile, so blocks can differ, but every block arrives at the
+  // barrier whatever it reads here
+  bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;
   const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double d2 = 0.0;
-  int my_rep = 0;
-  if (!halt && i < a.n_total) {
-    my_rep = a.rep[i];
+  // the same value in every block: the last block of the previous launch wrote it
+  const long long owed = thermo_owed(a);
+  if (owed) {
+    const int units = a.n_reps * a.rep_chunks;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {  // block-uniform
+      const int r = u / a.rep_chunks, ch = u % a.rep_chunks;
+      const RepDev& R = a.reps[r];
+      if (halt || !thermo_due(R, owed) || ch * 1024 >= R.n_vap) continue;
+      const double t = thermo_chunk_sum(a, R, ch * 1024, min(R.n_vap, ch * 1024 + 1024), pend);
+      if (threadIdx.x == 0) a.rep_part[(size_t)u * 8] = t;
+    }
+    if (!thermo_barrier(a, p, owed)) halt = true;
+  }
+  int trig = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; !halt && i < a.n_total; i += stride) {
+    const int my_rep = a.rep[i];
     const RepDev& R = a.reps[my_rep];
     dvec4 x = a.pos[i], v = a.vel[i];
     const dvec4 x_old = x;
     const dvec4 f = a.frc[i];
-    // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
-    // force) owed, both at once
-    const double h = pend ? R.dt_m : R.half_dt_m;
-    v.x += h * f.x;
-    v.y += h * f.y;
-    v.z += h * f.z;
+    if (owed) {
+      // the end of a thermostat step (for some replica): the owed kick, the scaling, then this
+      // step's half-kick -- as the settle kernels would do it, then this kernel
+      if (pend) kick_v(v, f, R.half_dt_m);
+      if (thermo_due(R, owed)) {
+        const double lam = __ldcg(&a.lambda[my_rep]);
+        v.x *= lam;
+        v.y *= lam;
+        v.z *= lam;
+      }
+      kick_v(v, f, R.half_dt_m);
+    } else {
+      // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
+      // force) owed, both at once
+      kick_v(v, f, pend ? R.dt_m : R.half_dt_m);
+    }
     x.x += R.dt * v.x;
     x.y += R.dt * v.y;
     x.z += R.dt * v.z;
@@ -374,7 +522,7 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     if (ge_pos(dy, R.hy)) dy -= R.Ly;
     else if (gt_pos(neg_bits(dy), R.hy)) dy += R.Ly;
     const double dz = x.z - r0.z;
-    d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
+    const double d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
     a.pos[i] = x;
     a.vel[i] = v;
     if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
@@ -386,15 +534,14 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
     } else if (flags & kIntLocalOffsets) {
       a.lpos[i] = local_offset(a, R, x, a.home[i]);
     }
+    // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild;
+    // molecules below the grouping threshold (nearly all) issue no atomic at all
+    if (ge_pos(d2, p.group_disp2))  // rare: only molecules well into their skin
+      atomicMax(&a.rep_disp2[my_rep], (unsigned long long)__double_as_longlong(d2));
+    trig |= ge_pos(d2, p.half_skin2) ? 1 : 0;
   }
-  // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild; blocks
-  // below the threshold (nearly all steps) issue no atomic at all
-  if (ge_pos(d2, p.group_disp2))  // rare: only molecules well into their skin
-    atomicMax(&a.rep_disp2[my_rep], (unsigned long long)__double_as_longlong(d2));
-  if (__syncthreads_or(ge_pos(d2, p.half_skin2)) && threadIdx.x == 0)
-    atomicExch(a.force_rebuild, 1);
-  if (!sc.use) return;
-  // the last block to finish decides this step's branches of the captured graph
+  if (__syncthreads_or(trig) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
+  // the last block to finish decides this step's rebuild branch (graph) and the thermostat it owes
   __shared__ int is_last;
   if (threadIdx.x == 0) {
     __threadfence();
@@ -405,72 +552,41 @@ __global__ void __launch_bounds__(256) k_integrate_first(Arrays a, PotDev p, Ste
   __threadfence();
   const long long s = *reinterpret_cast<volatile long long*>(a.step);
   int th = 0;
-  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x) {
-    const RepDev& R = a.reps[r];
-    if (R.n_th > 0 && R.n_vap > 0 && (s % R.n_th) == 0) th = 1;
-  }
+  for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x)
+    if (thermo_due(a.reps[r], s)) th = 1;
   th = __syncthreads_or(th);
   if (threadIdx.x == 0) {
     *a.blk_done = 0u;
-    const bool rb = !halt && atomicAdd(a.force_rebuild, 0) != 0;
-    if (sc.has_rebuild) cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
-    cudaGraphSetConditional(sc.thermo, (!halt && th) ? 1u : 0u);
+    const bool stop = halted(a);
+    *a.thermo_owed = (!stop && th) ? s : 0ll;
+    const bool rb = !stop && atomicAdd(a.force_rebuild, 0) != 0;
+    if (sc.use && sc.has_rebuild) cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
   }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Fig. 4 (Berendsen) on thermostat steps. sum v^2 per replica in a fixed order: blocks
-// (replica, chunk of 1024 molecules) write partial sums, one warp per replica adds them in chunk
-// order and sets lambda, then every molecule is scaled.
-__device__ __forceinline__ bool thermo_step(const Arrays& a, const RepDev& R) {
-  return R.n_th > 0 && R.n_vap > 0 && (*a.step % R.n_th) == 0;
-}
-
+// Settling outside a step (before a state read, the observables or a state load): the owed
+// half-kick (k_kick_pending, below the pair kernels), then the owed Berendsen scaling of Fig. 4 in
+// three kernels -- sum v^2 per (replica, chunk of 1024 molecules), one warp per replica adds the
+// chunks in order and sets lambda, every molecule is scaled -- with the same arithmetic as the step
+// kernel's. The owed step is cleared afterwards (launch_settle).
 __global__ void __launch_bounds__(256) k_thermo_partial(Arrays a) {
   count_launch(a);
   if (halted(a)) return;
   const int r = blockIdx.x / a.rep_chunks, ch = blockIdx.x % a.rep_chunks;
   const RepDev& R = a.reps[r];
-  if (!thermo_step(a, R)) return;
+  if (!thermo_due(R, thermo_owed(a))) return;
   const int k0 = ch * 1024, k1 = min(R.n_vap, k0 + 1024);
-  double acc = 0.0;
-  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const dvec4 v = a.vel[R.vap_off + k];
-    acc += v.x * v.x + v.y * v.y + v.z * v.z;
-  }
-  __shared__ double sh[8];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    a.rep_part[(size_t)blockIdx.x * 8] = t;
-  }
+  const double t = thermo_chunk_sum(a, R, k0, k1, 0);  // the kick was settled before
+  if (threadIdx.x == 0) a.rep_part[(size_t)blockIdx.x * 8] = t;
 }
 
 __global__ void k_thermo_lambda(Arrays a, PotDev p) {
   count_launch(a);
   if (halted(a)) return;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   if (r >= a.n_reps) return;
-  const RepDev& R = a.reps[r];
-  if (!thermo_step(a, R)) {
-    if (lane == 0) a.lambda[r] = 1.0;
-    return;
-  }
-  const int nch = (R.n_vap + 1023) / 1024;
-  double t = 0.0;
-  for (int ch = lane; ch < nch; ch += 32) t += a.rep_part[((size_t)r * a.rep_chunks + ch) * 8];
-  t = warp_sum(t);  // fixed butterfly: deterministic
-  if (lane == 0) {
-    const double T = p.mass * t / ((double)R.dims * (double)R.n_vap);
-    double lam = 1.0;
-    if (T > 0.0) lam = sqrt(1.0 + R.lam_coef * (R.T0 / T - 1.0));
-    a.lambda[r] = lam;
-    *a.any_scale = 1;
-  }
+  thermo_lambda_warp(a, p, r, thermo_owed(a));
 }
 
 __global__ void k_thermo_scale(Arrays a) {
@@ -690,9 +806,11 @@ __global__ void k_scatter(Arrays a, PotDev p) {
 // within a cell, molecules are ordered by their caller index: the sorted order depends only on
 // the positions, not on the order in which atomics were served. Records move from the staged copy
 // (k_cell_count) to their sorted place.
-__global__ void k_permute(Arrays a, PotDev p) {
+__global__ void k_permute(Arrays a, PotDev p, int count_build) {
   count_launch(a);
   if (halted(a) || !need_rebuild(a, p)) return;
+  // the cell method has no list build, which counts the builds otherwise
+  if (count_build && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n_total || !rep_rebuilds(a, a.rep[s])) return;  // replicas occupy fixed ranges
   const int src = a.perm_tmp[s];
@@ -1414,11 +1532,7 @@ __global__ void k_kick_pending(Arrays a, PotDev p) {
   if (pend && !halted(a) && i < a.n_total) {
     const RepDev& R = a.reps[a.rep[i]];
     dvec4 v = a.vel[i];
-    const dvec4 f = a.frc[i];
-    const double h = R.half_dt_m;
-    v.x += h * f.x;
-    v.y += h * f.y;
-    v.z += h * f.z;
+    kick_v(v, a.frc[i], R.half_dt_m);
     a.vel[i] = v;
   }
   __shared__ int last;
@@ -2212,6 +2326,376 @@ __global__ void __launch_bounds__(256) k_forces_df(Arrays a, PotDev p, int lpt) 
 }
 
 // ------------------------------------------------------------------------------------------------
+// Cell-tiled pair forces (pair_method 3): no Verlet list. A warp takes one row of cells (fixed iy,
+// iz of one replica) and walks its molecules in chunks of at most 32, one lane per molecule. For a
+// chunk spanning cells ix_lo .. ix_hi, the FP32 cell-local offsets of the vapour in the nine
+// neighbouring rows (dy, dz in {-1, 0, 1}), cells ix_lo - 1 .. ix_hi + 1 with the periodic wrap,
+// are staged in shared memory by coalesced float4 loads, each tagged with its molecule index. Every
+// lane then tests every staged candidate of its own 27 cells in FP32 -- the displacement
+// (l_i - l_j) - dc * cell side, exact as in the list build -- keeping the partners j > i (Newton's
+// third law: each vapour pair once) and every wall atom of the 27 cells (read from L2, where lanes of
+// one cell read the same addresses). A candidate whose FP32 r^2 lies below rc^2 (1 + 1e-5) goes to a
+// per-warp queue; when 32 are queued (or the chunk is done) every lane takes one queued pair and
+// evaluates its pair term in the context's precision -- FP64 on the FP64 positions, FP32 on the
+// offsets, or double-float -- with the cutoff decided in FP64 near rc as in the list kernels, so
+// the pair set is the FP64 one. The pair force goes to both molecules by FP64 atomic adds (the
+// forces start from zero), which the L2 executes: the FP64 pipe does only pair terms, with every
+// lane busy. With STATS the queue runs the FP64 observable terms instead (energy, virial, pair
+// counts, nearest wall atom), added to both ends by atomics. Cells are the list cells (side at
+// least max(rc, rc_w) + skin), rebuilt when a molecule has moved skin/2: every pair within the
+// cutoff lies in neighbouring cells.
+constexpr int kCellCap = 384;      // staged candidates per warp (vapour and wall atoms)
+constexpr int kCellSlots = 34;     // cells along x a chunk may span, plus the two neighbours
+
+// One staged neighbour run: row (dy, dz) of the chunk's row, vapour (runs 0-8) or wall atoms (runs
+// 9-17), cells ix_lo - 1 .. ix_hi + 1 as three pieces -- [left cell][ix_lo .. ix_hi][right cell],
+// x wrapped -- of the sorted arrays, staged from `base` (len 0: not staged).
+struct CellRun {
+  int s0, e0, s1, e1, s2, base, len, qb;   // piece starts / ends, staging offset, length, row
+};
+
+struct CellWarp {
+  float4 ent[kCellCap];            // staged FP32 offsets (cp.async)
+  int gid[kCellCap];               // their molecule or wall-atom index
+  int raw[18][kCellSlots];         // per run: the CSR start of cells ix_lo .. ix_hi + 1 (cp.async)
+  CellRun run[18];
+  double ox[32], oy[32], oz[32];   // FP64 positions of the chunk's molecules
+  float4 ol[32], oll[32];          // their FP32 offsets and double-float remainders
+  float4 qb[32];                   // queued partner offset
+  uint32_t qj[32];                 // queued partner: index | cell-offset code (list-entry packing)
+  int32_t qo[32];                  // queued owner lane
+};
+
+// asynchronous global -> shared copies (cp.async): issued without holding registers, waited for
+// once per chunk
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ int next_row(const Arrays& a) {
+  int c = 0;
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(a.work, 1);
+  c = __shfl_sync(kFull, c, 0);
+  return c < a.n_rows ? c : -1;
+}
+
+// cell id of row `rb` (first cell of the row) at x index ix, wrapped
+__device__ __forceinline__ int row_cell_at(int rb, int ix, int ncx) {
+  return rb + (ix < 0 ? ix + ncx : (ix >= ncx ? ix - ncx : ix));
+}
+
+// the queued pairs, one per lane (lanes >= Q idle); forces, or with STATS the observable terms,
+// added to both molecules by atomics. Returns the pairs within the cutoff this lane found.
+template <int PREC, bool STATS>
+__device__ int cell_flush(const Arrays& a, const PotDev& p, const RepDev& R, CellWarp& S, int Q,
+                          int m0, int N) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  int found = 0;
+  if (lane < Q) {
+    const int o = S.qo[lane];
+    const uint32_t e = S.qj[lane];
+    const int j = (int)(e & kIndexMask);
+    const bool wall = j >= N;
+    const int i = m0 + o;
+    if (STATS || PREC == kPrecFP64) {
+      const dvec4 xi = make_dvec4(S.ox[o], S.oy[o], S.oz[o], 0.0);
+      const dvec4 xj = partner_pos(a, e, N);
+      const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+      const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+      const double dz = xi.z - xj.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (lt_pos(r2, wall ? p.rcw2 : p.rc2)) {
+        found = 1;
+        const double inv2 = STATS ? 1.0 / r2 : rcp_nr(r2);
+        const double inv6 = inv2 * inv2 * inv2;
+        const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+        const double fr = inv2 * inv6 * fma(a12, inv6, -b6);
+        if (STATS) {
+          if (wall) {
+            atomicAdd(&a.pevw_i[i], inv6 * fma(p.e12w, inv6, -p.e6w) - p.ushift_w);
+            atomicAdd(&a.virw_i[i], fr * r2);
+            atomicAdd(&a.cnt_vw_i[i], 1);
+            atomicMin(reinterpret_cast<long long*>(&a.d2w_i[i]), __double_as_longlong(r2));
+          } else {
+            const double hu = 0.5 * (inv6 * fma(p.e12, inv6, -p.e6) - p.ushift);
+            const double hv = 0.5 * fr * r2;
+            atomicAdd(&a.pe_i[i], hu);
+            atomicAdd(&a.vir_i[i], hv);
+            atomicAdd(&a.cnt_vv_i[i], 1);
+            atomicAdd(&a.pe_i[j], hu);
+            atomicAdd(&a.vir_i[j], hv);
+            atomicAdd(&a.cnt_vv_i[j], 1);
+          }
+        } else {
+          const double px = fr * dx, py = fr * dy, pz = fr * dz;
+          atomicAdd(&a.frc[i].x, px);
+          atomicAdd(&a.frc[i].y, py);
+          atomicAdd(&a.frc[i].z, pz);
+          if (!wall) {  // Newton's third law: the partner receives -p
+            atomicAdd(&a.frc[j].x, neg_bits(px));
+            atomicAdd(&a.frc[j].y, neg_bits(py));
+            atomicAdd(&a.frc[j].z, neg_bits(pz));
+          }
+        }
+      }
+    } else if (PREC == kPrecMixed) {
+      const float4 li = S.ol[o], b = S.qb[lane];
+      const float dx = (li.x - b.x) - cell_shift((e >> 26) & 3u, R.lcxf);
+      const float dy = (li.y - b.y) - cell_shift((e >> 28) & 3u, R.lcyf);
+      const float dz = (li.z - b.z) - cell_shift(e >> 30, R.lczf);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      bool in = r2 < (wall ? p.rcw2f_lo : p.rc2f_lo);
+      if (!in) {  // the queue holds only r^2 below the upper band: decide in FP64
+        const dvec4 xj = partner_pos(a, e, N);
+        const double ex = image_hi(S.ox[o] - xj.x, R.Lx, R.hi_thr_x);
+        const double ey = image_hi(S.oy[o] - xj.y, R.Ly, R.hi_thr_y);
+        const double ez = S.oz[o] - xj.z;
+        in = ex * ex + ey * ey + ez * ez < (wall ? p.rcw2 : p.rc2);
+      }
+      if (in) {
+        found = 1;
+        const float a12 = wall ? p.a12wf : p.a12f, b6 = wall ? p.b6wf : p.b6f;
+        const float inv2 = __frcp_rn(r2);
+        const float inv6 = inv2 * inv2 * inv2;
+        const float fr = inv2 * inv6 * fmaf(a12, inv6, -b6);
+        const float px = fr * dx, py = fr * dy, pz = fr * dz;
+        atomicAdd(&a.frc[i].x, widen_f32(px));
+        atomicAdd(&a.frc[i].y, widen_f32(py));
+        atomicAdd(&a.frc[i].z, widen_f32(pz));
+        if (!wall) {
+          atomicAdd(&a.frc[j].x, widen_f32(-px));
+          atomicAdd(&a.frc[j].y, widen_f32(-py));
+          atomicAdd(&a.frc[j].z, widen_f32(-pz));
+        }
+      }
+    } else {  // kPrecDF64
+      dword px, py, pz;
+      if (df_pair_term(a, p, R, i, S.ol[o], S.oll[o], e, S.qb[lane], partner_lpos_lo(a, e, N), N,
+                       px, py, pz)) {
+        found = 1;
+        const double fx = dw_to_double(px), fy = dw_to_double(py), fz = dw_to_double(pz);
+        atomicAdd(&a.frc[i].x, fx);
+        atomicAdd(&a.frc[i].y, fy);
+        atomicAdd(&a.frc[i].z, fz);
+        if (!wall) {
+          atomicAdd(&a.frc[j].x, neg_bits(fx));
+          atomicAdd(&a.frc[j].y, neg_bits(fy));
+          atomicAdd(&a.frc[j].z, neg_bits(fz));
+        }
+      }
+    }
+  }
+  __syncwarp();
+  return found;
+}
+
+// append this lane's hit (if any) to the queue, flushing the queue first when it would overflow
+template <int PREC, bool STATS>
+__device__ __forceinline__ void cell_push(const Arrays& a, const PotDev& p, const RepDev& R,
+                                         CellWarp& S, int& Q, int& cnt, bool hit, uint32_t e,
+                                         const float4& b, int m0, int N) {
+  const unsigned hm = __ballot_sync(kFull, hit);
+  if (!hm) return;
+  const int lane = threadIdx.x & 31;
+  const int c = __popc(hm);
+  if (Q + c > 32) {
+    cnt += cell_flush<PREC, STATS>(a, p, R, S, Q, m0, N);
+    Q = 0;
+  }
+  if (hit) {
+    const int u = Q + __popc(hm & ((1u << lane) - 1u));
+    S.qj[u] = e;
+    S.qo[u] = lane;
+    S.qb[u] = b;
+  }
+  Q += c;
+}
+
+template <int PREC, bool STATS>
+__global__ void __launch_bounds__(256) k_forces_cells(Arrays a, PotDev p, int owe_kick) {
+  extern __shared__ __align__(16) unsigned char cell_smem[];
+  CellWarp& S = reinterpret_cast<CellWarp*>(cell_smem)[threadIdx.x >> 5];
+  count_launch(a);
+  if (!STATS) clear_rebuild_flags(a);
+  if (!STATS && owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
+  if (__syncthreads_or(halted(a) ? 1 : 0)) {  // uniform in the block: every block reports in
+    finish_chunks(a);
+    return;
+  }
+  const int N = a.n_total;
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  for (int row = next_row(a); row >= 0; row = next_row(a)) {
+    const int rb = a.row_cell[row];
+    const RepDev& R = a.reps[a.cell_rep[rb]];
+    const int ncx = R.ncx, ncy = R.ncy;
+    const int rl = (rb - R.cell_off) / ncx;
+    const int iy = rl % ncy, iz = rl / ncy;
+    const int m_begin = a.vstart[rb], m_end = a.vstart[rb + ncx];
+    int n = 0;
+    for (int m0 = m_begin; m0 < m_end; m0 += n) {
+      __syncwarp();  // every lane is done with the previous chunk's staging and queue
+      // the chunk: at most 32 molecules spanning at most kCellSlots - 2 cells, whose neighbour
+      // runs fit the staging (vapour always; wall atoms when some molecule has any nearby)
+      n = min(32, m_end - m0);
+      const int ix_lo = a.home[m0] & 1023;
+      int ixl = ix_lo, wn = 0;
+      if (lane < n) {
+        ixl = a.home[m0 + lane] & 1023;
+        wn = a.wnear[rb + ixl];
+      }
+      n = __popc(__ballot_sync(kFull, lane < n && ixl - ix_lo + 3 <= kCellSlots));
+      int ix_hi = 0, len = 0, longest = 0, s0 = 0, e0 = 0, s1 = 0, e1 = 0, s2 = 0, qb = 0;
+      for (;;) {
+        ix_hi = __shfl_sync(kFull, ixl, n - 1);
+        const bool walls = __any_sync(kFull, lane < n && wn > 0);
+        // lane q < 18: run q's pieces (a vapour run holding only lower indices is left out)
+        len = 0;
+        const int kind = lane >= 9, r = lane % 9;
+        const int jz = iz + r / 3 - 1;
+        if (lane < 18 && jz >= 0 && jz < R.ncz && (!kind || walls)) {
+          const int jy = (iy + r % 3 - 1 + ncy) % ncy;
+          qb = R.cell_off + (jz * ncy + jy) * ncx;
+          const int* __restrict__ arr = kind ? a.wstart : a.vstart;
+          const int cl = row_cell_at(qb, ix_lo - 1, ncx), cr = row_cell_at(qb, ix_hi + 1, ncx);
+          s0 = arr[cl];
+          e0 = arr[cl + 1];
+          s1 = arr[qb + ix_lo];
+          e1 = arr[qb + ix_hi + 1];
+          s2 = arr[cr];
+          const int e2 = arr[cr + 1];
+          if (kind || max(e0, max(e1, e2)) > m0) len = (e0 - s0) + (e1 - s1) + (e2 - s2);
+        }
+        // fewer molecules while a single run would not fit the staging (wall-heavy rows): every
+        // run is then staged and screened in at most a few windows
+        longest = __reduce_max_sync(kFull, len);
+        if (longest <= kCellCap || n == 1) break;
+        n = (n + 1) / 2;
+      }
+      const int W = ix_hi - ix_lo + 1;
+      int total = 0;
+      {  // the runs form one stream: run q starts at `base` (an exclusive scan of the lengths)
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        total = __shfl_sync(kFull, incl, 31);
+        if (lane < 18) S.run[lane] = CellRun{s0, e0, s1, e1, s2, incl - len, len, qb};
+      }
+      __syncwarp();
+      // the cell bounds of every run, and the chunk's molecules (loads in flight with the copies)
+      for (int q = 0; q < 18; ++q) {
+        const CellRun rq = S.run[q];
+        if (rq.len == 0) continue;
+        const int* __restrict__ arr = q >= 9 ? a.wstart : a.vstart;
+        for (int c = lane; c <= W; c += 32) cp_async4(&S.raw[q][c], arr + rq.qb + ix_lo + c);
+      }
+      const bool own = lane < n;
+      const int i = m0 + lane;
+      float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int ki = ixl - ix_lo + 1;  // the molecule's slot (1 .. W)
+      if (own) {
+        const dvec4 xi = a.pos[i];
+        S.ox[lane] = xi.x;
+        S.oy[lane] = xi.y;
+        S.oz[lane] = xi.z;
+        li = a.lpos[i];
+        S.ol[lane] = li;
+        if (PREC == kPrecDF64 && !STATS) S.oll[lane] = a.lpos_lo[i];
+      }
+      int Q = 0;
+      const float r2v = p.rc2f_hi, r2w = p.rcw2f_hi;
+      // the stream in windows of kCellCap entries: stage (asynchronous copies, one wait), then
+      // every lane screens the staged part of its own 27 cells -- vapour partners j > i, then wall
+      // atoms
+      for (int w0 = 0; w0 < total; w0 += kCellCap) {
+        const int w1 = min(total, w0 + kCellCap);
+        __syncwarp();  // the previous window is screened
+        for (int q = 0; q < 18; ++q) {
+          const CellRun rq = S.run[q];
+          const int k0 = max(0, w0 - rq.base), k1 = min(rq.len, w1 - rq.base);
+          if (k0 >= k1) continue;
+          const float4* __restrict__ src = q >= 9 ? a.wlpos : a.lpos;
+          const int l0 = rq.e0 - rq.s0, l1 = rq.e1 - rq.s1;
+          for (int k = k0 + lane; k < k1; k += 32) {
+            const int g = k < l0 ? rq.s0 + k : (k < l0 + l1 ? rq.s1 + (k - l0) : rq.s2 + (k - l0 - l1));
+            cp_async16(&S.ent[rq.base + k - w0], src + g);
+            S.gid[rq.base + k - w0] = g;
+          }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        for (int q = 0; q < 18; ++q) {
+          const CellRun rq = S.run[q];
+          const int k0 = max(0, w0 - rq.base), k1 = min(rq.len, w1 - rq.base);
+          if (k0 >= k1) continue;
+          const bool wall_run = q >= 9;
+          const uint32_t cy = (uint32_t)((q % 9) % 3), cz = (uint32_t)((q % 9) / 3);
+          const float sy = cell_shift(cy, R.lcyf), sz = cell_shift(cz, R.lczf);
+          const int l0 = rq.e0 - rq.s0;
+          // run-relative start of slot c (0: the left cell, 1 .. W: ix_lo .. ix_hi, W + 1: the
+          // right cell)
+          auto slot = [&](int c) {
+            return c == 0 ? 0 : (c <= W + 1 ? l0 + (S.raw[q][c - 1] - rq.s1) : rq.len);
+          };
+          const int b1 = own ? slot(ki) : 0, b2 = own ? slot(ki + 1) : 0;
+          const int lo = own ? max(slot(ki - 1), k0) : 0, hi = own ? min(slot(ki + 2), k1) : 0;
+          const int trips = __reduce_max_sync(kFull, max(hi - lo, 0));
+          const int off = rq.base - w0;
+          for (int t = 0; t < trips; ++t) {
+            const int k = lo + t;
+            const bool valid = k < hi;
+            const int kk = valid ? k + off : 0;
+            const float4 b = S.ent[kk];
+            const int g = S.gid[kk];
+            const uint32_t cx = k < b1 ? 0u : (k < b2 ? 1u : 2u);
+            const float dx = (li.x - b.x) - cell_shift(cx, R.lcxf);
+            const float dy = (li.y - b.y) - sy, dz = (li.z - b.z) - sz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const bool hit = valid && (wall_run ? r2 < r2w : (g > i && r2 < r2v));
+            const uint32_t e = (uint32_t)(wall_run ? N + g : g) | (cx << 26) | (cy << 28) |
+                               (cz << 30);
+            cell_push<PREC, STATS>(a, p, R, S, Q, cnt, hit, e, b, m0, N);
+          }
+        }
+      }
+      if (Q) cnt += cell_flush<PREC, STATS>(a, p, R, S, Q, m0, N);
+    }
+  }
+  if (!STATS) {
+    const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+    if (lane == 0 && c) atomicAdd(a.pair_count, c);
+  }
+  finish_chunks(a);
+}
+
+// the per-molecule observables the cell-tiled stats pass adds to by atomics start from zero (and
+// the nearest wall distance from infinity)
+__global__ void k_stats_init(Arrays a) {
+  count_launch(a);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_total) return;
+  a.pe_i[i] = 0.0;
+  a.vir_i[i] = 0.0;
+  a.pevw_i[i] = 0.0;
+  a.virw_i[i] = 0.0;
+  a.d2w_i[i] = __longlong_as_double(0x7ff0000000000000ll);
+  a.cnt_vv_i[i] = 0;
+  a.cnt_vw_i[i] = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
 // observables: pore assignment, occupancy, adsorbed count, axial profile (integer atomics: exact)
 
 __global__ void k_observe(Arrays a, PotDev p) {
@@ -2339,13 +2823,29 @@ __global__ void k_pore_final(Arrays a) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 
-void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c, int flags,
-                            cudaStream_t s) {
-  const int b = 256;
+// the step kernel's grid: every block resident at once (its thermostat barrier waits for all of
+// them), at most what covers the molecules once
+int integrate_grid(const Arrays& a, const Tuning& t) {
+  return std::max(1, std::min(nblocks(a.n_total, 256), t.sm_count * t.integrate_blocks_per_sm));
+}
+
+// launched as a cooperative kernel: the runtime refuses a grid whose blocks cannot all be resident
+// at once (the barrier's bounded wait is the second line of defence)
+void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
+                            int flags, const Tuning& t, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)integrate_grid(a, t));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (mixed)
-    k_integrate_first<true><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, flags);
+    cudaLaunchKernelEx(&cfg, k_integrate_first<true>, a, p, c, flags);
   else
-    k_integrate_first<false><<<nblocks(a.n_total, b), b, 0, s>>>(a, p, c, flags);
+    cudaLaunchKernelEx(&cfg, k_integrate_first<false>, a, p, c, flags);
 }
 
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s) {
@@ -2366,7 +2866,8 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
     k_scan_add<<<ntiles, 1024, 0, s>>>(a, p);
   }
   k_scatter<<<nt, b, 0, s>>>(a, p);
-  k_permute<<<nt, b, 0, s>>>(a, p);
+  k_permute<<<nt, b, 0, s>>>(a, p, t.cells);
+  if (t.cells) return;  // the cell method walks the sorted cells themselves: no lists, no order
   // the atomic forms walk only the front of each row: half rows
   k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
       a, p, half, t.atomic_acc, lpt);
@@ -2468,8 +2969,49 @@ void launch_df(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cud
   k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
 }
 
+// the cell-tiled kernels: one warp's shared memory is a CellWarp
+size_t cell_smem(int block) { return (size_t)(block / 32) * sizeof(CellWarp); }
+
+int cell_prec(bool mixed, const Tuning& t) {
+  return mixed ? kPrecMixed : (t.df64 ? kPrecDF64 : kPrecFP64);
+}
+
+int cell_grid(const Arrays& a, bool mixed, const Tuning& t) {
+  const int per_sm = mixed ? t.force_blocks_per_sm_mixed : t.force_blocks_per_sm_fp64;
+  return pair_grid((long long)std::max(a.n_rows, 1) * 32, t.force_block, per_sm, t);
+}
+
+template <bool STATS>
+void launch_cells_kernel(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t, int owe,
+                         cudaStream_t s) {
+  const int b = t.force_block, g = cell_grid(a, mixed, t);
+  const size_t sm = cell_smem(b);
+  switch (cell_prec(mixed, t)) {
+    case kPrecMixed: k_forces_cells<kPrecMixed, STATS><<<g, b, sm, s>>>(a, p, owe); break;
+    case kPrecDF64: k_forces_cells<kPrecDF64, STATS><<<g, b, sm, s>>>(a, p, owe); break;
+    default: k_forces_cells<kPrecFP64, STATS><<<g, b, sm, s>>>(a, p, owe); break;
+  }
+}
+
+void launch_cells(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
+                  const Tuning& t, cudaStream_t s) {
+  if (stats) {
+    k_stats_init<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+    launch_cells_kernel<true>(a, p, mixed, t, 0, s);
+    return;
+  }
+  // forces start from zero (k_integrate_first clears them in a step); the second half-kick of a
+  // step is deferred into the next first half-kick
+  if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+  launch_cells_kernel<false>(a, p, mixed, t, kick ? 1 : 0, s);
+}
+
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s) {
+  if (t.cells) {
+    launch_cells(a, p, mixed, stats, kick, t, s);
+    return;
+  }
   if (mixed) {
     switch (t.tpp_mixed) {
       case 1: launch_mixed<1>(a, p, stats, kick, t, s); break;
@@ -2530,6 +3072,10 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
 
 void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
                       cudaStream_t s) {
+  if (t.cells) {
+    launch_cells_kernel<false>(a, p, mixed, t, 0, s);
+    return;
+  }
   if (!mixed && t.all_pairs) {
     k_allpairs<false, false><<<nblocks(a.n_total, 128), 128, 0, s>>>(a, p);
     return;
@@ -2560,9 +3106,10 @@ void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning
 // state transfer: caller-order xyz arrays <-> cell-sorted device records
 
 // caller rows [off, off + n) staged for a state load, checked before they replace anything: every
-// position inside its replica's box (x and y in [-L/2, L/2), z in [-Lz/2, Lz/2]; NaN fails) and,
-// for a planar replica, y = vy = 0. The lowest offending row lands in *bad as 2 k (outside the
-// box) or 2 k + 1 (off the plane); *bad keeps kNoBadRow when every row passes.
+// position inside its replica's box (x and y in [-L/2, L/2), z in [-Lz/2, Lz/2]; NaN fails), for a
+// planar replica y = vy = 0, and every velocity component finite. The lowest offending row lands
+// in *bad as 3 k (outside the box), 3 k + 1 (off the plane) or 3 k + 2 (a non-finite velocity);
+// *bad keeps kNoBadRow when every row passes.
 __global__ void k_check_state(Arrays a, const double* __restrict__ xin,
                               const double* __restrict__ vin, int off, int n, int* bad) {
   count_launch(a);
@@ -2571,11 +3118,14 @@ __global__ void k_check_state(Arrays a, const double* __restrict__ xin,
   const int i = off + k;
   const RepDev& R = a.reps[a.rep[i]];
   const double x = xin[3 * (size_t)i], y = xin[3 * (size_t)i + 1], z = xin[3 * (size_t)i + 2];
+  const double vx = vin[3 * (size_t)i], vy = vin[3 * (size_t)i + 1], vz = vin[3 * (size_t)i + 2];
   int code = -1;
   if (!(x >= -R.hx && x < R.hx && y >= -R.hy && y < R.hy && z >= -R.hz && z <= R.hz))
-    code = 2 * k;
-  else if (R.dims == 2 && (y != 0.0 || vin[3 * (size_t)i + 1] != 0.0))
-    code = 2 * k + 1;
+    code = 3 * k;
+  else if (R.dims == 2 && (y != 0.0 || vy != 0.0))
+    code = 3 * k + 1;
+  else if (!(isfinite(vx) && isfinite(vy) && isfinite(vz)))
+    code = 3 * k + 2;
   if (code >= 0) atomicMin(bad, code);
 }
 
@@ -2624,25 +3174,44 @@ void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, 
   if (n > 0) k_store_rows<<<nblocks(n, 256), 256, 0, s>>>(a, src, out, off, n);
 }
 
-// one-time kernel attributes (before any launch or capture)
-cudaError_t configure_kernels() {
-  const cudaError_t e = cudaFuncSetAttribute(
+// one-time kernel attributes (before any launch or capture); *integrate_per_sm receives how many
+// blocks of the step kernel an SM holds at once
+cudaError_t configure_kernels(int* integrate_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(
       k_forces_half_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sizeof(PackWarp)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_forces_atomic_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(8 * sizeof(AtomicQueue)));
+  e = cudaFuncSetAttribute(k_forces_atomic_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(8 * sizeof(AtomicQueue)));
+  if (e != cudaSuccess) return e;
+  const int cs = (int)cell_smem(256);
+  if ((e = cudaFuncSetAttribute(k_forces_cells<kPrecFP64, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_forces_cells<kPrecMixed, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_forces_cells<kPrecDF64, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_forces_cells<kPrecFP64, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_forces_cells<kPrecMixed, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_forces_cells<kPrecDF64, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess)
+    return e;
+  int o1 = 0, o2 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_integrate_first<false>, 256, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_integrate_first<true>, 256, 0);
+  if (e != cudaSuccess) return e;
+  *integrate_per_sm = std::max(1, std::min(o1, o2));
+  return cudaSuccess;
 }
 
-void launch_settle_kick(const Arrays& a, const PotDev& p, cudaStream_t s) {
-  k_kick_pending<<<nblocks(a.n_total, 256), 256, 0, s>>>(a, p);
-}
-
-void launch_thermostat(const Arrays& a, const PotDev& p, cudaStream_t s) {
-  launch_settle_kick(a, p, s);  // the thermostat reads v(t+dt)
+void launch_settle(const Arrays& a, const PotDev& p, cudaStream_t s) {
+  k_kick_pending<<<nblocks(a.n_total, 256), 256, 0, s>>>(a, p);  // the thermostat reads v(t+dt)
   k_thermo_partial<<<a.n_reps * a.rep_chunks, 256, 0, s>>>(a);
   k_thermo_lambda<<<nblocks(a.n_reps, 8), 256, 0, s>>>(a, p);
-  const int b = 256;
-  k_thermo_scale<<<nblocks(a.n_total, b), b, 0, s>>>(a);
+  k_thermo_scale<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+  cudaMemsetAsync(a.thermo_owed, 0, sizeof(long long), s);  // paid
 }
 
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s) {

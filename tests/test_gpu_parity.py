@@ -345,8 +345,9 @@ def test_set_state_round_trip_and_restart_parity():
 
 def test_rejected_state_names_the_row_and_leaves_the_context_unchanged(shapes):
     """md_set_state checks the rows on the device before loading: a position outside the box (or
-    NaN) anywhere in a whole-context load is reported with its replica and molecule, nothing is
-    loaded, and the context steps on from where it was."""
+    NaN), or a velocity component that is not finite, anywhere in a whole-context load is reported
+    with its replica and molecule, nothing is loaded, and the context steps on from where it
+    was."""
     with md.Simulation(shapes) as sim, md.Simulation(shapes) as ref:
         sim.step(5)
         ref.step(5)
@@ -360,6 +361,12 @@ def test_rejected_state_names_the_row_and_leaves_the_context_unchanged(shapes):
             rr = 0 if row < n0 else 2
             first = 0 if rr == 0 else n0 + shapes[1].n_vapor
             assert f"replica {rr}: molecule {row - first} " in str(err.value)
+        for bad_value in (np.inf, np.nan):   # a velocity component that is not finite
+            vb = v.copy()
+            vb[n0 + 5, 1] = bad_value
+            with pytest.raises(md.MDError, match="non-finite velocity") as err:
+                sim.set_state(-1, x, vb)
+            assert "replica 1: molecule 5 " in str(err.value)
         x2, v2 = sim.state(-1)
         np.testing.assert_array_equal(x2, x)
         np.testing.assert_array_equal(v2, v)
