@@ -111,13 +111,16 @@ def parse():
                     help="timed steps as CUDA-graph replays (default) or plain launches (for ncu "
                          "launch lists)")
     ap.add_argument("--skin", default="",
-                    help="Verlet-list skin: a number, or 'auto' for the autotuner's choice "
-                         "(autotune.choose_skin); default: auto for the workloads whose "
+                    help="Verlet-list skin: a number, or 'auto' for the autotuner's choice of "
+                         "skin and cell side (autotune.choose_geometry); default: auto for the "
+                         "workloads whose "
                          "definition does not fix the skin (200k cylinder, 256-replica batch, "
                          "2M pore array), else 0.3")
-    ap.add_argument("--pair-method", choices=["auto", "lists", "cells"], default="auto",
+    ap.add_argument("--pair-method", choices=["auto", "lists", "cells", "small"], default="auto",
                     help="the pair kernel: auto (the autotuner picks between the Verlet-list walk "
-                         "and the cell-tiled kernel, atomic form), lists, or cells")
+                         "and the cell-tiled kernel, atomic form, and for FP64 contexts of at most "
+                         "16384 molecules the small-system method, by whole steps), lists, cells, "
+                         "or small (whole steps in one persistent launch)")
     ap.add_argument("--accumulate", choices=["atomic", "deterministic"], default="atomic",
                     help="reaction forces by FP64 atomic adds (half list, both precisions), or "
                          "the bit-reproducible forms (FP64 slot-and-gather, mixed full list)")
@@ -378,9 +381,16 @@ def prec_enum(md, name):
 def measure_precision(md, systems, precision, args, torch, stream, flush, world=1, potential=None):
     from paper_1812_07993_gb300 import autotune
     sim = md.Simulation(systems, potential, precision=precision, stream=stream)
+    sim.method_choice = None
     sim.set_tuning(force_accumulate=2 if args.accumulate == "atomic" else 1)
-    if args.pair_method != "auto":     # the autotuner then times that method's shapes only
-        sim.set_tuning(pair_method=3 if args.pair_method == "cells" else 1)
+    method = {"lists": 1, "cells": 3, "small": 4}.get(args.pair_method, 0)
+    if (args.pair_method == "auto" and precision == md.MD_PREC_FP64 and
+            sum(s.n_vapor for s in systems) <= autotune.SMALL_MAX):
+        sim.method_choice = autotune.choose_step_method(systems, potential, precision,
+                                                        stream=stream)
+        method = 4 if sim.method_choice["pair_method"] == 4 else 0
+    if method:                         # the autotuner then times that method's shapes only
+        sim.set_tuning(pair_method=method)
     sim.tune_info = None
     main = precision == prec_enum(md, args.precision)
     if args.force_tpp and main:   # the pin is the headline run's; the comparison run is tuned
@@ -437,6 +447,8 @@ def pair_kernel_name(sim, precision, accumulate):
     molecule as the template argument, as ncu names it)."""
     tpp = sim.tuning()["force_tpp"]
     atomic = accumulate == "atomic"
+    if sim.tuning()["pair_method"] == 4:
+        return "k_small_steps"
     if sim.tuning()["pair_method"] == 3:
         return "k_forces_cells<%d, 0>" % {"fp64": 0, "mixed": 1, "df64": 2}[precision]
     if precision == "df64":
@@ -640,14 +652,16 @@ def run_ours(args):
     skin_arg = args.skin or ("auto" if args.workload in SKIN_BY_AUTOTUNER else "0.3")
 
     def choose():
-        # the autotuner times whole MD steps for each candidate skin on fresh contexts (every
-        # candidate gives the same forces and pair counts) and keeps the fastest
+        # the autotuner times whole MD steps on fresh contexts for each candidate skin, then each
+        # cell side at the fastest skin (every candidate gives the same forces and pair counts),
+        # and keeps the fastest, cached per size class
         from paper_1812_07993_gb300 import autotune
-        return dict(autotune.choose_skin(systems, precision=prec, stream=stream),
-                    by="autotune.choose_skin")
+        return dict(autotune.choose_geometry(systems, precision=prec, stream=stream),
+                    by="autotune.choose_geometry")
 
     skin, skin_choice = bench_skin(skin_arg, rank, world, choose)
-    pot = dataclasses.replace(W.Potential(), skin=skin)
+    pot = dataclasses.replace(W.Potential(), skin=skin,
+                              cell_size=float((skin_choice or {}).get("cell_size") or 0.0))
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -668,7 +682,7 @@ def run_ours(args):
         cur = current_pairs(sim, nrep)
         extra["roofline"] = roofline(sim, torch, stream, flush, args.roofline_launches, cur,
                                      args.precision, args.accumulate, args.workload)
-        if sim.tuning()["pair_method"] != 2:
+        if sim.tuning()["pair_method"] not in (2, 4):
             extra["list_build"] = list_build(sim, torch, stream, flush,
                                              max(3, args.roofline_launches // 5), args.precision,
                                              args.accumulate, args.workload)
@@ -757,6 +771,7 @@ def run_ours(args):
                            "precision": args.precision,
                            "force_accumulate": args.accumulate,
                            "skin": pot.skin,
+                           "cell_size": pot.cell_size or max(pot.rc, pot.rc_w) + pot.skin,
                            "skin_choice": skin_choice,
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "launch_mode": args.launch_mode,
@@ -766,7 +781,8 @@ def run_ours(args):
                 "pairs_per_step": pairs_per_step,
                 "gpu_launches": launches,
                 "clocks": clocks.summary(),
-                "autotune": sim_tune}
+                "autotune": sim_tune,
+                "method_choice": getattr(sim, "method_choice", None)}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:

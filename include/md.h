@@ -55,7 +55,12 @@ typedef enum {
   MD_EUNSTABLE = 5,  /* a molecule left the box after reflection and wrap, or its position became
                         non-finite (a molecule that moves more than skin/2 between list builds
                         is not an error: the lists are rebuilt within the same step) */
-  MD_ETIMEOUT = 6    /* a bounded device spin wait gave up */
+  MD_ETIMEOUT = 6,   /* a bounded device spin wait gave up */
+  MD_EBOUNDS = 7     /* the checked build (compiled with -DMD_CHECKED, libmd_checked.so) found an
+                        index read from device data -- a list entry, the processing order, a pair
+                        slot, a cell or sort index -- outside its array; the access was replaced by
+                        an in-bounds one and the status made sticky. The normal build never
+                        returns it. */
 } md_status;
 
 /* MD_PREC_DF64: an FP64 context (positions, integration, cutoff decisions, accumulation, observables)
@@ -141,6 +146,11 @@ typedef struct {
   int32_t max_wall_neighbors;         /* wall neighbours a molecule may hold (0 = default 224);
                                          one list holds both, of max_neighbors +
                                          max_wall_neighbors entries (at most 1023) */
+  double cell_size;                   /* minimum side of the cells (0: the list radius
+                                         max(rc, rc_w) + skin, the smallest that works); larger
+                                         cells hold more molecules each, which changes only the
+                                         speed of the cell sort and the list build: the autotuner
+                                         chooses it per size class */
 } md_potential;
 
 /* Launch-shape knobs (0 in a field = keep the current value). */
@@ -171,7 +181,15 @@ typedef struct {
                               memory, screens every staged candidate, queues the pairs that may lie
                               within the cutoff and evaluates them with every lane busy, reaction
                               forces by FP64 atomic adds (force_accumulate 2 only); the rebuild is
-                              then the cell sort alone. Same pair set and forces in every method. */
+                              then the cell sort alone; 4 (FP64, at most 16384 molecules): small
+                              systems -- md_step(n) runs whole steps in cooperative launches (up to
+                              1000 steps each) with no lists and no sorting: per step every
+                              molecule advances, a bounded grid barrier, then a warp per molecule
+                              screens every vapour molecule of its replica and the wall atoms of
+                              its 27 cells in FP32 and evaluates the candidates in FP64, summing in
+                              a fixed order (bit-for-bit reproducible), with the second half-kick;
+                              the paper's system sizes (Sec. 4, Sec. 5). Same pair set and forces in
+                              every method. */
 } md_tuning;
 
 typedef struct {

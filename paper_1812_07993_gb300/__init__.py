@@ -23,10 +23,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libmd.so")
 _lib = None
 
-MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = range(7)
+MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT, MD_EBOUNDS = \
+    range(8)
 MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_DF64 = 0, 1, 2
 STATUS_NAMES = {0: "MD_OK", 1: "MD_EINVAL", 2: "MD_ENOMEM", 3: "MD_ECUDA", 4: "MD_EOVERFLOW",
-                5: "MD_EUNSTABLE", 6: "MD_ETIMEOUT"}
+                5: "MD_EUNSTABLE", 6: "MD_ETIMEOUT", 7: "MD_EBOUNDS"}
 
 
 class md_pore(ctypes.Structure):
@@ -54,7 +55,8 @@ class md_potential(ctypes.Structure):
                 ("rc_w", ctypes.c_double), ("skin", ctypes.c_double),
                 ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("r_ads", ctypes.c_double), ("bin_width", ctypes.c_double),
-                ("max_neighbors", ctypes.c_int32), ("max_wall_neighbors", ctypes.c_int32)]
+                ("max_neighbors", ctypes.c_int32), ("max_wall_neighbors", ctypes.c_int32),
+                ("cell_size", ctypes.c_double)]
 
 
 class md_tuning(ctypes.Structure):
@@ -120,16 +122,19 @@ _SIGNATURES = {
 
 
 def library_path() -> str:
-    return _LIB_PATH
+    """``libmd.so`` beside this file, or the library named by the environment variable
+    MD_LIBRARY (for instance the checked build, libmd_checked.so)."""
+    return os.environ.get("MD_LIBRARY") or _LIB_PATH
 
 
 def load_library():
-    """Load ``libmd.so`` (built by ``paper_1812_07993_gb300.build``). Raises if it is missing."""
+    """Load the library (built by ``paper_1812_07993_gb300.build``). Raises if it is missing."""
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB_PATH):
-            raise RuntimeError(f"{_LIB_PATH} is not built; run paper_1812_07993_gb300.build.build()")
-        lib = ctypes.CDLL(_LIB_PATH)
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run paper_1812_07993_gb300.build.build()")
+        lib = ctypes.CDLL(path)
         for name, (res, args) in _SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -154,7 +159,7 @@ def md_potential_from(pot: "workloads.Potential", precision: int = MD_PREC_FP64,
                       max_neighbors: int = 0, max_wall_neighbors: int = 0) -> md_potential:
     return md_potential(pot.eps, pot.sigma, pot.mass, pot.rc, pot.eps_w, pot.sigma_w, pot.rc_w,
                         pot.skin, pot.shift_energy, precision, pot.r_ads, pot.bin_width,
-                        max_neighbors, max_wall_neighbors)
+                        max_neighbors, max_wall_neighbors, getattr(pot, "cell_size", 0.0))
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -311,7 +316,8 @@ class Simulation:
         """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
         deterministic gather, 2 atomic reaction forces; pair_method: 1 Verlet lists, 2 all pairs
-        (FP64), 3 cell-tiled kernel without lists (atomic reaction forces)."""
+        (FP64), 3 cell-tiled kernel without lists (atomic reaction forces), 4 small systems
+        (FP64, at most 16384 molecules: whole steps in one persistent launch)."""
         t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
                       steps_per_graph, force_accumulate, pair_method)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)

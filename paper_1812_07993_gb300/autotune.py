@@ -1,9 +1,10 @@
-"""Autotuner: launch shape per size class, and the Verlet skin where a workload leaves it free.
+"""Autotuner: launch shape, Verlet skin and cell side, per size class.
 
 The timing of launch shapes runs in the library (``md_autotune``: CUDA events around the pair-force
 evaluation for every candidate shape); this module keys the result by a size class and caches it in
-a small JSON file, and chooses the skin by timing whole MD steps on fresh contexts. The paper's
-counterpart is its manual scan of threads per block (Sec. 4 and Sec. 5, Figs. 7 and 12).
+a small JSON file, and chooses the skin and the cell side by timing whole MD steps on fresh
+contexts, cached by size class too. The paper's counterpart is its manual scan of threads per block
+(Sec. 4 and Sec. 5, Figs. 7 and 12).
 """
 from __future__ import annotations
 
@@ -67,6 +68,26 @@ def tune(sim: Simulation, trials: int = 15, cache_path: Optional[str] = None,
             "size_class": key}
 
 
+def _time_steps(systems, pot, precision, steps, warmup, stream) -> Dict:
+    """Steps per second of a fresh context with an autotuned launch shape, over ``steps`` MD steps
+    after ``warmup``, with its list rebuilds; or the error of a context that is refused or whose
+    lists overflow."""
+    try:
+        with Simulation(systems, pot, precision=precision, stream=stream) as sim:
+            sim.autotune(7)
+            sim.step(warmup)
+            sim.sync()
+            o0 = sim.observables(0)[0]
+            t0 = time.perf_counter()
+            sim.step(steps)
+            sim.sync()
+            dt = time.perf_counter() - t0
+            o1 = sim.observables(0)[0]
+    except MDError as e:
+        return {"error": str(e)}
+    return {"steps_per_s": steps / dt, "rebuilds": o1["n_rebuilds"] - o0["n_rebuilds"]}
+
+
 def choose_skin(systems: Sequence["workloads.System"], potential: "workloads.Potential" = None,
                 precision: int = MD_PREC_FP64, skins=(0.2, 0.3, 0.4, 0.5, 0.6, 0.8),
                 steps: int = 100, warmup: int = 20, stream=None) -> Dict:
@@ -78,23 +99,91 @@ def choose_skin(systems: Sequence["workloads.System"], potential: "workloads.Pot
     pot = potential or workloads.Potential()
     table = []
     for skin in skins:
-        p = dataclasses.replace(pot, skin=skin)
-        try:
-            with Simulation(systems, p, precision=precision, stream=stream) as sim:
-                sim.autotune(7)
-                sim.step(warmup)
-                sim.sync()
-                o0 = sim.observables(0)[0]
-                t0 = time.perf_counter()
-                sim.step(steps)
-                sim.sync()
-                dt = time.perf_counter() - t0
-                o1 = sim.observables(0)[0]
-        except MDError as e:
-            table.append({"skin": skin, "error": str(e)})
-            continue
-        table.append({"skin": skin, "steps_per_s": steps / dt,
-                      "rebuilds": o1["n_rebuilds"] - o0["n_rebuilds"]})
+        table.append(dict(skin=skin, **_time_steps(systems, dataclasses.replace(pot, skin=skin),
+                                                   precision, steps, warmup, stream)))
     ok = [r for r in table if "steps_per_s" in r]
     best = max(ok, key=lambda r: r["steps_per_s"]) if ok else None
     return {"skin": best["skin"] if best else None, "table": table}
+
+
+def choose_geometry(systems: Sequence["workloads.System"], potential: "workloads.Potential" = None,
+                    precision: int = MD_PREC_FP64, skins=(0.2, 0.3, 0.4, 0.5, 0.6, 0.8),
+                    cell_scales=(1.0, 1.25, 1.5, 2.0), steps: int = 100, warmup: int = 20,
+                    stream=None, cache_path: Optional[str] = None, use_cache: bool = True) -> Dict:
+    """The Verlet skin and the cell side of a batch's size class, by whole MD steps on fresh
+    contexts: every candidate skin with cells of side rc + skin (choose_skin), then, at the fastest
+    skin, every cell scale (cell side = scale x (max(rc, rc_w) + skin)); the fastest pair is kept.
+    Neither changes the forces or the pair counts: the skin trades list length against rebuild
+    frequency, the cell side the work per cell of the sort and the list build against the number of
+    cells. The choice is cached per size class (precision, replica count, log2 of the molecule and
+    wall counts) beside the launch shapes. Returns {"skin", "cell_size" (0: the list radius),
+    "skin_table", "cell_table", "cached", "size_class"}."""
+    pot = potential or workloads.Potential()
+    path = cache_path or default_cache_path()
+    key = "geometry-" + size_class(systems, precision)
+    cache = _load(path) if use_cache else {}
+    if key in cache:
+        return dict(cache[key], cached=True, size_class=key)
+    sk = choose_skin(systems, pot, precision, skins, steps, warmup, stream)
+    result = {"skin": sk["skin"], "cell_size": 0.0, "skin_table": sk["table"], "cell_table": []}
+    if sk["skin"] is not None:
+        best_rate = max(r["steps_per_s"] for r in sk["table"] if r.get("skin") == sk["skin"])
+        base = dataclasses.replace(pot, skin=sk["skin"])
+        rl = max(pot.rc, pot.rc_w) + sk["skin"]
+        for scale in cell_scales:
+            if scale == 1.0:
+                continue
+            cell = scale * rl
+            row = dict(scale=scale, cell_size=cell,
+                       **_time_steps(systems, dataclasses.replace(base, cell_size=cell),
+                                     precision, steps, warmup, stream))
+            result["cell_table"].append(row)
+            if row.get("steps_per_s", 0.0) > best_rate:
+                best_rate = row["steps_per_s"]
+                result["cell_size"] = cell
+    if use_cache and result["skin"] is not None:
+        cache[key] = result
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path + ".tmp", "w") as fh:
+                json.dump(cache, fh, indent=1, sort_keys=True)
+            os.replace(path + ".tmp", path)
+        except OSError:
+            pass
+    return dict(result, cached=False, size_class=key)
+
+
+SMALL_MAX = 16384  # molecules of a context the small-system method (pair_method 4) takes
+
+
+def choose_step_method(systems: Sequence["workloads.System"],
+                       potential: "workloads.Potential" = None, precision: int = MD_PREC_FP64,
+                       steps: int = 200, warmup: int = 20, stream=None) -> Dict:
+    """For a context of at most SMALL_MAX molecules (FP64): whole MD steps with the autotuned
+    Verlet-list method against the small-system method (pair_method 4: whole steps in one
+    persistent launch, no lists), on fresh contexts, timed as ``steps`` single-step calls; returns
+    {"pair_method": 1 or 4, "table": [...]}. Larger or non-FP64 contexts keep the lists."""
+    n = sum(s.n_vapor for s in systems)
+    if precision != MD_PREC_FP64 or n > SMALL_MAX:
+        return {"pair_method": 1, "table": [], "reason": "not eligible for the small-system method"}
+    pot = potential or workloads.Potential()
+    table = []
+    for method in (1, 4):
+        try:
+            with Simulation(systems, pot, precision=precision, stream=stream) as sim:
+                sim.set_tuning(pair_method=method)
+                if method == 1:
+                    sim.autotune(7)
+                sim.step(warmup)
+                sim.sync()
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    sim.step(1)
+                sim.sync()
+                table.append({"pair_method": method,
+                              "steps_per_s": steps / (time.perf_counter() - t0)})
+        except MDError as e:
+            table.append({"pair_method": method, "error": str(e)})
+    ok = [r for r in table if "steps_per_s" in r]
+    best = max(ok, key=lambda r: r["steps_per_s"]) if ok else {"pair_method": 1}
+    return {"pair_method": best["pair_method"], "table": table}

@@ -96,8 +96,11 @@ double lj_u(double r2, double eps, double sigma) {
 md_status validate_potential(md_ctx* c, const md_potential* p) {
   if (!p) return fail(c, MD_EINVAL, "potential is NULL");
   for (double q : {p->eps, p->sigma, p->mass, p->rc, p->eps_w, p->sigma_w, p->rc_w, p->skin,
-                   p->r_ads, p->bin_width})
+                   p->r_ads, p->bin_width, p->cell_size})
     if (!std::isfinite(q)) return fail(c, MD_EINVAL, "potential: a parameter is not finite");
+  if (p->cell_size < 0 ||
+      (p->cell_size > 0 && p->cell_size < std::max(p->rc, p->rc_w) + p->skin))
+    return fail(c, MD_EINVAL, "cell_size must be 0 or at least max(rc, rc_w) + skin");
   if (!(p->eps >= 0 && p->sigma > 0 && p->mass > 0 && p->rc > 0 && p->eps_w >= 0 &&
         p->sigma_w > 0 && p->rc_w > 0 && p->skin >= 0 && p->bin_width > 0))
     return fail(c, MD_EINVAL,
@@ -129,7 +132,8 @@ md_status validate_system(md_ctx* c, const md_system* s, int r, double rl) {
   if (s->thermostat_every > 0 && s->tau_B > 0 && s->tau_B < s->thermostat_every * s->dt)
     return fail(c, MD_EINVAL, who + "tau_B below thermostat_every*dt would over-correct");
   if (!(std::floor(s->Lx / rl) >= 3 && std::floor(s->Ly / rl) >= 3))
-    return fail(c, MD_EINVAL, who + "box x/y must hold at least 3 cells of max(rc,rc_w)+skin");
+    return fail(c, MD_EINVAL,
+                who + "box x/y must hold at least 3 cells of max(rc,rc_w)+skin (or cell_size)");
   if (std::floor(s->Lx / rl) > 1023 || std::floor(s->Ly / rl) > 1023 ||
       std::floor(s->Lz / rl) > 1023)
     return fail(c, MD_EINVAL, who + "more than 1023 cells along an axis");
@@ -249,6 +253,7 @@ int status_to_code(int bits) {
   if (bits & kStatusOverflow) return MD_EOVERFLOW;
   if (bits & kStatusUnstable) return MD_EUNSTABLE;
   if (bits & kStatusTimeout) return MD_ETIMEOUT;
+  if (bits & kStatusBounds) return MD_EBOUNDS;
   return MD_OK;
 }
 
@@ -271,6 +276,12 @@ md_status sync_status(md_ctx* c) {
   if (c->last_status_bits) {
     md_status s = (md_status)status_to_code(c->last_status_bits);
     c->err = std::string("device reported: ") + md_status_string(s);
+    if (s == MD_EBOUNDS) {  // the checked build names the check that failed first
+      int32_t line = 0;
+      if (cudaMemcpy(&line, c->a.status + 1, sizeof(line), cudaMemcpyDeviceToHost) == cudaSuccess)
+        c->err += " (md_kernels.cu line " + std::to_string(line) + ")";
+      cudaGetLastError();
+    }
     return s;
   }
   return MD_OK;
@@ -402,8 +413,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if (!systems || n_reps <= 0) return bail(fail(c, MD_EINVAL, "no systems"));
   if ((st = validate_potential(c, pot)) != MD_OK) return bail(st);
   const double rl = std::max(pot->rc, pot->rc_w) + pot->skin;
+  const double cell = std::max(rl, pot->cell_size);  // cell side: at least the list radius
   for (int r = 0; r < n_reps; ++r)
-    if ((st = validate_system(c, &systems[r], r, rl)) != MD_OK) return bail(st);
+    if ((st = validate_system(c, &systems[r], r, cell)) != MD_OK) return bail(st);
   if (stream) {
     c->stream = (cudaStream_t)stream;
   } else {
@@ -412,7 +424,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     c->own_stream = true;
   }
   {
-    const cudaError_t e = configure_kernels(&c->tun.integrate_blocks_per_sm);
+    const cudaError_t e =
+        configure_kernels(&c->tun.integrate_blocks_per_sm, &c->tun.small_blocks_per_sm);
     if (e != cudaSuccess) return bail(fail(c, MD_ECUDA, cudaGetErrorString(e)));
   }
   c->n_reps = n_reps;
@@ -499,9 +512,9 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     const double tau = s->tau_B > 0 ? s->tau_B : s->thermostat_every * s->dt;
     R.lam_coef = s->thermostat_every > 0 ? s->thermostat_every * s->dt / tau : 0.0;
     R.slab_half = s->slab_half;
-    R.ncx = (int)std::floor(s->Lx / rl);
-    R.ncy = (int)std::floor(s->Ly / rl);
-    R.ncz = std::max(1, (int)std::floor(s->Lz / rl));
+    R.ncx = (int)std::floor(s->Lx / cell);
+    R.ncy = (int)std::floor(s->Ly / cell);
+    R.ncz = std::max(1, (int)std::floor(s->Lz / cell));
     R.lcx = s->Lx / R.ncx; R.lcy = s->Ly / R.ncy; R.lcz = s->Lz / R.ncz;
     R.lcxf = (float)R.lcx; R.lcyf = (float)R.lcy; R.lczf = (float)R.lcz;
     R.lcx_lo = (float)(R.lcx - (double)R.lcxf);
@@ -663,6 +676,12 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   int32_t* cell_rep_d = nullptr;
   ALLOC(cell_rep_d, (size_t)ncell_tot);
   A.cell_rep = cell_rep_d;
+  if (n_tot <= kSmallMax) {  // the small-system method's absolute FP32 positions
+    ALLOC(A.xf, N);
+    float4* wxf_d = nullptr;
+    ALLOC(wxf_d, (size_t)nw_tot);
+    A.wxf = wxf_d;
+  }
   int32_t *row_cell_d = nullptr, *wnear_d = nullptr;
   ALLOC(row_cell_d, row_cell.size());
   ALLOC(wnear_d, (size_t)ncell_tot);
@@ -680,7 +699,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.thermo_owed, 1); ALLOC(A.bar_arrive, 1); ALLOC(A.bar_release, 1);
   ALLOC(A.rep_disp2, (size_t)n_reps);
   ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.n_act, 1);
-  ALLOC(A.status, 1);
+  ALLOC(A.status, 2);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);
   ALLOC(A.max_nb, 1);
@@ -748,6 +767,14 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   if ((st = up(row_cell_d, row_cell.data(), row_cell.size() * sizeof(int32_t))) != MD_OK)
     return bail(st);
   if ((st = up(wnear_d, wnear.data(), wnear.size() * sizeof(int32_t))) != MD_OK) return bail(st);
+  std::vector<float4> wxf;
+  if (A.wxf) {
+    wxf.resize(nw_tot);
+    for (long long k = 0; k < nw_tot; ++k)
+      wxf[k] = make_float4((float)wpos[k].x, (float)wpos[k].y, (float)wpos[k].z, 0.f);
+    if ((st = up(const_cast<float4*>(A.wxf), wxf.data(), wxf.size() * sizeof(float4))) != MD_OK)
+      return bail(st);
+  }
   if ((st = up(reps_d, c->reps.data(), c->reps.size() * sizeof(RepDev))) != MD_OK) return bail(st);
   if ((st = up(ctr_d, ctr.data(), ctr.size() * sizeof(double))) != MD_OK) return bail(st);
   if ((st = up(pores_d, pores.data(), pores.size() * sizeof(PoreDev))) != MD_OK) return bail(st);
@@ -771,6 +798,7 @@ const char* md_status_string(md_status s) {
     case MD_EOVERFLOW: return "neighbour list or cell capacity exceeded";
     case MD_EUNSTABLE: return "unstable motion (non-finite or out-of-box position)";
     case MD_ETIMEOUT: return "device wait timed out";
+    case MD_EBOUNDS: return "index out of bounds (checked build)";
   }
   return "unknown status";
 }
@@ -817,14 +845,18 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
   if (t->force_accumulate < 0 || t->force_accumulate > 2)
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
-  if (t->pair_method < 0 || t->pair_method > 3)
-    return fail(c, MD_EINVAL,
-                "pair_method must be 0 (keep), 1 (Verlet lists), 2 (all pairs) or 3 (cells)");
-  if ((c->mixed || c->tun.df64) && t->pair_method == 2)
-    return fail(c, MD_EINVAL, "the all-pairs method is an FP64-path option");
+  if (t->pair_method < 0 || t->pair_method > 4)
+    return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists), 2 (all pairs), "
+                              "3 (cells) or 4 (small systems)");
+  if ((c->mixed || c->tun.df64) && (t->pair_method == 2 || t->pair_method == 4))
+    return fail(c, MD_EINVAL, "the all-pairs and small-system methods are FP64-path options");
+  if (t->pair_method == 4 && !c->a.xf)
+    return fail(c, MD_EINVAL, "the small-system method takes at most " +
+                                  std::to_string(kSmallMax) + " molecules");
   if (t->pair_method) {
     nt.all_pairs = t->pair_method == 2 ? 1 : 0;
     nt.cells = t->pair_method == 3 ? 1 : 0;
+    nt.small = t->pair_method == 4 ? 1 : 0;
   }
   const bool chosen = c->method_chosen || t->pair_method != 0;
   if (nt.cells && t->force_accumulate == 1)
@@ -835,7 +867,7 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
   relist = relist || nt.all_pairs != c->tun.all_pairs;  // lists fresh when they come back
-  relist = relist || nt.cells != c->tun.cells;
+  relist = relist || nt.cells != c->tun.cells || nt.small != c->tun.small;
   // the packed kernel screens with the FP32 cell-local offsets: refresh them on the way in
   relist = relist || (!c->mixed && (nt.tpp_fp64 == 32) != (c->tun.tpp_fp64 == 32));
   nt.atomic_acc = at;
@@ -859,7 +891,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->use_graph = c->use_graph ? 1 : 2;
   t->steps_per_graph = c->steps_per_graph;
   t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
-  t->pair_method = c->tun.cells ? 3 : (c->tun.all_pairs ? 2 : 1);
+  t->pair_method = c->tun.small ? 4 : c->tun.cells ? 3 : (c->tun.all_pairs ? 2 : 1);
   return MD_OK;
 }
 
@@ -878,6 +910,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   Tuning bestT = saved;
   double bestv = 1e300;
   md_status st = MD_OK;
+  const bool fixed_shape = saved.small;  // the small-system kernel has no shapes to choose
   const int tpps[6] = {1, 2, 4, 8, 16, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
   auto time_shape = [&](const Tuning& t) -> bool {
     launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);  // warm-up
@@ -901,7 +934,8 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   // the method is the caller's once chosen: a context on the cell method times its shapes alone,
   // one on the Verlet lists times theirs; otherwise both are timed (the cell method in the atomic
   // form only)
-  for (int lpt = 1; lpt >= 0 && st == MD_OK && !saved.cells; --lpt) {
+  if (fixed_shape && !time_shape(saved)) st = fail(c, MD_ECUDA, "autotune launch failed");
+  for (int lpt = 1; lpt >= 0 && st == MD_OK && !saved.cells && !fixed_shape; --lpt) {
     c->tun = saved;
     c->tun.lpt = lpt;
     c->tun.cells = 0;
@@ -931,7 +965,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     }
   }
   // the cell method (no lists) is a further form of the atomic half-pair evaluation
-  if (st == MD_OK && !saved.all_pairs &&
+  if (st == MD_OK && !saved.all_pairs && !fixed_shape &&
       (saved.cells || (saved.atomic_acc && !c->method_chosen))) {
     c->tun = saved;
     c->tun.cells = 1;
@@ -974,7 +1008,11 @@ md_status md_step(md_ctx* c, int64_t n) {
   md_status prev = device_status(c);
   if (prev != MD_OK) return prev;
   int64_t left = n;
-  if (c->use_graph && n >= c->steps_per_graph) {
+  if (c->tun.small) {  // whole steps in cooperative launches of at most 1000 steps each
+    for (; left > 0; left -= std::min<int64_t>(left, 1000))
+      launch_small_steps(c->a, c->pot, c->tun, (int)std::min<int64_t>(left, 1000), c->stream);
+  }
+  if (c->use_graph && n >= c->steps_per_graph && left > 0) {
     if (c->graph_steps != c->steps_per_graph) {
       md_status s = build_graph(c, c->steps_per_graph);
       if (s != MD_OK) return s;
@@ -1182,7 +1220,8 @@ md_status md_pair_pass(md_ctx* c) {
 
 md_status md_rebuild_lists(md_ctx* c) {
   if (!c) return MD_EINVAL;
-  if (c->tun.all_pairs) return fail(c, MD_EINVAL, "the all-pairs mode keeps no lists");
+  if (c->tun.all_pairs || c->tun.small)
+    return fail(c, MD_EINVAL, "the all-pairs and small-system methods keep no lists");
   md_status prev = device_status(c);
   if (prev != MD_OK) return prev;
   // every replica rebuilds (all-ones bytes: the largest displacement pattern)

@@ -29,6 +29,7 @@
 // molecule's home cell, 2 bits per axis (value + 1), in bits 26-31.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace mdk {
@@ -53,6 +54,28 @@ constexpr int kPrecDF64 = 2;
 constexpr int kStatusOverflow = 1;
 constexpr int kStatusUnstable = 2;
 constexpr int kStatusTimeout = 4;
+constexpr int kStatusBounds = 8;   // an index check of the checked build failed
+
+// Index checks of the checked build (compiled with -DMD_CHECKED): an index read from device data
+// (a list entry, the processing order, a pair slot, a cell or sort index) that lies outside
+// [0, lim) sets the sticky status bit kStatusBounds and is replaced by 0, so the access stays
+// inside its array and the run reports MD_EBOUNDS instead of trapping. In the normal build the
+// check is the index itself.
+// The first failing check records its source line (status[1]) for md_last_error.
+#ifdef MD_CHECKED
+__device__ __forceinline__ long long chk_index(int32_t* status, long long idx, long long lim,
+                                               int line) {
+  if (idx >= 0 && idx < lim) return idx;
+  atomicOr(status, kStatusBounds);
+  atomicCAS(status + 1, 0, line);
+  return 0;
+}
+#define MD_CHK(a, idx, lim)                                                                  \
+  ((typename std::decay<decltype(idx)>::type)::mdk::chk_index((a).status, (long long)(idx),    \
+                                                               (long long)(lim), __LINE__))
+#else
+#define MD_CHK(a, idx, lim) (idx)
+#endif
 
 struct RepDev {
   double Lx, Ly, Lz, hx, hy, hz;
@@ -125,6 +148,8 @@ struct Arrays {
   int32_t *vcount, *vstart;         // n_cells, n_cells + 1
   int32_t* scan_tiles;              // tile sums of the cell scan
   const int32_t* cell_rep;          // replica of each cell
+  float4* xf;                       // absolute FP32 positions (small-system kernel; else NULL)
+  const float4* wxf;                // and the wall's (static)
   const int32_t* row_cell;          // first cell of each row of cells (fixed iy, iz of a replica)
   const int32_t* wnear;             // wall atoms in each cell's 27-cell neighbourhood
   const RepDev* reps;
@@ -150,7 +175,8 @@ struct Arrays {
   unsigned long long* bar_release;  // the last epoch released
   unsigned int* kick_done;          // last-block detection in k_kick_pending
   unsigned int* chain_done;         // last-block detection in k_list_build
-  int32_t* status;
+  int32_t* status;                  // [0] sticky status bits; [1] the source line of the first
+                                    // failed index check (checked build)
   unsigned int* blk_done;           // last-block detection in k_integrate_first
   unsigned long long* n_rebuilds;
   unsigned long long* pair_count;   // 2 x pairs within cutoff, summed over steps (whole context)
@@ -182,6 +208,8 @@ struct Tuning {
   int atomic_acc = 0;                 // FP64: reaction forces by atomic adds (no gather)
   int all_pairs = 0;                  // FP64: every pair each step, no lists (the paper's F1)
   int cells = 0;                      // cell-tiled pair kernel: no Verlet lists (pair_method 3)
+  int small = 0;                      // whole steps in one persistent launch (pair_method 4)
+  int small_blocks_per_sm = 1;        // blocks of the small-system kernel an SM holds at once
   int df64 = 0;                       // FP64 context, pair terms in double-float (FP32 pairs)
   int sm_count = 152;
   int integrate_blocks_per_sm = 1;    // blocks of the step kernel an SM holds at once
@@ -229,7 +257,12 @@ void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const 
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s);
 // pair forces at the current positions; with `kick` the FP64 reverse gather is fused with the
 // second half-kick (Fig. 3), otherwise the gather only writes the forces
-cudaError_t configure_kernels(int* integrate_per_sm);
+cudaError_t configure_kernels(int* integrate_per_sm, int* small_per_sm);
+// small systems (pair_method 4): n whole MD steps in one cooperative launch (n = 0: the forces at
+// the current positions only)
+constexpr int kSmallMax = 16384;      // molecules of a context the small-system method takes
+void launch_small_steps(const Arrays& a, const PotDev& p, const Tuning& t, int nsteps,
+                        cudaStream_t s);
 // state transfer through device staging rows (caller order, xyz interleaved). The load checks
 // the rows first (positions inside the box, planar replicas in the plane) and loads nothing if
 // any fails; *bad (kNoBadRow beforehand) receives the lowest failing row k as 3 k (outside the

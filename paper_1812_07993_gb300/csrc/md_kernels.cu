@@ -393,9 +393,9 @@ __device__ void thermo_lambda_warp(const Arrays& a, const PotDev& p, int r, long
 
 constexpr long long kSpinLimit = 1ll << 22;  // polls of a grid-barrier wait (~0.5 s) before giving up
 
-// Grid barrier of the step kernel on a step that owes a thermostat: every block arrives once its
-// partial sums are written; the last to arrive turns them into lambda for every replica and then
-// releases the others. Arrivals count up without reset, so the k-th barrier of a context (the grid
+// Grid barrier of the step kernels (co-resident grids only): every block arrives once its work is
+// written; on a step that owes a thermostat (owed != 0) the last to arrive turns the partial sums
+// into lambda for every replica, and then releases the others. Arrivals count up without reset, so the k-th barrier of a context (the grid
 // size G is fixed) releases at bar_release = k, and an arrival that returns old reads its epoch as
 // old / G + 1. A wait is bounded: after kSpinLimit polls the block sets the sticky timeout status
 // and gives up. Returns whether the block may go on.
@@ -426,15 +426,89 @@ __device__ bool thermo_barrier(const Arrays& a, const PotDev& p, long long owed)
   }
   __syncthreads();
   if (s_last) {
-    for (int r = threadIdx.x >> 5; r < a.n_reps; r += blockDim.x >> 5)
-      thermo_lambda_warp(a, p, r, owed);
+    if (owed)
+      for (int r = threadIdx.x >> 5; r < a.n_reps; r += blockDim.x >> 5)
+        thermo_lambda_warp(a, p, r, owed);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       atomicMax(a.bar_release, s_epoch);
     }
   }
+  __syncthreads();  // (s_ok and s_last are read again only after the next barrier's first sync)
   return s_ok != 0;
+}
+
+// One molecule's part of a step's start: the owed second half-kick and, after a thermostat step of
+// its replica, the Berendsen scaling (lambda from the grid barrier), then Fig. 2's half-kick and
+// drift, the reflections, the x/y wrap and the instability test; the FP32 offsets or absolute
+// FP32 position the step's pair kernel screens with. Returns the squared displacement since the
+// molecule's position at the last list build (0 when it left the box).
+constexpr int kIntAbsolute = 8;  // also the absolute FP32 position (small-system kernel)
+
+__device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int pend,
+                                                   long long owed, int flags) {
+  const int my_rep = a.rep[i];
+  const RepDev& R = a.reps[my_rep];
+  dvec4 x = a.pos[i], v = a.vel[i];
+  const dvec4 x_old = x;
+  const dvec4 f = a.frc[i];
+  if (owed) {
+    // the end of a thermostat step (for some replica): the owed kick, the scaling, then this
+    // step's half-kick -- as the settle kernels would do it, then this kernel
+    if (pend) kick_v(v, f, R.half_dt_m);
+    if (thermo_due(R, owed)) {
+      const double lam = __ldcg(&a.lambda[my_rep]);
+      v.x *= lam;
+      v.y *= lam;
+      v.z *= lam;
+    }
+    kick_v(v, f, R.half_dt_m);
+  } else {
+    // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
+    // force) owed, both at once
+    kick_v(v, f, pend ? R.dt_m : R.half_dt_m);
+  }
+  x.x += R.dt * v.x;
+  x.y += R.dt * v.y;
+  x.z += R.dt * v.z;
+  // the boundary tests compare bit patterns (integer instructions; the FP64 pipe does only the
+  // arithmetic, and the adds behind the tests run only where a molecule crosses)
+  if (gt_pos(x.z, R.hz)) {
+    x.z = R.Lz - x.z;
+    v.z = -v.z;
+  } else if (gt_pos(neg_bits(x.z), R.hz)) {
+    x.z = -R.Lz - x.z;
+    v.z = -v.z;
+  }
+  if (R.hard) reflect_solid(a, R, x_old, x, v);
+  if (ge_pos(x.x, R.hx)) x.x -= R.Lx;
+  else if (gt_pos(neg_bits(x.x), R.hx)) x.x += R.Lx;
+  if (ge_pos(x.y, R.hy)) x.y -= R.Ly;
+  else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
+  const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
+  if (bad) atomicOr(a.status, kStatusUnstable);
+  const dvec4 r0 = a.pos_ref[i];
+  double dx = x.x - r0.x, dy = x.y - r0.y;
+  if (ge_pos(dx, R.hx)) dx -= R.Lx;
+  else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
+  if (ge_pos(dy, R.hy)) dy -= R.Ly;
+  else if (gt_pos(neg_bits(dy), R.hy)) dy += R.Ly;
+  const double dz = x.z - r0.z;
+  const double d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
+  a.pos[i] = x;
+  a.vel[i] = v;
+  if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+  if (flags & kIntLocalOffsetsLo) {
+    float4 hi, lo;
+    local_offset_df(a, R, x, a.home[i], hi, lo);
+    a.lpos[i] = hi;
+    a.lpos_lo[i] = lo;
+  } else if (flags & kIntLocalOffsets) {
+    a.lpos[i] = local_offset(a, R, x, a.home[i]);
+  }
+  if (flags & kIntAbsolute) a.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+  return d2;
 }
 
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
@@ -475,69 +549,11 @@ __global__ void __launch_bounds__(256, 4) k_integrate_first(Arrays a, PotDev p, 
   int trig = 0;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; !halt && i < a.n_total; i += stride) {
-    const int my_rep = a.rep[i];
-    const RepDev& R = a.reps[my_rep];
-    dvec4 x = a.pos[i], v = a.vel[i];
-    const dvec4 x_old = x;
-    const dvec4 f = a.frc[i];
-    if (owed) {
-      // the end of a thermostat step (for some replica): the owed kick, the scaling, then this
-      // step's half-kick -- as the settle kernels would do it, then this kernel
-      if (pend) kick_v(v, f, R.half_dt_m);
-      if (thermo_due(R, owed)) {
-        const double lam = __ldcg(&a.lambda[my_rep]);
-        v.x *= lam;
-        v.y *= lam;
-        v.z *= lam;
-      }
-      kick_v(v, f, R.half_dt_m);
-    } else {
-      // Fig. 2's half-kick; with a deferred second half-kick of the previous step (Fig. 3, same
-      // force) owed, both at once
-      kick_v(v, f, pend ? R.dt_m : R.half_dt_m);
-    }
-    x.x += R.dt * v.x;
-    x.y += R.dt * v.y;
-    x.z += R.dt * v.z;
-    // the boundary tests compare bit patterns (integer instructions; the FP64 pipe does only the
-    // arithmetic, and the adds behind the tests run only where a molecule crosses)
-    if (gt_pos(x.z, R.hz)) {
-      x.z = R.Lz - x.z;
-      v.z = -v.z;
-    } else if (gt_pos(neg_bits(x.z), R.hz)) {
-      x.z = -R.Lz - x.z;
-      v.z = -v.z;
-    }
-    if (R.hard) reflect_solid(a, R, x_old, x, v);
-    if (ge_pos(x.x, R.hx)) x.x -= R.Lx;
-    else if (gt_pos(neg_bits(x.x), R.hx)) x.x += R.Lx;
-    if (ge_pos(x.y, R.hy)) x.y -= R.Ly;
-    else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
-    const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
-    if (bad) atomicOr(a.status, kStatusUnstable);
-    const dvec4 r0 = a.pos_ref[i];
-    double dx = x.x - r0.x, dy = x.y - r0.y;
-    if (ge_pos(dx, R.hx)) dx -= R.Lx;
-    else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
-    if (ge_pos(dy, R.hy)) dy -= R.Ly;
-    else if (gt_pos(neg_bits(dy), R.hy)) dy += R.Ly;
-    const double dz = x.z - r0.z;
-    const double d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
-    a.pos[i] = x;
-    a.vel[i] = v;
-    if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
-    if (flags & kIntLocalOffsetsLo) {
-      float4 hi, lo;
-      local_offset_df(a, R, x, a.home[i], hi, lo);
-      a.lpos[i] = hi;
-      a.lpos_lo[i] = lo;
-    } else if (flags & kIntLocalOffsets) {
-      a.lpos[i] = local_offset(a, R, x, a.home[i]);
-    }
+    const double d2 = advance_molecule(a, i, pend, owed, flags);
     // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild;
     // molecules below the grouping threshold (nearly all) issue no atomic at all
     if (ge_pos(d2, p.group_disp2))  // rare: only molecules well into their skin
-      atomicMax(&a.rep_disp2[my_rep], (unsigned long long)__double_as_longlong(d2));
+      atomicMax(&a.rep_disp2[a.rep[i]], (unsigned long long)__double_as_longlong(d2));
     trig |= ge_pos(d2, p.half_skin2) ? 1 : 0;
   }
   if (__syncthreads_or(trig) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
@@ -800,7 +816,7 @@ __global__ void k_scatter(Arrays a, PotDev p) {
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_total || !rep_rebuilds(a, a.rep[i])) return;
-  a.perm_tmp[a.vstart[a.cell_tmp[i]] + a.slot_tmp[i]] = i;
+  a.perm_tmp[MD_CHK(a, a.vstart[MD_CHK(a, a.cell_tmp[i], a.n_cells)] + a.slot_tmp[i], a.n_total)] = i;
 }
 
 // within a cell, molecules are ordered by their caller index: the sorted order depends only on
@@ -813,13 +829,13 @@ __global__ void k_permute(Arrays a, PotDev p, int count_build) {
   if (count_build && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n_total || !rep_rebuilds(a, a.rep[s])) return;  // replicas occupy fixed ranges
-  const int src = a.perm_tmp[s];
-  const int c = a.cell_tmp[src];
+  const int src = MD_CHK(a, a.perm_tmp[s], a.n_total);
+  const int c = MD_CHK(a, a.cell_tmp[src], a.n_cells);
   const int my_id = a.id_alt[src];
   const int b = a.vstart[c], e = a.vstart[c + 1];
   int rank = 0;
-  for (int t = b; t < e; ++t) rank += a.id_alt[a.perm_tmp[t]] < my_id;
-  const int dst = b + rank;
+  for (int t = b; t < e; ++t) rank += a.id_alt[MD_CHK(a, a.perm_tmp[t], a.n_total)] < my_id;
+  const int dst = MD_CHK(a, b + rank, a.n_total);
   const dvec4 x = a.pos_alt[src];
   a.pos[dst] = x;
   a.vel[dst] = a.vel_alt[src];
@@ -926,7 +942,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   // it writes are its cell's molecules', so the order of the cells changes nothing)
   const int n_act = s_run ? *a.n_act : 0;
   for (int ac = blockIdx.x * kListWarps + w; ac < n_act; ac += gridDim.x * kListWarps) {
-    const int c = a.act_cells[ac];
+    const int c = MD_CHK(a, a.act_cells[ac], a.n_cells);
     const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
     if (i_end == i_begin) continue;
     const RepDev& R = a.reps[a.cell_rep[c]];
@@ -984,7 +1000,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
             const bool valid = q < W1;
             const uint32_t entry = valid ? stream[q - W0] : 0u;
             const int jj = (int)(entry & kIndexMask);
-            const int j = wallpass ? jj - N : jj;
+            const int j = !valid ? 0 : wallpass ? MD_CHK(a, jj - N, a.n_wall_total) : MD_CHK(a, jj, N);
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) b = wallpass ? a.wlpos[j] : a.lpos[j];
             const float ox = cell_shift((entry >> 26) & 3u, R.lcxf);
@@ -1098,7 +1114,7 @@ __global__ void __launch_bounds__(256) k_fwd_build(Arrays a, PotDev p) {
     const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
     uint32_t* __restrict__ fw = a.fwd + (size_t)i * capv;
     for (int k = threadIdx.x & 31; k < nvh; k += 32) {
-      const uint32_t j = row[k] & kIndexMask;
+      const uint32_t j = MD_CHK(a, row[k] & kIndexMask, a.n_total);
       const int nb = min(a.n_back[j], capv);
       const uint32_t* __restrict__ rj = a.nbr + (size_t)j * cap + cap;  // one past j's row
       int m = -1;
@@ -1182,20 +1198,20 @@ __device__ __forceinline__ bool lt_pos(double x, double y) {
 // two-entry form took ~9 % more FP64-pipe cycles).
 // FP32 cell-local offset of list entry e's partner (a vapour molecule or a wall atom)
 __device__ __forceinline__ float4 partner_lpos(const Arrays& a, uint32_t e, int N) {
-  const int j = (int)(e & kIndexMask);
+  const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
   return j >= N ? a.wlpos[j - N] : a.lpos[j];
 }
 
 // position of list entry e's partner (a vapour molecule or a wall atom)
 __device__ __forceinline__ dvec4 partner_pos(const Arrays& a, uint32_t e, int N) {
-  const int j = (int)(e & kIndexMask);
+  const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
   return j >= N ? a.wpos[j - N] : a.pos[j];
 }
 
 __device__ __forceinline__ bool pair_term(const Arrays& a, const PotDev& p, const RepDev& R,
                                           const dvec4& xi, uint32_t e, const dvec4& xj, int N,
                                           double& px, double& py, double& pz) {
-  const int j = (int)(e & kIndexMask);
+  const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
   const bool wall = j >= N;
   const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
   const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
@@ -1227,7 +1243,7 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
     double fx = 0.0, fy = 0.0, fz = 0.0;
     int i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
@@ -1249,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
           fz += pz;
           ++cnt;
         }
-        if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(px, py, pz, 0.0);
+        if (k < nvh) a.pairbuf[MD_CHK(a, fw[k], (long long)a.n_total * p.cap_v + 1)] = make_dvec4(px, py, pz, 0.0);
         e = en;
         xj = xn;
       }
@@ -1288,7 +1304,7 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
     double fx = 0.0, fy = 0.0, fz = 0.0;
     int i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
@@ -1305,7 +1321,7 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
           fy += py;
           fz += pz;
           if (k < nvh) {  // Newton's third law: the partner receives -p
-            const int j = (int)(e & kIndexMask);
+            const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
             atomicAdd(&a.frc[j].x, neg_bits(px));
             atomicAdd(&a.frc[j].y, neg_bits(py));
             atomicAdd(&a.frc[j].z, neg_bits(pz));
@@ -1361,7 +1377,7 @@ struct AtomicQueue {
 // sent to a vapour partner; returns whether the pair lies within the cutoff
 __device__ __forceinline__ bool queued_term(const Arrays& a, const PotDev& p, AtomicQueue& S, int u,
                                             uint32_t q, const dvec4& xj, int N) {
-  const int j = (int)(q & kIndexMask), m = (int)(q >> 27);
+  const int j = MD_CHK(a, (int)(q & kIndexMask), a.n_total + a.n_wall_total), m = (int)(q >> 27);
   const bool wall = j >= N;
   const double dx = image_hi(S.ox[m] - xj.x, S.oLx[m], S.othx[m]);
   const double dy = image_hi(S.oy[m] - xj.y, S.oLy[m], S.othy[m]);
@@ -1385,7 +1401,7 @@ __device__ __forceinline__ bool queued_term(const Arrays& a, const PotDev& p, At
 }
 
 __device__ __forceinline__ dvec4 queued_partner(const Arrays& a, uint32_t q, int N) {
-  const int j = (int)(q & kIndexMask);
+  const int j = MD_CHK(a, (int)(q & kIndexMask), a.n_total + a.n_wall_total);
   return j >= N ? a.wpos[j - N] : a.pos[j];
 }
 
@@ -1407,7 +1423,7 @@ __global__ void __launch_bounds__(256) k_forces_atomic_packed(Arrays a, PotDev p
     float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
     float lcx = 0.f, lcy = 0.f, lcz = 0.f;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       n = a.n_front[i];
       li = a.lpos[i];
       const RepDev& R = a.reps[a.rep[i]];
@@ -1672,7 +1688,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
     int i = 0, n = 0, nvh = 0, r = 0;
     float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       n = a.n_front[i];
       nvh = a.n_vh[i];
       r = a.rep[i];
@@ -1699,7 +1715,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
         e[s] = 0u;
         if (k < n) {
           e[s] = row[k];
-          const int j = (int)(e[s] & kIndexMask);
+          const int j = MD_CHK(a, (int)(e[s] & kIndexMask), a.n_total + a.n_wall_total);
           const bool wall = j >= N;
           const float4 b = wall ? a.wlpos[j - N] : a.lpos[j];
           const float dx = (li.x - b.x) - cell_shift((e[s] >> 26) & 3u, lcx);
@@ -1707,7 +1723,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
           const float dz = (li.z - b.z) - cell_shift(e[s] >> 30, lcz);
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < (wall ? p.rcw2f_hi : p.rc2f_hi)) hm |= 1u << s;
-          else if (k < nvh) a.pairbuf[fw[k]] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+          else if (k < nvh) a.pairbuf[MD_CHK(a, fw[k], (long long)a.n_total * p.cap_v + 1)] = make_dvec4(0.0, 0.0, 0.0, 0.0);
         }
       }
       // pack: the lane's survivors go to [seg, seg + c) of the queue, in slot order
@@ -1737,7 +1753,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
         const int m = mk >> 10, k = mk & 1023;
         const dvec4 xm = S.xi[m];
         const RepDev& Rm = a.reps[S.mr[m]];
-        const int j = (int)(en & kIndexMask);
+        const int j = MD_CHK(a, (int)(en & kIndexMask), a.n_total + a.n_wall_total);
         const bool wall = j >= N;
         const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
         const double dx = image_hi(xm.x - xj.x, Rm.Lx, Rm.hi_thr_x);
@@ -1754,7 +1770,7 @@ __global__ void __launch_bounds__(256) k_forces_half_packed(Arrays a, PotDev p, 
         S.ry[u] = py;
         S.rz[u] = pz;
         if (!wall && k < S.mv[m])
-          a.pairbuf[a.fwd[(size_t)S.mi[m] * capv + k]] = make_dvec4(px, py, pz, 0.0);
+          a.pairbuf[MD_CHK(a, a.fwd[(size_t)S.mi[m] * capv + k], (long long)a.n_total * capv + 1)] = make_dvec4(px, py, pz, 0.0);
         cnt += in ? 1 : 0;
       }
       __syncwarp();
@@ -1796,7 +1812,7 @@ __global__ void __launch_bounds__(256) k_stats_fp64(Arrays a, PotDev p, int half
     const int nf = a.n_front[i], n = nf + a.n_back[i];
     const uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
     for (int q = sub; q < n; q += TPP) {
-      const int j = (int)(row[q < nf ? q : cap - 1 - (q - nf)] & kIndexMask);
+      const int j = MD_CHK(a, (int)(row[q < nf ? q : cap - 1 - (q - nf)] & kIndexMask), a.n_total + a.n_wall_total);
       const bool wall = j >= N;
       const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
       const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
@@ -1920,7 +1936,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
     double d2w = __longlong_as_double(0x7ff0000000000000ll);
     int cvv = 0, cvw = 0, i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i];
       const dvec4 xi = a.pos[i];
@@ -1934,7 +1950,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
         const int qn = q + TPP;
         const uint32_t en = qn < n ? row[qn < nf ? qn : cap - 1 - (qn - nf)] : 0u;
         const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
-        const int j = (int)(e & kIndexMask);
+        const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
         const bool wall = j >= N;
         const float dx = (li.x - b.x) - cell_shift((e >> 26) & 3u, R.lcxf);
         const float dy = (li.y - b.y) - cell_shift((e >> 28) & 3u, R.lcyf);
@@ -2058,7 +2074,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     int i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i];
       const dvec4 xi = a.pos[i];
@@ -2071,7 +2087,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
         const int qn = q + TPP;
         const uint32_t en = qn < n ? row[qn] : 0u;
         const float4 bn = qn < n ? partner_lpos(a, en, N) : li;
-        const int j = (int)(e & kIndexMask);
+        const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
         const bool wall = j >= N;
         const float dx = (li.x - b.x) - cell_shift((e >> 26) & 3u, R.lcxf);
         const float dy = (li.y - b.y) - cell_shift((e >> 28) & 3u, R.lcyf);
@@ -2124,7 +2140,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
 
 // double-float remainder of list entry e's partner offset
 __device__ __forceinline__ float4 partner_lpos_lo(const Arrays& a, uint32_t e, int N) {
-  const int j = (int)(e & kIndexMask);
+  const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
   return j >= N ? a.wlpos_lo[j - N] : a.lpos_lo[j];
 }
 
@@ -2148,7 +2164,7 @@ __device__ __forceinline__ bool df_pair_term(const Arrays& a, const PotDev& p, c
                                              int i, const float4& li, const float4& ll,
                                              uint32_t e, const float4& b, const float4& bl, int N,
                                              dword& px, dword& py, dword& pz) {
-  const int j = (int)(e & kIndexMask);
+  const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
   const bool wall = j >= N;
   const uint32_t ox = (e >> 26) & 3u, oy = (e >> 28) & 3u, oz = e >> 30;
   const float shx = cell_shift(ox, R.lcxf), shy = cell_shift(oy, R.lcyf),
@@ -2210,7 +2226,7 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     int i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i], ll = a.lpos_lo[i];
       const int n = a.n_front[i];
@@ -2229,7 +2245,7 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
           df_accumulate(sx, cx, px);
           df_accumulate(sy, cy, py);
           df_accumulate(sz, cz, pz);
-          const int j = (int)(e & kIndexMask);
+          const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
           if (j < N) {  // Newton's third law: the partner receives -p
             atomicAdd(&a.frc[j].x, neg_bits(dw_to_double(px)));
             atomicAdd(&a.frc[j].y, neg_bits(dw_to_double(py)));
@@ -2278,7 +2294,7 @@ __global__ void __launch_bounds__(256) k_forces_df(Arrays a, PotDev p, int lpt) 
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     int i = 0;
     if (live) {
-      i = lpt ? a.order[t] : t;
+      i = lpt ? MD_CHK(a, a.order[t], N) : t;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i], ll = a.lpos_lo[i];
       const int nf = a.n_front[i], n = nf + a.n_back[i];
@@ -2403,7 +2419,7 @@ __device__ int cell_flush(const Arrays& a, const PotDev& p, const RepDev& R, Cel
   if (lane < Q) {
     const int o = S.qo[lane];
     const uint32_t e = S.qj[lane];
-    const int j = (int)(e & kIndexMask);
+    const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
     const bool wall = j >= N;
     const int i = m0 + o;
     if (STATS || PREC == kPrecFP64) {
@@ -2629,7 +2645,9 @@ __global__ void __launch_bounds__(256) k_forces_cells(Arrays a, PotDev p, int ow
           const float4* __restrict__ src = q >= 9 ? a.wlpos : a.lpos;
           const int l0 = rq.e0 - rq.s0, l1 = rq.e1 - rq.s1;
           for (int k = k0 + lane; k < k1; k += 32) {
-            const int g = k < l0 ? rq.s0 + k : (k < l0 + l1 ? rq.s1 + (k - l0) : rq.s2 + (k - l0 - l1));
+            const int g = MD_CHK(a, k < l0 ? rq.s0 + k : (k < l0 + l1 ? rq.s1 + (k - l0)
+                                                                    : rq.s2 + (k - l0 - l1)),
+                               q >= 9 ? a.n_wall_total : a.n_total);
             cp_async16(&S.ent[rq.base + k - w0], src + g);
             S.gid[rq.base + k - w0] = g;
           }
@@ -2694,6 +2712,222 @@ __global__ void k_stats_init(Arrays a) {
   a.cnt_vv_i[i] = 0;
   a.cnt_vw_i[i] = 0;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Small systems (pair_method 4, FP64, at most kSmallMax molecules): whole MD steps in one
+// cooperative launch, no lists and no sorting. Per step, separated by the bounded grid barrier:
+//   the owed Berendsen scaling of the previous step (partial sums, lambda at the barrier) and each
+//   molecule's half-kick, drift, reflections and wrap (advance_molecule), writing its absolute FP32
+//   position;
+//   a warp per molecule: every vapour molecule of its replica and the wall atoms of the 27 cells
+//   around it screened in FP32 on absolute positions (the periodic image taken in FP32, a screening
+//   band of 2e-4 of rc^2 above the cutoff), the candidates queued and evaluated in FP64 with every
+//   lane busy (pair_term: the FP64 cutoff decision and Eq. 2), the warp's sum -- a fixed
+//   butterfly, so runs are bit-for-bit reproducible -- written as the molecule's force, and the
+//   second half-kick (Fig. 3) applied.
+// Each vapour pair is evaluated from both ends (no atomics). The paper's systems (2,184 and 2,800
+// molecules, Sec. 4 and Sec. 5) are this size: their steps are bound by launch and memory latency,
+// which one launch for many steps removes.
+__device__ __forceinline__ bool any_thermo_due(const Arrays& a, long long s) {
+  for (int r = 0; r < a.n_reps; ++r)
+    if (thermo_due(a.reps[r], s)) return true;
+  return false;
+}
+
+constexpr int kSmallStage = 2816;  // FP32 positions a block stages at a time (45 KB)
+
+// The forces on molecules base .. base + 7, one per warp, with the second half-kick when KICK. The
+// vapour of the block's replica (that of molecule `base`) is staged in shared memory in windows
+// (cp.async) and screened from there; a molecule of another replica (a block straddling two) reads
+// its replica's positions from global memory. The wall atoms of the 27 cells around a molecule are
+// one stream: lanes 0-26 fetch the cells' ranges at once, and the lanes then walk the stream.
+template <bool KICK>
+__device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, float4* stage, int base,
+                            float rcs2, float rcws2) {
+  const int lane = threadIdx.x & 31, N = a.n_total;
+  const int i = base + (threadIdx.x >> 5);
+  const bool live = i < N;
+  const RepDev& RB = a.reps[a.rep[base]];
+  const int ri = live ? a.rep[i] : a.rep[base];
+  const bool staged = live && &a.reps[ri] == &RB;
+  const RepDev& R = a.reps[ri];
+  const dvec4 xi = live ? a.pos[i] : make_dvec4(0.0, 0.0, 0.0, 0.0);
+  const float4 xf = live ? a.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float Lx = R.Lx, Ly = R.Ly, hx = R.hx, hy = R.hy;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  int cnt = 0, Q = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    if (lane < Q) {
+      const uint32_t e = sq[lane];
+      double px, py, pz;
+      if (pair_term(a, p, R, xi, e, partner_pos(a, e, N), N, px, py, pz)) {
+        fx += px;
+        fy += py;
+        fz += pz;
+        cnt += (int)(e & kIndexMask) >= N ? 2 : 1;  // vapour pairs are met from both ends
+      }
+    }
+    __syncwarp();
+    Q = 0;
+  };
+  auto push = [&](bool hit, uint32_t e) {
+    const unsigned hm = __ballot_sync(kFull, hit);
+    if (!hm) return;
+    const int c = __popc(hm);
+    if (Q + c > 32) flush();
+    if (hit) sq[Q + __popc(hm & ((1u << lane) - 1u))] = e;
+    Q += c;
+  };
+  auto screen = [&](const float4& b, float lim) {
+    float dx = xf.x - b.x, dy = xf.y - b.y;
+    dx = dx >= hx ? dx - Lx : (dx < -hx ? dx + Lx : dx);
+    dy = dy >= hy ? dy - Ly : (dy < -hy ? dy + Ly : dy);
+    const float dz = xf.z - b.z;
+    return dx * dx + dy * dy + dz * dz < lim;
+  };
+  // vapour of the block's replica, window by window (the loop is the block's)
+  for (int w0 = RB.vap_off; w0 < RB.vap_off + RB.n_vap; w0 += kSmallStage) {
+    const int w1 = min(w0 + kSmallStage, RB.vap_off + RB.n_vap);
+    __syncthreads();  // the previous window is screened
+    for (int k = threadIdx.x; k < w1 - w0; k += blockDim.x) cp_async16(&stage[k], &a.xf[w0 + k]);
+    cp_async_wait_all();
+    __syncthreads();
+    if (staged)
+      for (int j0 = w0; j0 < w1; j0 += 32) {
+        const int j = j0 + lane;
+        const bool valid = j < w1 && j != i;
+        push(valid && screen(stage[valid ? j - w0 : 0], rcs2), (uint32_t)j);
+      }
+  }
+  if (live && !staged)  // a molecule of another replica than the block's
+    for (int j0 = R.vap_off; j0 < R.vap_off + R.n_vap; j0 += 32) {
+      const int j = j0 + lane;
+      const bool valid = j < R.vap_off + R.n_vap && j != i;
+      push(valid && screen(a.xf[valid ? j : i], rcs2), (uint32_t)j);
+    }
+  if (live && R.n_wall > 0) {  // the wall atoms of the 27 cells around the molecule
+    const int ix = min(max((int)floorf((xf.x + hx) / R.lcxf), 0), R.ncx - 1);
+    const int iy = min(max((int)floorf((xf.y + hy) / R.lcyf), 0), R.ncy - 1);
+    const int iz = min(max((int)floorf((xf.z + (float)R.hz) / R.lczf), 0), R.ncz - 1);
+    int ws = 0, nw = 0;
+    if (lane < 27) {
+      const int jz = iz + lane / 9 - 1;
+      if (jz >= 0 && jz < R.ncz) {
+        const int jy = (iy + (lane / 3) % 3 - 1 + R.ncy) % R.ncy;
+        const int jx = (ix + lane % 3 - 1 + R.ncx) % R.ncx;
+        const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+        ws = a.wstart[cn];
+        nw = a.wstart[cn + 1] - ws;
+      }
+    }
+    int incl = nw;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - nw, T = __shfl_sync(kFull, incl, 31);
+    constexpr int kBatch = 4;  // stream entries a lane loads before screening them
+    for (int k0 = 0; k0 < T; k0 += 32 * kBatch) {
+      int w[kBatch];
+      float4 b[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int k = k0 + 32 * u + lane;
+        // the cell holding stream entry k: the last cell whose stream start is at most k
+        int lo = 0, hi = 26;
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (k >= __shfl_sync(kFull, excl, mid)) lo = mid;
+          else hi = mid - 1;
+        }
+        // (every lane takes part in the shuffles; the result is kept only inside the stream)
+        const int wk = __shfl_sync(kFull, ws, lo) + (k - __shfl_sync(kFull, excl, lo));
+        w[u] = k < T ? wk : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) b[u] = a.wxf[w[u] >= 0 ? w[u] : 0];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        push(w[u] >= 0 && screen(b[u], rcws2), (uint32_t)(N + (w[u] >= 0 ? w[u] : 0)));
+    }
+  }
+  if (Q) flush();
+  fx = warp_sum(fx);
+  fy = warp_sum(fy);
+  fz = warp_sum(fz);
+  if (live && lane == 0) {
+    a.frc[i] = make_dvec4(fx, fy, fz, 0.0);
+    if (KICK) {  // Fig. 3: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+      dvec4 v = a.vel[i];
+      kick_v(v, make_dvec4(fx, fy, fz, 0.0), R.half_dt_m);
+      a.vel[i] = v;
+    }
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(256) k_small_steps(Arrays a, PotDev p, int nsteps) {
+  __shared__ uint32_t sq[8][32];
+  __shared__ __align__(16) float4 stage[kSmallStage];
+  count_launch(a);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nb8 = gridDim.x * (blockDim.x >> 5);  // molecules the grid takes per round
+  const float rcs2 = (float)(p.rc2 * (1.0 + 2e-4)), rcws2 = (float)(p.rcw2 * (1.0 + 2e-4));
+  // the step counter, the owed kick and thermostat, read by every block before any block writes
+  const long long s0 = *reinterpret_cast<volatile long long*>(a.step);
+  int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
+  long long owed = thermo_owed(a);
+  bool ok = thermo_barrier(a, p, 0);
+  int cnt = 0;
+  if (nsteps == 0) {  // the forces at the current positions (md_compute_forces): positions may
+                      // have been loaded or re-sorted since the last step wrote their FP32 copy
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total; i += gridDim.x * blockDim.x) {
+      const dvec4 x = a.pos[i];
+      a.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+    }
+    ok = thermo_barrier(a, p, 0);
+    const bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;  // uniform in the block
+    for (int base = blockIdx.x * 8; ok && !halt && base < a.n_total; base += nb8)
+      cnt += small_forces<false>(a, p, sq[wib], stage, base, rcs2, rcws2);
+  }
+  for (int k = 0; k < nsteps && ok; ++k) {
+    const long long s = s0 + k + 1;
+    if (owed) {  // the previous step's thermostat: v(t+dt)^2 per (replica, chunk), lambda
+      const int units = a.n_reps * a.rep_chunks;
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int r = u / a.rep_chunks, ch = u % a.rep_chunks;
+        const RepDev& R = a.reps[r];
+        if (!thermo_due(R, owed) || ch * 1024 >= R.n_vap) continue;
+        const double t = thermo_chunk_sum(a, R, ch * 1024, min(R.n_vap, ch * 1024 + 1024), pend);
+        if (threadIdx.x == 0) a.rep_part[(size_t)u * 8] = t;
+      }
+      ok = thermo_barrier(a, p, owed);
+      if (!ok) break;
+    }
+    const bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;  // uniform in the block
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; !halt && i < a.n_total;
+         i += gridDim.x * blockDim.x)
+      advance_molecule(a, i, pend, owed, kIntAbsolute);
+    ok = thermo_barrier(a, p, 0);
+    if (!ok) break;
+    for (int base = blockIdx.x * 8; !halt && base < a.n_total; base += nb8)
+      cnt += small_forces<true>(a, p, sq[wib], stage, base, rcs2, rcws2);
+    ok = thermo_barrier(a, p, 0);
+    pend = 0;
+    owed = any_thermo_due(a, s) ? s : 0;
+  }
+  const unsigned long long c = warp_sum((unsigned long long)cnt);
+  if (lane == 0 && c && nsteps > 0) atomicAdd(a.pair_count, c);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nsteps > 0) {
+    *a.step = s0 + nsteps;
+    *a.kick_pending = 0;                      // every step kicked itself
+    *a.thermo_owed = halted(a) ? 0 : owed;    // the last step's scaling, paid later
+  }
+}
+
 
 // ------------------------------------------------------------------------------------------------
 // observables: pore assignment, occupancy, adsorbed count, axial profile (integer atomics: exact)
@@ -2822,6 +3056,21 @@ __global__ void k_pore_final(Arrays a) {
 
 // ------------------------------------------------------------------------------------------------
 // launchers
+
+void launch_small_steps(const Arrays& a, const PotDev& p, const Tuning& t, int nsteps,
+                        cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::max(1, std::min(nblocks(a.n_total, 8),
+                                                    t.sm_count * t.small_blocks_per_sm)));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_small_steps, a, p, nsteps);
+}
 
 // the step kernel's grid: every block resident at once (its thermostat barrier waits for all of
 // them), at most what covers the molecules once
@@ -3008,6 +3257,11 @@ void launch_cells(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool
 
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s) {
+  if (t.small) {  // (a step kicks inside the small-system kernel: here the forces alone)
+    if (stats) k_allpairs<true, false><<<nblocks(a.n_total, 128), 128, 0, s>>>(a, p);
+    else launch_small_steps(a, p, t, 0, s);
+    return;
+  }
   if (t.cells) {
     launch_cells(a, p, mixed, stats, kick, t, s);
     return;
@@ -3072,6 +3326,10 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
 
 void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
                       cudaStream_t s) {
+  if (t.small) {
+    launch_small_steps(a, p, t, 0, s);
+    return;
+  }
   if (t.cells) {
     launch_cells_kernel<false>(a, p, mixed, t, 0, s);
     return;
@@ -3155,7 +3413,7 @@ __global__ void k_store_rows(Arrays a, const dvec4* __restrict__ src, double* __
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int i = off + k;
-  const size_t row = (size_t)a.reps[a.rep[i]].vap_off + (size_t)a.id[i];
+  const size_t row = MD_CHK(a, (size_t)a.reps[a.rep[i]].vap_off + (size_t)a.id[i], a.n_total);
   const dvec4 v = src[i];
   out[3 * row] = v.x;
   out[3 * row + 1] = v.y;
@@ -3176,7 +3434,7 @@ void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, 
 
 // one-time kernel attributes (before any launch or capture); *integrate_per_sm receives how many
 // blocks of the step kernel an SM holds at once
-cudaError_t configure_kernels(int* integrate_per_sm) {
+cudaError_t configure_kernels(int* integrate_per_sm, int* small_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(
       k_forces_half_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sizeof(PackWarp)));
   if (e != cudaSuccess) return e;
@@ -3203,6 +3461,10 @@ cudaError_t configure_kernels(int* integrate_per_sm) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_integrate_first<true>, 256, 0);
   if (e != cudaSuccess) return e;
   *integrate_per_sm = std::max(1, std::min(o1, o2));
+  int o3 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_small_steps, 256, 0);
+  if (e != cudaSuccess) return e;
+  *small_per_sm = std::max(1, o3);
   return cudaSuccess;
 }
 

@@ -66,6 +66,7 @@ class Potential:
     shift_energy: int = 1
     r_ads: float = 1.5       # a vapour molecule counts as adsorbed when a wall atom is closer than this
     bin_width: float = 0.5   # axial (z) density-profile bin width
+    cell_size: float = 0.0   # minimum cell side of the GPU path (0: max(rc, rc_w) + skin); no physics
 
 
 @dataclasses.dataclass

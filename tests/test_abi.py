@@ -64,9 +64,20 @@ def test_struct_layout_matches_c(tmp_path):
 
 
 def test_status_strings(lib):
-    for s in range(7):
-        assert lib.md_status_string(s)
+    for s in range(8):
+        assert lib.md_status_string(s) and lib.md_status_string(s) != b"unknown status"
     assert lib.md_status_string(99) == b"unknown status"
+
+
+def test_checked_build_exports_every_declared_function():
+    """The MD_CHECKED variant (index checks reporting MD_EBOUNDS) builds and exports the same
+    entry points."""
+    path = mdbuild.build(checked=True)
+    assert path.endswith("libmd_checked.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(md_\w+)\b", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
 
 
 def small_system(**kw):

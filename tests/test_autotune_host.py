@@ -18,13 +18,23 @@ PLAN = {
 }
 
 
+# per cell scale (cell side / (rc + skin)): a factor on the seconds per step, or a refusal
+CELL_PLAN = {1.0: 1.0, 1.25: 0.8, 1.5: 0.9, 2.0: "create"}
+
+
 class FakeSim:
     clock = 0.0
 
     def __init__(self, systems, potential, precision=0, stream=None):
-        self.plan = PLAN[potential.skin]
-        if self.plan.get("error") == "create":
+        self.plan = dict(PLAN[potential.skin])
+        scale = 1.0
+        if potential.cell_size:
+            scale = round(potential.cell_size / (max(potential.rc, potential.rc_w) + potential.skin), 6)
+        factor = CELL_PLAN[scale]
+        if self.plan.get("error") == "create" or factor == "create":
             raise md.MDError(md.MD_EINVAL, "box x/y must hold at least 3 cells")
+        if "sec" in self.plan:
+            self.plan["sec"] *= factor
         self.steps = 0
 
     def __enter__(self):
@@ -70,3 +80,16 @@ def test_choose_skin_keeps_the_fastest_and_records_the_refused(fake):
 def test_choose_skin_with_no_usable_candidate(fake):
     got = autotune.choose_skin([W.cylinder_pore_1k()], skins=(0.5, 0.8))
     assert got["skin"] is None and len(got["table"]) == 2
+
+
+def test_choose_geometry_picks_skin_then_cell_side_and_caches(fake, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    got = autotune.choose_geometry([W.cylinder_pore_1k()], steps=100, warmup=20,
+                                   cache_path=cache)
+    assert got["skin"] == 0.4 and not got["cached"]
+    assert got["cell_size"] == pytest.approx(1.25 * 2.9)
+    rows = {r["scale"]: r for r in got["cell_table"]}
+    assert set(rows) == {1.25, 1.5, 2.0} and "error" in rows[2.0]
+    assert rows[1.25]["steps_per_s"] == pytest.approx(1 / (0.8 * 1.1e-3))
+    again = autotune.choose_geometry([W.cylinder_pore_1k()], cache_path=cache)
+    assert again["cached"] and again["skin"] == 0.4 and again["cell_size"] == got["cell_size"]

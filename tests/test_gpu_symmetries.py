@@ -44,6 +44,7 @@ FORMS = [
     ("fp64-cells", md.MD_PREC_FP64, 2, 3, 1e-13, 1e-12),
     ("mixed-cells", md.MD_PREC_MIXED, 2, 3, 1e-7, 1e-8),
     ("df64-cells", md.MD_PREC_DF64, 2, 3, 1e-12, 1e-11),
+    ("fp64-small", md.MD_PREC_FP64, 1, 4, 1e-13, 1e-12),
 ]
 
 

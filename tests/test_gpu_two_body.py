@@ -35,7 +35,7 @@ def systems():
 
 FP64_FORMS = [  # (force_tpp (0: keep), force_accumulate, pair_method: 1 lists, 2 all, 3 cells)
     (1, 2, 1), (2, 2, 1), (4, 2, 1), (8, 2, 1), (16, 2, 1), (32, 2, 1),
-    (2, 1, 1), (32, 1, 1), (2, 2, 2), (0, 2, 3),
+    (2, 1, 1), (32, 1, 1), (2, 2, 2), (0, 2, 3), (0, 0, 4),
 ]
 
 

@@ -269,3 +269,30 @@ def test_skin_choice_changes_speed_not_physics(batch):
     rows = {r["skin"]: r for r in got["table"]}
     assert all("steps_per_s" in rows[k] and rows[k]["steps_per_s"] > 0 for k in (0.2, 0.8))
     assert rows[0.8]["rebuilds"] <= rows[0.2]["rebuilds"]
+
+
+def test_cell_side_changes_speed_not_physics(batch, tmp_path):
+    """Cells larger than the list radius hold more molecules each: the forces, the pair counts and
+    a 20-step trajectory are those of the smallest cells (every pair within the list radius still
+    lies in neighbouring cells); choose_geometry times the candidates and caches its choice."""
+    import dataclasses
+    systems = batch[:3]
+    out = []
+    for cell in (0.0, 4.5):
+        pot = dataclasses.replace(W.Potential(), skin=0.3, cell_size=cell)
+        with md.Simulation(systems, pot) as sim:
+            sim.set_tuning(force_accumulate=1)   # deterministic: runs comparable step by step
+            f0 = sim.forces(-1)
+            o = [sim.observables(r)[0] for r in range(len(systems))]
+            sim.step(20)
+            out.append((f0, [(x["pairs_vv"], x["pairs_vw"]) for x in o], sim.state(-1)))
+    rms = np.sqrt((out[0][0] ** 2).sum(1).mean())
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-12 * rms
+    assert out[0][1] == out[1][1]
+    assert np.abs(out[0][2][1] - out[1][2][1]).max() <= 1e-9
+    with pytest.raises(md.MDError, match="cell_size"):
+        md.Simulation(systems, dataclasses.replace(W.Potential(), cell_size=2.0))
+    got = autotune.choose_geometry(systems, skins=(0.3, 0.6), cell_scales=(1.0, 1.5), steps=40,
+                                   warmup=5, cache_path=str(tmp_path / "t.json"))
+    assert got["skin"] in (0.3, 0.6) and got["cell_size"] in (0.0, 1.5 * (2.5 + got["skin"]))
+    assert autotune.choose_geometry(systems, cache_path=str(tmp_path / "t.json"))["cached"]
