@@ -190,6 +190,11 @@ typedef struct {
                               a fixed order (bit-for-bit reproducible), with the second half-kick;
                               the paper's system sizes (Sec. 4, Sec. 5). Same pair set and forces in
                               every method. */
+  int32_t chunk_walk;      /* the atomic Verlet-list kernels (force_accumulate 2, force_tpp below
+                              32): 1 dynamic -- every warp takes its next chunk of molecules from a
+                              work counter; 2 static -- warp w takes chunks w, w + W, ... of the
+                              length-ordered molecules, with the next chunk's molecule index loaded
+                              while this chunk runs (two round trips to memory fewer per chunk) */
 } md_tuning;
 
 typedef struct {
@@ -240,7 +245,8 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 /* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 7 and 12): time
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
  * force_tpp {1,2,4,8,16, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
- * x order_by_length {on,off} on the Verlet lists, and, in the atomic form (force_accumulate 2),
+ * x order_by_length {on,off} on the Verlet lists (in the atomic form also x chunk_walk {dynamic,
+ * static} below force_tpp 32), and, in the atomic form (force_accumulate 2),
  * the cell method (pair_method 3) x force_blocks_per_sm {1,2,4} x force_block {128,256}. Once the
  * caller has set pair_method with md_set_tuning, the tuner keeps that method and times its shapes
  * alone -- with

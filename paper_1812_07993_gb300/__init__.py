@@ -63,7 +63,8 @@ class md_tuning(ctypes.Structure):
     _fields_ = [("force_block", ctypes.c_int32), ("force_blocks_per_sm", ctypes.c_int32),
                 ("force_tpp", ctypes.c_int32), ("order_by_length", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32),
-                ("force_accumulate", ctypes.c_int32), ("pair_method", ctypes.c_int32)]
+                ("force_accumulate", ctypes.c_int32), ("pair_method", ctypes.c_int32),
+                ("chunk_walk", ctypes.c_int32)]
 
 
 class md_obs(ctypes.Structure):
@@ -312,14 +313,16 @@ class Simulation:
         return d, occ[:npores], ads, prof
 
     def set_tuning(self, force_block=0, force_blocks_per_sm=0, force_tpp=0, order_by_length=0,
-                   use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0):
+                   use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0,
+                   chunk_walk=0):
         """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
         deterministic gather, 2 atomic reaction forces; pair_method: 1 Verlet lists, 2 all pairs
         (FP64), 3 cell-tiled kernel without lists (atomic reaction forces), 4 small systems
-        (FP64, at most 16384 molecules: whole steps in one persistent launch)."""
+        (FP64, at most 16384 molecules: whole steps in one persistent launch); chunk_walk (the atomic
+        list kernels): 1 dynamic, 2 static round robin with the next molecule prefetched."""
         t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
-                      steps_per_graph, force_accumulate, pair_method)
+                      steps_per_graph, force_accumulate, pair_method, chunk_walk)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)
 
     def autotune(self, trials: int = 15):

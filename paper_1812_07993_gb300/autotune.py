@@ -51,6 +51,7 @@ def tune(sim: Simulation, trials: int = 15, cache_path: Optional[str] = None,
         t = cache[key]["tuning"]
         sim.set_tuning(force_block=t["force_block"], force_blocks_per_sm=t["force_blocks_per_sm"],
                        force_tpp=t["force_tpp"], order_by_length=t["order_by_length"],
+                       chunk_walk=t.get("chunk_walk", 0),
                        pair_method=t.get("pair_method", 0) if t.get("pair_method") in (1, 3)
                        else 0)
         return {"tuning": t, "us": cache[key]["us"], "cached": True,

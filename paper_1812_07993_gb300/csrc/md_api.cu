@@ -845,6 +845,9 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->steps_per_graph < 0) return fail(c, MD_EINVAL, "steps_per_graph < 0");
   if (t->force_accumulate < 0 || t->force_accumulate > 2)
     return fail(c, MD_EINVAL, "force_accumulate must be 0 (keep), 1 (deterministic) or 2 (atomic)");
+  if (t->chunk_walk < 0 || t->chunk_walk > 2)
+    return fail(c, MD_EINVAL, "chunk_walk must be 0 (keep), 1 (dynamic) or 2 (static)");
+  if (t->chunk_walk) nt.static_chunks = t->chunk_walk == 2 ? 1 : 0;
   if (t->pair_method < 0 || t->pair_method > 4)
     return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists), 2 (all pairs), "
                               "3 (cells) or 4 (small systems)");
@@ -892,6 +895,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->steps_per_graph = c->steps_per_graph;
   t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
   t->pair_method = c->tun.small ? 4 : c->tun.cells ? 3 : (c->tun.all_pairs ? 2 : 1);
+  t->chunk_walk = c->tun.static_chunks ? 2 : 1;
   return MD_OK;
 }
 
@@ -948,18 +952,20 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
           // the all-pairs kernel has a fixed shape: time it once
           if (c->tun.all_pairs && (tp != tpps[0] || bp != bpss[0] || bk != blocks[0] || !lpt))
             continue;
-          Tuning t = c->tun;
-          t.force_block = bk;
-          if (c->mixed) {
-            t.tpp_mixed = tp;
-            t.force_blocks_per_sm_mixed = bp;
-          } else {
-            t.tpp_fp64 = tp;
-            t.force_blocks_per_sm_fp64 = bp;
-          }
-          if (!time_shape(t)) {
-            st = fail(c, MD_ECUDA, "autotune launch failed");
-            break;
+          for (int walk = 0; walk < 2 && st == MD_OK; ++walk) {
+            // the static walk is a shape of the atomic list kernels below force_tpp 32
+            if (walk && !(c->tun.atomic_acc && tp < 32 && !c->tun.all_pairs)) continue;
+            Tuning t = c->tun;
+            t.force_block = bk;
+            t.static_chunks = walk;
+            if (c->mixed) {
+              t.tpp_mixed = tp;
+              t.force_blocks_per_sm_mixed = bp;
+            } else {
+              t.tpp_fp64 = tp;
+              t.force_blocks_per_sm_fp64 = bp;
+            }
+            if (!time_shape(t)) st = fail(c, MD_ECUDA, "autotune launch failed");
           }
         }
     }

@@ -209,6 +209,7 @@ struct Tuning {
   int all_pairs = 0;                  // FP64: every pair each step, no lists (the paper's F1)
   int cells = 0;                      // cell-tiled pair kernel: no Verlet lists (pair_method 3)
   int small = 0;                      // whole steps in one persistent launch (pair_method 4)
+  int static_chunks = 0;              // atomic list kernels: static round-robin chunk walk
   int small_blocks_per_sm = 1;        // blocks of the small-system kernel an SM holds at once
   int df64 = 0;                       // FP64 context, pair terms in double-float (FP32 pairs)
   int sm_count = 152;

@@ -1153,6 +1153,40 @@ __device__ __forceinline__ int next_chunk(const Arrays& a) {
   return c * MPW < a.n_total ? c : -1;
 }
 
+// The chunks of a warp, in one of two walks. Dynamic (stat 0): each chunk from the work counter,
+// so the longest-first chunks go to whichever warp is free. Static (stat 1): warp w takes chunks
+// w, w + W, w + 2W, ... of the length-ordered molecules (W warps in the grid) -- no atomic per
+// chunk -- and the next chunk's molecule index (its place in the processing order) is loaded while
+// this chunk runs, taking two round trips to memory off each chunk's chain of dependent loads.
+template <int MPW, int TPP>
+struct ChunkWalk {
+  int chunk, nw, ip;
+  __device__ __forceinline__ int molecule(const Arrays& a, int t, int lpt) const {
+    return lpt ? MD_CHK(a, a.order[t], a.n_total) : t;
+  }
+  __device__ __forceinline__ void start(const Arrays& a, int stat, int lpt) {
+    const int lane = threadIdx.x & 31;
+    nw = gridDim.x * (blockDim.x >> 5);
+    chunk = stat ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : next_chunk<MPW>(a);
+    if (stat && chunk * MPW >= a.n_total) chunk = -1;
+    const int t = chunk >= 0 ? chunk * MPW + lane / TPP : a.n_total;
+    ip = stat && t < a.n_total ? molecule(a, t, lpt) : 0;
+  }
+  // the molecule of this lane in the current chunk (t < n_total), and the next chunk prefetched
+  __device__ __forceinline__ int take(const Arrays& a, int stat, int lpt, int t) {
+    if (!stat) return t < a.n_total ? molecule(a, t, lpt) : 0;
+    const int here = ip;
+    const int nxt = (chunk + nw) * MPW < a.n_total ? chunk + nw : -1;
+    const int tn = nxt >= 0 ? nxt * MPW + (threadIdx.x & 31) / TPP : a.n_total;
+    ip = tn < a.n_total ? molecule(a, tn, lpt) : 0;
+    return here;
+  }
+  __device__ __forceinline__ void advance(const Arrays& a, int stat) {
+    if (stat) chunk = (chunk + nw) * MPW < a.n_total ? chunk + nw : -1;
+    else chunk = next_chunk<MPW>(a);
+  }
+};
+
 // sum over the TPP lanes that share a molecule (fixed butterfly order: deterministic)
 template <int TPP, typename T>
 __device__ __forceinline__ T group_sum(T v) {
@@ -1287,7 +1321,7 @@ __global__ void __launch_bounds__(256) k_forces_half(Arrays a, PotDev p, int lpt
 // forces agree with the deterministic form to rounding, not bit for bit.
 template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, int lpt,
-                                                            int owe_kick) {
+                                                            int owe_kick, int stat) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
   clear_rebuild_flags(a);
@@ -1297,14 +1331,18 @@ __global__ void __launch_bounds__(256) k_forces_half_atomic(Arrays a, PotDev p, 
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
-  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+  ChunkWalk<MPW, TPP> walk;
+  walk.start(a, stat, lpt);
+  for (; walk.chunk >= 0; walk.advance(a, stat)) {
+    const int chunk = walk.chunk;
     const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     double fx = 0.0, fy = 0.0, fz = 0.0;
+    const int im = walk.take(a, stat, lpt, t);
     int i = 0;
     if (live) {
-      i = lpt ? MD_CHK(a, a.order[t], N) : t;
+      i = im;
       const RepDev& R = a.reps[a.rep[i]];
       const dvec4 xi = a.pos[i];
       const int n = a.n_front[i], nvh = a.n_vh[i];
@@ -2058,7 +2096,7 @@ __global__ void __launch_bounds__(256) k_forces_mixed(Arrays a, PotDev p, int lp
 // zero beforehand; the summation order of the atomic adds varies from run to run.
 template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p, int lpt,
-                                                             int owe_kick) {
+                                                             int owe_kick, int stat) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
   clear_rebuild_flags(a);
@@ -2067,14 +2105,18 @@ __global__ void __launch_bounds__(256) k_forces_mixed_atomic(Arrays a, PotDev p,
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
-  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+  ChunkWalk<MPW, TPP> walk;
+  walk.start(a, stat, lpt);
+  for (; walk.chunk >= 0; walk.advance(a, stat)) {
+    const int chunk = walk.chunk;
     const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const int im = walk.take(a, stat, lpt, t);
     int i = 0;
     if (live) {
-      i = lpt ? MD_CHK(a, a.order[t], N) : t;
+      i = im;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i];
       const dvec4 xi = a.pos[i];
@@ -2210,7 +2252,7 @@ __device__ __forceinline__ void df_accumulate(float& s, float& c, const dword& p
 // forces must be zero beforehand.
 template <int TPP>
 __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, int lpt,
-                                                          int owe_kick) {
+                                                          int owe_kick, int stat) {
   constexpr int MPW = 32 / TPP;
   count_launch(a);
   clear_rebuild_flags(a);
@@ -2219,14 +2261,18 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
   const int N = a.n_total, cap = p.cap;
   const int lane = threadIdx.x & 31, sub = lane & (TPP - 1);
   int cnt = 0;
-  for (int chunk = next_chunk<MPW>(a); chunk >= 0; chunk = next_chunk<MPW>(a)) {
+  ChunkWalk<MPW, TPP> walk;
+  walk.start(a, stat, lpt);
+  for (; walk.chunk >= 0; walk.advance(a, stat)) {
+    const int chunk = walk.chunk;
     const int cnt0 = cnt;
     const int t = chunk * MPW + lane / TPP;
     const bool live = t < N;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const int im = walk.take(a, stat, lpt, t);
     int i = 0;
     if (live) {
-      i = lpt ? MD_CHK(a, a.order[t], N) : t;
+      i = im;
       const RepDev& R = a.reps[a.rep[i]];
       const float4 li = a.lpos[i], ll = a.lpos_lo[i];
       const int n = a.n_front[i];
@@ -3145,7 +3191,7 @@ void launch_mixed(const Arrays& a, const PotDev& p, bool stats, bool kick, const
     // forces start from zero (k_integrate_first clears them in a step); the second half-kick of
     // a step is deferred into the next first half-kick
     if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
-    k_forces_mixed_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
+    k_forces_mixed_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0, t.static_chunks);
     return;
   }
   if (stats) {
@@ -3174,7 +3220,7 @@ void launch_fp64(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, c
                                s>>>(a, p, t.lpt, kick ? 1 : 0);
     } else {
       k_forces_half_atomic<TPP><<<pair_grid((long long)a.n_total * TPP, b, per_sm, t), b, 0,
-                                  s>>>(a, p, t.lpt, kick ? 1 : 0);
+                                  s>>>(a, p, t.lpt, kick ? 1 : 0, t.static_chunks);
     }
     return;
   }
@@ -3215,7 +3261,7 @@ void launch_df(const Arrays& a, const PotDev& p, bool kick, const Tuning& t, cud
   // forces start from zero (k_integrate_first clears them in a step); the second half-kick of a
   // step is deferred into the next first half-kick
   if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
-  k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0);
+  k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, kick ? 1 : 0, t.static_chunks);
 }
 
 // the cell-tiled kernels: one warp's shared memory is a CellWarp
@@ -3313,14 +3359,14 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
   const int b = t.force_block;
   if (mixed) {
     const int gm = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_mixed, t);
-    if (t.atomic_acc) k_forces_mixed_atomic<TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0);
+    if (t.atomic_acc) k_forces_mixed_atomic<TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0, t.static_chunks);
     else k_forces_mixed<false, false, TPP><<<gm, b, 0, s>>>(a, p, t.lpt, 0);
     return;
   }
   const int g = pair_grid((long long)a.n_total * TPP, b, t.force_blocks_per_sm_fp64, t);
-  if (t.df64 && t.atomic_acc) k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  if (t.df64 && t.atomic_acc) k_forces_df_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0, t.static_chunks);
   else if (t.df64) k_forces_df<false, TPP><<<g, b, 0, s>>>(a, p, t.lpt);
-  else if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0);
+  else if (t.atomic_acc) k_forces_half_atomic<TPP><<<g, b, 0, s>>>(a, p, t.lpt, 0, t.static_chunks);
   else k_forces_half<TPP><<<g, b, 0, s>>>(a, p, t.lpt);
 }
 

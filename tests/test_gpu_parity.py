@@ -163,6 +163,34 @@ def test_every_fp64_launch_shape_matches_oracle(shapes, shapes_after_ten, tpp, b
             check_observables(sim, r, s, st)
 
 
+@pytest.mark.parametrize("precision,tol", [(md.MD_PREC_FP64, FORCE_TOL), (md.MD_PREC_DF64, FORCE_TOL),
+                                           (md.MD_PREC_MIXED, 1e-5)])
+@pytest.mark.parametrize("tpp,lpt", [(1, 1), (2, 1), (4, 2), (16, 1)])
+def test_static_chunk_walk_matches_oracle(shapes, shapes_after_ten, precision, tol, tpp, lpt):
+    """The static round-robin chunk walk of the atomic list kernels (the next chunk's molecule
+    prefetched) covers every molecule once: the oracle's forces and pair counts, and in FP64 and
+    double-float the 10-step trajectories."""
+    with md.Simulation(shapes, precision=precision) as sim:
+        sim.set_tuning(force_accumulate=2, force_tpp=tpp, order_by_length=lpt, chunk_walk=2,
+                       force_blocks_per_sm=2)
+        assert sim.tuning()["chunk_walk"] == 2
+        sim.compute_forces()
+        for r, s in enumerate(shapes):
+            g, _, stats = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
+            f = sim.forces(r)
+            if precision == md.MD_PREC_MIXED:
+                assert rms_rel_err(f, g) <= tol, s.name
+            else:
+                assert force_err(f, g) <= tol, s.name
+            o = sim.observables(r)[0]
+            assert (o["pairs_vv"], o["pairs_vw"]) == (stats["pairs_vv"], stats["pairs_vw"])
+        sim.step(10)
+        if precision != md.MD_PREC_MIXED:
+            for r, (s, st) in enumerate(zip(shapes, shapes_after_ten)):
+                x, v = sim.state(r)
+                assert np.abs(wrapped_diff(x, st.x, s)).max() <= TRAJ_TOL, s.name
+
+
 def test_atomic_accumulation_agrees_with_deterministic_to_rounding(shapes):
     """The atomic form sums the same FP64 pair forces in another order: forces agree to a few
     ulps of the force scale, trajectories over 20 steps to round-off growth."""
