@@ -161,7 +161,16 @@ typedef struct {
   int32_t force_tpp;       /* lanes that split one molecule's neighbour list: 1, 2, 4, 8 or 16;
                               FP64 also 32: a warp owns 32 molecules, screens their lists in
                               FP32 and packs the surviving pairs so that every lane of the
-                              FP64 pair terms is busy */
+                              FP64 pair terms is busy; 64 (force_accumulate 2 only, every
+                              precision): the flat stream -- at each rebuild the front rows of
+                              all molecules are copied into one stream of entries (allocated on
+                              first use: up to 128 entries a molecule on average, more is
+                              MD_EOVERFLOW), which the warps split evenly, 32 entries at a time;
+                              each entry is screened in FP32 and (FP64, double-float) the
+                              survivors are queued in registers and evaluated 32 at a time; both
+                              ends of a pair receive its force by FP64 atomic adds (for dilute
+                              systems: a few entries per row). order_by_length and chunk_walk do
+                              not apply to it */
   int32_t order_by_length; /* 1: process molecules longest list first; 2: in cell order */
   int32_t use_graph;       /* 1: md_step replays a captured CUDA graph; 2: plain launches */
   int32_t steps_per_graph; /* MD steps captured per graph replay */
@@ -190,8 +199,8 @@ typedef struct {
                               a fixed order (bit-for-bit reproducible), with the second half-kick;
                               the paper's system sizes (Sec. 4, Sec. 5). Same pair set and forces in
                               every method. */
-  int32_t chunk_walk;      /* the atomic Verlet-list kernels (force_accumulate 2, force_tpp below
-                              32): 1 dynamic -- every warp takes its next chunk of molecules from a
+  int32_t chunk_walk;      /* the atomic Verlet-list kernels (force_accumulate 2, force_tpp 1 to
+                              16): 1 dynamic -- every warp takes its next chunk of molecules from a
                               work counter; 2 static -- warp w takes chunks w, w + W, ... of the
                               length-ordered molecules, with the next chunk's molecule index loaded
                               while this chunk runs (two round trips to memory fewer per chunk) */
@@ -244,9 +253,10 @@ md_status md_get_tuning(const md_ctx* ctx, md_tuning* t);
 
 /* Autotuner (the paper scans threads per block by hand, Sec. 4 and Sec. 5, Figs. 7 and 12): time
  * the pair-force evaluation (md_compute_forces) for every launch shape of a fixed candidate set --
- * force_tpp {1,2,4,8,16, and 32 at FP64} x force_blocks_per_sm {1,2,4,8} x force_block {128,256}
- * x order_by_length {on,off} on the Verlet lists (in the atomic form also x chunk_walk {dynamic,
- * static} below force_tpp 32), and, in the atomic form (force_accumulate 2),
+ * force_tpp {1,2,4,8,16, 32 at FP64, and 64 in the atomic form} x force_blocks_per_sm {1,2,4,8} x
+ * force_block {128,256} x order_by_length {on,off} on the Verlet lists (in the atomic form also x
+ * chunk_walk {dynamic, static} at force_tpp 1 to 16), and, in the atomic form
+ * (force_accumulate 2),
  * the cell method (pair_method 3) x force_blocks_per_sm {1,2,4} x force_block {128,256}. Once the
  * caller has set pair_method with md_set_tuning, the tuner keeps that method and times its shapes
  * alone -- with

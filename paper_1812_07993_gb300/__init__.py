@@ -315,7 +315,8 @@ class Simulation:
     def set_tuning(self, force_block=0, force_blocks_per_sm=0, force_tpp=0, order_by_length=0,
                    use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0,
                    chunk_walk=0):
-        """Launch-shape knobs (0 keeps a value). use_graph: 1 graph replay, 2 plain launches;
+        """Launch-shape knobs (0 keeps a value). force_tpp: lanes per molecule's list (1..16), 32
+        the FP64 packed kernel, 64 the flat stream (atomic form); use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
         deterministic gather, 2 atomic reaction forces; pair_method: 1 Verlet lists, 2 all pairs
         (FP64), 3 cell-tiled kernel without lists (atomic reaction forces), 4 small systems

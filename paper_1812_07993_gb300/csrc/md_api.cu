@@ -292,7 +292,7 @@ md_status sync_status(md_ctx* c) {
 int integrate_flags(const md_ctx* c) {
   int f = 0;
   if (c->tun.atomic_acc || c->tun.cells) f |= kIntZeroForces;
-  if (c->mixed || c->tun.tpp_fp64 == 32 || c->tun.cells) f |= kIntLocalOffsets;
+  if (c->mixed || c->tun.tpp_fp64 >= 32 || c->tun.cells) f |= kIntLocalOffsets;
   if (c->tun.df64) f |= kIntLocalOffsets | kIntLocalOffsetsLo;
   return f;
 }
@@ -817,6 +817,30 @@ md_status md_create_batch(const md_system* systems, int32_t n_replicas, const md
   return create_impl(systems, n_replicas, pot, stream, out);
 }
 
+// the flat stream's arrays (force_tpp 64), allocated on first use (their capacity: kFlatPerMol
+// entries a molecule, at most a row's); *fresh says whether they are new (then the stream must be
+// filled by a rebuild, and graphs captured before hold none of them)
+md_status ensure_flat(md_ctx* c, bool* fresh) {
+  *fresh = false;
+  if (c->a.flat_ent) return MD_OK;
+  const long long cap = (long long)c->a.n_total * std::min(c->pot.cap, kFlatPerMol);
+  uint32_t* ent = nullptr;
+  int32_t *own = nullptr, *part = nullptr, *n = nullptr;
+  md_status st;
+  if ((st = dalloc(c, &ent, (size_t)cap)) != MD_OK) return st;
+  if ((st = dalloc(c, &own, (size_t)cap)) != MD_OK) return st;
+  if ((st = dalloc(c, &part, (size_t)c->a.n_total / kFlatBlock + 2)) != MD_OK) return st;
+  if ((st = dalloc(c, &n, 1)) != MD_OK) return st;
+  c->a.flat_own = own;
+  c->a.flat_part = part;
+  c->a.n_flat = n;
+  c->a.flat_cap = cap;
+  c->a.flat_ent = ent;
+  *fresh = true;
+  destroy_graph(c);
+  return MD_OK;
+}
+
 md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (!c || !t) return MD_EINVAL;
   Tuning nt = c->tun;
@@ -833,8 +857,9 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   }
   if (t->force_tpp) {
     if (t->force_tpp != 1 && t->force_tpp != 2 && t->force_tpp != 4 && t->force_tpp != 8 &&
-        t->force_tpp != 16 && !(t->force_tpp == 32 && !c->mixed && !c->tun.df64))
-      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4, 8 or 16 (or 32 at FP64)");
+        t->force_tpp != 16 && t->force_tpp != kFlatTpp &&
+        !(t->force_tpp == 32 && !c->mixed && !c->tun.df64))
+      return fail(c, MD_EINVAL, "force_tpp must be 1, 2, 4, 8, 16 or 64 (or 32 at FP64)");
     if (c->mixed) nt.tpp_mixed = t->force_tpp;
     else nt.tpp_fp64 = t->force_tpp;
   }
@@ -866,13 +891,22 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
     return fail(c, MD_EINVAL, "the cell method adds reaction forces by atomics (force_accumulate 2)");
   const int at = nt.cells ? 1
                  : t->force_accumulate ? (t->force_accumulate == 2 ? 1 : 0) : c->tun.atomic_acc;
+  if (!at && (c->mixed ? nt.tpp_mixed : nt.tpp_fp64) == kFlatTpp)
+    return fail(c, MD_EINVAL, "force_tpp 64 (the flat stream) adds reaction forces by atomics "
+                              "(force_accumulate 2)");
   bool relist = t->order_by_length && (t->order_by_length == 1) != (c->tun.lpt != 0);
   if (t->order_by_length) nt.lpt = t->order_by_length == 1;
   relist = relist || at != c->tun.atomic_acc;  // the deterministic form needs the pair map
   relist = relist || nt.all_pairs != c->tun.all_pairs;  // lists fresh when they come back
   relist = relist || nt.cells != c->tun.cells || nt.small != c->tun.small;
   // the packed kernel screens with the FP32 cell-local offsets: refresh them on the way in
-  relist = relist || (!c->mixed && (nt.tpp_fp64 == 32) != (c->tun.tpp_fp64 == 32));
+  relist = relist || (!c->mixed && (nt.tpp_fp64 >= 32) != (c->tun.tpp_fp64 >= 32));
+  if ((c->mixed ? nt.tpp_mixed : nt.tpp_fp64) == kFlatTpp) {  // the stream is filled at rebuilds
+    bool fresh = false;
+    md_status st = ensure_flat(c, &fresh);
+    if (st != MD_OK) return st;
+    relist = relist || fresh;
+  }
   nt.atomic_acc = at;
   c->tun = nt;
   c->method_chosen = chosen;
@@ -915,7 +949,15 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   double bestv = 1e300;
   md_status st = MD_OK;
   const bool fixed_shape = saved.small;  // the small-system kernel has no shapes to choose
-  const int tpps[6] = {1, 2, 4, 8, 16, 32}, bpss[4] = {1, 2, 4, 8}, blocks[2] = {128, 256};
+  if (saved.atomic_acc && !saved.all_pairs && !saved.cells && !fixed_shape) {
+    bool fresh = false;  // the flat stream is a candidate: its arrays, filled by the rebuilds below
+    if ((s = ensure_flat(c, &fresh)) != MD_OK) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return s;
+    }
+  }
+  const int tpps[7] = {1, 2, 4, 8, 16, 32, kFlatTpp}, bpss[4] = {1, 2, 4, 8},
+            blocks[2] = {128, 256};
   auto time_shape = [&](const Tuning& t) -> bool {
     launch_forces(c->a, c->pot, c->mixed, false, false, t, c->stream);  // warm-up
     for (int k = 0; k < trials; ++k) {
@@ -947,14 +989,18 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     for (int tp : tpps) {
       // the packed kernels are the FP64 path's
       if (tp == 32 && (c->mixed || c->tun.df64)) continue;
+      // the flat stream is an atomic form
+      if (tp == kFlatTpp && (!c->tun.atomic_acc || c->tun.all_pairs)) continue;
       for (int bp : bpss)
         for (int bk : blocks) {
           // the all-pairs kernel has a fixed shape: time it once
           if (c->tun.all_pairs && (tp != tpps[0] || bp != bpss[0] || bk != blocks[0] || !lpt))
             continue;
           for (int walk = 0; walk < 2 && st == MD_OK; ++walk) {
-            // the static walk is a shape of the atomic list kernels below force_tpp 32
+            // the static walk is a shape of the atomic list kernels of force_tpp 1 to 16
             if (walk && !(c->tun.atomic_acc && tp < 32 && !c->tun.all_pairs)) continue;
+            // the flat stream splits the whole list: one processing order is enough
+            if (tp == kFlatTpp && !lpt) continue;
             Tuning t = c->tun;
             t.force_block = bk;
             t.static_chunks = walk;

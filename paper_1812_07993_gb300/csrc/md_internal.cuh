@@ -49,6 +49,10 @@ constexpr int kMaxCap = 1023;  // longest list (vapour + wall neighbours) a mole
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecMixed = 1;
 constexpr int kPrecDF64 = 2;
+// force_tpp of the flat stream: a chunk's rows screened as one stream of entries (atomic form)
+constexpr int kFlatTpp = 64;
+constexpr int kFlatPerMol = 128;  // the flat stream's capacity per molecule (at most the row's)
+constexpr int kFlatBlock = 1024;  // molecules per block of the stream's fill
 
 // sticky device status bits
 constexpr int kStatusOverflow = 1;
@@ -135,6 +139,13 @@ struct Arrays {
   int32_t *n_front, *n_back, *n_vh; // front / back lengths; vapour entries at the front
   // optional processing order (longest list first)
   int32_t *order, *hist, *hstart;
+  // the flat stream (force_tpp 64): the front rows in one array, filled at each rebuild once
+  // allocated (NULL until then): entry k is list entry flat_ent[k] of molecule flat_own[k]
+  uint32_t* flat_ent;
+  int32_t* flat_own;
+  int32_t* flat_part;               // entries per block of the fill
+  int32_t* n_flat;                  // the stream's length
+  long long flat_cap;               // entries the stream holds (more: MD_EOVERFLOW)
   int32_t* work;                    // next chunk of the pair kernel
   unsigned int* work_done;          // blocks of the pair kernel that finished
   // FP64 half-list path
@@ -201,7 +212,8 @@ struct Tuning {
   int force_blocks_per_sm_fp64 = 1;   // resident blocks per SM of the pair kernels (grid size)
   int force_blocks_per_sm_mixed = 4;
   int tpp_fp64 = 2;                   // lanes sharing one molecule's list in the pair kernels;
-                                      // 32: the FP64 packed kernel (lanes share packed pairs)
+                                      // 32: the FP64 packed kernel (lanes share packed pairs);
+                                      // 64 (kFlatTpp): the flat stream (atomic form)
   int tpp_mixed = 4;
   int gather_tpp = 2;                 // lanes per molecule in the FP64 reverse gather
   int lpt = 1;                        // process molecules longest list first

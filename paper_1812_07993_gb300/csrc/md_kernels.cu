@@ -2320,6 +2320,271 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
   finish_chunks(a);
 }
 
+// ------------------------------------------------------------------------------------------------
+// The flat stream (force_tpp 64; atomic form), for dilute systems: a row there holds a few entries,
+// and a kernel that walks molecules spends its time on each molecule's chain of dependent loads
+// (its row's place, the row, the partners) with too few molecules per SM to hide it, and on lanes
+// idling through other lanes' pair terms. Here the front rows of all molecules are copied at each
+// rebuild into one stream -- entry k of it is list entry flat_ent[k] of molecule flat_own[k], the
+// molecules in their stored (cell) order -- and the pair kernel splits the stream evenly: warp w of
+// W takes tiles [w T / W, (w + 1) T / W) of the T tiles of 32 entries, so every warp has the same
+// number of entries whatever the rows' lengths, with no work counter and no per-molecule loop. A
+// lane loads its entries' owners and partners (kStreamBatch tiles at once), screens each entry in
+// FP32 on the cell-local offsets and -- FP64 and double-float -- the entries that may lie within the
+// cutoff (FP32 r^2 below rc^2 (1 + 1e-5)) join the warp's queue, a ring in shared memory; whenever
+// 32 are waiting the pair terms run with every lane busy (the cutoff decided in FP64, Eq. 2 in FP64
+// or double-float words). The mixed form evaluates its FP32 pair
+// terms where it screens them. Both ends of a pair receive its force by FP64 atomic adds (the owner
+// +p, a vapour partner -p): no per-molecule sum, so no FP64 adds besides the pair term's own. The
+// forces must be zero beforehand; the order of the adds varies from run to run.
+constexpr int kStreamBatch = 4;   // tiles of 32 entries a lane loads before screening them
+
+// The stream's fill, first pass: the front entries of each block of kFlatBlock molecules
+__global__ void __launch_bounds__(kFlatBlock) k_flat_count(Arrays a, PotDev p) {
+  count_launch(a);
+  __shared__ int ws[kFlatBlock / 32];
+  __shared__ int s_go;
+  if (threadIdx.x == 0) s_go = !halted(a) && need_rebuild(a, p);
+  __syncthreads();
+  if (!s_go) return;  // (uniform in the block)
+  const int i = blockIdx.x * kFlatBlock + threadIdx.x;
+  int n = i < a.n_total ? a.n_front[i] : 0;
+  n = warp_sum(n);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = warp_sum(ws[threadIdx.x]);
+    if (threadIdx.x == 0) a.flat_part[blockIdx.x] = t;
+  }
+}
+
+// Second pass: each block's place in the stream (the sum of the blocks before it), each molecule's
+// place in its block (a block scan), then every warp copies its 32 rows, 32 entries at a time. The
+// last block writes the stream's length.
+__global__ void __launch_bounds__(kFlatBlock) k_flat_fill(Arrays a, PotDev p) {
+  count_launch(a);
+  __shared__ int ws[kFlatBlock / 32];
+  __shared__ int s_base, s_go;
+  if (threadIdx.x == 0) s_go = !halted(a) && need_rebuild(a, p);
+  __syncthreads();
+  if (!s_go) return;  // (uniform in the block)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the sum of the earlier blocks' counts, in a fixed order
+  int b = 0;
+  for (int k = threadIdx.x; k < blockIdx.x; k += kFlatBlock) b += a.flat_part[k];
+  b = warp_sum(b);
+  if (lane == 0) ws[wid] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = warp_sum(ws[threadIdx.x]);
+    if (threadIdx.x == 0) s_base = t;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kFlatBlock + threadIdx.x;
+  const int n = i < a.n_total ? a.n_front[i] : 0;
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[wid] = incl;  // (read below after the barrier; overwrites the sums above)
+  __syncthreads();
+  int wbase = s_base;
+  for (int k = 0; k < wid; ++k) wbase += ws[k];
+  const int excl = incl - n, T = __shfl_sync(kFull, incl, 31);
+  const int cap = p.cap;
+  for (int k0 = 0; k0 < T; k0 += 32) {
+    const int k = k0 + lane;
+    // the owner of warp entry k: the last lane whose prefix is at most k (its row is not empty)
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (k >= __shfl_sync(kFull, excl, mid)) lo = mid;
+      else hi = mid - 1;
+    }
+    const int slot = k - __shfl_sync(kFull, excl, lo);
+    const int io = __shfl_sync(kFull, i, lo);
+    const long long d = (long long)wbase + k;
+    if (k < T && d >= a.flat_cap) atomicOr(a.status, kStatusOverflow);  // the stream is full
+    if (k < T && d < a.flat_cap) {
+      a.flat_ent[d] = a.nbr[(size_t)MD_CHK(a, io, a.n_total) * cap + MD_CHK(a, slot, cap)];
+      a.flat_own[d] = io;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kFlatBlock - 1)
+    *a.n_flat = (int)min((long long)wbase + T, a.flat_cap);
+}
+
+// One FP64 pair term without a branch (the queued pairs of the flat stream: nearly all lie within
+// the cutoff): the force on the owner, zero beyond the cutoff (decided in FP64); returns whether
+// the pair lies within it. Two such chains of one lane interleave on the FP64 pipe.
+__device__ __forceinline__ bool pair_term_nb(const PotDev& p, const RepDev& R, const dvec4& xi,
+                                             const dvec4& xj, bool wall, double& px, double& py,
+                                             double& pz) {
+  const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+  const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+  const double dz = xi.z - xj.z;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
+  const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
+  const double inv2 = rcp_nr(r2);
+  const double inv6 = inv2 * inv2 * inv2;
+  const double fr = in ? inv2 * inv6 * fma(a12, inv6, -b6) : 0.0;
+  px = fr * dx;
+  py = fr * dy;
+  pz = fr * dz;
+  return in;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_forces_flat(Arrays a, PotDev p, int owe_kick) {
+  // the warp's queue of screened pairs (FP64 and double-float): a ring of 64 slots in shared
+  // memory -- owner, its replica, the list entry -- of which the Q from `head` on are waiting
+  __shared__ int s_own[8][64], s_rep[8][64];
+  __shared__ uint32_t s_ent[8][64];
+  count_launch(a);
+  clear_rebuild_flags(a);
+  if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
+  if (halted(a)) return;
+  const int N = a.n_total, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int E = *a.n_flat;
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  const long long tiles = (E + 31) >> 5;
+  const int t0 = (int)(tiles * w / W), t1 = (int)(tiles * (w + 1) / W);
+  int cnt = 0, Q = 0, head = 0;
+  // the pair terms of the next `n` waiting slots, one per lane (n <= 32)
+  auto evaluate = [&](int n) {
+    __syncwarp();
+    if (lane < n) {
+      const int slot = (head + lane) & 63;
+      const int qi = s_own[wib][slot];
+      const uint32_t qe = s_ent[wib][slot];
+      const RepDev& RQ = a.reps[s_rep[wib][slot]];
+      const int j = MD_CHK(a, (int)(qe & kIndexMask), a.n_total + a.n_wall_total);
+      double fx, fy, fz;
+      bool in;
+      if constexpr (PREC == kPrecDF64) {
+        const float4 li = a.lpos[qi], ll = a.lpos_lo[qi];
+        const float4 b = partner_lpos(a, qe, N), bl = partner_lpos_lo(a, qe, N);
+        dword px, py, pz;
+        in = df_pair_term(a, p, RQ, qi, li, ll, qe, b, bl, N, px, py, pz);
+        fx = dw_to_double(px);
+        fy = dw_to_double(py);
+        fz = dw_to_double(pz);
+      } else {
+        in = pair_term_nb(p, RQ, a.pos[qi], partner_pos(a, qe, N), j >= N, fx, fy, fz);
+      }
+      if (in) {
+        atomicAdd(&a.frc[qi].x, fx);
+        atomicAdd(&a.frc[qi].y, fy);
+        atomicAdd(&a.frc[qi].z, fz);
+        if (j < N) {  // Newton's third law: the partner receives -p
+          atomicAdd(&a.frc[j].x, neg_bits(fx));
+          atomicAdd(&a.frc[j].y, neg_bits(fy));
+          atomicAdd(&a.frc[j].z, neg_bits(fz));
+        }
+        ++cnt;
+      }
+    }
+    head = (head + n) & 63;
+    Q -= n;
+    __syncwarp();
+  };
+  // the lanes whose entry passed the screen (hit) append it to the ring in lane order; 32 waiting
+  // slots run (at most 31 wait before a push of at most 32: the ring never overflows)
+  auto push = [&](bool hit, int hi, int hr, uint32_t he) {
+    const unsigned hm = __ballot_sync(kFull, hit);
+    if (hit) {
+      const int slot = (head + Q + __popc(hm & ((1u << lane) - 1u))) & 63;
+      s_own[wib][slot] = hi;
+      s_rep[wib][slot] = hr;
+      s_ent[wib][slot] = he;
+    }
+    Q += __popc(hm);
+    if (Q >= 32) evaluate(32);
+  };
+  // a batch of kStreamBatch tiles: the entries and owners (the next batch's load while this one is
+  // screened), then the owners' and partners' offsets
+  uint32_t en[kStreamBatch];
+  int on[kStreamBatch];
+  auto load_batch = [&](int tb) {
+#pragma unroll
+    for (int u = 0; u < kStreamBatch; ++u) {
+      const int k = (tb + u) * 32 + lane;
+      const bool valid = tb + u < t1 && k < E;
+      en[u] = valid ? a.flat_ent[k] : 0u;
+      on[u] = valid ? MD_CHK(a, a.flat_own[k], N) : -1;
+    }
+  };
+  if (t0 < t1) load_batch(t0);
+  for (int tb = t0; tb < t1; tb += kStreamBatch) {
+    uint32_t e[kStreamBatch];
+    int own[kStreamBatch];
+    float4 li[kStreamBatch], b[kStreamBatch];
+    int rr[kStreamBatch];
+#pragma unroll
+    for (int u = 0; u < kStreamBatch; ++u) {
+      e[u] = en[u];
+      own[u] = on[u];
+      const int i = own[u] >= 0 ? own[u] : 0;
+      li[u] = a.lpos[i];
+      rr[u] = a.rep[i];
+      b[u] = partner_lpos(a, e[u], N);
+    }
+    if (tb + kStreamBatch < t1) load_batch(tb + kStreamBatch);  // (warp-uniform)
+#pragma unroll
+    for (int u = 0; u < kStreamBatch; ++u) {
+      const RepDev& R = a.reps[rr[u]];
+      const uint32_t eu = e[u];
+      const int j = MD_CHK(a, (int)(eu & kIndexMask), a.n_total + a.n_wall_total);
+      const bool wall = j >= N;
+      const float dx = (li[u].x - b[u].x) - cell_shift((eu >> 26) & 3u, R.lcxf);
+      const float dy = (li[u].y - b[u].y) - cell_shift((eu >> 28) & 3u, R.lcyf);
+      const float dz = (li[u].z - b[u].z) - cell_shift(eu >> 30, R.lczf);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const bool valid = own[u] >= 0;
+      if constexpr (PREC == kPrecMixed) {
+        const float lo = wall ? p.rcw2f_lo : p.rc2f_lo, hi = wall ? p.rcw2f_hi : p.rc2f_hi;
+        bool in = valid && r2 < lo;
+        if (valid && !in && r2 < hi) {  // near rc: the FP64 decision, as the FP64 kernels take it
+          const dvec4 xi = a.pos[own[u]];
+          const dvec4 xj = wall ? a.wpos[j - N] : a.pos[j];
+          const double ex = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
+          const double ey = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+          const double ez = xi.z - xj.z;
+          in = lt_pos(ex * ex + ey * ey + ez * ez, wall ? p.rcw2 : p.rc2);
+        }
+        if (in) {
+          const float a12 = wall ? p.a12wf : p.a12f, b6 = wall ? p.b6wf : p.b6f;
+          const float inv2 = __frcp_rn(r2);
+          const float inv6 = inv2 * inv2 * inv2;
+          const float fr = inv2 * inv6 * fmaf(a12, inv6, -b6);
+          const float px = fr * dx, py = fr * dy, pz = fr * dz;
+          atomicAdd(&a.frc[own[u]].x, widen_f32(px));
+          atomicAdd(&a.frc[own[u]].y, widen_f32(py));
+          atomicAdd(&a.frc[own[u]].z, widen_f32(pz));
+          if (!wall) {  // Newton's third law: the partner receives -p
+            atomicAdd(&a.frc[j].x, widen_f32(-px));
+            atomicAdd(&a.frc[j].y, widen_f32(-py));
+            atomicAdd(&a.frc[j].z, widen_f32(-pz));
+          }
+          ++cnt;
+        }
+      } else {
+        push(valid && r2 < (wall ? p.rcw2f_hi : p.rc2f_hi), own[u], rr[u], eu);
+      }
+    }
+  }
+  if constexpr (PREC != kPrecMixed) {
+    if (Q) evaluate(Q);
+  }
+  const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
+  if (lane == 0 && c) atomicAdd(a.pair_count, c);
+}
+
 // Double-float pair terms, full list (front + back of each row), deterministic: every vapour
 // pair is evaluated from both ends, with no atomics; each molecule sums its own row in slot order
 // and writes its force, with the second half-kick fused when KICK (Fig. 3). The same sum from the
@@ -3168,6 +3433,11 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
       a, p, half, t.atomic_acc, lpt);
   if (lpt) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   if (!mixed && !t.df64 && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
+  if (a.flat_ent) {  // the front rows as one stream (the flat stream's input), once allocated
+    const int nf = std::max(1, nblocks(a.n_total, kFlatBlock));
+    k_flat_count<<<nf, kFlatBlock, 0, s>>>(a, p);
+    k_flat_fill<<<nf, kFlatBlock, 0, s>>>(a, p);
+  }
 }
 
 // the per-molecule pair observables that half rows accumulate by atomics start from zero
@@ -3301,8 +3571,32 @@ void launch_cells(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool
   launch_cells_kernel<false>(a, p, mixed, t, kick ? 1 : 0, s);
 }
 
+// the flat stream (force_tpp 64, atomic form): the front rows as one stream, split evenly
+bool flat_form(bool mixed, const Tuning& t) {
+  return t.atomic_acc && !t.cells && !t.small && !t.all_pairs &&
+         (mixed ? t.tpp_mixed : t.tpp_fp64) == kFlatTpp;
+}
+
+void launch_flat(const Arrays& a, const PotDev& p, bool mixed, int owe, const Tuning& t,
+                 cudaStream_t s) {
+  // the warps split the stream evenly: SMs x blocks per SM blocks, whatever the stream's length
+  const int b = t.force_block;
+  const int g = std::max(1, t.sm_count * (mixed ? t.force_blocks_per_sm_mixed
+                                                : t.force_blocks_per_sm_fp64));
+  if (mixed) k_forces_flat<kPrecMixed><<<g, b, 0, s>>>(a, p, owe);
+  else if (t.df64) k_forces_flat<kPrecDF64><<<g, b, 0, s>>>(a, p, owe);
+  else k_forces_flat<kPrecFP64><<<g, b, 0, s>>>(a, p, owe);
+}
+
 void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, bool kick,
                    const Tuning& t, cudaStream_t s) {
+  if (!stats && flat_form(mixed, t)) {
+    // forces start from zero (k_integrate_first clears them in a step); the second half-kick of
+    // a step is deferred into the next first half-kick
+    if (!kick) k_zero_forces<<<nblocks(a.n_total, 256), 256, 0, s>>>(a);
+    launch_flat(a, p, mixed, kick ? 1 : 0, t, s);
+    return;
+  }
   if (t.small) {  // (a step kicks inside the small-system kernel: here the forces alone)
     if (stats) k_allpairs<true, false><<<nblocks(a.n_total, 128), 128, 0, s>>>(a, p);
     else launch_small_steps(a, p, t, 0, s);
@@ -3372,6 +3666,10 @@ void pair_pass_tpp(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t
 
 void launch_pair_pass(const Arrays& a, const PotDev& p, bool mixed, const Tuning& t,
                       cudaStream_t s) {
+  if (flat_form(mixed, t)) {
+    launch_flat(a, p, mixed, 0, t, s);
+    return;
+  }
   if (t.small) {
     launch_small_steps(a, p, t, 0, s);
     return;
