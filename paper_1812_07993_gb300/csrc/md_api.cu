@@ -458,7 +458,8 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   P.ushift_w = pot->shift_energy ? lj_u(P.rcw2, pot->eps_w, pot->sigma_w) : 0.0;
   P.mass = pot->mass;
   P.inv_mass = 1.0 / pot->mass;
-  P.half_skin2 = 0.25 * pot->skin * pot->skin;
+  // (0.1 % early: the FP32 displacement errs by ~1e-6 of the skin, far inside that margin)
+  P.half_skin2 = 0.25 * pot->skin * pot->skin * (1.0 - 1e-3);
   P.group_disp2 = 0.36 * P.half_skin2;  // 0.6 skin/2
   P.r_ads2 = pot->r_ads * pot->r_ads;
   P.rc2f = (float)P.rc2;
@@ -516,6 +517,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     R.ncy = (int)std::floor(s->Ly / cell);
     R.ncz = std::max(1, (int)std::floor(s->Lz / cell));
     R.lcx = s->Lx / R.ncx; R.lcy = s->Ly / R.ncy; R.lcz = s->Lz / R.ncz;
+    R.ilcx = 1.0 / R.lcx; R.ilcy = 1.0 / R.lcy; R.ilcz = 1.0 / R.lcz;
     R.lcxf = (float)R.lcx; R.lcyf = (float)R.lcy; R.lczf = (float)R.lcz;
     R.lcx_lo = (float)(R.lcx - (double)R.lcxf);
     R.lcy_lo = (float)(R.lcy - (double)R.lcyf);
@@ -647,7 +649,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   const size_t N = (size_t)n_tot;
 #define ALLOC(ptr, cnt)                                 \
   if ((st = dalloc(c, &(ptr), (cnt))) != MD_OK) return bail(st)
-  ALLOC(A.pos, N); ALLOC(A.vel, N); ALLOC(A.frc, N); ALLOC(A.pos_ref, N);
+  ALLOC(A.pos, N); ALLOC(A.vel, N); ALLOC(A.frc, N); ALLOC(A.lref, N);
   ALLOC(A.pos_alt, N); ALLOC(A.vel_alt, N); ALLOC(A.frc_alt, N);
   ALLOC(A.lpos, N); ALLOC(A.lpos_lo, N);
   ALLOC(c->stage_x, 3 * N); ALLOC(c->stage_v, 3 * N);
@@ -698,7 +700,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1); ALLOC(A.chain_done, 1);
   ALLOC(A.thermo_owed, 1); ALLOC(A.bar_arrive, 1); ALLOC(A.bar_release, 1);
   ALLOC(A.rep_disp2, (size_t)n_reps);
-  ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.n_act, 1);
+  ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.act_rep, (size_t)ncell_tot); ALLOC(A.n_act, 1);
   ALLOC(A.status, 2);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);
@@ -753,7 +755,6 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
     }
   }
   if ((st = up(A.pos, pos.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
-  if ((st = up(A.pos_ref, pos.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
   if ((st = up(A.vel, vel.data(), N * sizeof(dvec4))) != MD_OK) return bail(st);
   if ((st = up(A.id, id.data(), N * sizeof(int32_t))) != MD_OK) return bail(st);
   if ((st = up(A.rep, rep.data(), N * sizeof(int32_t))) != MD_OK) return bail(st);
@@ -901,6 +902,9 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   relist = relist || nt.cells != c->tun.cells || nt.small != c->tun.small;
   // the packed kernel screens with the FP32 cell-local offsets: refresh them on the way in
   relist = relist || (!c->mixed && (nt.tpp_fp64 >= 32) != (c->tun.tpp_fp64 >= 32));
+  // the flat stream's rebuilds keep no processing order, the other kernels' no stream
+  relist = relist || ((c->mixed ? nt.tpp_mixed : nt.tpp_fp64) == kFlatTpp) !=
+                         ((c->mixed ? c->tun.tpp_mixed : c->tun.tpp_fp64) == kFlatTpp);
   if ((c->mixed ? nt.tpp_mixed : nt.tpp_fp64) == kFlatTpp) {  // the stream is filled at rebuilds
     bool fresh = false;
     md_status st = ensure_flat(c, &fresh);
@@ -985,6 +989,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     c->tun = saved;
     c->tun.lpt = lpt;
     c->tun.cells = 0;
+    c->tun.flat_fill = c->a.flat_ent ? 1 : 0;  // every list kernel's inputs, for the timings
     if ((st = rebuild_and_forces(c)) != MD_OK) break;
     for (int tp : tpps) {
       // the packed kernels are the FP64 path's
@@ -1041,6 +1046,7 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
     return st;
   }
   c->tun = bestT;
+  c->tun.flat_fill = 0;
   destroy_graph(c);
   // lists (and their processing order) for the chosen shape; forces at the same positions
   if ((st = rebuild_and_forces(c)) != MD_OK) return st;

@@ -4,9 +4,10 @@
 // Layout in HBM (all replicas of a context packed back to back):
 //   vapour, in cell-sorted order (re-sorted at every list build):
 //     pos, vel, frc   32-byte aligned double4 (x, y, z, unused): one 256-bit access per molecule
-//     pos_ref         positions at the last list build (skin check)
 //     lpos            float4, position relative to the centre of the home cell (FP32 staging for the
-//                     list build and the mixed-precision pair kernel)
+//                     list build, the screens and the mixed-precision pair kernels)
+//     lref            float4, lpos at the last list build (the skin check: the displacement since
+//                     then is lpos - lref, both from the same centre)
 //     lpos_lo         float4, that offset minus lpos, rounded to FP32: with lpos the double-float
 //                     offset of the double-float pair kernels
 //     home, id, rep   int32: home cell (packed ix | iy << 10 | iz << 20), caller index within the
@@ -21,6 +22,8 @@
 //     pairbuf         forces of the pairs held by lower partners, [molecule * cap_v + back slot],
 //                     plus one spare entry at the end
 //     fpart           partial force of the half-list pass
+//   flat stream (force_tpp 64, allocated on first use): flat_ent / flat_own, the front rows of all
+//     molecules in cell order, copied at every rebuild
 //   wall (static, sorted by cell once at creation): wpos double4, wlpos and wlpos_lo float4,
 //     wstart (CSR)
 //   cells: per-replica grids of side >= max(rc, rc_w) + skin, at least 3 across x and y.
@@ -31,6 +34,8 @@
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
+
+#include "md_fpconv.cuh"
 
 namespace mdk {
 
@@ -86,6 +91,7 @@ struct RepDev {
   double T0, dt, lam_coef;          // lam_coef = n_th dt / tau_B
   double slab_half;
   double lcx, lcy, lcz;             // cell sides
+  double ilcx, ilcy, ilcz;          // and their inverses (the device's cell assignment)
   double bin_width;
   float lcxf, lcyf, lczf;
   uint32_t hi_thr_x, hi_thr_y;      // high word of L/2: |d| above it needs the periodic image
@@ -129,10 +135,11 @@ struct PotDev {
 
 // Device pointers of one context (passed by value to kernels).
 struct Arrays {
-  dvec4 *pos, *vel, *frc, *pos_ref;
+  dvec4 *pos, *vel, *frc;
   dvec4 *pos_alt, *vel_alt, *frc_alt;
   float4* lpos;
   float4* lpos_lo;                  // double-float pair terms: lpos's remainder, offset - lpos
+  float4* lref;                     // lpos at the last list build (skin check)
   int32_t *home, *id, *rep, *id_alt;
   int32_t *cell_tmp, *slot_tmp, *perm_tmp;
   uint32_t* nbr;                    // [molecule * cap + slot]: front (j > i, walls), back (j < i)
@@ -177,6 +184,7 @@ struct Arrays {
                                     // pattern of a double; 0 below it); all-ones bytes when the
                                     // host asks for a rebuild; cleared by the pair kernel
   int32_t* act_cells;               // cells with molecules of the replicas being rebuilt
+  int32_t* act_rep;                 // and their replicas
   int32_t* n_act;                   // their number
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
@@ -222,6 +230,8 @@ struct Tuning {
   int cells = 0;                      // cell-tiled pair kernel: no Verlet lists (pair_method 3)
   int small = 0;                      // whole steps in one persistent launch (pair_method 4)
   int static_chunks = 0;              // atomic list kernels: static round-robin chunk walk
+  int flat_fill = 0;                  // rebuilds fill the flat stream and the processing order
+                                      // whatever the kernel (the tuner's timings)
   int small_blocks_per_sm = 1;        // blocks of the small-system kernel an SM holds at once
   int df64 = 0;                       // FP64 context, pair terms in double-float (FP32 pairs)
   int sm_count = 152;
@@ -249,6 +259,12 @@ __host__ __device__ inline bool in_pore(int kind, double r0, double r1, double r
 
 __host__ __device__ inline int cell_coord(double u, double half, double l, int nc) {
   int c = (int)floor((u + half) / l);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// the same with the inverse side (a multiplication: FP64 division is a long sequence on this part)
+__host__ __device__ inline int cell_coord_mul(double u, double half, double il, int nc) {
+  int c = (int)floor((u + half) * il);
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 

@@ -107,12 +107,12 @@ __device__ __forceinline__ void local_offset_d(const Arrays& a, const RepDev& R,
   else if ((__double_as_longlong(ly) ^ sgn) > hyb) ly += R.Ly;
 }
 
-// the offset rounded to FP32, for the list test and the mixed terms
+// the offset rounded to FP32, for the list test, the screens, the mixed terms and the skin check
 __device__ __forceinline__ float4 local_offset(const Arrays& a, const RepDev& R, const dvec4& x,
                                                int home) {
   double lx, ly, lz;
   local_offset_d(a, R, x, home, lx, ly, lz);
-  return make_float4((float)lx, (float)ly, (float)lz, 0.f);
+  return make_float4(narrow_f64(lx), narrow_f64(ly), narrow_f64(lz), 0.f);
 }
 
 // 1/x for a positive normal double x in [2^-126, 2^127] (squared distances), without an FP64
@@ -153,40 +153,14 @@ __device__ __forceinline__ float cell_shift(uint32_t code, float lc) {
   return code == 0u ? -lc : (code == 2u ? lc : 0.f);
 }
 
-// exact widening of an FP32 number to FP64 (IEEE 754 binary32 -> binary64) with integer operations
-// only (a hardware conversion runs on the FP64 pipe's rate): sign kept, exponent rebiased by
-// 1023 - 127 = 896, mantissa moved up by 29 bits; zero, subnormals (renormalised), infinities and
-// NaNs handled by their own cases
-__device__ __forceinline__ double widen_f32(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned sgn = u & 0x80000000u, m = u & 0x7fffffffu;
-  unsigned hi, lo;
-  if (m - 0x00800000u < 0x7f000000u) {  // normal: biased exponent in [1, 254]
-    hi = sgn | ((m >> 3) + (896u << 20));
-    lo = m << 29;
-  } else if (m == 0u) {
-    hi = sgn;
-    lo = 0u;
-  } else if (m >= 0x7f800000u) {        // infinity or NaN: all-ones exponent
-    hi = sgn | 0x7ff00000u | ((m & 0x007fffffu) >> 3);
-    lo = m << 29;
-  } else {                              // subnormal: m * 2^-149, normalised
-    const int sh = __clz(m) - 8;        // moves the leading bit to bit 23
-    const unsigned mn = (m << sh) & 0x007fffffu;
-    hi = sgn | ((unsigned)(897 - sh) << 20) | (mn >> 3);
-    lo = mn << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // the offset as a double-float pair: hi = FP32 rounding (lpos), lo = FP32 rounding of the rest
 __device__ __forceinline__ void local_offset_df(const Arrays& a, const RepDev& R, const dvec4& x,
                                                 int home, float4& hi, float4& lo) {
   double lx, ly, lz;
   local_offset_d(a, R, x, home, lx, ly, lz);
-  hi = make_float4((float)lx, (float)ly, (float)lz, 0.f);
-  lo = make_float4((float)(lx - widen_f32(hi.x)), (float)(ly - widen_f32(hi.y)),
-                   (float)(lz - widen_f32(hi.z)), 0.f);
+  hi = make_float4(narrow_f64(lx), narrow_f64(ly), narrow_f64(lz), 0.f);
+  lo = make_float4(narrow_f64(lx - widen_f32(hi.x)), narrow_f64(ly - widen_f32(hi.y)),
+                   narrow_f64(lz - widen_f32(hi.z)), 0.f);
 }
 
 // ---- double-float ("double-word") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, two
@@ -488,25 +462,23 @@ __device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int p
   else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
   const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
   if (bad) atomicOr(a.status, kStatusUnstable);
-  const dvec4 r0 = a.pos_ref[i];
-  double dx = x.x - r0.x, dy = x.y - r0.y;
-  if (ge_pos(dx, R.hx)) dx -= R.Lx;
-  else if (gt_pos(neg_bits(dx), R.hx)) dx += R.Lx;
-  if (ge_pos(dy, R.hy)) dy -= R.Ly;
-  else if (gt_pos(neg_bits(dy), R.hy)) dy += R.Ly;
-  const double dz = x.z - r0.z;
-  const double d2 = bad ? 0.0 : dx * dx + dy * dy + dz * dz;
   a.pos[i] = x;
   a.vel[i] = v;
   if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+  // the FP32 offset from the home cell's centre (periodic in x and y); the displacement since the
+  // last build is its change, both offsets taken from the same centre: FP32 work, no FP64
+  float4 hi;
   if (flags & kIntLocalOffsetsLo) {
-    float4 hi, lo;
+    float4 lo;
     local_offset_df(a, R, x, a.home[i], hi, lo);
-    a.lpos[i] = hi;
     a.lpos_lo[i] = lo;
-  } else if (flags & kIntLocalOffsets) {
-    a.lpos[i] = local_offset(a, R, x, a.home[i]);
+  } else {
+    hi = local_offset(a, R, x, a.home[i]);
   }
+  if (flags & (kIntLocalOffsets | kIntLocalOffsetsLo)) a.lpos[i] = hi;
+  const float4 r0 = a.lref[i];
+  const float dx = hi.x - r0.x, dy = hi.y - r0.y, dz = hi.z - r0.z;
+  const double d2 = bad ? 0.0 : widen_f32(dx * dx + dy * dy + dz * dz);
   if (flags & kIntAbsolute) a.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
   return d2;
 }
@@ -712,9 +684,11 @@ __global__ void k_cell_count(Arrays a, PotDev p) {
   if (own) {
     const RepDev& R = a.reps[a.rep[i]];
     const dvec4 x = a.pos[i];
-    const int ix = cell_coord(x.x, R.hx, R.lcx, R.ncx);
-    const int iy = cell_coord(x.y, R.hy, R.lcy, R.ncy);
-    const int iz = cell_coord(x.z, R.hz, R.lcz, R.ncz);
+    // (a multiplication by the inverse side, not an FP64 division: a molecule a rounding error
+    // outside its cell stays far inside the margin the early skin check leaves)
+    const int ix = cell_coord_mul(x.x, R.hx, R.ilcx, R.ncx);
+    const int iy = cell_coord_mul(x.y, R.hy, R.ilcy, R.ncy);
+    const int iz = cell_coord_mul(x.z, R.hz, R.ilcz, R.ncz);
     c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
     a.cell_tmp[i] = c;
     const int slot = atomicAdd(&a.vcount[c], 1);
@@ -731,7 +705,10 @@ __global__ void k_cell_count(Arrays a, PotDev p) {
     int base = 0;
     if (lane == leader) base = atomicAdd(a.n_act, __popc(fm));
     base = __shfl_sync(kFull, base, leader);
-    if (first) a.act_cells[base + __popc(fm & ((1u << lane) - 1u))] = c;
+    if (first) {
+      a.act_cells[base + __popc(fm & ((1u << lane) - 1u))] = c;
+      a.act_rep[base + __popc(fm & ((1u << lane) - 1u))] = a.rep[i];
+    }
   }
 }
 
@@ -846,11 +823,11 @@ __global__ void k_permute(Arrays a, PotDev p, int count_build) {
   const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
   const int home = pack_home(ix, iy, iz);
   a.home[dst] = home;
-  a.pos_ref[dst] = x;
   float4 lhi, llo;
   local_offset_df(a, R, x, home, lhi, llo);
   a.lpos[dst] = lhi;
   a.lpos_lo[dst] = llo;
+  a.lref[dst] = lhi;  // the skin check's reference
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -922,6 +899,28 @@ __device__ void order_scan_block(const Arrays& a, const PotDev& p) {
   }
 }
 
+// lane l < 27 of a list-build warp: the vapour and wall ranges of neighbour cell l of cell c
+// (replica r) -- (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), periodic in x and y, none beyond z -- with
+// no vapour for a lower cell in the half-row build (a lower cell holds only lower molecule
+// indices in the cell-sorted order: no partner of a front). Empty ranges for c < 0 and lanes 27-31.
+__device__ __forceinline__ void cell_ranges(const Arrays& a, int c, int r, int front_only, int lane,
+                                            int& vj0, int& nv, int& wj0, int& nw) {
+  vj0 = nv = wj0 = nw = 0;
+  if (c < 0 || lane >= 27) return;
+  const RepDev& R = a.reps[r];
+  const int local = c - R.cell_off;
+  const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
+  const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+  const int jz = iz + dz;
+  if (jz < 0 || jz >= R.ncz) return;
+  const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
+  const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+  vj0 = a.vstart[cn];
+  nv = (front_only && cn < c) ? 0 : a.vstart[cn + 1] - vj0;
+  wj0 = a.wstart[cn];
+  nw = a.wstart[cn + 1] - wj0;
+}
+
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
 constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
 
@@ -941,31 +940,37 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   // a fixed grid; each warp takes the occupied cells of the rebuilding replicas in turn (the rows
   // it writes are its cell's molecules', so the order of the cells changes nothing)
   const int n_act = s_run ? *a.n_act : 0;
-  for (int ac = blockIdx.x * kListWarps + w; ac < n_act; ac += gridDim.x * kListWarps) {
-    const int c = MD_CHK(a, a.act_cells[ac], a.n_cells);
-    const int i_begin = a.vstart[c], i_end = a.vstart[c + 1];
-    if (i_end == i_begin) continue;
-    const RepDev& R = a.reps[a.cell_rep[c]];
-    const int local = c - R.cell_off;
-    const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
-    // lane l < 27 describes neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
-    int vj0 = 0, nv = 0, wj0 = 0, nw = 0;
-    uint32_t code = 0;
-    if (lane < 27) {
-      const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
-      const int jz = iz + dz;
-      if (jz >= 0 && jz < R.ncz) {
-        const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
-        const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
-        vj0 = a.vstart[cn];
-        // half rows: a lower cell holds only lower molecule indices (cell-sorted order), no partner
-        // of a front; its vapour is left out of the stream
-        nv = (front_only && cn < c) ? 0 : a.vstart[cn + 1] - vj0;
-        wj0 = a.wstart[cn];
-        nw = a.wstart[cn + 1] - wj0;
-      }
-      code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) | ((uint32_t)(dz + 1) << 30);
+  // lane l < 27 stands for neighbour cell l = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); lane 13 is
+  // the cell itself
+  const uint32_t code =
+      lane < 27 ? ((uint32_t)(lane % 3) << 26) | ((uint32_t)((lane / 3) % 3) << 28) |
+                      ((uint32_t)(lane / 9) << 30)
+                : 0u;
+  // the cells come in a pipeline: the cell after next's index and replica, and the next cell's
+  // neighbour ranges, load while this cell's candidates are screened
+  const int stride = gridDim.x * kListWarps;
+  int ac = blockIdx.x * kListWarps + w;
+  int c_cur = -1, r_cur = 0, c_nxt = -1, r_nxt = 0;
+  if (ac < n_act) {
+    c_cur = MD_CHK(a, a.act_cells[ac], a.n_cells);
+    r_cur = a.act_rep[ac];
+  }
+  if (ac + stride < n_act) {
+    c_nxt = MD_CHK(a, a.act_cells[ac + stride], a.n_cells);
+    r_nxt = a.act_rep[ac + stride];
+  }
+  int vj0, nv, wj0, nw;
+  cell_ranges(a, c_cur, r_cur, front_only, lane, vj0, nv, wj0, nw);
+  for (; c_cur >= 0; ac += stride) {
+    const RepDev& R = a.reps[r_cur];
+    int c_n2 = -1, r_n2 = 0;
+    if (ac + 2 * stride < n_act) {
+      c_n2 = MD_CHK(a, a.act_cells[ac + 2 * stride], a.n_cells);
+      r_n2 = a.act_rep[ac + 2 * stride];
     }
+    int nvj0, nnv, nwj0, nnw;
+    cell_ranges(a, c_nxt, r_nxt, front_only, lane, nvj0, nnv, nwj0, nnw);
+    const int i_begin = __shfl_sync(kFull, vj0, 13), i_end = i_begin + __shfl_sync(kFull, nv, 13);
     const unsigned lt = (1u << lane) - 1u;
     const int N = a.n_total, cap = p.cap;
     uint32_t* stream = sh_stream[w];
@@ -1051,7 +1056,15 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
     }
   #pragma unroll
     for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
-    if (lane == 0) atomicMax(a.max_nb, max_n);
+    if (lane == 0 && max_n) atomicMax(a.max_nb, max_n);
+    c_cur = c_nxt;
+    r_cur = r_nxt;
+    c_nxt = c_n2;
+    r_nxt = r_n2;
+    vj0 = nvj0;
+    nv = nnv;
+    wj0 = nwj0;
+    nw = nnw;
   }
   if (!order) return;
   // the kept rows of the replicas that do not rebuild count too
@@ -3408,6 +3421,8 @@ void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const 
     cudaLaunchKernelEx(&cfg, k_integrate_first<false>, a, p, c, flags);
 }
 
+bool flat_form(bool mixed, const Tuning& t);
+
 void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixed, cudaStream_t s) {
   const int b = 256;
   const int nt = nblocks(a.n_total, b);
@@ -3431,9 +3446,11 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   // the atomic forms walk only the front of each row: half rows
   k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
       a, p, half, t.atomic_acc, lpt);
-  if (lpt) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
+  // the flat stream needs no processing order; its fill runs for it (and for the tuner's timings)
+  const bool flat = flat_form(mixed, t);
+  if (lpt && (!flat || t.flat_fill)) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   if (!mixed && !t.df64 && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
-  if (a.flat_ent) {  // the front rows as one stream (the flat stream's input), once allocated
+  if (a.flat_ent && (flat || t.flat_fill)) {  // the front rows as one stream
     const int nf = std::max(1, nblocks(a.n_total, kFlatBlock));
     k_flat_count<<<nf, kFlatBlock, 0, s>>>(a, p);
     k_flat_fill<<<nf, kFlatBlock, 0, s>>>(a, p);
@@ -3743,7 +3760,8 @@ __global__ void k_load_state(Arrays a, const double* __restrict__ xin,
   const dvec4 x = make_dvec4(xin[3 * (size_t)i], xin[3 * (size_t)i + 1], xin[3 * (size_t)i + 2],
                              0.0);
   a.pos[i] = x;
-  a.pos_ref[i] = x;
+  // the skin check's reference, from the molecule's current home cell (a rebuild follows a load)
+  a.lref[i] = local_offset(a, a.reps[a.rep[i]], x, a.home[i]);
   a.vel[i] = make_dvec4(vin[3 * (size_t)i], vin[3 * (size_t)i + 1], vin[3 * (size_t)i + 2], 0.0);
   a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
   a.id[i] = i - a.reps[a.rep[i]].vap_off;

@@ -144,6 +144,6 @@ def test_options_outside_the_mode_are_rejected():
             with pytest.raises(md.MDError):
                 sim.set_tuning(**bad)
         t, us = sim.autotune(3)
-        assert t["force_tpp"] in (1, 2, 4, 8, 16) and us > 0
+        assert t["force_tpp"] in (1, 2, 4, 8, 16, 64) and us > 0
         g, _, _ = oracle.forces(oracle_params(s), s.x0, s.wall, method=1)
         assert force_err(sim.forces(), g) <= FORCE_TOL

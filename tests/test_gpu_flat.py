@@ -185,3 +185,16 @@ def test_flat_stream_agrees_with_the_per_molecule_atomic_kernel(shapes):
         a.set_tuning(force_accumulate=2, force_tpp=2)
         for r in range(len(shapes)):
             assert force_err(b.forces(r), a.forces(r)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision,tol", PRECS)
+def test_switching_from_the_flat_stream_to_a_per_molecule_kernel(shapes, precision, tol):
+    """The flat stream's rebuilds keep no processing order: switching to a kernel that walks the
+    length-ordered molecules rebuilds the lists (and the order) first."""
+    with flat_sim(shapes, precision) as sim:
+        sim.step(40)
+        assert sim.observables(0)[0]["n_rebuilds"] >= 2
+        sim.set_tuning(force_tpp=4, order_by_length=1)
+        check_forces(sim, shapes, precision, tol)
+        sim.step(5)
+        check_forces(sim, shapes, precision, tol)

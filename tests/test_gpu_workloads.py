@@ -160,7 +160,9 @@ def test_autotune_keeps_state_and_forces(precision, tmp_path):
         res = autotune.tune(sim, trials=3, cache_path=str(tmp_path / "t.json"))
         t = res["tuning"]
         packed = (32,) if precision == md.MD_PREC_FP64 else ()
-        assert t["force_tpp"] in (1, 2, 4, 8, 16) + packed and 1 <= t["force_blocks_per_sm"] <= 8
+        flat = (64,) if t["force_accumulate"] == 2 else ()  # the flat stream: atomic form only
+        assert t["force_tpp"] in (1, 2, 4, 8, 16) + packed + flat
+        assert 1 <= t["force_blocks_per_sm"] <= 8
         assert t["force_block"] in (128, 256) and t["order_by_length"] in (1, 2)
         assert res["us"] > 0 and not res["cached"]
         x1, v1 = sim.state(1)
