@@ -204,6 +204,12 @@ typedef struct {
                               work counter; 2 static -- warp w takes chunks w, w + W, ... of the
                               length-ordered molecules, with the next chunk's molecule index loaded
                               while this chunk runs (two round trips to memory fewer per chunk) */
+  int32_t list_build;      /* the Verlet-list build: 1 (default) the device chooses at each rebuild
+                              -- a thread per molecule when the rebuilding replicas hold at least
+                              65,536 molecules at under 2.5 per occupied cell (dilute vapour), else
+                              a warp per cell;
+                              2 a warp per cell; 3 a thread per molecule. Both give the same lists,
+                              entry for entry. */
 } md_tuning;
 
 typedef struct {

@@ -64,7 +64,7 @@ class md_tuning(ctypes.Structure):
                 ("force_tpp", ctypes.c_int32), ("order_by_length", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32),
                 ("force_accumulate", ctypes.c_int32), ("pair_method", ctypes.c_int32),
-                ("chunk_walk", ctypes.c_int32)]
+                ("chunk_walk", ctypes.c_int32), ("list_build", ctypes.c_int32)]
 
 
 class md_obs(ctypes.Structure):
@@ -314,16 +314,18 @@ class Simulation:
 
     def set_tuning(self, force_block=0, force_blocks_per_sm=0, force_tpp=0, order_by_length=0,
                    use_graph=0, steps_per_graph=0, force_accumulate=0, pair_method=0,
-                   chunk_walk=0):
+                   chunk_walk=0, list_build=0):
         """Launch-shape knobs (0 keeps a value). force_tpp: lanes per molecule's list (1..16), 32
         the FP64 packed kernel, 64 the flat stream (atomic form); use_graph: 1 graph replay, 2 plain launches;
         order_by_length: 1 longest list first, 2 cell order; force_accumulate (FP64): 1
         deterministic gather, 2 atomic reaction forces; pair_method: 1 Verlet lists, 2 all pairs
         (FP64), 3 cell-tiled kernel without lists (atomic reaction forces), 4 small systems
         (FP64, at most 16384 molecules: whole steps in one persistent launch); chunk_walk (the atomic
-        list kernels): 1 dynamic, 2 static round robin with the next molecule prefetched."""
+        list kernels): 1 dynamic, 2 static round robin with the next molecule prefetched;
+        list_build: 1 the device chooses by occupancy, 2 a warp per cell, 3 a thread per
+        molecule."""
         t = md_tuning(force_block, force_blocks_per_sm, force_tpp, order_by_length, use_graph,
-                      steps_per_graph, force_accumulate, pair_method, chunk_walk)
+                      steps_per_graph, force_accumulate, pair_method, chunk_walk, list_build)
         _check(load_library().md_set_tuning(self.ctx, ctypes.byref(t)), self.ctx)
 
     def autotune(self, trials: int = 15):

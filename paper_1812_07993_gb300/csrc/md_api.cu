@@ -700,7 +700,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.kick_pending, 1); ALLOC(A.kick_done, 1); ALLOC(A.chain_done, 1);
   ALLOC(A.thermo_owed, 1); ALLOC(A.bar_arrive, 1); ALLOC(A.bar_release, 1);
   ALLOC(A.rep_disp2, (size_t)n_reps);
-  ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.act_rep, (size_t)ncell_tot); ALLOC(A.n_act, 1);
+  ALLOC(A.act_cells, (size_t)ncell_tot); ALLOC(A.act_rep, (size_t)ncell_tot); ALLOC(A.act_home, (size_t)ncell_tot); ALLOC(A.n_act, 1);
   ALLOC(A.status, 2);
   ALLOC(A.n_rebuilds, 1);
   ALLOC(A.pair_count, 1);
@@ -874,6 +874,10 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   if (t->chunk_walk < 0 || t->chunk_walk > 2)
     return fail(c, MD_EINVAL, "chunk_walk must be 0 (keep), 1 (dynamic) or 2 (static)");
   if (t->chunk_walk) nt.static_chunks = t->chunk_walk == 2 ? 1 : 0;
+  if (t->list_build < 0 || t->list_build > 3)
+    return fail(c, MD_EINVAL, "list_build must be 0 (keep), 1 (device's choice), 2 (warp per cell) "
+                              "or 3 (thread per molecule)");
+  if (t->list_build) nt.list_mode = t->list_build - 1;
   if (t->pair_method < 0 || t->pair_method > 4)
     return fail(c, MD_EINVAL, "pair_method must be 0 (keep), 1 (Verlet lists), 2 (all pairs), "
                               "3 (cells) or 4 (small systems)");
@@ -934,6 +938,7 @@ md_status md_get_tuning(const md_ctx* c, md_tuning* t) {
   t->force_accumulate = c->tun.atomic_acc ? 2 : 1;
   t->pair_method = c->tun.small ? 4 : c->tun.cells ? 3 : (c->tun.all_pairs ? 2 : 1);
   t->chunk_walk = c->tun.static_chunks ? 2 : 1;
+  t->list_build = c->tun.list_mode + 1;
   return MD_OK;
 }
 

@@ -185,6 +185,7 @@ struct Arrays {
                                     // host asks for a rebuild; cleared by the pair kernel
   int32_t* act_cells;               // cells with molecules of the replicas being rebuilt
   int32_t* act_rep;                 // and their replicas
+  int32_t* act_home;                // and their coordinates (ix | iy << 10 | iz << 20)
   int32_t* n_act;                   // their number
   int32_t* kick_pending;            // 1: the second half-kick of the last step is still owed (the
                                     // FP64 atomic form defers it into the next first half-kick)
@@ -230,6 +231,8 @@ struct Tuning {
   int cells = 0;                      // cell-tiled pair kernel: no Verlet lists (pair_method 3)
   int small = 0;                      // whole steps in one persistent launch (pair_method 4)
   int static_chunks = 0;              // atomic list kernels: static round-robin chunk walk
+  int list_mode = 0;                  // list build: 0 the device chooses by occupancy, 1 a warp
+                                      // per cell, 2 a thread per molecule
   int flat_fill = 0;                  // rebuilds fill the flat stream and the processing order
                                       // whatever the kernel (the tuner's timings)
   int small_blocks_per_sm = 1;        // blocks of the small-system kernel an SM holds at once

@@ -679,16 +679,16 @@ __global__ void k_cell_count(Arrays a, PotDev p) {
   if (halted(a) || !need_rebuild(a, p)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool own = i < a.n_total && rep_rebuilds(a, a.rep[i]);
-  int c = 0;
+  int c = 0, ix = 0, iy = 0, iz = 0;
   bool first = false;
   if (own) {
     const RepDev& R = a.reps[a.rep[i]];
     const dvec4 x = a.pos[i];
     // (a multiplication by the inverse side, not an FP64 division: a molecule a rounding error
     // outside its cell stays far inside the margin the early skin check leaves)
-    const int ix = cell_coord_mul(x.x, R.hx, R.ilcx, R.ncx);
-    const int iy = cell_coord_mul(x.y, R.hy, R.ilcy, R.ncy);
-    const int iz = cell_coord_mul(x.z, R.hz, R.ilcz, R.ncz);
+    ix = cell_coord_mul(x.x, R.hx, R.ilcx, R.ncx);
+    iy = cell_coord_mul(x.y, R.hy, R.ilcy, R.ncy);
+    iz = cell_coord_mul(x.z, R.hz, R.ilcz, R.ncz);
     c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
     a.cell_tmp[i] = c;
     const int slot = atomicAdd(&a.vcount[c], 1);
@@ -706,8 +706,10 @@ __global__ void k_cell_count(Arrays a, PotDev p) {
     if (lane == leader) base = atomicAdd(a.n_act, __popc(fm));
     base = __shfl_sync(kFull, base, leader);
     if (first) {
-      a.act_cells[base + __popc(fm & ((1u << lane) - 1u))] = c;
-      a.act_rep[base + __popc(fm & ((1u << lane) - 1u))] = a.rep[i];
+      const int k = base + __popc(fm & ((1u << lane) - 1u));
+      a.act_cells[k] = c;
+      a.act_rep[k] = a.rep[i];
+      a.act_home[k] = pack_home(ix, iy, iz);
     }
   }
 }
@@ -841,12 +843,15 @@ __global__ void k_permute(Arrays a, PotDev p, int count_build) {
 // cell-local offsets as (l_i - l_j) - dc*cell, which is exactly antisymmetric, so i lists j exactly
 // when j lists i; the list radius carries a margin above the FP32 error.
 
-__device__ __forceinline__ void hist_add(const Arrays& a, int h, bool on) {
-  // warp-aggregated histogram update: one atomic per distinct length in the warp
+// warp-aggregated update of a block's length histogram in shared memory (one shared atomic per
+// distinct length in the warp); the block adds its nonzero counts to the global histogram once at
+// the end -- a few hundred thousand cells adding to a few global bins one by one would queue on
+// the same L2 addresses
+__device__ __forceinline__ void hist_add(int* s_hist, int h, bool on) {
   const unsigned act = __ballot_sync(kFull, on);
   if (!on) return;
   const unsigned grp = __match_any_sync(act, h);
-  if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.hist[h], __popc(grp));
+  if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_hist[h], __popc(grp));
 }
 
 // Processing order (optional). Molecules sorted by the length of the list the pair kernel walks
@@ -899,21 +904,163 @@ __device__ void order_scan_block(const Arrays& a, const PotDev& p) {
   }
 }
 
+// Which list build runs: mode 0 lets the device choose -- a thread per molecule when the
+// rebuilding replicas hold at least 65,536 molecules at under 2.5 per occupied cell (dilute vapour,
+// where a warp per cell idles through cells of one molecule; fewer molecules leave too few
+// threads to hide each one's serial walk), else a warp per cell; mode 1 forces the warp per cell,
+// mode 2 the thread per molecule. Both build kernels are launched and read the same device
+// values; the one not chosen returns at once.
+__device__ __forceinline__ bool molecule_build(const Arrays& a, int mode) {
+  if (mode != 0) return mode == 2;
+  long long nm = 0;
+  for (int r = 0; r < a.n_reps; ++r)
+    if (rep_rebuilds(a, r)) nm += a.reps[r].n_vap;
+  const long long na = *reinterpret_cast<volatile const int32_t*>(a.n_act);
+  return nm >= 65536 && 2 * nm < 5 * na;
+}
+
+// the end of either list build, by every thread of a block: the block's longest row into max_nb,
+// and with a processing order its length counts into the global histogram; the last block to
+// finish turns the counts into the start of each length
+__device__ void list_build_finish(const Arrays& a, const PotDev& p, int order, const int* s_hist,
+                                  int s_max, int* s_last) {
+  __syncthreads();
+  if (threadIdx.x == 0 && s_max) atomicMax(a.max_nb, s_max);
+  if (!order) return;
+  for (int b = threadIdx.x; b <= p.cap; b += blockDim.x)
+    if (s_hist[b]) atomicAdd(&a.hist[b], s_hist[b]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *s_last = atomicAdd(a.chain_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  order_scan_block(a, p);
+  if (threadIdx.x == 0) *a.chain_done = 0u;
+}
+
+// Verlet-list build, one thread per molecule, for dilute vapour. Each thread walks its home cell's
+// 27 neighbours in the warp build's order -- every vapour molecule of the 27 cells, then every wall
+// atom -- testing each candidate against its FP32 offset as the warp build does, and writes its own
+// row: the same entries in the same slots (front from the start, back from the end, in candidate
+// order), so either build gives the same lists. Candidates are loaded four at a time.
+constexpr int kListThreads = 128;
+
+__global__ void __launch_bounds__(kListThreads) k_list_build_mol(Arrays a, PotDev p, int half,
+                                                                 int front_only, int order,
+                                                                 int mode) {
+  count_launch(a);
+  if (!need_rebuild(a, p)) return;  // (the flag holds still while the chain runs)
+  __shared__ int s_run, s_last, s_max, s_go;
+  __shared__ int s_hist[kMaxCap + 1];
+  if (threadIdx.x == 0) s_go = molecule_build(a, mode);
+  __syncthreads();
+  if (!s_go) return;  // the warp build runs (uniform: every block reads the same values)
+  if (threadIdx.x == 0) {
+    s_run = !halted(a);
+    s_max = 0;
+  }
+  if (order)
+    for (int b = threadIdx.x; b <= p.cap; b += blockDim.x) s_hist[b] = 0;
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
+  const int N = a.n_total, cap = p.cap;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int len = 0;
+  bool counted = false;
+  if (s_run && i < N) {
+    const int r = a.rep[i];
+    if (!rep_rebuilds(a, r)) {  // a kept row counts towards the processing order as it is
+      len = order_length(a, p, i, half);
+      counted = true;
+    } else {
+      const RepDev& R = a.reps[r];
+      const int home = a.home[i];
+      const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
+      const int c = R.cell_off + (iz * R.ncy + iy) * R.ncx + ix;
+      const float4 li = a.lpos[i];
+      uint32_t* __restrict__ row = a.nbr + (size_t)i * cap;
+      int nf = 0, nb = 0, nvh = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool wallpass = pass == 1;
+        for (int l = 0; l < 27; ++l) {
+          const int dz = l / 9 - 1, dy = (l / 3) % 3 - 1, dx = l % 3 - 1;
+          const int jz = iz + dz;
+          if (jz < 0 || jz >= R.ncz) continue;
+          int jy = iy + dy, jx = ix + dx;  // periodic in x and y
+          jy += jy < 0 ? R.ncy : (jy >= R.ncy ? -R.ncy : 0);
+          jx += jx < 0 ? R.ncx : (jx >= R.ncx ? -R.ncx : 0);
+          const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
+          // half rows: a lower cell holds only lower molecule indices, no partner of a front
+          if (!wallpass && front_only && cn < c) continue;
+          const int k0 = wallpass ? a.wstart[cn] : a.vstart[cn];
+          const int k1 = wallpass ? a.wstart[cn + 1] : a.vstart[cn + 1];
+          const uint32_t code =
+              ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) | ((uint32_t)(dz + 1) << 30);
+          const float ox = cell_shift((uint32_t)(dx + 1), R.lcxf);
+          const float oy = cell_shift((uint32_t)(dy + 1), R.lcyf);
+          const float oz = cell_shift((uint32_t)(dz + 1), R.lczf);
+          for (int k = k0; k < k1; k += 4) {
+            float4 b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int kk = k + u < k1 ? k + u : k;
+              b[u] = wallpass ? a.wlpos[MD_CHK(a, kk, a.n_wall_total)] : a.lpos[MD_CHK(a, kk, N)];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = k + u;
+              if (j >= k1) break;
+              const float ddx = (li.x - b[u].x) - ox, ddy = (li.y - b[u].y) - oy,
+                          ddz = (li.z - b[u].z) - oz;
+              const bool hit = (wallpass || j != i) && ddx * ddx + ddy * ddy + ddz * ddz < p.rl2f;
+              if (!hit) continue;
+              const uint32_t entry = (uint32_t)(wallpass ? N + j : j) | code;
+              if (wallpass || j > i) {  // front, from the row's start
+                if (nf < cap) row[nf] = entry;
+                ++nf;
+              } else if (!front_only) {  // back, from the row's end
+                if (cap - 1 - nb >= 0) row[cap - 1 - nb] = entry;
+                ++nb;
+              }
+            }
+          }
+        }
+        if (!wallpass) nvh = nf;
+      }
+      const int nfc = min(nf, cap), nbc = min(nb, cap - nfc);
+      if (nf + nb > cap || (half && (nvh > p.cap_v || nb > p.cap_v)))
+        atomicOr(a.status, kStatusOverflow);
+      a.n_front[i] = nfc;
+      a.n_back[i] = nbc;
+      a.n_vh[i] = min(nvh, p.cap_v);
+      len = min(half ? nfc : nfc + nbc, cap);
+      counted = true;
+      atomicMax(&s_max, nf + nb);
+    }
+  }
+  if (order) hist_add(s_hist, len, counted);
+  list_build_finish(a, p, order, s_hist, s_max, &s_last);
+}
+
 // lane l < 27 of a list-build warp: the vapour and wall ranges of neighbour cell l of cell c
-// (replica r) -- (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), periodic in x and y, none beyond z -- with
+// (replica r, coordinates packed in home) -- (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), periodic in x and y, none beyond z -- with
 // no vapour for a lower cell in the half-row build (a lower cell holds only lower molecule
 // indices in the cell-sorted order: no partner of a front). Empty ranges for c < 0 and lanes 27-31.
-__device__ __forceinline__ void cell_ranges(const Arrays& a, int c, int r, int front_only, int lane,
-                                            int& vj0, int& nv, int& wj0, int& nw) {
+__device__ __forceinline__ void cell_ranges(const Arrays& a, int c, int r, int home, int front_only,
+                                            int lane, int& vj0, int& nv, int& wj0, int& nw) {
   vj0 = nv = wj0 = nw = 0;
   if (c < 0 || lane >= 27) return;
   const RepDev& R = a.reps[r];
-  const int local = c - R.cell_off;
-  const int ix = local % R.ncx, iy = (local / R.ncx) % R.ncy, iz = local / (R.ncx * R.ncy);
+  const int ix = home & 1023, iy = (home >> 10) & 1023, iz = (home >> 20) & 1023;
   const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
   const int jz = iz + dz;
   if (jz < 0 || jz >= R.ncz) return;
-  const int jy = (iy + dy + R.ncy) % R.ncy, jx = (ix + dx + R.ncx) % R.ncx;
+  int jy = iy + dy, jx = ix + dx;  // periodic in x and y
+  jy += jy < 0 ? R.ncy : (jy >= R.ncy ? -R.ncy : 0);
+  jx += jx < 0 ? R.ncx : (jx >= R.ncx ? -R.ncx : 0);
   const int cn = R.cell_off + (jz * R.ncy + jy) * R.ncx + jx;
   vj0 = a.vstart[cn];
   nv = (front_only && cn < c) ? 0 : a.vstart[cn + 1] - vj0;
@@ -924,16 +1071,26 @@ __device__ __forceinline__ void cell_ranges(const Arrays& a, int c, int r, int f
 constexpr int kListWarps = 4;      // warps (cells) per block of the list build
 constexpr int kStreamWin = 1024;   // candidate-stream window held in shared memory per warp
 
-__global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev p, int half,
-                                                                 int front_only, int order) {
+__global__ void __launch_bounds__(kListWarps * 32, 8) k_list_build(Arrays a, PotDev p, int half,
+                                                                 int front_only, int order,
+                                                                 int mode) {
   count_launch(a);
   if (!need_rebuild(a, p)) return;  // (the flag holds still while the chain runs)
   __shared__ uint32_t sh_stream[kListWarps][kStreamWin];
   __shared__ float4 sh_li[kListWarps][32];
-  __shared__ int s_run, s_last;
+  __shared__ int s_run, s_last, s_max, s_go;
+  __shared__ int s_hist[kMaxCap + 1];  // this block's list-length counts (processing order)
+  if (threadIdx.x == 0) s_go = !molecule_build(a, mode);
+  __syncthreads();
+  if (!s_go) return;  // the thread-per-molecule build runs (uniform in the block)
   // every block reports in at the end (the last one scans the length counts), so a block that
   // finds an error flag raised skips its work but not its report
-  if (threadIdx.x == 0) s_run = !halted(a);
+  if (threadIdx.x == 0) {
+    s_run = !halted(a);
+    s_max = 0;
+  }
+  if (order)
+    for (int b = threadIdx.x; b <= p.cap; b += blockDim.x) s_hist[b] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.n_rebuilds, 1ull);
@@ -950,26 +1107,29 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
   // neighbour ranges, load while this cell's candidates are screened
   const int stride = gridDim.x * kListWarps;
   int ac = blockIdx.x * kListWarps + w;
-  int c_cur = -1, r_cur = 0, c_nxt = -1, r_nxt = 0;
+  int c_cur = -1, r_cur = 0, h_cur = 0, c_nxt = -1, r_nxt = 0, h_nxt = 0;
   if (ac < n_act) {
     c_cur = MD_CHK(a, a.act_cells[ac], a.n_cells);
     r_cur = a.act_rep[ac];
+    h_cur = a.act_home[ac];
   }
   if (ac + stride < n_act) {
     c_nxt = MD_CHK(a, a.act_cells[ac + stride], a.n_cells);
     r_nxt = a.act_rep[ac + stride];
+    h_nxt = a.act_home[ac + stride];
   }
   int vj0, nv, wj0, nw;
-  cell_ranges(a, c_cur, r_cur, front_only, lane, vj0, nv, wj0, nw);
+  cell_ranges(a, c_cur, r_cur, h_cur, front_only, lane, vj0, nv, wj0, nw);
   for (; c_cur >= 0; ac += stride) {
     const RepDev& R = a.reps[r_cur];
-    int c_n2 = -1, r_n2 = 0;
+    int c_n2 = -1, r_n2 = 0, h_n2 = 0;
     if (ac + 2 * stride < n_act) {
       c_n2 = MD_CHK(a, a.act_cells[ac + 2 * stride], a.n_cells);
       r_n2 = a.act_rep[ac + 2 * stride];
+      h_n2 = a.act_home[ac + 2 * stride];
     }
     int nvj0, nnv, nwj0, nnw;
-    cell_ranges(a, c_nxt, r_nxt, front_only, lane, nvj0, nnv, nwj0, nnw);
+    cell_ranges(a, c_nxt, r_nxt, h_nxt, front_only, lane, nvj0, nnv, nwj0, nnw);
     const int i_begin = __shfl_sync(kFull, vj0, 13), i_end = i_begin + __shfl_sync(kFull, nv, 13);
     const unsigned lt = (1u << lane) - 1u;
     const int N = a.n_total, cap = p.cap;
@@ -1050,42 +1210,34 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list_build(Arrays a, PotDev
           a.n_vh[i] = min(nvh, p.cap_v);
           max_n = max(max_n, nf + nb);
         }
-        if (order) hist_add(a, min(half ? nfc : nfc + nbc, cap), own);
+        if (order) hist_add(s_hist, min(half ? nfc : nfc + nbc, cap), own);
       }
       __syncwarp();
     }
   #pragma unroll
     for (int o = 16; o; o >>= 1) max_n = max(max_n, __shfl_xor_sync(kFull, max_n, o));
-    if (lane == 0 && max_n) atomicMax(a.max_nb, max_n);
+    if (lane == 0 && max_n) atomicMax(&s_max, max_n);  // (the block's, added once at the end)
     c_cur = c_nxt;
     r_cur = r_nxt;
+    h_cur = h_nxt;
     c_nxt = c_n2;
     r_nxt = r_n2;
+    h_nxt = h_n2;
     vj0 = nvj0;
     nv = nnv;
     wj0 = nwj0;
     nw = nnw;
   }
-  if (!order) return;
   // the kept rows of the replicas that do not rebuild count too
-  if (s_run) {
+  if (order && s_run) {
     const int nw = gridDim.x * kListWarps;
     for (int base = (blockIdx.x * kListWarps + w) * 32; base < a.n_total; base += nw * 32) {
       const int i = base + lane;
       const bool own = i < a.n_total && !rep_rebuilds(a, a.rep[i]);
-      hist_add(a, own ? order_length(a, p, i, half) : 0, own);
+      hist_add(s_hist, own ? order_length(a, p, i, half) : 0, own);
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(a.chain_done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  order_scan_block(a, p);
-  if (threadIdx.x == 0) *a.chain_done = 0u;
+  list_build_finish(a, p, order, s_hist, s_max, &s_last);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -3444,11 +3596,15 @@ void launch_rebuild(const Arrays& a, const PotDev& p, const Tuning& t, bool mixe
   k_permute<<<nt, b, 0, s>>>(a, p, t.cells);
   if (t.cells) return;  // the cell method walks the sorted cells themselves: no lists, no order
   // the atomic forms walk only the front of each row: half rows
-  k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
-      a, p, half, t.atomic_acc, lpt);
   // the flat stream needs no processing order; its fill runs for it (and for the tuner's timings)
   const bool flat = flat_form(mixed, t);
-  if (lpt && (!flat || t.flat_fill)) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
+  const int order = lpt && (!flat || t.flat_fill) ? 1 : 0;
+  // the two list builds: the device runs the one that suits the occupancy (or the tuning's)
+  k_list_build<<<std::min(nblocks(a.n_cells, kListWarps), t.sm_count * 16), kListWarps * 32, 0, s>>>(
+      a, p, half, t.atomic_acc, order, t.list_mode);
+  k_list_build_mol<<<nblocks(a.n_total, kListThreads), kListThreads, 0, s>>>(
+      a, p, half, t.atomic_acc, order, t.list_mode);
+  if (order) k_order_assign<<<nt, b, 0, s>>>(a, p, half);
   if (!mixed && !t.df64 && !t.atomic_acc) k_fwd_build<<<std::min(nblocks(a.n_total, 8), t.sm_count * 8), 256, 0, s>>>(a, p);
   if (a.flat_ent && (flat || t.flat_fill)) {  // the front rows as one stream
     const int nf = std::max(1, nblocks(a.n_total, kFlatBlock));
