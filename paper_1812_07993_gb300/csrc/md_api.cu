@@ -680,6 +680,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   A.cell_rep = cell_rep_d;
   if (n_tot <= kSmallMax) {  // the small-system method's absolute FP32 positions
     ALLOC(A.xf, N);
+    ALLOC(A.xf_alt, N);
     float4* wxf_d = nullptr;
     ALLOC(wxf_d, (size_t)nw_tot);
     A.wxf = wxf_d;

@@ -167,6 +167,7 @@ struct Arrays {
   int32_t* scan_tiles;              // tile sums of the cell scan
   const int32_t* cell_rep;          // replica of each cell
   float4* xf;                       // absolute FP32 positions (small-system kernel; else NULL)
+  float4* xf_alt;                   // and their second buffer (positions: pos_alt)
   const float4* wxf;                // and the wall's (static)
   const int32_t* row_cell;          // first cell of each row of cells (fixed iy, iz of a replica)
   const int32_t* wnear;             // wall atoms in each cell's 27-cell neighbourhood

@@ -417,14 +417,18 @@ __device__ bool thermo_barrier(const Arrays& a, const PotDev& p, long long owed)
 // its replica, the Berendsen scaling (lambda from the grid barrier), then Fig. 2's half-kick and
 // drift, the reflections, the x/y wrap and the instability test; the FP32 offsets or absolute
 // FP32 position the step's pair kernel screens with. Returns the squared displacement since the
-// molecule's position at the last list build (0 when it left the box).
+// molecule's position at the last list build (0 when it left the box, and in the small-system
+// kernel, which keeps no lists). xin / xout: the positions read and written (the same array but in
+// the small-system kernel, which alternates two).
 constexpr int kIntAbsolute = 8;  // also the absolute FP32 position (small-system kernel)
 
 __device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int pend,
-                                                   long long owed, int flags) {
+                                                   long long owed, int flags,
+                                                   const dvec4* __restrict__ xin, dvec4* xout,
+                                                   float4* xfout) {
   const int my_rep = a.rep[i];
   const RepDev& R = a.reps[my_rep];
-  dvec4 x = a.pos[i], v = a.vel[i];
+  dvec4 x = xin[i], v = a.vel[i];
   const dvec4 x_old = x;
   const dvec4 f = a.frc[i];
   if (owed) {
@@ -462,9 +466,13 @@ __device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int p
   else if (gt_pos(neg_bits(x.y), R.hy)) x.y += R.Ly;
   const bool bad = !(abs_le(x.x, R.hx) && abs_le(x.y, R.hy) && abs_le(x.z, R.hz));
   if (bad) atomicOr(a.status, kStatusUnstable);
-  a.pos[i] = x;
+  xout[i] = x;
   a.vel[i] = v;
   if (flags & kIntZeroForces) a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+  if (flags & kIntAbsolute) {  // the small-system kernel: no lists, no skin check
+    xfout[i] = make_float4(narrow_f64(x.x), narrow_f64(x.y), narrow_f64(x.z), 0.f);
+    return 0.0;
+  }
   // the FP32 offset from the home cell's centre (periodic in x and y); the displacement since the
   // last build is its change, both offsets taken from the same centre: FP32 work, no FP64
   float4 hi;
@@ -478,9 +486,7 @@ __device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int p
   if (flags & (kIntLocalOffsets | kIntLocalOffsetsLo)) a.lpos[i] = hi;
   const float4 r0 = a.lref[i];
   const float dx = hi.x - r0.x, dy = hi.y - r0.y, dz = hi.z - r0.z;
-  const double d2 = bad ? 0.0 : widen_f32(dx * dx + dy * dy + dz * dz);
-  if (flags & kIntAbsolute) a.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
-  return d2;
+  return bad ? 0.0 : widen_f32(dx * dx + dy * dy + dz * dz);
 }
 
 // Fig. 2: v(t+dt/2) = v + a dt/2 ; r(t+dt) = r + v(t+dt/2) dt  (the same r(t+dt) as r + v dt + a dt^2/2)
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(256, 4) k_integrate_first(Arrays a, PotDev p, 
   int trig = 0;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; !halt && i < a.n_total; i += stride) {
-    const double d2 = advance_molecule(a, i, pend, owed, flags);
+    const double d2 = advance_molecule(a, i, pend, owed, flags, a.pos, a.pos, a.xf);
     // a molecule at or beyond skin/2 from its position at the last build triggers a rebuild;
     // molecules below the grouping threshold (nearly all) issue no atomic at all
     if (ge_pos(d2, p.group_disp2))  // rare: only molecules well into their skin
@@ -3219,7 +3225,8 @@ constexpr int kSmallStage = 2816;  // FP32 positions a block stages at a time (4
 // one stream: lanes 0-26 fetch the cells' ranges at once, and the lanes then walk the stream.
 template <bool KICK>
 __device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, float4* stage, int base,
-                            float rcs2, float rcws2) {
+                            float rcs2, float rcws2, const dvec4* __restrict__ P,
+                            const float4* __restrict__ XF) {
   const int lane = threadIdx.x & 31, N = a.n_total;
   const int i = base + (threadIdx.x >> 5);
   const bool live = i < N;
@@ -3227,8 +3234,8 @@ __device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, floa
   const int ri = live ? a.rep[i] : a.rep[base];
   const bool staged = live && &a.reps[ri] == &RB;
   const RepDev& R = a.reps[ri];
-  const dvec4 xi = live ? a.pos[i] : make_dvec4(0.0, 0.0, 0.0, 0.0);
-  const float4 xf = live ? a.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const dvec4 xi = live ? P[i] : make_dvec4(0.0, 0.0, 0.0, 0.0);
+  const float4 xf = live ? XF[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float Lx = R.Lx, Ly = R.Ly, hx = R.hx, hy = R.hy;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   int cnt = 0, Q = 0;
@@ -3237,11 +3244,12 @@ __device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, floa
     if (lane < Q) {
       const uint32_t e = sq[lane];
       double px, py, pz;
-      if (pair_term(a, p, R, xi, e, partner_pos(a, e, N), N, px, py, pz)) {
+      const int j = MD_CHK(a, (int)(e & kIndexMask), a.n_total + a.n_wall_total);
+      if (pair_term(a, p, R, xi, e, j >= N ? a.wpos[j - N] : P[j], N, px, py, pz)) {
         fx += px;
         fy += py;
         fz += pz;
-        cnt += (int)(e & kIndexMask) >= N ? 2 : 1;  // vapour pairs are met from both ends
+        cnt += j >= N ? 2 : 1;  // vapour pairs are met from both ends
       }
     }
     __syncwarp();
@@ -3266,7 +3274,7 @@ __device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, floa
   for (int w0 = RB.vap_off; w0 < RB.vap_off + RB.n_vap; w0 += kSmallStage) {
     const int w1 = min(w0 + kSmallStage, RB.vap_off + RB.n_vap);
     __syncthreads();  // the previous window is screened
-    for (int k = threadIdx.x; k < w1 - w0; k += blockDim.x) cp_async16(&stage[k], &a.xf[w0 + k]);
+    for (int k = threadIdx.x; k < w1 - w0; k += blockDim.x) cp_async16(&stage[k], &XF[w0 + k]);
     cp_async_wait_all();
     __syncthreads();
     if (staged)
@@ -3280,7 +3288,7 @@ __device__ int small_forces(const Arrays& a, const PotDev& p, uint32_t* sq, floa
     for (int j0 = R.vap_off; j0 < R.vap_off + R.n_vap; j0 += 32) {
       const int j = j0 + lane;
       const bool valid = j < R.vap_off + R.n_vap && j != i;
-      push(valid && screen(a.xf[valid ? j : i], rcs2), (uint32_t)j);
+      push(valid && screen(XF[valid ? j : i], rcs2), (uint32_t)j);
     }
   if (live && R.n_wall > 0) {  // the wall atoms of the 27 cells around the molecule
     const int ix = min(max((int)floorf((xf.x + hx) / R.lcxf), 0), R.ncx - 1);
@@ -3362,16 +3370,28 @@ __global__ void __launch_bounds__(256) k_small_steps(Arrays a, PotDev p, int nst
                       // have been loaded or re-sorted since the last step wrote their FP32 copy
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total; i += gridDim.x * blockDim.x) {
       const dvec4 x = a.pos[i];
-      a.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+      a.xf[i] = make_float4(narrow_f64(x.x), narrow_f64(x.y), narrow_f64(x.z), 0.f);
     }
     ok = thermo_barrier(a, p, 0);
     const bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;  // uniform in the block
     for (int base = blockIdx.x * 8; ok && !halt && base < a.n_total; base += nb8)
-      cnt += small_forces<false>(a, p, sq[wib], stage, base, rcs2, rcws2);
+      cnt += small_forces<false>(a, p, sq[wib], stage, base, rcs2, rcws2, a.pos, a.xf);
   }
+  // A block owns the molecules whose forces it takes (base + warp, base = its first 8, then every
+  // nb8 on) and advances exactly those, so a molecule's kick and its next drift are the same
+  // block's: one grid barrier a step (every position advanced before any force), with the
+  // positions in two buffers -- step k reads one and writes the other -- so that a block advancing
+  // into the new buffer never overwrites a position another block is still reading.
   for (int k = 0; k < nsteps && ok; ++k) {
     const long long s = s0 + k + 1;
+    const dvec4* xin = (k & 1) ? a.pos_alt : a.pos;
+    dvec4* xout = (k & 1) ? a.pos : a.pos_alt;
+    float4* xfout = (k & 1) ? a.xf : a.xf_alt;
     if (owed) {  // the previous step's thermostat: v(t+dt)^2 per (replica, chunk), lambda
+      if (k > 0) {  // every block's kick of the previous step is written
+        ok = thermo_barrier(a, p, 0);
+        if (!ok) break;
+      }
       const int units = a.n_reps * a.rep_chunks;
       for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const int r = u / a.rep_chunks, ch = u % a.rep_chunks;
@@ -3384,16 +3404,28 @@ __global__ void __launch_bounds__(256) k_small_steps(Arrays a, PotDev p, int nst
       if (!ok) break;
     }
     const bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;  // uniform in the block
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; !halt && i < a.n_total;
-         i += gridDim.x * blockDim.x)
-      advance_molecule(a, i, pend, owed, kIntAbsolute);
+    for (int r = threadIdx.x >> 3; !halt; r += blockDim.x >> 3) {
+      const int i = (blockIdx.x + r * gridDim.x) * 8 + (threadIdx.x & 7);
+      if (i >= a.n_total) break;
+      advance_molecule(a, i, pend, owed, kIntAbsolute, xin, xout, xfout);
+    }
     ok = thermo_barrier(a, p, 0);
     if (!ok) break;
     for (int base = blockIdx.x * 8; !halt && base < a.n_total; base += nb8)
-      cnt += small_forces<true>(a, p, sq[wib], stage, base, rcs2, rcws2);
-    ok = thermo_barrier(a, p, 0);
+      cnt += small_forces<true>(a, p, sq[wib], stage, base, rcs2, rcws2, xout, xfout);
+    __syncthreads();  // this block's kicks are written before it advances its molecules again
     pend = 0;
     owed = any_thermo_due(a, s) ? s : 0;
+  }
+  // an odd number of steps left the positions in the second buffer: each block copies its own
+  // (nothing reads the first buffer after the last step's barrier)
+  if (nsteps & 1) {
+    for (int r = threadIdx.x >> 3;; r += blockDim.x >> 3) {
+      const int i = (blockIdx.x + r * gridDim.x) * 8 + (threadIdx.x & 7);
+      if (i >= a.n_total) break;
+      a.pos[i] = a.pos_alt[i];
+      a.xf[i] = a.xf_alt[i];
+    }
   }
   const unsigned long long c = warp_sum((unsigned long long)cnt);
   if (lane == 0 && c && nsteps > 0) atomicAdd(a.pair_count, c);

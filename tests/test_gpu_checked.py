@@ -5,7 +5,8 @@ pair slot, a cell or sort index, a staged candidate -- is checked before its acc
 its array would be replaced by an in-bounds index and set the sticky status MD_EBOUNDS. The small
 cylinder, the four 20k pore shapes and a 12-replica uneven batch run 60 steps (list rebuilds
 included) in every pair form -- FP64 deterministic, atomic and packed, all pairs, mixed and
-double-float in both accumulations, the cell method in all three precisions -- in a separate
+double-float in both accumulations, the cell method in all three precisions, the flat stream, the
+small-system method and the thread-per-molecule list build -- in a separate
 process that loads the checked library: no check may fire (the synchronising calls would raise
 MD_EBOUNDS), and forces and pair counts must match the oracle as in the normal build.
 """
@@ -32,20 +33,24 @@ from paper_1812_07993_gb300 import workloads as W
 assert md.library_path().endswith("libmd_checked.so"), md.library_path()
 POT = W.Potential()
 FP64, MIXED, DF64 = md.MD_PREC_FP64, md.MD_PREC_MIXED, md.MD_PREC_DF64
-FORMS = [  # precision, force_accumulate, pair_method, force_tpp (0: keep), small systems only
-    (FP64, 1, 1, 2, False), (FP64, 2, 1, 2, False), (FP64, 2, 1, 32, False),
-    (FP64, 1, 1, 32, False), (FP64, 1, 2, 0, True), (MIXED, 1, 1, 4, False),
-    (MIXED, 2, 1, 4, False), (DF64, 2, 1, 4, False), (DF64, 1, 1, 4, False),
-    (FP64, 2, 3, 0, False), (MIXED, 2, 3, 0, False), (DF64, 2, 3, 0, False),
+FORMS = [  # precision, force_accumulate, pair_method, force_tpp (0: keep; 64 the flat stream),
+    # small systems only, list build (1 the device's choice, 3 a thread per molecule)
+    (FP64, 1, 1, 2, False, 1), (FP64, 2, 1, 2, False, 1), (FP64, 2, 1, 32, False, 1),
+    (FP64, 1, 1, 32, False, 1), (FP64, 1, 2, 0, True, 1), (MIXED, 1, 1, 4, False, 1),
+    (MIXED, 2, 1, 4, False, 1), (DF64, 2, 1, 4, False, 1), (DF64, 1, 1, 4, False, 1),
+    (FP64, 2, 3, 0, False, 1), (MIXED, 2, 3, 0, False, 1), (DF64, 2, 3, 0, False, 1),
+    (FP64, 2, 1, 64, False, 3), (MIXED, 2, 1, 64, False, 3), (DF64, 2, 1, 64, False, 1),
+    (FP64, 1, 1, 2, False, 3), (FP64, 0, 4, 0, True, 1),
 ]
 workloads = [[W.cylinder_pore_1k()], W.pore_shape_systems_20k(),
              W.replica_batch(n_replicas=12, n_max=20000)]
 for k, systems in enumerate(workloads):
-    for prec, acc, method, tpp, small_only in FORMS:
+    for prec, acc, method, tpp, small_only, build in FORMS:
         if small_only and k > 0:
             continue
         with md.Simulation(systems, precision=prec) as sim:
-            sim.set_tuning(force_accumulate=acc, pair_method=method, force_tpp=tpp)
+            sim.set_tuning(force_accumulate=acc, pair_method=method, force_tpp=tpp,
+                           list_build=build)
             sim.step(60)
             sim.sync()
             for r, s in enumerate(systems):

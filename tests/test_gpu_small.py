@@ -83,7 +83,7 @@ def test_forces_and_25_step_trajectory(name):
 def test_runs_are_bitwise_reproducible_and_a_read_changes_nothing():
     s = W.cylinder_pore_1k()
     out = []
-    for split in (None, 10):
+    for split in (None, 10, 7):  # (an odd launch leaves the positions in the second buffer)
         with small_sim([s]) as sim:
             if split:
                 sim.step(split)
@@ -93,8 +93,9 @@ def test_runs_are_bitwise_reproducible_and_a_read_changes_nothing():
             else:
                 sim.step(30)
             out.append(sim.state(0))
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    np.testing.assert_array_equal(out[0][1], out[1][1])
+    for x, v in out[1:]:
+        np.testing.assert_array_equal(out[0][0], x)
+        np.testing.assert_array_equal(out[0][1], v)
 
 
 def test_batch_of_small_replicas_matches_alone():

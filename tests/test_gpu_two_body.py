@@ -33,8 +33,9 @@ def systems():
     return T.cases()
 
 
-FP64_FORMS = [  # (force_tpp (0: keep), force_accumulate, pair_method: 1 lists, 2 all, 3 cells)
-    (1, 2, 1), (2, 2, 1), (4, 2, 1), (8, 2, 1), (16, 2, 1), (32, 2, 1),
+FP64_FORMS = [  # (force_tpp (0: keep; 64 the flat stream), force_accumulate, pair_method: 1
+    # lists, 2 all, 3 cells, 4 small systems)
+    (1, 2, 1), (2, 2, 1), (4, 2, 1), (8, 2, 1), (16, 2, 1), (32, 2, 1), (64, 2, 1),
     (2, 1, 1), (32, 1, 1), (2, 2, 2), (0, 2, 3), (0, 0, 4),
 ]
 
@@ -56,13 +57,13 @@ def test_fp64_pair_forms_within_a_few_ulps_of_exact(systems, tpp, acc, method):
     assert np.sqrt((e ** 2).mean()) <= 3e-16
 
 
-@pytest.mark.parametrize("tpp,acc,method", [(4, 2, 1), (2, 1, 1), (0, 2, 3)])
+@pytest.mark.parametrize("tpp,acc,method", [(4, 2, 1), (64, 2, 1), (2, 1, 1), (0, 2, 3)])
 def test_double_float_pair_terms_near_their_precision(systems, tpp, acc, method):
     e = _errors(systems, md.MD_PREC_DF64, tpp, acc, method)
     assert e.max() <= 5e-13, e.max()
 
 
-@pytest.mark.parametrize("tpp,acc,method", [(4, 2, 1), (4, 1, 1), (0, 2, 3)])
+@pytest.mark.parametrize("tpp,acc,method", [(4, 2, 1), (64, 2, 1), (4, 1, 1), (0, 2, 3)])
 def test_mixed_pair_terms_near_fp32(systems, tpp, acc, method):
     e = _errors(systems, md.MD_PREC_MIXED, tpp, acc, method)
     assert e.max() <= 1e-5, e.max()
