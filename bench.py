@@ -58,24 +58,27 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (the command is in profiles/), valid for the kernel source whose SHA-256 prefix is recorded:
 # traffic is reported as null for any other workload, kernel or source
 NCU_TRAFFIC = {
-    ("pore_shapes_4x20k", "k_forces_half_atomic<2>"):
-        {"bytes_per_launch": 17651968, "source_sha": "9b0d841deedbbce2"},
-    ("pore_shapes_4x20k", "k_forces_atomic_packed"):
-        {"bytes_per_launch": 19108352, "source_sha": "9b0d841deedbbce2"},
-    ("pore_shapes_4x20k", "k_forces_mixed_atomic<4>"):
-        {"bytes_per_launch": 18596864, "source_sha": "9b0d841deedbbce2"},
-    ("pore_shapes_4x20k", "k_forces_df_atomic<4>"):
-        {"bytes_per_launch": 17542144, "source_sha": "9b0d841deedbbce2"},
+    ("cylinder_pore_200k", "k_forces_flat<0>"):
+        {"bytes_per_launch": 23671808, "source_sha": "67b8bab3a4af23e1",
+         "source": "profiles/flat_stream_fp64_cylinder_pore_200k.md"},
+    ("pore_shapes_4x20k", "k_forces_flat<0>"):
+        {"bytes_per_launch": 14621696, "source_sha": "67b8bab3a4af23e1",
+         "source": "profiles/flat_stream_fp64_pore_shapes_4x20k.md"},
 }
 
-# k_list_build, the rebuild chain's dominant kernel, from one ncu capture (--set full) of the
-# relist that set_tuning triggers on the FP64 headline run (half rows): DRAM bytes per launch, its
-# duration there and its DRAM throughput as a fraction of the peak. Keyed like NCU_TRAFFIC.
+# The rebuild chain's dominant kernel -- the list build the device chose on that workload -- from
+# one ncu capture (--set full) inside the bench's rebuild range: DRAM bytes per launch, its
+# duration there and its DRAM throughput as a fraction of the peak. Keyed by (workload, precision,
+# accumulation), valid for the recorded kernel source.
 NCU_LIST_BUILD = {
+    ("cylinder_pore_200k", "fp64", "atomic"):
+        {"kernel": "k_list_build_mol", "dram_bytes_per_launch": 12566528, "duration_us": 81.1,
+         "dram_frac_of_peak": 0.0195, "source_sha": "67b8bab3a4af23e1",
+         "source": "profiles/list_builds_cylinder_pore_200k_and_pore_shapes_4x20k.md"},
     ("pore_shapes_4x20k", "fp64", "atomic"):
-        {"dram_bytes_per_launch": 3202304, "duration_us": 51.7, "dram_frac_of_peak": 0.0078,
-         "source_sha": "9b0d841deedbbce2",
-         "source": "profiles/list_build_integrate_pore_shapes_4x20k.md"},
+        {"kernel": "k_list_build", "dram_bytes_per_launch": 2981376, "duration_us": 52.9,
+         "dram_frac_of_peak": 0.0071, "source_sha": "67b8bab3a4af23e1",
+         "source": "profiles/list_builds_cylinder_pore_200k_and_pore_shapes_4x20k.md"},
 }
 
 
@@ -514,10 +517,11 @@ def roofline(sim, torch, stream, flush, nlaunch, pairs_per_launch, precision, ac
 
 
 def list_build(sim, torch, stream, flush, nlaunch, precision, accumulate, workload):
-    """The rebuild chain alone (md_rebuild_lists: cell sort, Verlet lists, processing order, for
-    every replica), timed with CUDA events on the library's stream, L2 flushed before each; beside
-    it the ncu figures of k_list_build, the chain's dominant kernel. That kernel is bound by
-    instruction issue, not by HBM: its DRAM traffic is a small fraction of the peak."""
+    """The rebuild chain alone (md_rebuild_lists: cell sort, Verlet lists, processing order or
+    flat stream, for every replica), timed with CUDA events on the library's stream, L2 flushed
+    before each; beside it the ncu figures of the list build the device chose, the chain's
+    dominant kernel. Both list builds are bound by instruction issue, not by HBM: their DRAM
+    traffic is a small fraction of the peak."""
     evs = []
     nvtx_push(torch, "rebuild")
     for _ in range(nlaunch):
@@ -536,11 +540,14 @@ def list_build(sim, torch, stream, flush, nlaunch, precision, accumulate, worklo
     nc = NCU_LIST_BUILD.get((workload, precision, accumulate))
     if cells or (nc and nc.get("source_sha") != kernel_sha()):
         nc = None
-    return {"kernel": "k_cell_count" if cells else "k_list_build", "bound": "issue",
+    kernel = ("k_cell_count" if cells else
+              nc["kernel"] if nc else "k_list_build or k_list_build_mol (the device's choice)")
+    return {"kernel": kernel, "bound": "issue",
             "rebuild_chain_ms": ms, "chains_timed": nlaunch,
             "chain": ("cell clear, count, scan, scatter, permute (all replicas; the cell method "
                       "builds no lists)" if cells else
-                      "cell clear, count, scan, scatter, permute, list build, order (all replicas)"),
+                      "cell clear, count, scan, scatter, permute, list build, then the processing "
+                      "order or the flat stream (all replicas)"),
             "ncu": ({"dram_bytes_per_launch": nc["dram_bytes_per_launch"],
                      "duration_us": nc["duration_us"],
                      "dram_frac_of_peak": nc["dram_frac_of_peak"],
