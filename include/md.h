@@ -382,6 +382,17 @@ md_status md_get_sizes(const md_ctx* ctx, int32_t replica, int64_t* n_vapor, int
  * counterpart in the paper. */
 int64_t md_kernel_launches(const md_ctx* ctx);
 
+/* Check of the failure path for device waits (the paper has no counterpart). The step kernels meet
+ * at a grid barrier (the thermostat's sums, and every step of the small-system method), whose
+ * waits are bounded: a block that waits too long raises MD_ETIMEOUT and returns instead of
+ * hanging. This call makes that happen on purpose -- a kernel of two blocks in which one never
+ * arrives -- waits for the other to give up (about a second), checks that the device reported
+ * MD_ETIMEOUT, then clears the status and the barrier so that the context goes on as before.
+ * *seconds (may be NULL) receives the GPU time until the wait gave up. Returns MD_OK when the
+ * timeout was reported, MD_ECUDA otherwise; a status already raised on the context is returned
+ * before anything runs. Synchronises. */
+md_status md_check_barrier_timeout(md_ctx* ctx, double* seconds);
+
 /* Human-readable text of a status, and the last error message of a context (never NULL);
  * md_last_error(NULL) gives the last md_create / md_create_batch failure of the calling thread.
  * No counterpart in the paper. */

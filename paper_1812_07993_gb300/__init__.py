@@ -111,6 +111,7 @@ _SIGNATURES = {
     "md_get_sizes": (ctypes.c_int, [_CTX, ctypes.c_int32, _I64P, _I64P,
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "md_kernel_launches": (ctypes.c_int64, [_CTX]),
+    "md_check_barrier_timeout": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "md_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(md_potential), ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
@@ -361,6 +362,14 @@ class Simulation:
         _check(load_library().md_transfer_bytes(self.ctx, ctypes.byref(h), ctypes.byref(d)),
                self.ctx)
         return h.value, d.value
+
+    def check_barrier_timeout(self) -> float:
+        """Make a bounded device wait run out on purpose and check that it reports MD_ETIMEOUT
+        (md_check_barrier_timeout); the context goes on as before. Returns the GPU seconds until
+        the wait gave up."""
+        sec = ctypes.c_double(0.0)
+        _check(load_library().md_check_barrier_timeout(self.ctx, ctypes.byref(sec)), self.ctx)
+        return sec.value
 
     def kernel_launches(self) -> int:
         return int(load_library().md_kernel_launches(self.ctx))

@@ -1061,6 +1061,38 @@ md_status md_autotune(md_ctx* c, int32_t trials, md_tuning* best, double* best_u
   return MD_OK;
 }
 
+md_status md_check_barrier_timeout(md_ctx* c, double* seconds) {
+  if (!c) return MD_EINVAL;
+  md_status s = sync_status(c);
+  if (s != MD_OK) return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, MD_ECUDA, "cudaEventCreate");
+  }
+  cudaEventRecord(e0, c->stream);
+  launch_barrier_check(c->a, c->pot, c->stream);
+  cudaEventRecord(e1, c->stream);
+  const cudaError_t le = cudaGetLastError();
+  s = le == cudaSuccess ? sync_status(c) : MD_ECUDA;
+  float ms = 0.f;
+  if (le == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (le != cudaSuccess) return fail(c, MD_ECUDA, cudaGetErrorString(le));
+  // the status word and the barrier's count back as they were: the context goes on
+  CUDA_TRY(c, cudaMemsetAsync(c->a.status, 0, 2 * sizeof(int32_t), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->a.bar_arrive, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->last_status_bits = 0;
+  c->err.clear();
+  if (seconds) *seconds = ms * 1e-3;
+  if (s != MD_ETIMEOUT)
+    return fail(c, MD_ECUDA, std::string("the bounded wait did not report its timeout (status: ") +
+                                 md_status_string(s) + ")");
+  return MD_OK;
+}
+
 md_status md_step(md_ctx* c, int64_t n) {
   if (!c) return MD_EINVAL;
   if (n < 0) return fail(c, MD_EINVAL, "negative step count");

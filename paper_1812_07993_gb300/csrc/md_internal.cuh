@@ -192,8 +192,8 @@ struct Arrays {
                                     // FP64 atomic form defers it into the next first half-kick)
   long long* thermo_owed;           // the step whose Berendsen scaling is still owed (0: none):
                                     // paid by the next step kernel, or by launch_settle
-  unsigned long long* bar_arrive;   // the step kernel's grid barrier: arrivals (never reset) and
-  unsigned long long* bar_release;  // the last epoch released
+  unsigned long long* bar_arrive;   // the step kernels' grid barrier: arrivals at the current one
+  unsigned long long* bar_release;  // and its generation (advanced by each completed barrier)
   unsigned int* kick_done;          // last-block detection in k_kick_pending
   unsigned int* chain_done;         // last-block detection in k_list_build
   int32_t* status;                  // [0] sticky status bits; [1] the source line of the first
@@ -313,6 +313,8 @@ void launch_forces(const Arrays& a, const PotDev& p, bool mixed, bool stats, boo
 // pay what the last step left owed -- its deferred second half-kick and its Berendsen scaling --
 // before anything outside a step reads or replaces velocities
 void launch_settle(const Arrays& a, const PotDev& p, cudaStream_t s);
+// a check of the bounded grid-barrier wait: raises the timeout status on purpose (about a second)
+void launch_barrier_check(const Arrays& a, const PotDev& p, cudaStream_t s);
 void launch_observables(const Arrays& a, const PotDev& p, cudaStream_t s);
 
 }  // namespace mdk

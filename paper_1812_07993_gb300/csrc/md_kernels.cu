@@ -369,25 +369,25 @@ constexpr long long kSpinLimit = 1ll << 22;  // polls of a grid-barrier wait (~0
 
 // Grid barrier of the step kernels (co-resident grids only): every block arrives once its work is
 // written; on a step that owes a thermostat (owed != 0) the last to arrive turns the partial sums
-// into lambda for every replica, and then releases the others. Arrivals count up without reset, so the k-th barrier of a context (the grid
-// size G is fixed) releases at bar_release = k, and an arrival that returns old reads its epoch as
-// old / G + 1. A wait is bounded: after kSpinLimit polls the block sets the sticky timeout status
-// and gives up. Returns whether the block may go on.
+// into lambda for every replica, and then releases the others. A generation barrier: a block
+// reads the release generation, then arrives; the block whose arrival completes the count resets
+// the count to zero and advances the generation, which every other block waits to see change. So
+// any grid size works, launch after launch (a context's kernels may differ in grid). A wait is
+// bounded: after kSpinLimit polls the block sets the sticky timeout status and gives up (the count
+// is then left off zero: a context that reported MD_ETIMEOUT must be destroyed). Returns whether
+// the block may go on.
 __device__ bool thermo_barrier(const Arrays& a, const PotDev& p, long long owed) {
   __shared__ int s_last, s_ok;
-  __shared__ unsigned long long s_epoch;
   __syncthreads();  // the block's partial sums are written
   if (threadIdx.x == 0) {
+    const unsigned long long gen = *reinterpret_cast<volatile unsigned long long*>(a.bar_release);
     __threadfence();
-    const unsigned long long G = gridDim.x;
     const unsigned long long old = atomicAdd(a.bar_arrive, 1ull);
-    const unsigned long long epoch = old / G + 1;
-    s_epoch = epoch;
-    s_last = (old % G) == G - 1;
+    s_last = old == gridDim.x - 1ull;
     s_ok = 1;
     if (!s_last) {
       long long spins = 0;
-      while (*reinterpret_cast<volatile unsigned long long*>(a.bar_release) < epoch) {
+      while (*reinterpret_cast<volatile unsigned long long*>(a.bar_release) == gen) {
         if (++spins > kSpinLimit) {
           atomicOr(a.status, kStatusTimeout);
           s_ok = 0;
@@ -406,11 +406,22 @@ __device__ bool thermo_barrier(const Arrays& a, const PotDev& p, long long owed)
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicMax(a.bar_release, s_epoch);
+      atomicExch(a.bar_arrive, 0ull);  // the next barrier counts from zero
+      __threadfence();
+      atomicAdd(a.bar_release, 1ull);  // the others go on
     }
   }
   __syncthreads();  // (s_ok and s_last are read again only after the next barrier's first sync)
   return s_ok != 0;
+}
+
+// A check of the bounded wait: every block but the last arrives at the barrier; the last never
+// does, so the others' waits run out after kSpinLimit polls and raise the timeout status -- the
+// failure a lost block would cause, made on purpose, with nothing left waiting.
+__global__ void k_barrier_check(Arrays a, PotDev p) {
+  count_launch(a);
+  if (blockIdx.x == gridDim.x - 1) return;  // the arrival that never comes
+  thermo_barrier(a, p, 0);
 }
 
 // One molecule's part of a step's start: the owed second half-kick and, after a thermostat step of
@@ -3588,6 +3599,10 @@ int integrate_grid(const Arrays& a, const Tuning& t) {
 
 // launched as a cooperative kernel: the runtime refuses a grid whose blocks cannot all be resident
 // at once (the barrier's bounded wait is the second line of defence)
+void launch_barrier_check(const Arrays& a, const PotDev& p, cudaStream_t s) {
+  k_barrier_check<<<2, 32, 0, s>>>(a, p);
+}
+
 void launch_integrate_first(const Arrays& a, const PotDev& p, bool mixed, const StepConds& c,
                             int flags, const Tuning& t, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
