@@ -3372,10 +3372,12 @@ __global__ void __launch_bounds__(256) k_small_steps(Arrays a, PotDev p, int nst
   const int nb8 = gridDim.x * (blockDim.x >> 5);  // molecules the grid takes per round
   const float rcs2 = (float)(p.rc2 * (1.0 + 2e-4)), rcws2 = (float)(p.rcw2 * (1.0 + 2e-4));
   // the step counter, the owed kick and thermostat, read by every block before any block writes
+  // (block 0 writes them back only at the end, after the first step's barrier, which every block
+  // reaches having read them: no barrier is needed before the first step)
   const long long s0 = *reinterpret_cast<volatile long long*>(a.step);
   int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
   long long owed = thermo_owed(a);
-  bool ok = thermo_barrier(a, p, 0);
+  bool ok = true;
   int cnt = 0;
   if (nsteps == 0) {  // the forces at the current positions (md_compute_forces): positions may
                       // have been loaded or re-sorted since the last step wrote their FP32 copy
