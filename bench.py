@@ -630,8 +630,9 @@ def first_steps(md, systems, potential, stream, nsteps):
 
 def e2e(sim, systems, nsteps, pairs_per_step, torch):
     """Whole-job steps through the public API with host buffers: every step uploads the state of
-    every replica from pinned host memory (md_set_state, replica -1: lists rebuilt, forces
-    evaluated), runs one MD step and reads every force back (md_get_forces, replica -1)."""
+    every replica from pinned host memory (md_set_state, replica -1: lists rebuilt where the skin
+    test asks for it, forces evaluated), runs one MD step and reads every force back
+    (md_get_forces, replica -1)."""
     n = sum(s.n_vapor for s in systems)
     bufs = [torch.empty((n, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
     x, v, f = (b.numpy() for b in bufs)

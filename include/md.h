@@ -294,7 +294,10 @@ md_status md_get_state(md_ctx* ctx, int32_t replica, double* x, double* v);
  * replica = -1 sets every replica from arrays concatenated in replica order.
  * - The rows go by one copy per array into device staging rows.
  * - A kernel checks every row there, then a kernel writes the records only if all rows passed.
- * - Lists are rebuilt and forces re-evaluated.
+ * - The list methods keep the stored order: each record takes its own molecule's row, and lists
+ *   are rebuilt only for the replicas where some molecule lies at least skin/2 from its position
+ *   at the last build (a step's skin test, item 2 at the top of this header). The all-pairs and
+ *   small-system methods keep no lists. Forces are re-evaluated.
  * A failing row gives MD_EINVAL, with its replica and molecule in md_last_error, and leaves the
  * positions and velocities as they were (an owed half-kick is still paid). The step counter is
  * unchanged. Synchronises once at the start and once at the end. */

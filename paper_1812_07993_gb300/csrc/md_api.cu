@@ -319,6 +319,14 @@ md_status rebuild_and_forces(md_ctx* c) {
   return sync_status(c);
 }
 
+// the rebuild chain (its kernels return at once unless the flags ask for a rebuild), then forces
+md_status rebuild_if_due_and_forces(md_ctx* c) {
+  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+  launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  return sync_status(c);
+}
+
 void destroy_graph(md_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -1194,6 +1202,9 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
   // what the last step owes (its second half-kick, its thermostat) is paid before the load resets
   // the flags (a state-preserving step, taken whether or not the rows pass their check)
   launch_settle(c->a, c->pot, c->stream);
+  // the list methods keep the stored order and rebuild only where the skin test asks for it; the
+  // all-pairs and small-system methods keep no lists
+  const bool keep = !c->tun.all_pairs && !c->tun.small;
   if (n) {
     const size_t bytes = 3 * (size_t)n * sizeof(double);
     CUDA_TRY(c, cudaMemcpyAsync(c->stage_x + 3 * (size_t)off, x, bytes, cudaMemcpyHostToDevice,
@@ -1204,13 +1215,19 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
     // every row is checked on the device (inside its replica's box; planar replicas in the
     // plane) before the load, which leaves the state untouched if any row fails
     CUDA_TRY(c, cudaMemsetAsync(c->bad_row, 0x7f, sizeof(int32_t), c->stream));
-    launch_load_state(c->a, c->stage_x, c->stage_v, off, n, c->bad_row, c->stream);
+    if (keep) {  // the load raises the rebuild flags as a step's skin check does
+      CUDA_TRY(c, cudaMemsetAsync(c->a.force_rebuild, 0, sizeof(int), c->stream));
+      CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0,
+                                  sizeof(unsigned long long) * (size_t)c->n_reps, c->stream));
+    }
+    launch_load_state(c->a, c->pot, c->stage_x, c->stage_v, off, n, c->bad_row, keep, c->stream);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(c->status_host + 1, c->bad_row, sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, c->stream));
     c->bytes_d2h += sizeof(int32_t);
   }
-  const md_status st = rebuild_and_forces(c);   // waits for the stream, the check's row included
+  // (both wait for the stream, the check's row included)
+  const md_status st = keep ? rebuild_if_due_and_forces(c) : rebuild_and_forces(c);
   const int32_t bad = c->status_host[1];
   c->status_host[1] = kNoBadRow;
   if (n && bad != kNoBadRow) {

@@ -299,10 +299,13 @@ void launch_small_steps(const Arrays& a, const PotDev& p, const Tuning& t, int n
 // state transfer through device staging rows (caller order, xyz interleaved). The load checks
 // the rows first (positions inside the box, planar replicas in the plane) and loads nothing if
 // any fails; *bad (kNoBadRow beforehand) receives the lowest failing row k as 3 k (outside the
-// box), 3 k + 1 (off the plane) or 3 k + 2 (a non-finite velocity).
+// box), 3 k + 1 (off the plane) or 3 k + 2 (a non-finite velocity). keep_order (the list methods):
+// the records keep their stored order and raise the rebuild flags by the skin test (which must be
+// clear beforehand); otherwise the stored order restarts as the caller's and a full rebuild must
+// follow.
 constexpr int kNoBadRow = 0x7f7f7f7f;  // the byte pattern 0x7f repeated (a memset)
-void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
-                       int* bad, cudaStream_t s);
+void launch_load_state(const Arrays& a, const PotDev& p, const double* xin, const double* vin,
+                       int off, int n, int* bad, bool keep_order, cudaStream_t s);
 void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,
                        cudaStream_t s);
 // the pair kernel alone (no clearing, gather or kick): for timing the dominant kernel

@@ -3973,6 +3973,44 @@ __global__ void k_load_state(Arrays a, const double* __restrict__ xin,
   if (k == 0) *a.kick_pending = 0;  // owed kicks were settled before the load
 }
 
+// The load that keeps the stored order (the list methods): record i takes the caller row of the
+// molecule it holds (row vap_off + id[i] of xin/vin), so the lists, cells and stream still name the
+// right molecules; its FP32 offsets are refreshed and its displacement from its position at the
+// last build is tested as a step tests it -- the replicas where some molecule lies at least skin/2
+// away are flagged (those past the grouping threshold with them), and the chain that follows
+// rebuilds only those, so the lists stay complete (every pair within rc is listed while no
+// molecule is skin/2 from its reference). Forces cleared. Nothing is loaded when k_check_state
+// found a bad row.
+__global__ void k_load_state_keep(Arrays a, PotDev p, const double* __restrict__ xin,
+                                  const double* __restrict__ vin, int off, int n, const int* bad) {
+  count_launch(a);
+  if (*bad != kNoBadRow) return;  // (the same word for every thread)
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int trig = 0;
+  if (k < n) {
+    const int i = off + k;
+    const int r = a.rep[i];
+    const RepDev& R = a.reps[r];
+    const size_t row = MD_CHK(a, (size_t)R.vap_off + (size_t)a.id[i], (size_t)a.n_total);
+    const dvec4 x = make_dvec4(xin[3 * row], xin[3 * row + 1], xin[3 * row + 2], 0.0);
+    a.pos[i] = x;
+    a.vel[i] = make_dvec4(vin[3 * row], vin[3 * row + 1], vin[3 * row + 2], 0.0);
+    a.frc[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    float4 lhi, llo;
+    local_offset_df(a, R, x, a.home[i], lhi, llo);
+    a.lpos[i] = lhi;
+    a.lpos_lo[i] = llo;
+    const float4 r0 = a.lref[i];
+    const float dx = lhi.x - r0.x, dy = lhi.y - r0.y, dz = lhi.z - r0.z;
+    const double d2 = widen_f32(dx * dx + dy * dy + dz * dz);
+    if (ge_pos(d2, p.group_disp2))
+      atomicMax(&a.rep_disp2[r], (unsigned long long)__double_as_longlong(d2));
+    trig = ge_pos(d2, p.half_skin2) ? 1 : 0;
+  }
+  if (__syncthreads_or(trig) && threadIdx.x == 0) atomicExch(a.force_rebuild, 1);
+  if (k == 0) *a.kick_pending = 0;  // owed kicks were settled before the load
+}
+
 // out rows (caller order, xyz interleaved) of molecules [off, off + n) from the records src
 __global__ void k_store_rows(Arrays a, const dvec4* __restrict__ src, double* __restrict__ out,
                              int off, int n) {
@@ -3987,11 +4025,14 @@ __global__ void k_store_rows(Arrays a, const dvec4* __restrict__ src, double* __
   out[3 * row + 2] = v.z;
 }
 
-void launch_load_state(const Arrays& a, const double* xin, const double* vin, int off, int n,
-                       int* bad, cudaStream_t s) {
+void launch_load_state(const Arrays& a, const PotDev& p, const double* xin, const double* vin,
+                       int off, int n, int* bad, bool keep_order, cudaStream_t s) {
   if (n <= 0) return;
   k_check_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n, bad);
-  k_load_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n, bad);
+  if (keep_order)
+    k_load_state_keep<<<nblocks(n, 256), 256, 0, s>>>(a, p, xin, vin, off, n, bad);
+  else
+    k_load_state<<<nblocks(n, 256), 256, 0, s>>>(a, xin, vin, off, n, bad);
 }
 
 void launch_store_rows(const Arrays& a, const dvec4* src, double* out, int off, int n,

@@ -310,7 +310,7 @@ def test_whole_context_transfers_match_per_replica(shapes):
         x2, v2 = sim.state(-1)
         np.testing.assert_array_equal(x2, x)
         np.testing.assert_array_equal(v2, v)
-        # forces re-evaluated at the same positions (lists rebuilt): equal to rounding
+        # forces re-evaluated at the same positions (the lists kept): equal to rounding
         assert force_err(sim.forces(-1), f) <= 1e-13
         bad = x.copy()
         bad[len(shapes[0].x0) + 5, 2] = 1e3
