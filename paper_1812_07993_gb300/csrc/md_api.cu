@@ -266,11 +266,25 @@ md_status device_status(md_ctx* c) {
   return MD_OK;
 }
 
-md_status sync_status(md_ctx* c) {
+// the status word's copy to the host, enqueued
+md_status enqueue_status(md_ctx* c) {
   CUDA_TRY(c, cudaMemcpyAsync(c->status_host, c->a.status, sizeof(int32_t),
                               cudaMemcpyDeviceToHost, c->stream));
   c->bytes_d2h += sizeof(int32_t);
+  return MD_OK;
+}
+
+md_status status_after_sync(md_ctx* c);
+
+md_status sync_status(md_ctx* c) {
+  md_status e = enqueue_status(c);
+  if (e != MD_OK) return e;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return status_after_sync(c);
+}
+
+// the status word copied by enqueue_status, once the stream has reached it
+md_status status_after_sync(md_ctx* c) {
   c->status_pending = false;
   c->last_status_bits = *c->status_host;
   if (c->last_status_bits) {
@@ -1184,12 +1198,12 @@ md_status md_get_state(md_ctx* c, int32_t r, double* x, double* v) {
 
 md_status md_get_forces(md_ctx* c, int32_t r, double* f) {
   if (!check_replica_or_all(c, r) || !f) return fail(c, MD_EINVAL, "bad replica or NULL output");
-  md_status s = sync_status(c);
-  if (s == MD_ECUDA) return s;
-  md_status t = fetch_rows(c, r, c->a.frc, c->stage_x, f);
+  // the status word and the rows behind one synchronisation
+  md_status t = enqueue_status(c);
   if (t != MD_OK) return t;
+  if ((t = fetch_rows(c, r, c->a.frc, c->stage_x, f)) != MD_OK) return t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return s;
+  return status_after_sync(c);
 }
 
 md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
