@@ -2513,10 +2513,10 @@ __global__ void __launch_bounds__(256) k_forces_df_atomic(Arrays a, PotDev p, in
 // number of entries whatever the rows' lengths, with no work counter and no per-molecule loop. A
 // lane loads its entries' owners and partners (kStreamBatch tiles at once), screens each entry in
 // FP32 on the cell-local offsets and -- FP64 and double-float -- the entries that may lie within the
-// cutoff (FP32 r^2 below rc^2 (1 + 1e-5)) join the warp's queue, a ring in shared memory; whenever
-// 32 are waiting the pair terms run with every lane busy (the cutoff decided in FP64, Eq. 2 in FP64
-// or double-float words). The mixed form evaluates its FP32 pair
-// terms where it screens them. Both ends of a pair receive its force by FP64 atomic adds (the owner
+// cutoff (FP32 r^2 below rc^2 (1 + 1e-5)) join the warp's queue, a ring in shared memory; the pair
+// terms run 32 at a time with every lane busy (the cutoff decided in FP64, Eq. 2 in FP64 or
+// double-float words), FP64 with the positions of each round of 32 loaded while the round before
+// it runs. The mixed form evaluates its FP32 pair terms where it screens them. Both ends of a pair receive its force by FP64 atomic adds (the owner
 // +p, a vapour partner -p): no per-molecule sum, so no FP64 adds besides the pair term's own. The
 // forces must be zero beforehand; the order of the adds varies from run to run.
 constexpr int kStreamBatch = 4;   // tiles of 32 entries a lane loads before screening them
@@ -2599,15 +2599,22 @@ __global__ void __launch_bounds__(kFlatBlock) k_flat_fill(Arrays a, PotDev p) {
     *a.n_flat = (int)min((long long)wbase + T, a.flat_cap);
 }
 
-// One FP64 pair term without a branch (the queued pairs of the flat stream: nearly all lie within
-// the cutoff): the force on the owner, zero beyond the cutoff (decided in FP64); returns whether
-// the pair lies within it. Two such chains of one lane interleave on the FP64 pipe.
+// One FP64 pair term without a branch on the cutoff (the queued pairs of the flat stream: nearly
+// all lie within it): the force on the owner, zero beyond the cutoff (decided in FP64); returns
+// whether the pair lies within it.
 __device__ __forceinline__ bool pair_term_nb(const PotDev& p, const RepDev& R, const dvec4& xi,
-                                             const dvec4& xj, bool wall, double& px, double& py,
-                                             double& pz) {
-  const double dx = image_hi(xi.x - xj.x, R.Lx, R.hi_thr_x);
-  const double dy = image_hi(xi.y - xj.y, R.Ly, R.hi_thr_y);
+                                             const dvec4& xj, bool wall, unsigned act, double& px,
+                                             double& py, double& pz) {
+  double dx = xi.x - xj.x, dy = xi.y - xj.y;
   const double dz = xi.z - xj.z;
+  // the periodic image's adds run only in a round where some lane's pair crosses an x or y edge
+  // (rare in a stream in cell order); act: the lanes running this call
+  const bool cross = ((uint32_t)__double2hiint(dx) & 0x7fffffffu) >= R.hi_thr_x ||
+                     ((uint32_t)__double2hiint(dy) & 0x7fffffffu) >= R.hi_thr_y;
+  if (__any_sync(act, cross)) {
+    dx = image_hi(dx, R.Lx, R.hi_thr_x);
+    dy = image_hi(dy, R.Ly, R.hi_thr_y);
+  }
   const double r2 = dx * dx + dy * dy + dz * dz;
   const bool in = lt_pos(r2, wall ? p.rcw2 : p.rc2);
   const double a12 = wall ? p.a12w : p.a12, b6 = wall ? p.b6w : p.b6;
@@ -2620,45 +2627,80 @@ __device__ __forceinline__ bool pair_term_nb(const PotDev& p, const RepDev& R, c
   return in;
 }
 
+// One round of the FP64 flat stream's queue, held by a lane: the owner, its partner and their
+// FP64 positions, loaded one round before the pair terms run
+struct FlatRound {
+  dvec4 xi, xj;
+  int qi, j, rep;
+};
+
 template <int PREC>
 __global__ void __launch_bounds__(256) k_forces_flat(Arrays a, PotDev p, int owe_kick) {
-  // the warp's queue of screened pairs (FP64 and double-float): a ring of 64 slots in shared
-  // memory -- owner, its replica, the list entry -- of which the Q from `head` on are waiting
-  __shared__ int s_own[8][64], s_rep[8][64];
-  __shared__ uint32_t s_ent[8][64];
+  // the warp's queue of screened pairs (FP64 and double-float): a ring in shared memory -- owner,
+  // its replica, the list entry -- of which the Q from `head` on are waiting. FP64 keeps 128
+  // slots: a round's positions load while the round before it runs (up to 63 wait, one round
+  // loaded among them, before a push of 32)
+  constexpr int kRing = PREC == kPrecFP64 ? 128 : 64;
+  __shared__ int s_own[8][kRing], s_rep[8][kRing];
+  __shared__ uint32_t s_ent[8][kRing];
   count_launch(a);
   clear_rebuild_flags(a);
   if (owe_kick && blockIdx.x == 0 && threadIdx.x == 0) *a.kick_pending = 1;
+  const int E = *a.n_flat;  // (loaded beside the status word: one round trip for both)
   if (halted(a)) return;
   const int N = a.n_total, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int E = *a.n_flat;
   const long long W = (long long)gridDim.x * (blockDim.x >> 5);
   const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   const long long tiles = (E + 31) >> 5;
   const int t0 = (int)(tiles * w / W), t1 = (int)(tiles * (w + 1) / W);
   int cnt = 0, Q = 0, head = 0;
-  // the pair terms of the next `n` waiting slots, one per lane (n <= 32)
+  // FP64: the positions of the `n` slots from h, one per lane, into r (their loads in flight)
+  auto load_round = [&](FlatRound& r, int h, int n) {
+    if (lane < n) {
+      const int slot = (h + lane) & (kRing - 1);
+      r.qi = s_own[wib][slot];
+      r.rep = s_rep[wib][slot];
+      r.j = MD_CHK(a, (int)(s_ent[wib][slot] & kIndexMask), a.n_total + a.n_wall_total);
+      r.xi = a.pos[r.qi];
+      r.xj = r.j >= N ? a.wpos[r.j - N] : a.pos[r.j];
+    }
+  };
+  // FP64: the pair terms of a loaded round of n slots, both ends' atomic adds
+  auto run_round = [&](const FlatRound& r, int n) {
+    const unsigned act = __ballot_sync(kFull, lane < n);
+    if (lane < n) {
+      double fx, fy, fz;
+      if (pair_term_nb(p, a.reps[r.rep], r.xi, r.xj, r.j >= N, act, fx, fy, fz)) {
+        atomicAdd(&a.frc[r.qi].x, fx);
+        atomicAdd(&a.frc[r.qi].y, fy);
+        atomicAdd(&a.frc[r.qi].z, fz);
+        if (r.j < N) {  // Newton's third law: the partner receives -p
+          atomicAdd(&a.frc[r.j].x, neg_bits(fx));
+          atomicAdd(&a.frc[r.j].y, neg_bits(fy));
+          atomicAdd(&a.frc[r.j].z, neg_bits(fz));
+        }
+        ++cnt;
+      }
+    }
+  };
+  // FP64: two round buffers used in turn (no register copies between them, so a round's loads
+  // stay in flight while the other round runs); `ld` rounds (0 or 1) are loaded, from head on
+  FlatRound rb[2];
+  int ld = 0, cur = 0;
+  // the pair terms of the next `n` waiting slots, one per lane (n <= 32): double-float
   auto evaluate = [&](int n) {
     __syncwarp();
     if (lane < n) {
-      const int slot = (head + lane) & 63;
+      const int slot = (head + lane) & (kRing - 1);
       const int qi = s_own[wib][slot];
       const uint32_t qe = s_ent[wib][slot];
       const RepDev& RQ = a.reps[s_rep[wib][slot]];
       const int j = MD_CHK(a, (int)(qe & kIndexMask), a.n_total + a.n_wall_total);
-      double fx, fy, fz;
-      bool in;
-      if constexpr (PREC == kPrecDF64) {
-        const float4 li = a.lpos[qi], ll = a.lpos_lo[qi];
-        const float4 b = partner_lpos(a, qe, N), bl = partner_lpos_lo(a, qe, N);
-        dword px, py, pz;
-        in = df_pair_term(a, p, RQ, qi, li, ll, qe, b, bl, N, px, py, pz);
-        fx = dw_to_double(px);
-        fy = dw_to_double(py);
-        fz = dw_to_double(pz);
-      } else {
-        in = pair_term_nb(p, RQ, a.pos[qi], partner_pos(a, qe, N), j >= N, fx, fy, fz);
-      }
+      const float4 li = a.lpos[qi], ll = a.lpos_lo[qi];
+      const float4 b = partner_lpos(a, qe, N), bl = partner_lpos_lo(a, qe, N);
+      dword px, py, pz;
+      const bool in = df_pair_term(a, p, RQ, qi, li, ll, qe, b, bl, N, px, py, pz);
+      const double fx = dw_to_double(px), fy = dw_to_double(py), fz = dw_to_double(pz);
       if (in) {
         atomicAdd(&a.frc[qi].x, fx);
         atomicAdd(&a.frc[qi].y, fy);
@@ -2671,22 +2713,45 @@ __global__ void __launch_bounds__(256) k_forces_flat(Arrays a, PotDev p, int owe
         ++cnt;
       }
     }
-    head = (head + n) & 63;
+    head = (head + n) & (kRing - 1);
     Q -= n;
     __syncwarp();
   };
-  // the lanes whose entry passed the screen (hit) append it to the ring in lane order; 32 waiting
-  // slots run (at most 31 wait before a push of at most 32: the ring never overflows)
+  // the lanes whose entry passed the screen (hit) append it to the ring in lane order. Double-float:
+  // 32 waiting slots run (at most 31 wait before a push of at most 32). FP64: the first 32 are
+  // loaded; once 64 wait, the next 32 load and the loaded round runs (at most 63 wait before a
+  // push: 95 of 128 slots)
   auto push = [&](bool hit, int hi, int hr, uint32_t he) {
     const unsigned hm = __ballot_sync(kFull, hit);
     if (hit) {
-      const int slot = (head + Q + __popc(hm & ((1u << lane) - 1u))) & 63;
+      const int slot = (head + Q + __popc(hm & ((1u << lane) - 1u))) & (kRing - 1);
       s_own[wib][slot] = hi;
       s_rep[wib][slot] = hr;
       s_ent[wib][slot] = he;
     }
     Q += __popc(hm);
-    if (Q >= 32) evaluate(32);
+    if constexpr (PREC == kPrecFP64) {
+      __syncwarp();
+      if (!ld && Q >= 32) {  // (the first load: nothing ran yet, cur is 0)
+        load_round(rb[0], head, 32);
+        ld = 1;
+      }
+      if (ld && Q >= 64) {
+        if (cur == 0) {
+          load_round(rb[1], head + 32, 32);
+          run_round(rb[0], 32);
+        } else {
+          load_round(rb[0], head + 32, 32);
+          run_round(rb[1], 32);
+        }
+        cur ^= 1;
+        head = (head + 32) & (kRing - 1);
+        Q -= 32;
+      }
+      __syncwarp();
+    } else {
+      if (Q >= 32) evaluate(32);
+    }
   };
   // a batch of kStreamBatch tiles: the entries and owners (the next batch's load while this one is
   // screened), then the owners' and partners' offsets
@@ -2760,7 +2825,25 @@ __global__ void __launch_bounds__(256) k_forces_flat(Arrays a, PotDev p, int owe
       }
     }
   }
-  if constexpr (PREC != kPrecMixed) {
+  if constexpr (PREC == kPrecFP64) {
+    // what is left: a loaded round and up to 31 more, or fewer than 32 unloaded
+    __syncwarp();
+    if (ld) {
+      const int rest = Q - 32;  // in [0, 32)
+      if (cur == 0) {
+        load_round(rb[1], head + 32, rest);
+        run_round(rb[0], 32);
+        run_round(rb[1], rest);
+      } else {
+        load_round(rb[0], head + 32, rest);
+        run_round(rb[1], 32);
+        run_round(rb[0], rest);
+      }
+    } else if (Q) {
+      load_round(rb[0], head, Q);
+      run_round(rb[0], Q);
+    }
+  } else if constexpr (PREC != kPrecMixed) {
     if (Q) evaluate(Q);
   }
   const unsigned long long c = warp_sum((unsigned long long)(2 * cnt));
