@@ -142,6 +142,8 @@ WORKLOADS = {
     "cylinder_pore_200k": "150x150x300 box, slab |z|<30, cylinder r10, 200,000 vapour, T*=0.9",
     "replica_batch_256": ("256 replicas: shape uniform over cylinder/cone/slit/ink-bottle, R~U[2,10], "
                           "N log-uniform [1k,50k], T*~U[0.8,1.2], density 0.02 outside |z|<8"),
+    "replica_batch_32": ("32 replicas drawn as the 256-replica batch's are (461,031 vapour, "
+                         "2,392,655 wall atoms): a smaller case for kernel captures"),
     "pore_array_2m": ("400x400x200 box, 4x4 pores (cylinder/cone/ink-bottle, R~U[4,10]) in slab "
                       "|z|<20, 2,000,000 vapour, T*=0.85"),
     "paper_prism_pore": ("the paper's 3D geometry in reduced units: a 5x5x50 prism pore closed on "
@@ -184,6 +186,8 @@ def make_workload(name: str):
         return [W.cylinder_pore_200k()], name
     if name == "replica_batch_256":
         return W.replica_batch(256), name
+    if name == "replica_batch_32":
+        return W.replica_batch(32), name
     if name == "pore_array_2m":
         return [W.pore_array_2m()], name
     if name == "drying_pore_6k":
