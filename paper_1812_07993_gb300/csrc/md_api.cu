@@ -34,7 +34,8 @@ struct md_ctx {
   std::vector<ReplicaHost> rh;
   std::vector<void*> allocs;
   std::string err;
-  int32_t* status_host = nullptr;   // pinned: [0] device status bits, [1] the state check's row
+  int32_t* status_host = nullptr;   // pinned: [0] device status bits, [1] the state check's row,
+                                    // [2] the state load's rebuild flag
   int32_t* bad_row = nullptr;       // device: lowest row a state load's check rejected
   cudaEvent_t status_event = nullptr;
   bool status_pending = false;
@@ -327,14 +328,6 @@ md_status rebuild_and_forces(md_ctx* c) {
   // every replica rebuilds (all-ones bytes: the largest displacement pattern)
   CUDA_TRY(c, cudaMemsetAsync(c->a.rep_disp2, 0xff, sizeof(unsigned long long) * (size_t)c->n_reps,
                               c->stream));
-  launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
-  launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
-  CUDA_TRY(c, cudaGetLastError());
-  return sync_status(c);
-}
-
-// the rebuild chain (its kernels return at once unless the flags ask for a rebuild), then forces
-md_status rebuild_if_due_and_forces(md_ctx* c) {
   launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
   launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
   CUDA_TRY(c, cudaGetLastError());
@@ -752,7 +745,7 @@ md_status create_impl(const md_system* systems, int32_t n_reps, const md_potenti
   ALLOC(A.rep_sums, (size_t)n_reps * 8);
   ALLOC(c->bad_row, 1);
 #undef ALLOC
-  cudaError_t e = cudaMallocHost(&c->status_host, 2 * sizeof(int32_t));
+  cudaError_t e = cudaMallocHost(&c->status_host, 3 * sizeof(int32_t));
   if (e != cudaSuccess) return bail(fail(c, MD_ENOMEM, "pinned status word"));
   c->status_host[0] = 0;
   c->status_host[1] = kNoBadRow;
@@ -1240,8 +1233,28 @@ md_status md_set_state(md_ctx* c, int32_t r, const double* x, const double* v) {
                                 cudaMemcpyDeviceToHost, c->stream));
     c->bytes_d2h += sizeof(int32_t);
   }
-  // (both wait for the stream, the check's row included)
-  const md_status st = keep ? rebuild_if_due_and_forces(c) : rebuild_and_forces(c);
+  md_status st;
+  if (keep) {
+    // the check's row and the load's rebuild flag read back together; the rebuild chain is
+    // launched only when some replica asks for it, and forces only after a load that happened
+    c->status_host[2] = 0;
+    if (n) {
+      CUDA_TRY(c, cudaMemcpyAsync(c->status_host + 2, c->a.force_rebuild, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, c->stream));
+      c->bytes_d2h += sizeof(int32_t);
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    if (n && c->status_host[1] != kNoBadRow) {
+      st = sync_status(c);  // nothing was loaded: the forces stand
+    } else {
+      if (c->status_host[2]) launch_rebuild(c->a, c->pot, c->tun, c->mixed, c->stream);
+      launch_forces(c->a, c->pot, c->mixed, false, false, c->tun, c->stream);
+      CUDA_TRY(c, cudaGetLastError());
+      st = sync_status(c);
+    }
+  } else {
+    st = rebuild_and_forces(c);  // (waits for the stream, the check's row included)
+  }
   const int32_t bad = c->status_host[1];
   c->status_host[1] = kNoBadRow;
   if (n && bad != kNoBadRow) {
