@@ -59,10 +59,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # traffic is reported as null for any other workload, kernel or source
 NCU_TRAFFIC = {
     ("cylinder_pore_200k", "k_forces_flat<0>"):
-        {"bytes_per_launch": 23700992, "source_sha": "8e4aaf20bd41b8bc",
+        {"bytes_per_launch": 23693056, "source_sha": "57dfe9f1543d79eb",
          "source": "profiles/flat_stream_fp64_cylinder_pore_200k.md"},
     ("pore_shapes_4x20k", "k_forces_flat<0>"):
-        {"bytes_per_launch": 14652160, "source_sha": "8e4aaf20bd41b8bc",
+        {"bytes_per_launch": 14651904, "source_sha": "57dfe9f1543d79eb",
          "source": "profiles/flat_stream_fp64_pore_shapes_4x20k.md"},
 }
 
@@ -72,12 +72,12 @@ NCU_TRAFFIC = {
 # accumulation), valid for the recorded kernel source.
 NCU_LIST_BUILD = {
     ("cylinder_pore_200k", "fp64", "atomic"):
-        {"kernel": "k_list_build_mol", "dram_bytes_per_launch": 12539904, "duration_us": 79.8,
-         "dram_frac_of_peak": 0.0198, "source_sha": "8e4aaf20bd41b8bc",
+        {"kernel": "k_list_build_mol", "dram_bytes_per_launch": 12547328, "duration_us": 83.0,
+         "dram_frac_of_peak": 0.0191, "source_sha": "57dfe9f1543d79eb",
          "source": "profiles/list_builds_cylinder_pore_200k_and_pore_shapes_4x20k.md"},
     ("pore_shapes_4x20k", "fp64", "atomic"):
-        {"kernel": "k_list_build", "dram_bytes_per_launch": 2969600, "duration_us": 51.9,
-         "dram_frac_of_peak": 0.0072, "source_sha": "8e4aaf20bd41b8bc",
+        {"kernel": "k_list_build", "dram_bytes_per_launch": 2978816, "duration_us": 50.4,
+         "dram_frac_of_peak": 0.0075, "source_sha": "57dfe9f1543d79eb",
          "source": "profiles/list_builds_cylinder_pore_200k_and_pore_shapes_4x20k.md"},
 }
 

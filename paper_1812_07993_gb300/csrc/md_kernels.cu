@@ -437,7 +437,8 @@ __device__ __forceinline__ double advance_molecule(const Arrays& a, int i, int p
                                                    long long owed, int flags,
                                                    const dvec4* __restrict__ xin, dvec4* xout,
                                                    float4* xfout) {
-  const int my_rep = a.rep[i];
+  // (with one replica its record loads beside the molecule's own words, not after its index)
+  const int my_rep = a.n_reps == 1 ? 0 : a.rep[i];
   const RepDev& R = a.reps[my_rep];
   dvec4 x = xin[i], v = a.vel[i];
   const dvec4 x_old = x;
@@ -517,13 +518,15 @@ __global__ void __launch_bounds__(256, 4) k_integrate_first(Arrays a, PotDev p, 
     *a.step += 1;
     *a.any_scale = 0;
   }
-  // uniform within the block (the partial sums below synchronise the block); another block of this
-  // launch may raise a status bit meanwhile, so blocks can differ, but every block arrives at the
-  // barrier whatever it reads here
-  bool halt = __syncthreads_or(halted(a) ? 1 : 0) != 0;
+  // the words this launch branches on, loaded together (one round trip to memory for all three)
+  const int st = halted(a) ? 1 : 0;
   const int pend = *reinterpret_cast<volatile const int32_t*>(a.kick_pending);
   // the same value in every block: the last block of the previous launch wrote it
   const long long owed = thermo_owed(a);
+  // uniform within the block (the partial sums below synchronise the block); another block of this
+  // launch may raise a status bit meanwhile, so blocks can differ, but every block arrives at the
+  // barrier whatever it reads here
+  bool halt = __syncthreads_or(st) != 0;
   if (owed) {
     const int units = a.n_reps * a.rep_chunks;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {  // block-uniform
@@ -555,17 +558,22 @@ __global__ void __launch_bounds__(256, 4) k_integrate_first(Arrays a, PotDev p, 
   __syncthreads();
   if (!is_last) return;
   __threadfence();
+  // every word the decision needs, loaded together: the step, the status and the rebuild flag
+  // (every other block raised it, if at all, before its fence and its count above)
   const long long s = *reinterpret_cast<volatile long long*>(a.step);
+  bool stop = false, rb = false;
+  if (threadIdx.x == 0) {
+    stop = halted(a);
+    rb = *reinterpret_cast<volatile const int32_t*>(a.force_rebuild) != 0;
+  }
   int th = 0;
   for (int r = threadIdx.x; r < a.n_reps; r += blockDim.x)
     if (thermo_due(a.reps[r], s)) th = 1;
   th = __syncthreads_or(th);
   if (threadIdx.x == 0) {
     *a.blk_done = 0u;
-    const bool stop = halted(a);
     *a.thermo_owed = (!stop && th) ? s : 0ll;
-    const bool rb = !stop && atomicAdd(a.force_rebuild, 0) != 0;
-    if (sc.use && sc.has_rebuild) cudaGraphSetConditional(sc.rebuild, rb ? 1u : 0u);
+    if (sc.use && sc.has_rebuild) cudaGraphSetConditional(sc.rebuild, (!stop && rb) ? 1u : 0u);
   }
 }
 
