@@ -85,3 +85,23 @@ def test_drying_pore_filled_inside_dilute_outside():
     assert rho_out / rho_in == pytest.approx(0.2, abs=0.02)
     b = W.drying_cylinder_pore()
     np.testing.assert_array_equal(s.x0, b.x0)
+
+
+def test_bench_workload_names_build_their_own_systems():
+    """Every workload name the bench accepts builds that workload (the 4x20k pore shapes are the
+    fallback, so a name the builder missed would silently time them instead); the two largest
+    are checked by name only, their generation taking tens of seconds."""
+    import bench
+    for name in sorted(bench.WORKLOADS):
+        if name in ("pore_array_2m", "replica_batch_256"):
+            continue
+        systems, label = bench.make_workload(name)
+        assert label == name
+        if name == "replica_batch_32":
+            assert len(systems) == 32
+            assert sum(s.n_vapor for s in systems) == 461031
+            assert sum(len(s.wall) for s in systems) == 2392655
+    import inspect
+    src = inspect.getsource(bench.make_workload)
+    for name in ("pore_array_2m", "replica_batch_256"):
+        assert f'name == "{name}"' in src
