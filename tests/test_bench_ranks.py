@@ -82,3 +82,26 @@ def test_single_rank_is_the_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.job_totals(3.5, 123, 1) == (3.5, 123.0)
+
+
+def test_reference_arm_prints_one_contract_line_on_the_host():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores (no GPU needed) and prints
+    one JSON line with the contract's keys: the metric, a positive value, the workload, and the
+    cpu_baseline and e2e objects describing the same run."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cylinder_pore_1k", "--steps", "3", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 1
+    assert d["config"]["workload"] == "cylinder_pore_1k"
+    for k in ("metric", "unit", "n_gpus", "ms_per_step", "higher_is_better", "scaling", "dtype",
+              "data", "vs_baseline"):
+        assert k in d
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
